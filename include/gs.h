@@ -1,0 +1,245 @@
+/*
+ * gs.h -- C ABI of the GB300 (sm_103a) differentiable Gaussian splatting
+ * library for the mapping and pose-refinement hot path of TAMBRIDGE
+ * (arXiv 2405.19614).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All array arguments are DEVICE pointers unless marked "host".  The caller
+ *    owns every buffer, including workspaces; the library never allocates,
+ *    never frees and never synchronises the stream inside a call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is only enqueued; results are ready when the stream is.
+ *  - Synchronous argument errors return a gs_status_t and enqueue nothing.
+ *    Asynchronous errors (pair capacity exceeded, bounded wait expired) are
+ *    OR-ed into a device status word (bit 1 << GS_ERR_CAPACITY, 1 << GS_ERR_TIMEOUT)
+ *    that the caller reads after the stream; outputs are then incomplete but
+ *    every access stays in bounds.
+ *  - Views: up to GS_MAX_VIEWS cameras per call, possibly of different sizes.
+ *    Per-view arrays are concatenated: projected records and radii at
+ *    [v * n + i]; pixels at pix_base[v] + y * width + x with pix_base the
+ *    running sum of width*height; tiles at tile_base[v] + ty * tiles_x + tx with
+ *    tile_base the running sum of tiles_x * tiles_y.
+ *  - Pixel (x, y) is sampled at (x + 0.5, y + 0.5); u = fx * X/Z + cx.
+ *  - Poses are world -> camera row-major 3x4 [R | t] (device, FP32) so that an
+ *    on-device pose update needs no host round trip; the twist is
+ *    xi = (rho, phi) with pose(xi) = Exp(xi) * E and gradients at xi = 0.
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_MAX_VIEWS 64
+#define GS_TILE 16 /* tiles are 16 x 16 pixels */
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1,
+    GS_ERR_CUDA = 2,
+    GS_ERR_CAPACITY = 3,
+    GS_ERR_TIMEOUT = 4,
+    GS_ERR_UNSUPPORTED = 5
+} gs_status_t;
+
+/* Host-side camera intrinsics and image size (Sec. 3.4 "Projection": K). */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} gs_view_t;
+
+/* Gaussian parameters, structure of arrays (Sec. 3.4 "Gaussian
+ * Representation", generalised to anisotropic scales and SH colour):
+ * means [n,3], log_scales [n,3], quats [n,4] as (w, x, y, z), not necessarily
+ * normalised, opacity_logit [n] (opacity = sigmoid), sh [n, (deg+1)^2, 3]. */
+typedef struct {
+    const float *means, *log_scales, *quats, *opacity_logit, *sh;
+    int64_t n;
+    int32_t sh_degree; /* 0..3 */
+} gs_params_t;
+
+/* Gradients with the same layouts as gs_params_t; accumulated (+=). */
+typedef struct {
+    float *means, *log_scales, *quats, *opacity_logit, *sh;
+} gs_param_grads_t;
+
+typedef struct {
+    float near_z; /* cull if camera z <= near_z (0.2) */
+    float blur;   /* low-pass variance added to the 2D covariance (0.3 px^2) */
+} gs_options_t;
+
+/* Output of gs_project, one entry per (view, Gaussian) at [v * n + i]:
+ *   rec [., 12] floats: (u, v, z, opacity), (conicA, conicB, conicC, r0),
+ *                       (red, green, blue, r1) where r0 = x0 | y0 << 16 and
+ *                       r1 = x1 | y1 << 16 (bit patterns) give the inclusive
+ *                       tile rectangle; 16-byte aligned;
+ *   radii [.]   int32 support radius in pixels, 0 = not drawn in that view;
+ *   tiles_touched [.] uint32 number of tiles of the rectangle. */
+typedef struct {
+    float *rec;
+    int32_t *radii;
+    uint32_t *tiles_touched;
+} gs_projected_t;
+
+/* Output of gs_bin_sort:
+ *   keys [capacity] uint64: (global tile id << 32) | bits(z), ascending;
+ *   vals [capacity] uint32: Gaussian index within its view;
+ *   ranges [n_tiles_total, 2] uint32: [start, end) of each tile's list;
+ *   n_pairs: device uint32, number of (Gaussian, tile) pairs (may exceed the
+ *            capacity, in which case status has the capacity bit set);
+ *   status: device uint32 error word (see above); never cleared by the library. */
+typedef struct {
+    uint64_t *keys;
+    uint32_t *vals;
+    uint32_t *ranges;
+    uint32_t *n_pairs;
+    uint32_t *status;
+    int64_t capacity;
+} gs_bins_t;
+
+/* Forward image outputs, per pixel (see pixel layout above):
+ * rgb [P,3], depth [P], alpha [P] (= border mask M_b), final_T [P],
+ * n_contrib [P] (list entries consumed up to the last blended one). */
+typedef struct {
+    float *rgb, *depth, *alpha, *final_T;
+    uint32_t *n_contrib;
+} gs_image_t;
+
+/* Library version string. */
+const char *gs_version(void);
+
+/* Text for a status code. */
+const char *gs_status_string(gs_status_t s);
+
+/* Total tiles and pixels over the views (host helper). */
+gs_status_t gs_layout(const gs_view_t *views /* host */, int32_t n_views, int64_t *n_tiles_total,
+                      int64_t *n_pixels_total);
+
+/* a1. Projection (Sec. 3.4 "Projection": mu2D = K E_t mu / d, r2D = f r / d;
+ * EWA footprint of the rasteriser of Sec. 4.1).  For every view and Gaussian:
+ * camera transform, 2D covariance J W S W^T J^T + blur, support radius
+ * ceil(3 sqrt(lambda_max)), tile rectangle, conic, opacity = sigmoid(logit),
+ * colour = max(0, SH(dir) + 0.5).  Radius, rectangle and depth follow a fixed
+ * FP32 operation order so that binning is reproducible bit for bit.
+ * params: device SoA; views: host [n_views]; viewmats: device [n_views, 12].
+ * out: caller-allocated arrays of n_views * params->n entries.
+ * Errors: GS_ERR_INVALID_ARG for null pointers, n < 0, n_views outside
+ * [1, GS_MAX_VIEWS], sh_degree outside [0, 3] or non-positive image sizes. */
+gs_status_t gs_project(const gs_params_t *params, const gs_view_t *views, const float *viewmats,
+                       int32_t n_views, const gs_options_t *opt, gs_projected_t *out, void *stream);
+
+/* Bytes of workspace gs_bin_sort needs for n_records = n_views * n and the
+ * given pair capacity and total tile count. */
+size_t gs_bin_sort_workspace_size(int64_t n_records, int64_t pair_capacity, int64_t n_tiles_total);
+
+/* a2-a4. Binning in front-to-back order (Sec. 3.4 "Differentiable
+ * Rasterization": Gaussians arranged front to back before alpha blending).
+ * Scans tiles_touched, emits one (key, value) per (Gaussian, tile), sorts the
+ * keys with a stable onesweep LSD radix sort over their 32 + ceil(log2 tiles)
+ * significant bits, and writes each tile's [start, end).  Ties keep the
+ * Gaussian index order.  Pairs beyond bins->capacity are dropped and flagged.
+ * workspace: device, >= gs_bin_sort_workspace_size bytes, 256-byte aligned. */
+gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const gs_view_t *views, int32_t n_views,
+                        gs_bins_t *bins, void *workspace, size_t workspace_bytes, void *stream);
+
+/* a5. Forward compositing (Sec. 3.4: C(p) = sum c_i f_i prod_{j<i} (1 - f_j),
+ * D(p) likewise with the depths d_i; Sec. 3.3: M_b(p) = sum f_i prod (1 - f_j)).
+ * alpha_i = min(0.99, o_i exp(-1/2 d^T conic d)); entries with alpha < 1/255
+ * are skipped; compositing stops before an entry that would bring T below
+ * 1e-4.  One persistent launch over all (view, tile) work items.
+ * work_counter: device uint32 scratch, reset inside the call. */
+gs_status_t gs_render_fwd(const gs_projected_t *proj, int64_t n, const gs_bins_t *bins,
+                          const gs_view_t *views, int32_t n_views, gs_image_t *img,
+                          uint32_t *work_counter, void *stream);
+
+/* Work counts of a5 for measurement: per pixel, the list entries evaluated
+ * (n_eval [P]) and blended (n_blend [P]) by the forward compositing under the
+ * same skip and stop rules.  Writes no image. */
+gs_status_t gs_render_stats(const gs_projected_t *proj, int64_t n, const gs_bins_t *bins,
+                            const gs_view_t *views, int32_t n_views, uint32_t *n_eval, uint32_t *n_blend,
+                            uint32_t *work_counter, void *stream);
+
+/* a6. L1 rendering losses with the optional filter gate (Sec. 3.3
+ * G(p) = [D_c > 0][D_g > 0][M_b > gamma]; Sec. 3.3 joint loss w2 L_c + w3 L_d;
+ * Sec. 3.4 L_m L1 terms):  L = w_c/(3P) sum G |C - C^| + w_d/P sum G |D - D^|
+ * over all P pixels of the batch.  Adds L to *loss (device float) and WRITES
+ * d_rgb [P,3] and d_depth [P] (sign(0) = 0; zero where the gate is closed). */
+gs_status_t gs_loss_l1(const float *rgb, const float *depth, const float *alpha, const float *target_rgb,
+                       const float *target_depth, int64_t n_pixels, float w_c, float w_d,
+                       int32_t use_gate, float gamma, float *loss, float *d_rgb, float *d_depth,
+                       void *stream);
+
+/* Bytes of the per-(view, Gaussian) 2D gradient buffer: n_views * n * 12 floats. */
+size_t gs_grad2d_size(int64_t n, int32_t n_views);
+
+/* a7. Backward of the compositing for upstream gradients d_rgb [P,3],
+ * d_depth [P], d_alpha [P] (each may be NULL = zero).  Recomputes each
+ * pixel's blend state from final_T and n_contrib, reduces per-Gaussian
+ * gradients within each warp by shuffles, then within the block, and adds
+ * them with vector atomics into grad2d [n_views * n, 12] laid out as
+ * (du, dv, dconicA, dconicB), (dconicC, dopacity, dred, dgreen),
+ * (dblue, dz, 0, 0).  grad2d is accumulated (+=). */
+gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t n, const gs_bins_t *bins,
+                                 const gs_view_t *views, int32_t n_views, const gs_image_t *img,
+                                 const float *d_rgb, const float *d_depth, const float *d_alpha,
+                                 float *grad2d, uint32_t *work_counter, void *stream);
+
+/* a8. Backward of the projection: chains grad2d to the parameter gradients
+ * (summed over views, accumulated into grads) and to each view's twist
+ * gradient d_twist [n_views, 6] (+=; NULL to skip).  Entries of grad2d it
+ * reads are set back to zero, so a buffer that starts zeroed is zero again
+ * when the call completes. */
+gs_status_t gs_project_bwd(const gs_params_t *params, const gs_view_t *views, const float *viewmats,
+                           int32_t n_views, const gs_options_t *opt, const gs_projected_t *proj,
+                           float *grad2d, gs_param_grads_t *grads, float *d_twist, void *stream);
+
+/* a7 + a8. The whole backward of the render (reverse of Sec. 3.4 projection and
+ * compositing): gs_render_bwd_splats followed by gs_project_bwd.  grad2d must
+ * be zero on entry (it is zero again on completion); parameter gradients and
+ * d_twist are accumulated.  Used for mapping (pose fixed, Sec. 3.4) with
+ * d_twist = NULL and for pose refinement (Sec. 3.3) with d_twist set. */
+gs_status_t gs_render_bwd(const gs_params_t *params, const gs_view_t *views, const float *viewmats,
+                          int32_t n_views, const gs_options_t *opt, const gs_projected_t *proj,
+                          const gs_bins_t *bins, const gs_image_t *img, const float *d_rgb,
+                          const float *d_depth, const float *d_alpha, float *grad2d,
+                          gs_param_grads_t *grads, float *d_twist, uint32_t *work_counter, void *stream);
+
+/* a9. Keypoint re-projection loss (Sec. 3.2 Eq. lba; Sec. 3.3 tracking-centred
+ * encoder):  L = (weight/n) sum_i || obs_i - pi(K_v, E_v, P_i) ||_2 over
+ * points P_i [n,3] (world) observed at obs [n,2] pixels in view view_ids[i]
+ * ([n] int32, NULL = view 0).  Points with camera z <= near_z are left out.
+ * Adds L to *loss and dL/dxi (at xi = 0) to d_twist [n_views, 6]. */
+gs_status_t gs_reproj_loss_grad(const float *points, const float *obs, const int32_t *view_ids, int64_t n,
+                                const gs_view_t *views, const float *viewmats, int32_t n_views,
+                                float weight, float near_z, float *loss, float *d_twist, void *stream);
+
+/* One Adam learning-rate group: elements [offset, offset + count). */
+typedef struct {
+    int64_t offset, count;
+    float lr;
+} gs_adam_group_t;
+
+#define GS_MAX_ADAM_GROUPS 8
+
+/* a10. Adam step (Sec. 3.4: "iteratively refined using gradient-based
+ * optimization"; the optimiser is not named): for each group, m = b1 m +
+ * (1-b1) g, v = b2 v + (1-b2) g^2, p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 -
+ * b2^t)) + eps) with t = step[0] + 1.  step: device int32[2] = {steps done,
+ * scratch that must start at 0}; the call sets step[0] = t on completion, so
+ * a captured graph replays successive steps.  groups: host array. */
+gs_status_t gs_adam_step(float *param, const float *grad, float *m, float *v, const gs_adam_group_t *groups,
+                         int32_t n_groups, float beta1, float beta2, float eps, int32_t *step, void *stream);
+
+/* Pose update of the tracking loop: E_v <- Exp(xi_v) E_v, then xi_v <- 0, for
+ * viewmats [n_views, 12] and twist [n_views, 6] (device). */
+gs_status_t gs_pose_update(float *viewmats, float *twist, int32_t n_views, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H_ */

@@ -1,0 +1,261 @@
+"""GB300 (sm_103a) differentiable Gaussian splatting for the mapping and pose
+refinement hot path of TAMBRIDGE (arXiv 2405.19614).
+
+The compute runs in libgs.so (hand-written CUDA behind the C ABI of
+include/gs.h).  This package only marshals arguments: the ``gs_*`` functions
+below have the names of the C entry points and take torch tensors that already
+live on the GPU; ``Rasterizer`` owns the buffers of one configuration and
+``rasterize`` is the autograd entry point.  PyTorch provides device memory and
+streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import torch
+
+from . import _lib
+from ._lib import (GS_MAX_ADAM_GROUPS, GS_MAX_VIEWS, GS_TILE, GsAdamGroup, GsBins, GsError, GsImage, GsOptions,
+                   GsParamGrads, GsParams, GsProjected, GsView, check)
+
+__all__ = ["gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_stats", "gs_loss_l1", "gs_render_bwd", "gs_render_bwd_splats",
+           "gs_project_bwd", "gs_reproj_loss_grad", "gs_adam_step", "gs_pose_update", "Rasterizer", "rasterize",
+           "GsError", "lib"]
+
+
+def lib():
+    return _lib.load()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise GsError("tensor must be on the GPU")
+    if not t.is_contiguous():
+        raise GsError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_views(intr, size):
+    """ctypes array of gs_view_t from intr [V,4] (fx, fy, cx, cy) and size [V,2]."""
+    intr = [[float(x) for x in row] for row in (intr.tolist() if hasattr(intr, "tolist") else intr)]
+    size = [[int(x) for x in row] for row in (size.tolist() if hasattr(size, "tolist") else size)]
+    V = len(intr)
+    arr = (GsView * V)()
+    for v in range(V):
+        arr[v].fx, arr[v].fy, arr[v].cx, arr[v].cy = intr[v]
+        arr[v].width, arr[v].height = size[v]
+    return arr
+
+
+def _params(p):
+    return GsParams(_ptr(p["means"]), _ptr(p["log_scales"]), _ptr(p["quats"]), _ptr(p["opacity_logit"]),
+                    _ptr(p["sh"]), int(p["means"].shape[0]), int(p["sh_degree"]))
+
+
+def _grads(g):
+    return GsParamGrads(_ptr(g["means"]), _ptr(g["log_scales"]), _ptr(g["quats"]), _ptr(g["opacity_logit"]),
+                        _ptr(g["sh"]))
+
+
+# --------------------------------------------------------------------------
+# one wrapper per C entry point
+# --------------------------------------------------------------------------
+
+def gs_project(params, views, viewmats, proj, near_z=0.2, blur=0.3, stream=None):
+    opt = GsOptions(near_z, blur)
+    pj = GsProjected(_ptr(proj["rec"]), _ptr(proj["radii"]), _ptr(proj["tiles_touched"]))
+    check(lib().gs_project(ctypes.byref(_params(params)), views, _ptr(viewmats), len(views), ctypes.byref(opt),
+                           ctypes.byref(pj), _stream(stream)), "gs_project")
+
+
+def _proj(proj):
+    return GsProjected(_ptr(proj["rec"]), _ptr(proj["radii"]), _ptr(proj["tiles_touched"]))
+
+
+def _bins(bins):
+    return GsBins(_ptr(bins["keys"]), _ptr(bins["vals"]), _ptr(bins["ranges"]), _ptr(bins["n_pairs"]),
+                  _ptr(bins["status"]), int(bins["keys"].shape[0]))
+
+
+def _img(img):
+    return GsImage(_ptr(img["rgb"]), _ptr(img["depth"]), _ptr(img["alpha"]), _ptr(img["final_T"]),
+                   _ptr(img["n_contrib"]))
+
+
+def gs_bin_sort_workspace_size(n_records, capacity, n_tiles):
+    return int(lib().gs_bin_sort_workspace_size(n_records, capacity, n_tiles))
+
+
+def gs_bin_sort(proj, n, views, bins, workspace, stream=None):
+    check(lib().gs_bin_sort(ctypes.byref(_proj(proj)), n, views, len(views), ctypes.byref(_bins(bins)),
+                            _ptr(workspace), workspace.numel(), _stream(stream)), "gs_bin_sort")
+
+
+def gs_render_fwd(proj, n, bins, views, img, work_counter, stream=None):
+    check(lib().gs_render_fwd(ctypes.byref(_proj(proj)), n, ctypes.byref(_bins(bins)), views, len(views),
+                              ctypes.byref(_img(img)), _ptr(work_counter), _stream(stream)), "gs_render_fwd")
+
+
+def gs_render_stats(proj, n, bins, views, n_eval, n_blend, work_counter, stream=None):
+    check(lib().gs_render_stats(ctypes.byref(_proj(proj)), n, ctypes.byref(_bins(bins)), views, len(views),
+                                _ptr(n_eval), _ptr(n_blend), _ptr(work_counter), _stream(stream)), "gs_render_stats")
+
+
+def gs_loss_l1(rgb, depth, alpha, target_rgb, target_depth, w_c, w_d, use_gate, gamma, loss, d_rgb, d_depth,
+               stream=None):
+    check(lib().gs_loss_l1(_ptr(rgb), _ptr(depth), _ptr(alpha), _ptr(target_rgb), _ptr(target_depth),
+                           depth.numel(), w_c, w_d, int(use_gate), gamma, _ptr(loss), _ptr(d_rgb), _ptr(d_depth),
+                           _stream(stream)), "gs_loss_l1")
+
+
+def gs_render_bwd_splats(proj, n, bins, views, img, d_rgb, d_depth, d_alpha, grad2d, work_counter, stream=None):
+    check(lib().gs_render_bwd_splats(ctypes.byref(_proj(proj)), n, ctypes.byref(_bins(bins)), views, len(views),
+                                     ctypes.byref(_img(img)), _ptr(d_rgb), _ptr(d_depth), _ptr(d_alpha),
+                                     _ptr(grad2d), _ptr(work_counter), _stream(stream)), "gs_render_bwd_splats")
+
+
+def gs_project_bwd(params, views, viewmats, proj, grad2d, grads, d_twist, near_z=0.2, blur=0.3, stream=None):
+    opt = GsOptions(near_z, blur)
+    check(lib().gs_project_bwd(ctypes.byref(_params(params)), views, _ptr(viewmats), len(views), ctypes.byref(opt),
+                               ctypes.byref(_proj(proj)), _ptr(grad2d), ctypes.byref(_grads(grads)), _ptr(d_twist),
+                               _stream(stream)), "gs_project_bwd")
+
+
+def gs_render_bwd(params, views, viewmats, proj, bins, img, d_rgb, d_depth, d_alpha, grad2d, grads, d_twist,
+                  work_counter, near_z=0.2, blur=0.3, stream=None):
+    opt = GsOptions(near_z, blur)
+    check(lib().gs_render_bwd(ctypes.byref(_params(params)), views, _ptr(viewmats), len(views), ctypes.byref(opt),
+                              ctypes.byref(_proj(proj)), ctypes.byref(_bins(bins)), ctypes.byref(_img(img)),
+                              _ptr(d_rgb), _ptr(d_depth), _ptr(d_alpha), _ptr(grad2d), ctypes.byref(_grads(grads)),
+                              _ptr(d_twist), _ptr(work_counter), _stream(stream)), "gs_render_bwd")
+
+
+def gs_reproj_loss_grad(points, obs, view_ids, views, viewmats, weight, loss, d_twist, near_z=0.2, stream=None):
+    check(lib().gs_reproj_loss_grad(_ptr(points), _ptr(obs), _ptr(view_ids), points.shape[0], views,
+                                    _ptr(viewmats), len(views), weight, near_z, _ptr(loss), _ptr(d_twist),
+                                    _stream(stream)), "gs_reproj_loss_grad")
+
+
+def gs_adam_step(param, grad, m, v, groups, step, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    """groups: list of (offset, count, lr)."""
+    if not 1 <= len(groups) <= GS_MAX_ADAM_GROUPS:
+        raise GsError("between 1 and 8 Adam groups")
+    arr = (GsAdamGroup * len(groups))(*[GsAdamGroup(int(o), int(c), float(lr)) for o, c, lr in groups])
+    check(lib().gs_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), arr, len(groups), beta1, beta2, eps,
+                             _ptr(step), _stream(stream)), "gs_adam_step")
+
+
+def gs_pose_update(viewmats, twist, stream=None):
+    check(lib().gs_pose_update(_ptr(viewmats), _ptr(twist), viewmats.shape[0], _stream(stream)), "gs_pose_update")
+
+
+# --------------------------------------------------------------------------
+# buffer owner for one configuration
+# --------------------------------------------------------------------------
+
+def _layout(size):
+    ntx = [(int(w) + GS_TILE - 1) // GS_TILE for w, _ in size]
+    nty = [(int(h) + GS_TILE - 1) // GS_TILE for _, h in size]
+    n_tiles = sum(a * b for a, b in zip(ntx, nty))
+    n_pix = sum(int(w) * int(h) for w, h in size)
+    return n_tiles, n_pix
+
+
+class Rasterizer:
+    """Device buffers and launches for n Gaussians rendered into a fixed set of
+    views (sizes and intrinsics fixed; poses are device tensors and may change).
+    One forward/backward pair in flight at a time: outputs live in the
+    rasterizer's buffers until the next forward."""
+
+    def __init__(self, n, sh_degree, intr, size, pair_capacity=None, device="cuda", near_z=0.2, blur=0.3):
+        self.n, self.sh_degree = int(n), int(sh_degree)
+        self.size = [(int(w), int(h)) for w, h in (size.tolist() if hasattr(size, "tolist") else size)]
+        self.views = make_views(intr, self.size)
+        self.V = len(self.size)
+        if not 1 <= self.V <= GS_MAX_VIEWS:
+            raise GsError(f"between 1 and {GS_MAX_VIEWS} views")
+        self.near_z, self.blur = float(near_z), float(blur)
+        self.n_tiles, self.n_pix = _layout(self.size)
+        if pair_capacity is None:
+            pair_capacity = max(1 << 16, 8 * self.n * self.V)
+        self.capacity = int(min(pair_capacity, (1 << 30) - 1))
+        d = torch.device(device)
+        R = self.V * self.n
+        i32, f32 = torch.int32, torch.float32
+        self.proj = dict(rec=torch.empty(R * 12, dtype=f32, device=d), radii=torch.empty(R, dtype=i32, device=d),
+                         tiles_touched=torch.empty(R, dtype=i32, device=d))
+        self.bins = dict(keys=torch.empty(self.capacity, dtype=torch.int64, device=d),
+                         vals=torch.empty(self.capacity, dtype=i32, device=d),
+                         ranges=torch.zeros(self.n_tiles, 2, dtype=i32, device=d),
+                         n_pairs=torch.zeros(1, dtype=i32, device=d), status=torch.zeros(1, dtype=i32, device=d))
+        ws = gs_bin_sort_workspace_size(R, self.capacity, self.n_tiles)
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=d)
+        P = self.n_pix
+        self.img = dict(rgb=torch.empty(P, 3, dtype=f32, device=d), depth=torch.empty(P, dtype=f32, device=d),
+                        alpha=torch.empty(P, dtype=f32, device=d), final_T=torch.empty(P, dtype=f32, device=d),
+                        n_contrib=torch.empty(P, dtype=i32, device=d))
+        self.grad2d = torch.zeros(R * 12, dtype=f32, device=d)
+        self.work_counter = torch.zeros(1, dtype=i32, device=d)
+
+    def forward(self, params, viewmats, stream=None):
+        """Project, bin and composite; results in self.img (device, async)."""
+        gs_project(params, self.views, viewmats, self.proj, self.near_z, self.blur, stream)
+        gs_bin_sort(self.proj, self.n, self.views, self.bins, self.workspace, stream)
+        gs_render_fwd(self.proj, self.n, self.bins, self.views, self.img, self.work_counter, stream)
+        return self.img
+
+    def backward(self, params, viewmats, d_rgb, d_depth, d_alpha, grads, d_twist=None, stream=None):
+        """Accumulate parameter gradients (and per-view twist gradients) for
+        upstream image gradients; self.grad2d is left zeroed."""
+        gs_render_bwd(params, self.views, viewmats, self.proj, self.bins, self.img, d_rgb, d_depth, d_alpha,
+                      self.grad2d, grads, d_twist, self.work_counter, self.near_z, self.blur, stream)
+
+    def status(self):
+        """Host read of the asynchronous error word (synchronises)."""
+        return int(self.bins["status"].item())
+
+    def n_pairs(self):
+        return int(self.bins["n_pairs"].item())
+
+
+class _RasterizeFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rast, sh_degree, viewmats, twist, means, log_scales, quats, opacity_logit, sh):
+        params = dict(means=means, log_scales=log_scales, quats=quats, opacity_logit=opacity_logit, sh=sh,
+                      sh_degree=sh_degree)
+        img = rast.forward(params, viewmats)
+        ctx.rast = rast
+        ctx.sh_degree = sh_degree
+        ctx.save_for_backward(viewmats, means, log_scales, quats, opacity_logit, sh)
+        ctx.want_twist = twist is not None and twist.requires_grad
+        return img["rgb"], img["depth"], img["alpha"]
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_alpha):
+        viewmats, means, log_scales, quats, opacity_logit, sh = ctx.saved_tensors
+        params = dict(means=means, log_scales=log_scales, quats=quats, opacity_logit=opacity_logit, sh=sh,
+                      sh_degree=ctx.sh_degree)
+        grads = dict(means=torch.zeros_like(means), log_scales=torch.zeros_like(log_scales),
+                     quats=torch.zeros_like(quats), opacity_logit=torch.zeros_like(opacity_logit),
+                     sh=torch.zeros_like(sh))
+        d_twist = torch.zeros(viewmats.shape[0], 6, device=means.device) if ctx.want_twist else None
+        c = lambda t: None if t is None else t.contiguous()
+        ctx.rast.backward(params, viewmats, c(g_rgb), c(g_depth), c(g_alpha), grads, d_twist)
+        return (None, None, None, d_twist, grads["means"], grads["log_scales"], grads["quats"],
+                grads["opacity_logit"], grads["sh"])
+
+
+def rasterize(rast, params, viewmats, twist=None):
+    """Differentiable render: returns (rgb [P,3], depth [P], alpha [P]).
+    twist: optional [V,6] leaf standing for the left perturbation Exp(xi) E of
+    each pose at xi = 0 (its value is not read); its .grad receives dL/dxi."""
+    return _RasterizeFn.apply(rast, int(params["sh_degree"]), viewmats, twist, params["means"],
+                              params["log_scales"], params["quats"], params["opacity_logit"], params["sh"])

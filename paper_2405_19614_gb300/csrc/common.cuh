@@ -1,0 +1,119 @@
+// Internal helpers of the sm_103a splatting library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+
+namespace gs {
+
+constexpr int kTile = GS_TILE;              // 16 x 16 pixel tiles
+constexpr int kTilePix = kTile * kTile;     // 256 pixels = 256 threads per render block
+constexpr uint32_t kFullMask = 0xffffffffu;
+
+// Per-view constants passed by value to kernels.
+struct ViewInfo {
+    float fx, fy, cx, cy;
+    int32_t width, height, tiles_x, tiles_y;
+    int32_t tile_base, pad;
+    int64_t pix_base;
+};
+
+struct ViewTable {
+    int32_t n_views;
+    int32_t n_tiles_total;
+    int64_t n_pix_total;
+    ViewInfo v[GS_MAX_VIEWS];
+};
+
+static_assert(sizeof(ViewTable) <= 3200, "view table must fit in kernel parameters");
+
+inline gs_status_t make_view_table(const gs_view_t *views, int32_t n_views, ViewTable *vt)
+{
+    if (!views || n_views < 1 || n_views > GS_MAX_VIEWS) return GS_ERR_INVALID_ARG;
+    vt->n_views = n_views;
+    int64_t tiles = 0, pix = 0;
+    for (int i = 0; i < n_views; i++) {
+        const gs_view_t &s = views[i];
+        if (s.width <= 0 || s.height <= 0 || s.width > (1 << 20) || s.height > (1 << 20)) return GS_ERR_INVALID_ARG;
+        if (!(s.fx > 0.0f) || !(s.fy > 0.0f)) return GS_ERR_INVALID_ARG;
+        ViewInfo &d = vt->v[i];
+        d.fx = s.fx;
+        d.fy = s.fy;
+        d.cx = s.cx;
+        d.cy = s.cy;
+        d.width = s.width;
+        d.height = s.height;
+        d.tiles_x = (s.width + kTile - 1) / kTile;
+        d.tiles_y = (s.height + kTile - 1) / kTile;
+        d.tile_base = (int32_t)tiles;
+        d.pad = 0;
+        d.pix_base = pix;
+        tiles += (int64_t)d.tiles_x * d.tiles_y;
+        pix += (int64_t)s.width * s.height;
+        if (tiles >= (int64_t(1) << 31)) return GS_ERR_INVALID_ARG;
+    }
+    vt->n_tiles_total = (int32_t)tiles;
+    vt->n_pix_total = pix;
+    return GS_OK;
+}
+
+// View that owns a global tile id (views are few; a linear scan is enough).
+__device__ __forceinline__ int view_of_tile(const ViewTable &vt, int tile)
+{
+    int v = 0;
+    #pragma unroll 1
+    for (int k = 1; k < vt.n_views; k++)
+        if (tile >= vt.v[k].tile_base) v = k;
+    return v;
+}
+
+__device__ __forceinline__ void raise_status(uint32_t *status, gs_status_t code)
+{
+    if (status) atomicOr(status, 1u << (unsigned)code);
+}
+
+inline gs_status_t launch_status()
+{
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+inline cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int num_sms()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// Warp-wide sum.
+__device__ __forceinline__ float warp_sum(float x)
+{
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFullMask, x, o);
+    return x;
+}
+
+// Opacity of one splat at a pixel: shared by the forward and backward passes so
+// that both take the same skip / stop decisions bit for bit.  power =
+// -1/2 (A dx^2 + C dy^2) - B dx dy with d = mean - pixel centre.
+__device__ __forceinline__ float splat_power(float mx, float my, float A, float B, float C, float sx,
+                                             float sy, float *dx_out, float *dy_out)
+{
+    float dx = __fsub_rn(mx, sx), dy = __fsub_rn(my, sy);
+    float q = __fmaf_rn(__fmul_rn(C, dy), dy, __fmul_rn(__fmul_rn(A, dx), dx));
+    float p = __fmaf_rn(-__fmul_rn(B, dy), dx, __fmul_rn(-0.5f, q));
+    *dx_out = dx;
+    *dy_out = dy;
+    return p;
+}
+
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+
+}  // namespace gs

@@ -1,0 +1,317 @@
+// a1. Projection of every Gaussian into every view (Sec. 3.4 "Projection":
+// mu2D = K E_t mu / d, r2D = f r / d, generalised to the EWA footprint of the
+// rasteriser used in Sec. 4.1).
+//
+// One thread per Gaussian loops over all views, so the structure-of-arrays
+// parameters are read from HBM once per launch however many views there are.
+// The radius, tile rectangle and depth follow a fixed sequence of correctly
+// rounded FP32 operations (explicit __f*_rn intrinsics, never contracted) so
+// that the tile keys are reproducible bit for bit; everything else (conic,
+// opacity, colour) is ordinary FP32.
+#include "common.cuh"
+#include "sh.cuh"
+
+namespace gs {
+
+#define MUL __fmul_rn
+#define ADD __fadd_rn
+#define SUB __fsub_rn
+#define DIV __fdiv_rn
+
+// exp for the geometry: Cody-Waite reduction (ln 2 split into a 15-bit head
+// and a tail), degree-7 Taylor polynomial of e^r in Horner form with fused
+// multiply-adds, exact scaling by 2^k; argument clamped to [-80, 80].  Each
+// step is one correctly rounded operation, so the result is reproducible on
+// any IEEE machine that runs the same steps.
+__device__ __forceinline__ float geom_expf(float x)
+{
+    x = (x > 80.0f) ? 80.0f : x;
+    x = (x < -80.0f) ? -80.0f : x;
+    float k = rintf(MUL(x, 0x1.715476p+0f));
+    float r = __fmaf_rn(-k, 0x1.62e4p-1f, x);
+    r = __fmaf_rn(-k, 0x1.7f7d1cp-20f, r);
+    float p = 0x1.a01a02p-13f;
+    p = __fmaf_rn(p, r, 0x1.6c16c2p-10f);
+    p = __fmaf_rn(p, r, 0x1.111112p-7f);
+    p = __fmaf_rn(p, r, 0x1.555556p-5f);
+    p = __fmaf_rn(p, r, 0x1.555556p-3f);
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    if (p != p) return p;
+    int ki = (int)k;
+    return MUL(p, __int_as_float((ki + 127) << 23));
+}
+
+struct Geom {
+    float u, v, z;
+    float ca, cb, cc;   // 2D covariance including the blur
+    int32_t radius;
+    int32_t x0, y0, x1, y1;
+};
+
+// The FP32 geometry contract.  Returns false when the Gaussian touches no tile.
+__device__ __forceinline__ bool geometry(const float m[3], const float ls[3], const float q[4], const float *E,
+                                         const ViewInfo &V, float near_z, float blur, Geom &g)
+{
+    float x = ADD(ADD(ADD(MUL(E[0], m[0]), MUL(E[1], m[1])), MUL(E[2], m[2])), E[3]);
+    float y = ADD(ADD(ADD(MUL(E[4], m[0]), MUL(E[5], m[1])), MUL(E[6], m[2])), E[7]);
+    float z = ADD(ADD(ADD(MUL(E[8], m[0]), MUL(E[9], m[1])), MUL(E[10], m[2])), E[11]);
+    if (!(z > near_z)) return false;
+
+    float nq = ADD(ADD(ADD(MUL(q[0], q[0]), MUL(q[1], q[1])), MUL(q[2], q[2])), MUL(q[3], q[3]));
+    if (!(nq > 0.0f)) return false;
+    float sq = __fsqrt_rn(nq);
+    float w = DIV(q[0], sq), a = DIV(q[1], sq), b = DIV(q[2], sq), c = DIV(q[3], sq);
+    float R[3][3];
+    R[0][0] = SUB(1.0f, MUL(2.0f, ADD(MUL(b, b), MUL(c, c))));
+    R[0][1] = MUL(2.0f, SUB(MUL(a, b), MUL(w, c)));
+    R[0][2] = MUL(2.0f, ADD(MUL(a, c), MUL(w, b)));
+    R[1][0] = MUL(2.0f, ADD(MUL(a, b), MUL(w, c)));
+    R[1][1] = SUB(1.0f, MUL(2.0f, ADD(MUL(a, a), MUL(c, c))));
+    R[1][2] = MUL(2.0f, SUB(MUL(b, c), MUL(w, a)));
+    R[2][0] = MUL(2.0f, SUB(MUL(a, c), MUL(w, b)));
+    R[2][1] = MUL(2.0f, ADD(MUL(b, c), MUL(w, a)));
+    R[2][2] = SUB(1.0f, MUL(2.0f, ADD(MUL(a, a), MUL(b, b))));
+
+    float s[3] = {geom_expf(ls[0]), geom_expf(ls[1]), geom_expf(ls[2])};
+    float M[3][3];
+    #pragma unroll
+    for (int i = 0; i < 3; i++)
+        #pragma unroll
+        for (int j = 0; j < 3; j++) M[i][j] = MUL(R[i][j], s[j]);
+    float S[3][3];
+    #pragma unroll
+    for (int i = 0; i < 3; i++)
+        #pragma unroll
+        for (int j = i; j < 3; j++) {
+            S[i][j] = ADD(ADD(MUL(M[i][0], M[j][0]), MUL(M[i][1], M[j][1])), MUL(M[i][2], M[j][2]));
+            S[j][i] = S[i][j];
+        }
+
+    float limx = MUL(1.3f, DIV(MUL(0.5f, (float)V.width), V.fx));
+    float limy = MUL(1.3f, DIV(MUL(0.5f, (float)V.height), V.fy));
+    float xz = DIV(x, z), yz = DIV(y, z);
+    xz = fminf(limx, fmaxf(-limx, xz));
+    yz = fminf(limy, fmaxf(-limy, yz));
+    float tx = MUL(xz, z), ty = MUL(yz, z);
+    float z2 = MUL(z, z);
+    float J00 = DIV(V.fx, z), J02 = -DIV(MUL(V.fx, tx), z2);
+    float J11 = DIV(V.fy, z), J12 = -DIV(MUL(V.fy, ty), z2);
+
+    float T[2][3];
+    #pragma unroll
+    for (int j = 0; j < 3; j++) {
+        T[0][j] = ADD(MUL(J00, E[0 + j]), MUL(J02, E[8 + j]));
+        T[1][j] = ADD(MUL(J11, E[4 + j]), MUL(J12, E[8 + j]));
+    }
+    float U[2][3];
+    #pragma unroll
+    for (int i = 0; i < 2; i++)
+        #pragma unroll
+        for (int j = 0; j < 3; j++)
+            U[i][j] = ADD(ADD(MUL(T[i][0], S[0][j]), MUL(T[i][1], S[1][j])), MUL(T[i][2], S[2][j]));
+    float ca = ADD(ADD(ADD(MUL(U[0][0], T[0][0]), MUL(U[0][1], T[0][1])), MUL(U[0][2], T[0][2])), blur);
+    float cb = ADD(ADD(MUL(U[0][0], T[1][0]), MUL(U[0][1], T[1][1])), MUL(U[0][2], T[1][2]));
+    float cc = ADD(ADD(ADD(MUL(U[1][0], T[1][0]), MUL(U[1][1], T[1][1])), MUL(U[1][2], T[1][2])), blur);
+
+    float det = SUB(MUL(ca, cc), MUL(cb, cb));
+    if (!(det > 0.0f)) return false;
+    float mid = MUL(0.5f, ADD(ca, cc));
+    float disc = SUB(MUL(mid, mid), det);
+    float lam = ADD(mid, __fsqrt_rn(fmaxf(disc, 0.0f)));
+    float rad = ceilf(MUL(3.0f, __fsqrt_rn(lam)));
+
+    float u = ADD(DIV(MUL(V.fx, x), z), V.cx);
+    float v = ADD(DIV(MUL(V.fy, y), z), V.cy);
+    if (!(fabsf(u) < 0x1p24f && fabsf(v) < 0x1p24f && rad < 0x1p24f)) return false;
+
+    const float tw = (float)kTile;
+    float fx0 = floorf(DIV(SUB(u, rad), tw)), fx1 = floorf(DIV(ADD(u, rad), tw));
+    float fy0 = floorf(DIV(SUB(v, rad), tw)), fy1 = floorf(DIV(ADD(v, rad), tw));
+    fx0 = fmaxf(fx0, 0.0f);
+    fy0 = fmaxf(fy0, 0.0f);
+    fx1 = fminf(fx1, (float)(V.tiles_x - 1));
+    fy1 = fminf(fy1, (float)(V.tiles_y - 1));
+    if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
+
+    g.u = u;
+    g.v = v;
+    g.z = z;
+    g.ca = ca;
+    g.cb = cb;
+    g.cc = cc;
+    g.radius = (int32_t)rad;
+    g.x0 = (int32_t)fx0;
+    g.y0 = (int32_t)fy0;
+    g.x1 = (int32_t)fx1;
+    g.y1 = (int32_t)fy1;
+    return true;
+}
+
+#undef MUL
+#undef ADD
+#undef SUB
+#undef DIV
+
+struct ProjectArgs {
+    const float *means, *log_scales, *quats, *opacity_logit, *sh;
+    const float *viewmats;
+    int64_t n;
+    float near_z, blur;
+    float4 *rec;
+    int32_t *radii;
+    uint32_t *tiles_touched;
+};
+
+template <int DEG>
+__global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable vt)
+{
+    constexpr int K = ShCount<DEG>::value;
+    __shared__ float s_E[GS_MAX_VIEWS][12];
+    __shared__ float s_c[GS_MAX_VIEWS][3];
+    for (int k = threadIdx.x; k < vt.n_views * 12; k += blockDim.x) s_E[k / 12][k % 12] = a.viewmats[k];
+    __syncthreads();
+    for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) {
+        // camera centre c = -R^T t
+        const float *E = s_E[v];
+        #pragma unroll
+        for (int i = 0; i < 3; i++) s_c[v][i] = -(E[i] * E[3] + E[4 + i] * E[7] + E[8 + i] * E[11]);
+    }
+    __syncthreads();
+
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    float m[3], ls[3], q[4];
+    #pragma unroll
+    for (int k = 0; k < 3; k++) {
+        m[k] = __ldg(a.means + 3 * i + k);
+        ls[k] = __ldg(a.log_scales + 3 * i + k);
+    }
+    const float4 q4 = __ldg(reinterpret_cast<const float4 *>(a.quats) + i);
+    q[0] = q4.x;
+    q[1] = q4.y;
+    q[2] = q4.z;
+    q[3] = q4.w;
+    const float opacity = 1.0f / (1.0f + __expf(-__ldg(a.opacity_logit + i)));
+    float sh[K * 3];
+    const float *shp = a.sh + (int64_t)K * 3 * i;
+    if constexpr ((K * 3) % 4 == 0) {
+        #pragma unroll
+        for (int k = 0; k < K * 3 / 4; k++) {
+            float4 t = __ldg(reinterpret_cast<const float4 *>(shp) + k);
+            sh[4 * k] = t.x;
+            sh[4 * k + 1] = t.y;
+            sh[4 * k + 2] = t.z;
+            sh[4 * k + 3] = t.w;
+        }
+    } else {
+        #pragma unroll
+        for (int k = 0; k < K * 3; k++) sh[k] = __ldg(shp + k);
+    }
+
+    #pragma unroll 1
+    for (int v = 0; v < vt.n_views; v++) {
+        const int64_t o = (int64_t)v * a.n + i;
+        Geom g;
+        if (!geometry(m, ls, q, s_E[v], vt.v[v], a.near_z, a.blur, g)) {
+            a.radii[o] = 0;
+            a.tiles_touched[o] = 0;
+            continue;
+        }
+        const float inv = 1.0f / (g.ca * g.cc - g.cb * g.cb);
+        float dx = m[0] - s_c[v][0], dy = m[1] - s_c[v][1], dz = m[2] - s_c[v][2];
+        const float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= rn;
+        dy *= rn;
+        dz *= rn;
+        float Y[K];
+        sh_basis<DEG>(dx, dy, dz, Y);
+        float col[3];
+        #pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            float acc = 0.5f;
+            #pragma unroll
+            for (int k = 0; k < K; k++) acc += sh[3 * k + ch] * Y[k];
+            col[ch] = fmaxf(acc, 0.0f);
+        }
+        const uint32_t r0 = (uint32_t)g.x0 | ((uint32_t)g.y0 << 16);
+        const uint32_t r1 = (uint32_t)g.x1 | ((uint32_t)g.y1 << 16);
+        a.rec[3 * o + 0] = make_float4(g.u, g.v, g.z, opacity);
+        a.rec[3 * o + 1] = make_float4(g.cc * inv, -g.cb * inv, g.ca * inv, __uint_as_float(r0));
+        a.rec[3 * o + 2] = make_float4(col[0], col[1], col[2], __uint_as_float(r1));
+        a.radii[o] = g.radius;
+        a.tiles_touched[o] = (uint32_t)((g.x1 - g.x0 + 1) * (g.y1 - g.y0 + 1));
+    }
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" gs_status_t gs_project(const gs_params_t *params, const gs_view_t *views, const float *viewmats,
+                                  int32_t n_views, const gs_options_t *opt, gs_projected_t *out, void *stream)
+{
+    if (!params || !viewmats || !opt || !out) return GS_ERR_INVALID_ARG;
+    if (params->n < 0 || params->sh_degree < 0 || params->sh_degree > 3) return GS_ERR_INVALID_ARG;
+    ViewTable vt;
+    gs_status_t st = make_view_table(views, n_views, &vt);
+    if (st != GS_OK) return st;
+    if (params->n == 0) return GS_OK;
+    if (!params->means || !params->log_scales || !params->quats || !params->opacity_logit || !params->sh ||
+        !out->rec || !out->radii || !out->tiles_touched)
+        return GS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(out->rec) & 15) || (reinterpret_cast<uintptr_t>(params->quats) & 15))
+        return GS_ERR_INVALID_ARG;
+    if ((params->sh_degree == 1 || params->sh_degree == 3) && (reinterpret_cast<uintptr_t>(params->sh) & 15))
+        return GS_ERR_INVALID_ARG;
+    ProjectArgs a;
+    a.means = params->means;
+    a.log_scales = params->log_scales;
+    a.quats = params->quats;
+    a.opacity_logit = params->opacity_logit;
+    a.sh = params->sh;
+    a.viewmats = viewmats;
+    a.n = params->n;
+    a.near_z = opt->near_z;
+    a.blur = opt->blur;
+    a.rec = reinterpret_cast<float4 *>(out->rec);
+    a.radii = out->radii;
+    a.tiles_touched = out->tiles_touched;
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((params->n + threads - 1) / threads);
+    cudaStream_t s = as_stream(stream);
+    switch (params->sh_degree) {
+    case 0: project_kernel<0><<<blocks, threads, 0, s>>>(a, vt); break;
+    case 1: project_kernel<1><<<blocks, threads, 0, s>>>(a, vt); break;
+    case 2: project_kernel<2><<<blocks, threads, 0, s>>>(a, vt); break;
+    default: project_kernel<3><<<blocks, threads, 0, s>>>(a, vt); break;
+    }
+    return launch_status();
+}
+
+extern "C" gs_status_t gs_layout(const gs_view_t *views, int32_t n_views, int64_t *n_tiles_total,
+                                 int64_t *n_pixels_total)
+{
+    ViewTable vt;
+    gs_status_t st = make_view_table(views, n_views, &vt);
+    if (st != GS_OK) return st;
+    if (n_tiles_total) *n_tiles_total = vt.n_tiles_total;
+    if (n_pixels_total) *n_pixels_total = vt.n_pix_total;
+    return GS_OK;
+}
+
+extern "C" const char *gs_version(void) { return "gs-sm103a 0.1"; }
+
+extern "C" const char *gs_status_string(gs_status_t s)
+{
+    switch (s) {
+    case GS_OK: return "ok";
+    case GS_ERR_INVALID_ARG: return "invalid argument";
+    case GS_ERR_CUDA: return "CUDA error";
+    case GS_ERR_CAPACITY: return "pair capacity exceeded";
+    case GS_ERR_TIMEOUT: return "bounded wait expired";
+    case GS_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}

@@ -1,0 +1,366 @@
+// a8. Backward of the projection (reverse of Sec. 3.4 "Projection"; the pose
+// gradient serves the Sec. 3.3 joint optimisation, the parameter gradients the
+// Sec. 3.4 mapping).
+//
+// One thread per Gaussian loops over all views, so the gradients summed over
+// views are written to HBM once.  Per view it reads the (view, Gaussian) 2D
+// gradients, clears them, recomputes the projection in FP32 and applies the
+// chain rule:
+//   conic = Sigma2D^-1,  Sigma2D = J Sc J^T + blur I,  Sc = W S W^T,
+//   S = M M^T,  M = R(q / |q|) diag(exp(log_scale)),
+//   mu2D = (fx x/z + cx, fy y/z + cy),  depth = z,  p = (x, y, z) = W mu + t,
+//   J = [[fx/z, 0, -fx tx/z^2], [0, fy/z, -fy ty/z^2]] with tx = clamp(x/z) z,
+//   opacity = sigmoid(logit),  colour = max(0, SH(dir) + 1/2),
+//   dir = (mu - c) / |mu - c|,  c = -W^T t.
+// Twist xi = (rho, phi) with pose Exp(xi) E at xi = 0: p -> p + rho + phi x p,
+// Sc -> Exp(phi) Sc Exp(phi)^T, c -> c - W^T rho.
+#include "common.cuh"
+#include "sh.cuh"
+
+namespace gs {
+
+struct ProjectBwdArgs {
+    const float *means, *log_scales, *quats, *opacity_logit, *sh;
+    const float *viewmats;
+    int64_t n;
+    float blur;
+    const int32_t *radii;
+    float4 *grad2d;
+    float *g_means, *g_log_scales, *g_quats, *g_opacity_logit, *g_sh;
+    float *d_twist;
+};
+
+template <int DEG>
+__global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a, ViewTable vt)
+{
+    constexpr int K = ShCount<DEG>::value;
+    __shared__ float s_E[GS_MAX_VIEWS][12];
+    __shared__ float s_c[GS_MAX_VIEWS][3];
+    __shared__ float s_tw[GS_MAX_VIEWS][6];
+    for (int k = threadIdx.x; k < vt.n_views * 12; k += blockDim.x) s_E[k / 12][k % 12] = a.viewmats[k];
+    for (int k = threadIdx.x; k < vt.n_views * 6; k += blockDim.x) s_tw[k / 6][k % 6] = 0.0f;
+    __syncthreads();
+    for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) {
+        const float *E = s_E[v];
+        #pragma unroll
+        for (int i = 0; i < 3; i++) s_c[v][i] = -(E[i] * E[3] + E[4 + i] * E[7] + E[8 + i] * E[11]);
+    }
+    __syncthreads();
+
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < a.n;
+    const int lane = threadIdx.x & 31;
+    const bool want_twist = a.d_twist != nullptr;
+
+    float m[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, ol = 0.0f;
+    float sh[K * 3];
+    #pragma unroll
+    for (int k = 0; k < K * 3; k++) sh[k] = 0.0f;
+    if (active) {
+        #pragma unroll
+        for (int k = 0; k < 3; k++) {
+            m[k] = a.means[3 * i + k];
+            ls[k] = a.log_scales[3 * i + k];
+        }
+        const float4 q4 = reinterpret_cast<const float4 *>(a.quats)[i];
+        q[0] = q4.x;
+        q[1] = q4.y;
+        q[2] = q4.z;
+        q[3] = q4.w;
+        ol = a.opacity_logit[i];
+        const float *shp = a.sh + (int64_t)K * 3 * i;
+        #pragma unroll
+        for (int k = 0; k < K * 3; k++) sh[k] = shp[k];
+    }
+    // quantities that do not depend on the view
+    const float qn2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    const float qinv = rsqrtf(fmaxf(qn2, 1e-30f));
+    const float w = q[0] * qinv, qa = q[1] * qinv, qb = q[2] * qinv, qc = q[3] * qinv;
+    float Rq[3][3];
+    Rq[0][0] = 1.f - 2.f * (qb * qb + qc * qc);
+    Rq[0][1] = 2.f * (qa * qb - w * qc);
+    Rq[0][2] = 2.f * (qa * qc + w * qb);
+    Rq[1][0] = 2.f * (qa * qb + w * qc);
+    Rq[1][1] = 1.f - 2.f * (qa * qa + qc * qc);
+    Rq[1][2] = 2.f * (qb * qc - w * qa);
+    Rq[2][0] = 2.f * (qa * qc - w * qb);
+    Rq[2][1] = 2.f * (qb * qc + w * qa);
+    Rq[2][2] = 1.f - 2.f * (qa * qa + qb * qb);
+    const float s[3] = {expf(ls[0]), expf(ls[1]), expf(ls[2])};
+    float M[3][3], S[3][3];
+    #pragma unroll
+    for (int r = 0; r < 3; r++)
+        #pragma unroll
+        for (int c = 0; c < 3; c++) M[r][c] = Rq[r][c] * s[c];
+    #pragma unroll
+    for (int r = 0; r < 3; r++)
+        #pragma unroll
+        for (int c = 0; c < 3; c++) S[r][c] = M[r][0] * M[c][0] + M[r][1] * M[c][1] + M[r][2] * M[c][2];
+    const float opac = 1.0f / (1.0f + expf(-ol));
+
+    float gm[3] = {0, 0, 0}, gMacc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gol = 0.0f;
+    float gsh[K * 3];
+    #pragma unroll
+    for (int k = 0; k < K * 3; k++) gsh[k] = 0.0f;
+
+    #pragma unroll 1
+    for (int v = 0; v < vt.n_views; v++) {
+        float tw[6] = {0, 0, 0, 0, 0, 0};
+        const int64_t o = (int64_t)v * a.n + i;
+        if (active && a.radii[o] > 0) {
+            const float4 G0 = a.grad2d[3 * o], G1 = a.grad2d[3 * o + 1], G2v = a.grad2d[3 * o + 2];
+            const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            a.grad2d[3 * o] = zero4;
+            a.grad2d[3 * o + 1] = zero4;
+            a.grad2d[3 * o + 2] = zero4;
+            const float gu = G0.x, gv = G0.y, gA = G0.z, gB = G0.w, gC = G1.x, gop = G1.y;
+            const float gcol[3] = {G1.z, G1.w, G2v.x};
+            const float gz = G2v.y;
+            const float *E = s_E[v];
+            const ViewInfo &V = vt.v[v];
+            const float W[3][3] = {{E[0], E[1], E[2]}, {E[4], E[5], E[6]}, {E[8], E[9], E[10]}};
+            const float x = W[0][0] * m[0] + W[0][1] * m[1] + W[0][2] * m[2] + E[3];
+            const float y = W[1][0] * m[0] + W[1][1] * m[1] + W[1][2] * m[2] + E[7];
+            const float z = W[2][0] * m[0] + W[2][1] * m[1] + W[2][2] * m[2] + E[11];
+            // camera-space covariance Sc = W S W^T
+            float WS[3][3], Sc[3][3];
+            #pragma unroll
+            for (int r = 0; r < 3; r++)
+                #pragma unroll
+                for (int c = 0; c < 3; c++) WS[r][c] = W[r][0] * S[0][c] + W[r][1] * S[1][c] + W[r][2] * S[2][c];
+            #pragma unroll
+            for (int r = 0; r < 3; r++)
+                #pragma unroll
+                for (int c = 0; c < 3; c++) Sc[r][c] = WS[r][0] * W[c][0] + WS[r][1] * W[c][1] + WS[r][2] * W[c][2];
+            const float limx = 1.3f * (0.5f * (float)V.width / V.fx);
+            const float limy = 1.3f * (0.5f * (float)V.height / V.fy);
+            const float rz = 1.0f / z, rz2 = rz * rz;
+            const float xz = x * rz, yz = y * rz;
+            const bool clx = xz < -limx || xz > limx, cly = yz < -limy || yz > limy;
+            const float Lx = xz < 0.f ? -limx : limx, Ly = yz < 0.f ? -limy : limy;
+            const float tx = (clx ? Lx : xz) * z, ty = (cly ? Ly : yz) * z;
+            const float J00 = V.fx * rz, J02 = -V.fx * tx * rz2, J11 = V.fy * rz, J12 = -V.fy * ty * rz2;
+            // J Sc rows (J has zeros at [0][1] and [1][0])
+            float JS0[3], JS1[3];
+            #pragma unroll
+            for (int c = 0; c < 3; c++) {
+                JS0[c] = J00 * Sc[0][c] + J02 * Sc[2][c];
+                JS1[c] = J11 * Sc[1][c] + J12 * Sc[2][c];
+            }
+            const float ca = JS0[0] * J00 + JS0[2] * J02 + a.blur;
+            const float cb = JS0[1] * J11 + JS0[2] * J12;
+            const float cc = JS1[1] * J11 + JS1[2] * J12 + a.blur;
+            const float det = ca * cc - cb * cb;
+            const float id2 = 1.0f / (det * det);
+            // conic (A, B, C) = (c, -b, a) / det  ->  covariance (a, b, c)
+            const float ga = (-gA * cc * cc + gB * cb * cc - gC * cb * cb) * id2;
+            const float gb = (2.f * gA * cb * cc - gB * (det + 2.f * cb * cb) + 2.f * gC * ca * cb) * id2;
+            const float gc = (-gA * cb * cb + gB * ca * cb - gC * ca * ca) * id2;
+            const float hb = 0.5f * gb;
+            // Gc = J^T G2 J with G2 = [[ga, hb], [hb, gc]]
+            const float u0 = ga * J02 + hb * J12, u1 = hb * J02 + gc * J12;
+            float Gc[3][3];
+            Gc[0][0] = J00 * ga * J00;
+            Gc[0][1] = J00 * hb * J11;
+            Gc[0][2] = J00 * u0;
+            Gc[1][1] = J11 * gc * J11;
+            Gc[1][2] = J11 * u1;
+            Gc[2][2] = J02 * u0 + J12 * u1;
+            Gc[1][0] = Gc[0][1];
+            Gc[2][0] = Gc[0][2];
+            Gc[2][1] = Gc[1][2];
+            // dL/dJ = 2 G2 J Sc
+            const float gJ00 = 2.f * (ga * JS0[0] + hb * JS1[0]);
+            const float gJ02 = 2.f * (ga * JS0[2] + hb * JS1[2]);
+            const float gJ11 = 2.f * (hb * JS0[1] + gc * JS1[1]);
+            const float gJ12 = 2.f * (hb * JS0[2] + gc * JS1[2]);
+            float gpx = gu * V.fx * rz, gpy = gv * V.fy * rz;
+            float gpz = -(gu * V.fx * x + gv * V.fy * y) * rz2 + gz;
+            gpz -= (gJ00 * V.fx + gJ11 * V.fy) * rz2;
+            if (!clx) {
+                gpx -= gJ02 * V.fx * rz2;
+                gpz += gJ02 * 2.f * V.fx * x * rz2 * rz;
+            } else {
+                gpz += gJ02 * V.fx * Lx * rz2;
+            }
+            if (!cly) {
+                gpy -= gJ12 * V.fy * rz2;
+                gpz += gJ12 * 2.f * V.fy * y * rz2 * rz;
+            } else {
+                gpz += gJ12 * V.fy * Ly * rz2;
+            }
+            #pragma unroll
+            for (int c = 0; c < 3; c++) gm[c] += W[0][c] * gpx + W[1][c] * gpy + W[2][c] * gpz;
+            // world covariance gradient Gw = W^T Gc W, accumulated over views
+            float GcW[3][3];
+            #pragma unroll
+            for (int r = 0; r < 3; r++)
+                #pragma unroll
+                for (int c = 0; c < 3; c++) GcW[r][c] = Gc[r][0] * W[0][c] + Gc[r][1] * W[1][c] + Gc[r][2] * W[2][c];
+            #pragma unroll
+            for (int r = 0; r < 3; r++)
+                #pragma unroll
+                for (int c = 0; c < 3; c++)
+                    gMacc[r][c] += W[0][r] * GcW[0][c] + W[1][r] * GcW[1][c] + W[2][r] * GcW[2][c];
+            gol += gop * opac * (1.0f - opac);
+            // colour through the SH of the view direction
+            const float vx = m[0] - s_c[v][0], vy = m[1] - s_c[v][1], vz = m[2] - s_c[v][2];
+            const float rn = rsqrtf(vx * vx + vy * vy + vz * vz);
+            const float dx = vx * rn, dy = vy * rn, dz = vz * rn;
+            float Y[K], wk[K];
+            sh_basis<DEG>(dx, dy, dz, Y);
+            #pragma unroll
+            for (int k = 0; k < K; k++) wk[k] = 0.0f;
+            #pragma unroll
+            for (int ch = 0; ch < 3; ch++) {
+                float acc = 0.5f;
+                #pragma unroll
+                for (int k = 0; k < K; k++) acc += sh[3 * k + ch] * Y[k];
+                if (acc < 0.0f) continue;
+                #pragma unroll
+                for (int k = 0; k < K; k++) {
+                    gsh[3 * k + ch] += Y[k] * gcol[ch];
+                    wk[k] += sh[3 * k + ch] * gcol[ch];
+                }
+            }
+            float gdir[3];
+            sh_basis_grad<DEG>(dx, dy, dz, wk, gdir);
+            const float dd = gdir[0] * dx + gdir[1] * dy + gdir[2] * dz;
+            const float gvx = (gdir[0] - dx * dd) * rn, gvy = (gdir[1] - dy * dd) * rn, gvz = (gdir[2] - dz * dd) * rn;
+            gm[0] += gvx;
+            gm[1] += gvy;
+            gm[2] += gvz;
+            if (want_twist) {
+                tw[0] = gpx + W[0][0] * gvx + W[0][1] * gvy + W[0][2] * gvz;
+                tw[1] = gpy + W[1][0] * gvx + W[1][1] * gvy + W[1][2] * gvz;
+                tw[2] = gpz + W[2][0] * gvx + W[2][1] * gvy + W[2][2] * gvz;
+                // (Sc Gc - Gc Sc) entries (1,2), (2,0), (0,1)
+                float A12 = 0.f, A20 = 0.f, A01 = 0.f;
+                #pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    A12 += Sc[1][k] * Gc[k][2] - Gc[1][k] * Sc[k][2];
+                    A20 += Sc[2][k] * Gc[k][0] - Gc[2][k] * Sc[k][0];
+                    A01 += Sc[0][k] * Gc[k][1] - Gc[0][k] * Sc[k][1];
+                }
+                tw[3] = y * gpz - z * gpy + 2.f * A12;
+                tw[4] = z * gpx - x * gpz + 2.f * A20;
+                tw[5] = x * gpy - y * gpx + 2.f * A01;
+            }
+        }
+        if (want_twist) {
+            #pragma unroll
+            for (int k = 0; k < 6; k++) {
+                const float r = warp_sum(tw[k]);
+                if (lane == 0 && r != 0.0f) atomicAdd(&s_tw[v][k], r);
+            }
+        }
+    }
+
+    if (active) {
+        // M = Rq diag(s):  dL/dM = 2 Gw M
+        float gM[3][3];
+        #pragma unroll
+        for (int r = 0; r < 3; r++)
+            #pragma unroll
+            for (int c = 0; c < 3; c++)
+                gM[r][c] = 2.f * (gMacc[r][0] * M[0][c] + gMacc[r][1] * M[1][c] + gMacc[r][2] * M[2][c]);
+        float gR[3][3];
+        #pragma unroll
+        for (int c = 0; c < 3; c++) {
+            float gsv = 0.f;
+            #pragma unroll
+            for (int r = 0; r < 3; r++) {
+                gsv += gM[r][c] * Rq[r][c];
+                gR[r][c] = gM[r][c] * s[c];
+            }
+            a.g_log_scales[3 * i + c] += gsv * s[c];
+        }
+        float gq[4];
+        gq[0] = 2.f * (-qc * gR[0][1] + qb * gR[0][2] + qc * gR[1][0] - qa * gR[1][2] - qb * gR[2][0] + qa * gR[2][1]);
+        gq[1] = 2.f * (qb * gR[0][1] + qc * gR[0][2] + qb * gR[1][0] - w * gR[1][2] + qc * gR[2][0] + w * gR[2][1]) -
+                4.f * qa * (gR[1][1] + gR[2][2]);
+        gq[2] = 2.f * (qa * gR[0][1] + w * gR[0][2] + qa * gR[1][0] + qc * gR[1][2] - w * gR[2][0] + qc * gR[2][1]) -
+                4.f * qb * (gR[0][0] + gR[2][2]);
+        gq[3] = 2.f * (-w * gR[0][1] + qa * gR[0][2] + w * gR[1][0] + qb * gR[1][2] + qa * gR[2][0] + qb * gR[2][1]) -
+                4.f * qc * (gR[0][0] + gR[1][1]);
+        const float qd = gq[0] * w + gq[1] * qa + gq[2] * qb + gq[3] * qc;
+        const float qn[4] = {w, qa, qb, qc};
+        #pragma unroll
+        for (int k = 0; k < 4; k++) a.g_quats[4 * i + k] += (gq[k] - qn[k] * qd) * qinv;
+        #pragma unroll
+        for (int k = 0; k < 3; k++) a.g_means[3 * i + k] += gm[k];
+        a.g_opacity_logit[i] += gol;
+        float *gshp = a.g_sh + (int64_t)K * 3 * i;
+        #pragma unroll
+        for (int k = 0; k < K * 3; k++) gshp[k] += gsh[k];
+    }
+    if (want_twist) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < vt.n_views * 6; k += blockDim.x) {
+            const float r = s_tw[k / 6][k % 6];
+            if (r != 0.0f) atomicAdd(a.d_twist + k, r);
+        }
+    }
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" gs_status_t gs_project_bwd(const gs_params_t *params, const gs_view_t *views, const float *viewmats,
+                                      int32_t n_views, const gs_options_t *opt, const gs_projected_t *proj,
+                                      float *grad2d, gs_param_grads_t *grads, float *d_twist, void *stream)
+{
+    if (!params || !viewmats || !opt || !proj || !grad2d || !grads) return GS_ERR_INVALID_ARG;
+    if (params->n < 0 || params->sh_degree < 0 || params->sh_degree > 3) return GS_ERR_INVALID_ARG;
+    ViewTable vt;
+    gs_status_t st = make_view_table(views, n_views, &vt);
+    if (st != GS_OK) return st;
+    if (params->n == 0) return GS_OK;
+    if (!params->means || !params->log_scales || !params->quats || !params->opacity_logit || !params->sh ||
+        !proj->radii || !grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logit ||
+        !grads->sh)
+        return GS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(grad2d) & 15) || (reinterpret_cast<uintptr_t>(params->quats) & 15))
+        return GS_ERR_INVALID_ARG;
+    ProjectBwdArgs a;
+    a.means = params->means;
+    a.log_scales = params->log_scales;
+    a.quats = params->quats;
+    a.opacity_logit = params->opacity_logit;
+    a.sh = params->sh;
+    a.viewmats = viewmats;
+    a.n = params->n;
+    a.blur = opt->blur;
+    a.radii = proj->radii;
+    a.grad2d = reinterpret_cast<float4 *>(grad2d);
+    a.g_means = grads->means;
+    a.g_log_scales = grads->log_scales;
+    a.g_quats = grads->quats;
+    a.g_opacity_logit = grads->opacity_logit;
+    a.g_sh = grads->sh;
+    a.d_twist = d_twist;
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((params->n + threads - 1) / threads);
+    cudaStream_t s = as_stream(stream);
+    switch (params->sh_degree) {
+    case 0: project_bwd_kernel<0><<<blocks, threads, 0, s>>>(a, vt); break;
+    case 1: project_bwd_kernel<1><<<blocks, threads, 0, s>>>(a, vt); break;
+    case 2: project_bwd_kernel<2><<<blocks, threads, 0, s>>>(a, vt); break;
+    default: project_bwd_kernel<3><<<blocks, threads, 0, s>>>(a, vt); break;
+    }
+    return launch_status();
+}
+
+extern "C" gs_status_t gs_render_bwd(const gs_params_t *params, const gs_view_t *views, const float *viewmats,
+                                     int32_t n_views, const gs_options_t *opt, const gs_projected_t *proj,
+                                     const gs_bins_t *bins, const gs_image_t *img, const float *d_rgb,
+                                     const float *d_depth, const float *d_alpha, float *grad2d,
+                                     gs_param_grads_t *grads, float *d_twist, uint32_t *work_counter, void *stream)
+{
+    if (!params) return GS_ERR_INVALID_ARG;
+    gs_status_t st = gs_render_bwd_splats(proj, params->n, bins, views, n_views, img, d_rgb, d_depth, d_alpha,
+                                          grad2d, work_counter, stream);
+    if (st != GS_OK) return st;
+    return gs_project_bwd(params, views, viewmats, n_views, opt, proj, grad2d, grads, d_twist, stream);
+}

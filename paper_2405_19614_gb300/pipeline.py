@@ -1,0 +1,150 @@
+"""One mapping / pose-refinement iteration over a batch of keyframes, built from
+the C-ABI calls (Sec. 3.4 online mapping; Sec. 3.3 joint optimisation).
+
+A step is: project (a1) -> bin + sort (a2-a4) -> composite (a5) -> L1 loss and
+gate (a6) -> backward of the compositing and projection, with per-view twist
+gradients (a7, a8) -> keypoint re-projection term (a9) -> Adam on all Gaussian
+parameters (a10).  Everything is enqueued on one stream without a host
+synchronisation, so a step can be captured in a CUDA graph and replayed.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import (Rasterizer, gs_adam_step, gs_loss_l1, gs_reproj_loss_grad)
+
+PARAM_ORDER = ("means", "log_scales", "quats", "opacity_logit", "sh")
+DEFAULT_LR = dict(means=1.6e-4, log_scales=5e-3, quats=1e-3, opacity_logit=5e-2, sh=2.5e-3)
+
+
+def _seg_widths(n, sh_degree):
+    K = (sh_degree + 1) ** 2
+    return dict(means=3 * n, log_scales=3 * n, quats=4 * n, opacity_logit=n, sh=3 * K * n)
+
+
+class FlatParams:
+    """All Gaussian parameters in one float32 device buffer (segments 256-byte
+    aligned), with tensor views for each kind, so the optimiser is one launch."""
+
+    def __init__(self, scene, device):
+        n = int(scene["means"].shape[0])
+        deg = int(scene["sh_degree"])
+        widths = _seg_widths(n, deg)
+        self.offsets, off = {}, 0
+        for k in PARAM_ORDER:
+            self.offsets[k] = off
+            off += (widths[k] + 63) // 64 * 64
+        self.total = off
+        self.n, self.sh_degree, self.widths = n, deg, widths
+        self.buf = torch.zeros(self.total, dtype=torch.float32, device=device)
+        host = np.zeros(self.total, np.float32)
+        for k in PARAM_ORDER:
+            host[self.offsets[k]:self.offsets[k] + widths[k]] = np.asarray(scene[k], np.float32).reshape(-1)
+        self.buf.copy_(torch.from_numpy(host))
+
+    def views(self, buf=None):
+        b = self.buf if buf is None else buf
+        K = (self.sh_degree + 1) ** 2
+        shapes = dict(means=(self.n, 3), log_scales=(self.n, 3), quats=(self.n, 4), opacity_logit=(self.n,),
+                      sh=(self.n, K, 3))
+        out = {k: b[self.offsets[k]:self.offsets[k] + self.widths[k]].view(*shapes[k]) for k in PARAM_ORDER}
+        out["sh_degree"] = self.sh_degree
+        return out
+
+
+class MappingStep:
+    """Buffers and launches of one joint mapping / tracking iteration."""
+
+    def __init__(self, scene, intr, size, viewmats, target_rgb, target_depth, w_c=1.0, w_d=0.5,
+                 use_gate=False, gamma=0.99, keypoints=None, w_rpj=1.5, lrs=None, pair_capacity=None,
+                 device="cuda"):
+        dev = torch.device(device)
+        self.flat = FlatParams(scene, dev)
+        self.params = self.flat.views()
+        self.grad_buf = torch.zeros_like(self.flat.buf)
+        self.grads = self.flat.views(self.grad_buf)
+        self.m = torch.zeros_like(self.flat.buf)
+        self.v = torch.zeros_like(self.flat.buf)
+        self.step_count = torch.zeros(2, dtype=torch.int32, device=dev)
+        lrs = dict(DEFAULT_LR, **(lrs or {}))
+        self.groups = [(self.flat.offsets[k], self.flat.widths[k], lrs[k]) for k in PARAM_ORDER]
+        self.rast = Rasterizer(self.flat.n, self.flat.sh_degree, intr, size, pair_capacity, dev)
+        self.viewmats = torch.as_tensor(np.asarray(viewmats, np.float32).reshape(-1, 12), device=dev).contiguous()
+        self.target_rgb = target_rgb
+        self.target_depth = target_depth
+        P = self.rast.n_pix
+        self.d_rgb = torch.zeros(P, 3, device=dev)
+        self.d_depth = torch.zeros(P, device=dev)
+        self.loss = torch.zeros(1, device=dev)
+        self.d_twist = torch.zeros(self.rast.V, 6, device=dev)
+        self.w_c, self.w_d, self.use_gate, self.gamma = float(w_c), float(w_d), bool(use_gate), float(gamma)
+        self.keypoints = keypoints  # dict(points [n,3], obs [n,2], view_ids [n]) on the device
+        self.w_rpj = float(w_rpj)
+        self.optimise_params = True
+
+    def run(self, timers=None, stream=None):
+        """Enqueue one iteration.  timers: optional dict stage -> list to which
+        (start, end) CUDA events are appended."""
+        def mark(name):
+            if timers is None:
+                return None
+            e = torch.cuda.Event(enable_timing=True)
+            e.record()
+            return (name, e)
+
+        def close(tok):
+            if tok is None:
+                return
+            e = torch.cuda.Event(enable_timing=True)
+            e.record()
+            timers.setdefault(tok[0], []).append((tok[1], e))
+
+        r = self.rast
+        tok = mark("zero")
+        self.grad_buf.zero_()
+        self.loss.zero_()
+        self.d_twist.zero_()
+        close(tok)
+        from . import gs_bin_sort, gs_project, gs_render_fwd, gs_render_bwd_splats, gs_project_bwd
+        tok = mark("project")
+        gs_project(self.params, r.views, self.viewmats, r.proj, r.near_z, r.blur, stream)
+        close(tok)
+        tok = mark("bin_sort")
+        gs_bin_sort(r.proj, r.n, r.views, r.bins, r.workspace, stream)
+        close(tok)
+        tok = mark("render_fwd")
+        gs_render_fwd(r.proj, r.n, r.bins, r.views, r.img, r.work_counter, stream)
+        close(tok)
+        tok = mark("loss")
+        gs_loss_l1(r.img["rgb"], r.img["depth"], r.img["alpha"], self.target_rgb, self.target_depth, self.w_c,
+                   self.w_d, self.use_gate, self.gamma, self.loss, self.d_rgb, self.d_depth, stream)
+        close(tok)
+        tok = mark("render_bwd")
+        gs_render_bwd_splats(r.proj, r.n, r.bins, r.views, r.img, self.d_rgb, self.d_depth, None, r.grad2d,
+                             r.work_counter, stream)
+        close(tok)
+        tok = mark("project_bwd")
+        gs_project_bwd(self.params, r.views, self.viewmats, r.proj, r.grad2d, self.grads, self.d_twist, r.near_z,
+                       r.blur, stream)
+        close(tok)
+        if self.keypoints is not None:
+            tok = mark("reproj")
+            kp = self.keypoints
+            gs_reproj_loss_grad(kp["points"], kp["obs"], kp.get("view_ids"), r.views, self.viewmats, self.w_rpj,
+                                self.loss, self.d_twist, r.near_z, stream)
+            close(tok)
+        if self.optimise_params:
+            tok = mark("adam")
+            gs_adam_step(self.flat.buf, self.grad_buf, self.m, self.v, self.groups, self.step_count, stream=stream)
+            close(tok)
+
+    def kernels_per_step(self):
+        """Kernels of this library launched by one run() (memsets excluded)."""
+        import math
+        n_bits = 32 + max(0, math.ceil(math.log2(max(self.rast.n_tiles, 1))))
+        passes = (n_bits + 7) // 8
+        k = 1 + (3 + 1 + passes + 1) + 1 + 1 + 1 + 1  # project, bin (count, scan, emit, hist, passes, ranges), fwd, loss, bwd, pbwd
+        k += 1 if self.keypoints is not None else 0
+        k += 1 if self.optimise_params else 0
+        return k

@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars: radii, tile rectangles, depths, keys, per-tile lists and ranges
+bit-exact; RGB, depth and alpha within 1e-4 absolute of the FP64 oracle on
+pixels with no near-threshold decision (their count is reported); gradients
+within 1e-3 relative L2 per parameter tensor (printed per output), with the
+upstream gradient of near-threshold pixels zeroed on both sides.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2405_19614_gb300 as gs
+import scenes
+from gpu_util import (PARAM_KEYS, gpu_bins, gpu_geom, make_rast, oracle_targets, params_on_device, rel_l2, t,
+                      viewmats_on_device, zero_grads)
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2405_19614_gb300.build import build
+    build()
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def _cases():
+    # (name, scene, cams): small, several tiles, ragged edges, uneven multi-view
+    c1 = scenes.config(1)
+    yield "plain-2k-64x48", c1["scene"], c1["cams"]
+    sc = scenes.cube_scene(3000, seed=77, sh_degree=3, log_scale=(-3.2, 0.5))
+    vms = np.stack([scenes.look_at((0.3 * k - 0.3, -0.2, -0.4), (0.0, 0.1, 3.0)) for k in range(3)])
+    cams = scenes.cams_from([[70, 70, 50, 30], [90, 80, 61.5, 40], [40, 40, 18, 17]],
+                            [[100, 61], [123, 77], [37, 35]], vms)
+    yield "sh3-3views-ragged", sc, cams
+
+
+CASES = list(_cases())
+
+
+def _run(scene, cams, capacity=None):
+    rast = make_rast(scene, cams, capacity)
+    p = params_on_device(scene)
+    vm = viewmats_on_device(cams)
+    rast.forward(p, vm)
+    torch.cuda.synchronize()
+    return rast, p, vm
+
+
+@pytest.mark.parametrize("name,scene,cams", CASES, ids=[c[0] for c in CASES])
+def test_projection_and_binning_bit_exact(name, scene, cams):
+    rast, p, vm = _run(scene, cams)
+    assert rast.status() == 0
+    geom = oracle.project_geom(scene, cams)
+    rec, radii, tt, rect = gpu_geom(rast)
+    np.testing.assert_array_equal(radii, geom["radius"])
+    vis = geom["radius"] > 0
+    np.testing.assert_array_equal(tt, geom["tiles_touched"])
+    np.testing.assert_array_equal(rect[vis], geom["rect"][vis])
+    np.testing.assert_array_equal(rec[vis][:, 0:3].view(np.uint32), geom["uvz"][vis].view(np.uint32))
+    bins = oracle.bin_tiles(cams, geom)
+    keys, vals, ranges = gpu_bins(rast)
+    assert rast.n_pairs() == bins["n_pairs"]
+    np.testing.assert_array_equal(keys, bins["keys"])
+    np.testing.assert_array_equal(vals, bins["vals"])
+    np.testing.assert_array_equal(ranges, bins["ranges"])
+    # the non-exact per-splat quantities against FP64
+    proj = oracle.project64(scene, cams, geom)
+    np.testing.assert_allclose(rec[vis][:, 4:7], proj[vis][:, 3:6], rtol=2e-4, atol=1e-6)
+    np.testing.assert_allclose(rec[vis][:, 3], proj[vis][:, 6], rtol=1e-5, atol=1e-7)
+    np.testing.assert_allclose(rec[vis][:, 8:11], proj[vis][:, 7:10], rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("name,scene,cams", CASES, ids=[c[0] for c in CASES])
+def test_render_forward_parity(name, scene, cams):
+    rast, p, vm = _run(scene, cams)
+    ref = oracle.forward(scene, cams)["img"]
+    keep = ref["flags"] == 0
+    print(f"{name}: {(~keep).sum()} of {keep.size} pixels near a threshold, left out")
+    assert keep.mean() > 0.995
+    img = {k: v.cpu().numpy() for k, v in rast.img.items()}
+    for k in ("rgb", "depth", "alpha", "final_T"):
+        err = np.abs(img[k][keep] - ref[k][keep]).max()
+        print(f"{name}: max |{k} err| = {err:.3e}")
+        assert err <= IMG_TOL, k
+    np.testing.assert_array_equal(img["n_contrib"][keep], ref["n_contrib"][keep])
+
+
+def _backward_case(scene, cams, target_scene=None, twist=True):
+    rast, p, vm = _run(scene, cams)
+    ref = oracle.forward(scene, cams)
+    keep = ref["img"]["flags"] == 0
+    if target_scene is not None:
+        t_rgb, t_depth = oracle_targets(target_scene, cams)
+    else:
+        rng = np.random.default_rng(0)
+        t_rgb = rng.uniform(0, 1, ref["img"]["rgb"].shape).astype(np.float32)
+        t_depth = rng.uniform(0, 5, ref["img"]["depth"].shape).astype(np.float32)
+    L, dC, dD = oracle.loss_l1(ref["img"], t_rgb, t_depth, 1.0, 1.0)
+    # an extra alpha term exercises the border-mask gradient
+    dA = np.random.default_rng(1).normal(0, 1e-4, ref["img"]["alpha"].shape)
+    dC[~keep] = 0.0
+    dD[~keep] = 0.0
+    dA[~keep] = 0.0
+    gref = oracle.backward(scene, cams, ref, dC, dD, dA)
+    grads = zero_grads(p)
+    d_twist = torch.zeros(len(cams["size"]), 6, device=vm.device) if twist else None
+    rast.backward(p, vm, t(dC), t(dD), t(dA), grads, d_twist)
+    torch.cuda.synchronize()
+    assert rast.status() == 0
+    assert float(rast.grad2d.abs().max()) == 0.0  # left zeroed for the next call
+    out = {k: grads[k].cpu().numpy() for k in PARAM_KEYS}
+    if twist:
+        out["twist"] = d_twist.cpu().numpy()
+    return out, gref
+
+
+@pytest.mark.parametrize("name,scene,cams", CASES, ids=[c[0] for c in CASES])
+def test_backward_parity(name, scene, cams):
+    out, gref = _backward_case(scene, cams)
+    for k in (*PARAM_KEYS, "twist"):
+        e = rel_l2(out[k], gref[k])
+        print(f"{name}: grad {k:14s} rel-L2 err = {e:.3e}")
+        assert e <= GRAD_TOL, k
+
+
+def test_splat_gradients_parity():
+    c = scenes.config(1)
+    scene, cams = c["scene"], c["cams"]
+    rast, p, vm = _run(scene, cams)
+    ref = oracle.forward(scene, cams)
+    keep = ref["img"]["flags"] == 0
+    rng = np.random.default_rng(2)
+    P = ref["bins"]["n_pix"]
+    dC, dD, dA = rng.normal(0, 1, (P, 3)), rng.normal(0, 1, P), rng.normal(0, 1, P)
+    dC[~keep] = 0
+    dD[~keep] = 0
+    dA[~keep] = 0
+    g2d = oracle.render_bwd(cams, ref["proj"], ref["bins"], ref["geom"]["n"], dC, dD, dA)
+    gs.gs_render_bwd_splats(rast.proj, rast.n, rast.bins, rast.views, rast.img, t(dC), t(dD), t(dA), rast.grad2d,
+                            rast.work_counter)
+    torch.cuda.synchronize()
+    G = rast.grad2d.view(-1, 12).cpu().numpy()[:, :10]
+    names = ("u", "v", "conicA", "conicB", "conicC", "opacity", "r", "g", "b", "z")
+    for k, nm in enumerate(names):
+        e = rel_l2(G[:, k], g2d[:, k])
+        print(f"2D grad {nm:8s} rel-L2 err = {e:.3e}")
+        assert e <= GRAD_TOL, nm
+
+
+def test_batched_views_equal_plain_views():
+    """Rendering several views in one launch gives the same images as one view per launch."""
+    name, scene, cams = CASES[1]
+    rast, p, vm = _run(scene, cams)
+    batched = {k: v.cpu().numpy() for k, v in rast.img.items()}
+    base = 0
+    for v in range(len(cams["size"])):
+        cv = scenes.cams_from(cams["intr"][v:v + 1], cams["size"][v:v + 1], cams["viewmats"][v:v + 1])
+        r1, _, _ = _run(scene, cv)
+        P = int(cams["size"][v][0] * cams["size"][v][1])
+        for k in ("rgb", "depth", "alpha", "final_T", "n_contrib"):
+            np.testing.assert_array_equal(r1.img[k].cpu().numpy(), batched[k][base:base + P])
+        base += P
+
+
+def test_loss_l1_and_gate_parity():
+    rng = np.random.default_rng(3)
+    P = 5000
+    img = dict(rgb=rng.uniform(0, 1, (P, 3)).astype(np.float32), depth=rng.uniform(0, 3, P).astype(np.float32),
+               alpha=rng.uniform(0.95, 1.0, P).astype(np.float32))
+    img["depth"][:100] = 0.0
+    t_rgb = rng.uniform(0, 1, (P, 3)).astype(np.float32)
+    t_depth = rng.uniform(0, 3, P).astype(np.float32)
+    t_depth[100:200] = 0.0
+    for gate in (False, True):
+        L, dC, dD = oracle.loss_l1(img, t_rgb, t_depth, 0.5, 1.0, gate=gate, gamma=0.99)
+        loss = torch.zeros(1, device="cuda")
+        d_rgb = torch.empty(P, 3, device="cuda")
+        d_depth = torch.empty(P, device="cuda")
+        gs.gs_loss_l1(t(img["rgb"]), t(img["depth"]), t(img["alpha"]), t(t_rgb), t(t_depth), 0.5, 1.0, gate, 0.99,
+                      loss, d_rgb, d_depth)
+        torch.cuda.synchronize()
+        assert abs(float(loss) - L) <= 1e-5 * abs(L)
+        np.testing.assert_allclose(d_rgb.cpu().numpy(), dC, rtol=1e-6, atol=1e-12)
+        np.testing.assert_allclose(d_depth.cpu().numpy(), dD, rtol=1e-6, atol=1e-12)
+
+
+def test_reprojection_parity():
+    rng = np.random.default_rng(4)
+    vms = np.stack([scenes.look_at((0.2 * k, -0.1, 0.0), (0.1, 0.2, 3.0)) for k in range(2)])
+    cams = scenes.cams_from([[525, 525, 320, 240]] * 2, [[640, 480]] * 2, vms)
+    n = 1000
+    pts = rng.uniform(-1, 1, (n, 3)) + [0, 0, 3]
+    pts[:5, 2] = -2.0  # behind the cameras: left out
+    pts = pts.astype(np.float32)
+    vid = rng.integers(0, 2, n).astype(np.int32)
+    obs = rng.uniform(0, 640, (n, 2)).astype(np.float32)
+    L, g = oracle.reproj(pts.astype(np.float64), obs.astype(np.float64), cams, weight=1.5, view_ids=vid)
+    loss = torch.zeros(1, device="cuda")
+    d_twist = torch.zeros(2, 6, device="cuda")
+    gs.gs_reproj_loss_grad(t(pts), t(obs), t(vid, torch.int32), gs.make_views(cams["intr"], cams["size"]),
+                           viewmats_on_device(cams), 1.5, loss, d_twist)
+    torch.cuda.synchronize()
+    assert abs(float(loss) - L) <= 1e-5 * L
+    e = rel_l2(d_twist.cpu().numpy(), g)
+    print(f"re-projection twist grad rel-L2 err = {e:.3e}")
+    assert e <= GRAD_TOL
+
+
+def test_adam_and_step_counter():
+    rng = np.random.default_rng(5)
+    n = 10_001
+    p0 = rng.standard_normal(n)
+    groups = [(0, 3001, 1e-3), (3001, 5000, 2e-2), (8001, 2000, 5e-4)]
+    P, M, Vv = p0.copy(), np.zeros(n), np.zeros(n)
+    tp, tm, tv = t(p0), torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    step = torch.zeros(2, dtype=torch.int32, device="cuda")
+    for it in range(1, 4):
+        gr = rng.standard_normal(n)
+        for off, cnt, lr in groups:
+            sl = slice(off, off + cnt)
+            pp, mm, vv = P[sl].copy(), M[sl].copy(), Vv[sl].copy()
+            oracle.adam(pp, np.ascontiguousarray(gr[sl]), mm, vv, lr=lr, t=it)
+            P[sl], M[sl], Vv[sl] = pp, mm, vv
+        gs.gs_adam_step(tp, t(gr), tm, tv, groups, step)
+        torch.cuda.synchronize()
+        assert int(step[0]) == it and int(step[1]) == 0
+        np.testing.assert_allclose(tp.cpu().numpy(), P, rtol=1e-5, atol=1e-6)
+
+
+def test_pose_update_matches_oracle_exp():
+    rng = np.random.default_rng(6)
+    vms = np.stack([scenes.look_at((0.1 * k, 0.0, 0.0), (0.0, 0.0, 3.0)) for k in range(3)])
+    xi = rng.normal(0, 0.05, (3, 6))
+    xi[2] = 1e-8
+    vm = viewmats_on_device(dict(viewmats=vms))
+    tw = t(xi)
+    gs.gs_pose_update(vm, tw)
+    torch.cuda.synchronize()
+    for v in range(3):
+        ref = oracle.se3_exp_apply(xi[v].astype(np.float32).astype(np.float64), vms[v].astype(np.float64))
+        np.testing.assert_allclose(vm[v].view(3, 4).cpu().numpy(), ref, atol=2e-6)
+    assert float(tw.abs().max()) == 0.0
+
+
+def test_edge_cases_empty_and_tiny():
+    cams = scenes.pinhole(37, 23, 30.0)  # ragged 3 x 2 tiles
+    # all Gaussians behind the camera
+    sc = scenes.cube_scene(50, seed=8)
+    sc["means"][:, 2] = -3.0
+    rast, p, vm = _run(sc, cams)
+    assert rast.n_pairs() == 0 and rast.status() == 0
+    assert float(rast.img["alpha"].abs().max()) == 0.0 and float(rast.img["final_T"].min()) == 1.0
+    grads = zero_grads(p)
+    rast.backward(p, vm, torch.ones(37 * 23, 3, device="cuda"), None, None, grads)
+    torch.cuda.synchronize()
+    assert all(float(g.abs().max()) == 0.0 for g in grads.values())
+    # a single Gaussian
+    sc1 = scenes.cube_scene(1, seed=9, log_scale=(-2.0, 0.0))
+    sc1["means"][:] = [0.05, -0.02, 2.0]
+    rast, p, vm = _run(sc1, cams)
+    ref = oracle.forward(sc1, cams)["img"]
+    keep = ref["flags"] == 0
+    assert np.abs(rast.img["alpha"].cpu().numpy()[keep] - ref["alpha"][keep]).max() <= IMG_TOL
+
+
+def test_capacity_overflow_is_reported_not_fatal():
+    c = scenes.config(1)
+    rast, p, vm = _run(c["scene"], c["cams"], capacity=500)
+    geom = oracle.project_geom(c["scene"], c["cams"])
+    assert rast.status() & (1 << 3)
+    assert rast.n_pairs() == int(geom["tiles_touched"].sum()) > 500
+    # the pipeline still completes with in-bounds output
+    assert torch.isfinite(rast.img["rgb"]).all()
