@@ -1,0 +1,517 @@
+#!/usr/bin/env python
+"""Throughput of the differentiable Gaussian-splatting hot path on one GB300.
+
+A step is one joint mapping iteration over a batch of keyframes through the C
+ABI: project -> bin + onesweep sort -> composite -> L1 loss -> backward
+(compositing + projection, with per-view SE(3) twist gradients) -> keypoint
+re-projection term -> Adam on all Gaussian parameters.  Default workload:
+1M Gaussians (SH degree 3) on synthetic room surfaces, 8 keyframes of
+1200x680, rendered and backpropagated in one batched launch per stage.
+
+Prints one JSON line (metric fwd+bwd Mpix/s).  --impl reference times the CPU
+oracle instead, on a bounded crop of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import scenes  # noqa: E402
+
+METRIC = "fwd+bwd Mpix/s and mapping iters/s, batched vs plain on one GB300, at oracle tol"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", type=int, default=4, help="1..5 (see scenes.config)")
+    ap.add_argument("--scale", type=float, default=1.0, help="Gaussian count scale (1 = full size)")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile-steps", type=int, default=0, help="run N untimed steps and exit (for ncu)")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (replicas only: each rank runs the whole workload)
+# --------------------------------------------------------------------------
+
+def dist_init():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), power=float(f[3]), hw=f[5], hwt=f[6],
+                                 swt=f[7], swp=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                            ("swp", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "power_w_max": max(r["power"] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# workload
+# --------------------------------------------------------------------------
+
+def build_workload(idx, scale, device):
+    import torch
+
+    import paper_2405_19614_gb300 as gs
+    from paper_2405_19614_gb300.pipeline import MappingStep
+
+    c = scenes.config(idx, scale)
+    scene, cams = c["scene"], c["cams"]
+    n = scene["means"].shape[0]
+    V = len(cams["size"])
+    cap = int(min((1 << 30) - 1, max(1 << 20, 12 * n * V)))
+    # targets: a render of the second seeded scene (setup, not timed)
+    ts = c.get("target_scene") or scenes.surface_scene(n, 999, scenes.room_layout(idx))
+    tr = gs.Rasterizer(n, ts["sh_degree"], cams["intr"], cams["size"], cap, device)
+    tp = {k: torch.as_tensor(ts[k], device=device) for k in ("means", "log_scales", "quats", "opacity_logit", "sh")}
+    tp["sh_degree"] = ts["sh_degree"]
+    vm = torch.as_tensor(cams["viewmats"].reshape(-1, 12), device=device)
+    tr.forward(tp, vm)
+    torch.cuda.synchronize()
+    assert tr.status() == 0, "target render overflowed its pair capacity"
+    t_rgb = tr.img["rgb"].clone()
+    t_depth = tr.img["depth"].clone()
+    depth_host = t_depth.cpu().numpy()
+    del tr, tp
+    # 1000 keypoints per view back-projected from the target depth, 1 px noise
+    pts, obs, vid = [], [], []
+    base = 0
+    for v in range(V):
+        w, h = (int(x) for x in cams["size"][v])
+        px, py = scenes.keypoint_pixels(1000 + v, w, h, 1000)
+        d_img = depth_host[base:base + w * h]
+        p, ok = scenes.backproject(cams["viewmats"][v], cams["intr"][v], px, py, d_img, w)
+        rng = np.random.default_rng(2000 + v)
+        o = np.stack([px + 0.5, py + 0.5], 1) + rng.normal(0, 1.0, (len(px), 2))
+        pts.append(p[ok])
+        obs.append(o[ok])
+        vid.append(np.full(int(ok.sum()), v, np.int32))
+        base += w * h
+    kp = dict(points=torch.as_tensor(np.concatenate(pts).astype(np.float32), device=device),
+              obs=torch.as_tensor(np.concatenate(obs).astype(np.float32), device=device),
+              view_ids=torch.as_tensor(np.concatenate(vid), device=device))
+    step = MappingStep(scene, cams["intr"], cams["size"], cams["viewmats"], t_rgb, t_depth, w_c=c.get("w_c", 1.0),
+                       w_d=c.get("w_d", 0.5), use_gate=c.get("gate", False), keypoints=kp, pair_capacity=cap,
+                       device=device)
+    return c, step, cap
+
+
+def plain_steps(c, step, cap, device):
+    """The same iteration, one view per launch: a rasterizer per view that
+    shares the parameter and gradient buffers; one Adam at the end."""
+    import paper_2405_19614_gb300 as gs
+    cams = c["cams"]
+    rs = []
+    for v in range(len(cams["size"])):
+        r = gs.Rasterizer(step.flat.n, step.flat.sh_degree, cams["intr"][v:v + 1], cams["size"][v:v + 1],
+                          max(1 << 20, cap // len(cams["size"]) * 2), device)
+        rs.append(r)
+    return rs
+
+
+def run_plain(c, step, rs):
+    import paper_2405_19614_gb300 as gs
+    step.grad_buf.zero_()
+    step.loss.zero_()
+    step.d_twist.zero_()
+    base = 0
+    for v, r in enumerate(rs):
+        vm = step.viewmats[v:v + 1]
+        P = r.n_pix
+        r.forward(step.params, vm)
+        gs.gs_loss_l1(r.img["rgb"], r.img["depth"], r.img["alpha"], step.target_rgb[base:base + P],
+                      step.target_depth[base:base + P], step.w_c * P / step.rast.n_pix,
+                      step.w_d * P / step.rast.n_pix, step.use_gate, step.gamma, step.loss,
+                      step.d_rgb[base:base + P], step.d_depth[base:base + P])
+        r.backward(step.params, vm, step.d_rgb[base:base + P], step.d_depth[base:base + P], None, step.grads,
+                   step.d_twist[v:v + 1])
+        base += P
+    kp = step.keypoints
+    gs.gs_reproj_loss_grad(kp["points"], kp["obs"], kp["view_ids"], step.rast.views, step.viewmats, step.w_rpj,
+                           step.loss, step.d_twist)
+    gs.gs_adam_step(step.flat.buf, step.grad_buf, step.m, step.v, step.groups, step.step_count)
+
+
+def work_counts(step):
+    """Algorithmic work of one step from the step's own buffers (after a run)."""
+    import torch
+
+    import paper_2405_19614_gb300 as gs
+    r = step.rast
+    n_eval = torch.zeros(r.n_pix, dtype=torch.int32, device="cuda")
+    n_blend = torch.zeros(r.n_pix, dtype=torch.int32, device="cuda")
+    gs.gs_render_stats(r.proj, r.n, r.bins, r.views, n_eval, n_blend, r.work_counter)
+    torch.cuda.synchronize()
+    radii = r.proj["radii"]
+    return dict(N=r.n, V=r.V, P=r.n_pix, T=r.n_tiles, K=r.n_pairs(), V_vis=int((radii > 0).sum()),
+                E=int(n_eval.sum(dtype=torch.int64)), B=int(n_blend.sum(dtype=torch.int64)),
+                C=int(r.img["n_contrib"].sum(dtype=torch.int64)), sh_floats=3 * (r.sh_degree + 1) ** 2)
+
+
+def stage_work(w):
+    """Per-stage algorithmic bytes (HBM-bound stages) or FP32 flops (compositing)."""
+    N, V, P, K, Vv, E, B, C, S = (w[k] for k in ("N", "V", "P", "K", "V_vis", "E", "B", "C", "sh_floats"))
+    param_b = 4 * (3 + 3 + 4 + 1 + S)
+    passes = math.ceil((32 + math.ceil(math.log2(max(w["T"], 2)))) / 8)
+    return {
+        "project": ("hbm", param_b * N + 8 * V * N + 48 * Vv),
+        "bin_sort": ("hbm", 8 * V * N + 12 * Vv + 12 * K + 8 * K + passes * 24 * K + 8 * K + 8 * w["T"]),
+        # per evaluation 14 FP32 ops (offset, quadratic form, exp, opacity, clamp, test);
+        # per blended entry 14 more (transmittance, weight, three colour and one depth FMA)
+        "render_fwd": ("alu", 14 * E + 14 * B),
+        "loss": ("hbm", P * (12 + 4 + 12 + 4 + 12 + 4)),
+        # per entry up to the last blend 14 ops to recompute alpha; per blended
+        # entry ~46 ops of reverse mode (T recovery, 10 partial derivatives)
+        "render_bwd": ("alu", 14 * C + 46 * B),
+        "project_bwd": ("hbm", param_b * N + 96 * Vv + 2 * param_b * N),
+        "adam": ("hbm", 28 * (param_b // 4) * N),
+    }
+
+
+# --------------------------------------------------------------------------
+# CPU oracle baseline (a bounded crop of the same workload)
+# --------------------------------------------------------------------------
+
+def crop_cams(cams, v, y0, rows):
+    intr = np.asarray(cams["intr"][v], np.float64).copy()
+    intr[3] -= y0
+    W = int(cams["size"][v][0])
+    return scenes.cams_from([intr], [[W, rows]], cams["viewmats"][v:v + 1])
+
+
+def oracle_step(scene, cams, t_rgb, t_depth, w_c, w_d):
+    import oracle
+    f = oracle.forward(scene, cams)
+    L, dC, dD = oracle.loss_l1(f["img"], t_rgb, t_depth, w_c, w_d)
+    oracle.backward(scene, cams, f, dC, dD)
+    return f["bins"]["n_pix"]
+
+
+def cpu_sample(c, target_seconds, rows=None):
+    """Times the oracle's fwd+bwd on a crop of view 0 (rows starting at a
+    multiple of 16, so tiles are those of the full view)."""
+    cams = c["cams"]
+    W, H = (int(x) for x in cams["size"][0])
+    y0 = (H // 2) // 16 * 16
+    tgt_rng = np.random.default_rng(7)
+
+    def run(r):
+        cc = crop_cams(cams, 0, y0, r)
+        P = W * r
+        t_rgb = tgt_rng.uniform(0, 1, (P, 3))
+        t_depth = tgt_rng.uniform(0, 4, P)
+        t0 = time.perf_counter()
+        oracle_step(c["scene"], cc, t_rgb, t_depth, c.get("w_c", 1.0), c.get("w_d", 0.5))
+        return time.perf_counter() - t0, P
+
+    if rows is None:
+        dt, P = run(16)
+        per_row = dt / 16
+        rows = int(max(16, min(H - y0, target_seconds / max(per_row, 1e-6))) // 16 * 16)
+    dt, P = run(rows)
+    return dict(seconds=dt, pixels=P, rows=rows, width=W)
+
+
+# --------------------------------------------------------------------------
+# arms
+# --------------------------------------------------------------------------
+
+def main_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    c = scenes.config(args.workload, args.scale)
+    per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    probe = cpu_sample(c, per_step)
+    rows = probe["rows"]
+    for _ in range(args.warmup):
+        cpu_sample(c, per_step, rows)
+    tot, pix = 0.0, 0
+    for _ in range(args.steps):
+        s = cpu_sample(c, per_step, rows)
+        tot += s["seconds"]
+        pix += s["pixels"]
+    v = pix / tot / 1e6
+    sample = f"oracle fwd+bwd of a {probe['width']}x{rows} crop of view 0 (all Gaussians projected)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": c["name"], "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main_ours(args):
+    import torch
+
+    rank, world, local = dist_init()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    from paper_2405_19614_gb300.build import build
+    if rank == 0:
+        build()
+    barrier(world)
+    c, step, cap = build_workload(args.workload, args.scale, device)
+    px_per_step = step.rast.n_pix
+
+    # warm-up (also sets kernel attributes before any capture)
+    for _ in range(max(1, args.warmup)):
+        step.run()
+    torch.cuda.synchronize()
+    if step.rast.status() != 0:
+        raise SystemExit(f"device status {step.rast.status()}: pair capacity or wait exceeded")
+    if args.profile_steps:
+        for _ in range(args.profile_steps):
+            step.run()
+        torch.cuda.synchronize()
+        return
+
+    # timed region: eager launches with per-stage events on the launching stream
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    timers = {}
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        step.run(timers)
+    t1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, world)
+    stage_ms = {k: sum(a.elapsed_time(b) for a, b in v) / len(v) for k, v in timers.items()}
+
+    # the same step captured once as a CUDA graph and replayed
+    graph_ms = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            step.run()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            step.run()
+        for _ in range(args.warmup):
+            g.replay()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        graph_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    except Exception as exc:  # graph capture is reported, not required
+        graph_ms = None
+        print(f"graph capture failed: {exc}", file=sys.stderr)
+
+    # end to end through the public API: host keyframes in, loss out, every step
+    import paper_2405_19614_gb300  # noqa: F401
+    h_rgb = step.target_rgb.cpu().pin_memory()
+    h_depth = step.target_depth.cpu().pin_memory()
+    h_vm = step.viewmats.cpu().pin_memory()
+    h_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        step.run()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step.target_rgb.copy_(h_rgb, non_blocking=True)
+        step.target_depth.copy_(h_depth, non_blocking=True)
+        step.viewmats.copy_(h_vm, non_blocking=True)
+        step.run()
+        h_loss.copy_(step.loss, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    h2d = h_rgb.numel() * 4 + h_depth.numel() * 4 + h_vm.numel() * 4
+
+    # plain path: one view per launch, same scene, same step contents
+    plain = None
+    if not args.no_plain and step.rast.V > 1:
+        rs = plain_steps(c, step, cap, device)
+        for _ in range(2):
+            run_plain(c, step, rs)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            run_plain(c, step, rs)
+        e1.record()
+        torch.cuda.synchronize()
+        plain_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+        plain = {"value": world * px_per_step / plain_ms / 1e3, "ms_per_step": plain_ms}
+        del rs
+
+    w = work_counts(step)
+    works = stage_work(w)
+    dom = max(stage_ms, key=lambda k: stage_ms[k] if k in works else -1)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(device).multi_processor_count
+    alu_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 TFLOP/s (FMA = 2)
+
+    def roof(stage):
+        kind, amount = works[stage]
+        sec = stage_ms[stage] / 1e3
+        if kind == "hbm":
+            return {"bound": "hbm", "achieved": amount / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": amount / sec / 1e9 / hbm_peak, "algorithmic_bytes": amount}
+        return {"bound": "alu", "achieved": amount / sec / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": amount / sec / 1e12 / alu_peak, "algorithmic_flops": amount}
+
+    roofline = dict(roof(dom), kernel=dom, traffic=None)
+    stages = {k: {"ms": stage_ms[k], **({"frac": roof(k)["frac"], "bound": roof(k)["bound"]} if k in works else {})}
+              for k in stage_ms}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        s = cpu_sample(c, args.cpu_seconds)
+        cpu = {"value": s["pixels"] / s["seconds"] / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle fwd+bwd of a {s['width']}x{s['rows']} crop of view 0 "
+                         f"({s['seconds']:.1f} s, all Gaussians projected)"}
+
+    value = world * px_per_step / ms / 1e3
+    out = {
+        "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": c["name"], "gaussians": w["N"], "views": w["V"], "pixels_per_step": px_per_step,
+                   "pairs": w["K"], "visible": w["V_vis"], "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (params 236 MB + pair arrays), no flush"},
+        "iters_per_s": 1e3 / ms,
+        "graph": None if graph_ms is None else {"ms_per_step": graph_ms, "value": world * px_per_step / graph_ms / 1e3},
+        "plain": plain,
+        "batched_vs_plain": None if plain is None else plain["ms_per_step"] / ms,
+        "e2e": {"value": world * px_per_step / e2e_ms / 1e3, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 4},
+        "gpu_launches": step.kernels_per_step() * args.steps,
+        "stages": stages,
+        "work": w,
+        "roofline": roofline,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        main_reference(a)
+    else:
+        main_ours(a)

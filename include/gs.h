@@ -191,9 +191,10 @@ gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t n, const gs
 
 /* a8. Backward of the projection: chains grad2d to the parameter gradients
  * (summed over views, accumulated into grads) and to each view's twist
- * gradient d_twist [n_views, 6] (+=; NULL to skip).  Entries of grad2d it
- * reads are set back to zero, so a buffer that starts zeroed is zero again
- * when the call completes. */
+ * gradient d_twist [n_views, 6] (+=; NULL to skip).  grads = NULL selects the
+ * pose-only mode of tracking (Sec. 3.3: the pose is refined, the map is not):
+ * only d_twist is written.  Entries of grad2d it reads are set back to zero,
+ * so a buffer that starts zeroed is zero again when the call completes. */
 gs_status_t gs_project_bwd(const gs_params_t *params, const gs_view_t *views, const float *viewmats,
                            int32_t n_views, const gs_options_t *opt, const gs_projected_t *proj,
                            float *grad2d, gs_param_grads_t *grads, float *d_twist, void *stream);
@@ -201,7 +202,7 @@ gs_status_t gs_project_bwd(const gs_params_t *params, const gs_view_t *views, co
 /* a7 + a8. The whole backward of the render (reverse of Sec. 3.4 projection and
  * compositing): gs_render_bwd_splats followed by gs_project_bwd.  grad2d must
  * be zero on entry (it is zero again on completion); parameter gradients and
- * d_twist are accumulated.  Used for mapping (pose fixed, Sec. 3.4) with
+ * d_twist are accumulated; grads may be NULL (pose only).  Used for mapping (pose fixed, Sec. 3.4) with
  * d_twist = NULL and for pose refinement (Sec. 3.3) with d_twist set. */
 gs_status_t gs_render_bwd(const gs_params_t *params, const gs_view_t *views, const float *viewmats,
                           int32_t n_views, const gs_options_t *opt, const gs_projected_t *proj,

@@ -61,8 +61,14 @@ def _params(p):
 
 
 def _grads(g):
+    if g is None:
+        return None
     return GsParamGrads(_ptr(g["means"]), _ptr(g["log_scales"]), _ptr(g["quats"]), _ptr(g["opacity_logit"]),
                         _ptr(g["sh"]))
+
+
+def _gref(grads):
+    return None if grads is None else ctypes.byref(_grads(grads))
 
 
 # --------------------------------------------------------------------------
@@ -125,7 +131,7 @@ def gs_render_bwd_splats(proj, n, bins, views, img, d_rgb, d_depth, d_alpha, gra
 def gs_project_bwd(params, views, viewmats, proj, grad2d, grads, d_twist, near_z=0.2, blur=0.3, stream=None):
     opt = GsOptions(near_z, blur)
     check(lib().gs_project_bwd(ctypes.byref(_params(params)), views, _ptr(viewmats), len(views), ctypes.byref(opt),
-                               ctypes.byref(_proj(proj)), _ptr(grad2d), ctypes.byref(_grads(grads)), _ptr(d_twist),
+                               ctypes.byref(_proj(proj)), _ptr(grad2d), _gref(grads), _ptr(d_twist),
                                _stream(stream)), "gs_project_bwd")
 
 
@@ -134,7 +140,7 @@ def gs_render_bwd(params, views, viewmats, proj, bins, img, d_rgb, d_depth, d_al
     opt = GsOptions(near_z, blur)
     check(lib().gs_render_bwd(ctypes.byref(_params(params)), views, _ptr(viewmats), len(views), ctypes.byref(opt),
                               ctypes.byref(_proj(proj)), ctypes.byref(_bins(bins)), ctypes.byref(_img(img)),
-                              _ptr(d_rgb), _ptr(d_depth), _ptr(d_alpha), _ptr(grad2d), ctypes.byref(_grads(grads)),
+                              _ptr(d_rgb), _ptr(d_depth), _ptr(d_alpha), _ptr(grad2d), _gref(grads),
                               _ptr(d_twist), _ptr(work_counter), _stream(stream)), "gs_render_bwd")
 
 

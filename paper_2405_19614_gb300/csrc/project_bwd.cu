@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a, View
         }
     }
 
-    if (active) {
+    if (active && a.g_means) {
         // M = Rq diag(s):  dL/dM = 2 Gw M
         float gM[3][3];
         #pragma unroll
@@ -311,15 +311,17 @@ extern "C" gs_status_t gs_project_bwd(const gs_params_t *params, const gs_view_t
                                       int32_t n_views, const gs_options_t *opt, const gs_projected_t *proj,
                                       float *grad2d, gs_param_grads_t *grads, float *d_twist, void *stream)
 {
-    if (!params || !viewmats || !opt || !proj || !grad2d || !grads) return GS_ERR_INVALID_ARG;
+    if (!params || !viewmats || !opt || !proj || !grad2d) return GS_ERR_INVALID_ARG;
+    if (!grads && !d_twist) return GS_ERR_INVALID_ARG;
     if (params->n < 0 || params->sh_degree < 0 || params->sh_degree > 3) return GS_ERR_INVALID_ARG;
     ViewTable vt;
     gs_status_t st = make_view_table(views, n_views, &vt);
     if (st != GS_OK) return st;
     if (params->n == 0) return GS_OK;
     if (!params->means || !params->log_scales || !params->quats || !params->opacity_logit || !params->sh ||
-        !proj->radii || !grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logit ||
-        !grads->sh)
+        !proj->radii)
+        return GS_ERR_INVALID_ARG;
+    if (grads && (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logit || !grads->sh))
         return GS_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(grad2d) & 15) || (reinterpret_cast<uintptr_t>(params->quats) & 15))
         return GS_ERR_INVALID_ARG;
@@ -334,11 +336,11 @@ extern "C" gs_status_t gs_project_bwd(const gs_params_t *params, const gs_view_t
     a.blur = opt->blur;
     a.radii = proj->radii;
     a.grad2d = reinterpret_cast<float4 *>(grad2d);
-    a.g_means = grads->means;
-    a.g_log_scales = grads->log_scales;
-    a.g_quats = grads->quats;
-    a.g_opacity_logit = grads->opacity_logit;
-    a.g_sh = grads->sh;
+    a.g_means = grads ? grads->means : nullptr;  // NULL grads: pose-only (twist gradients only)
+    a.g_log_scales = grads ? grads->log_scales : nullptr;
+    a.g_quats = grads ? grads->quats : nullptr;
+    a.g_opacity_logit = grads ? grads->opacity_logit : nullptr;
+    a.g_sh = grads ? grads->sh : nullptr;
     a.d_twist = d_twist;
     const int threads = 128;
     const unsigned blocks = (unsigned)((params->n + threads - 1) / threads);

@@ -148,3 +148,56 @@ class MappingStep:
         k += 1 if self.keypoints is not None else 0
         k += 1 if self.optimise_params else 0
         return k
+
+
+class TrackingStep:
+    """Pose-only refinement of one or more views (Sec. 3.3 joint optimisation):
+    L = w1 L_rpj + w2 L_c + w3 L_d with the filter gate G(p); the map is held
+    fixed.  Each run() takes one Adam step on the twists xi (rho with lr_rho,
+    phi with lr_phi) and folds them into the poses, E <- Exp(xi) E, on device."""
+
+    def __init__(self, params, intr, size, viewmats, target_rgb, target_depth, keypoints=None, w_rpj=1.5,
+                 w_c=0.5, w_d=1.0, gamma=0.99, lr_rho=5e-4, lr_phi=3e-4, pair_capacity=None, device="cuda"):
+        dev = torch.device(device)
+        self.params = params
+        n = int(params["means"].shape[0])
+        self.rast = Rasterizer(n, params["sh_degree"], intr, size, pair_capacity, dev)
+        V = self.rast.V
+        if V > GS_MAX_TRACK_VIEWS:
+            raise ValueError(f"at most {GS_MAX_TRACK_VIEWS} views per tracking step")
+        self.viewmats = torch.as_tensor(np.asarray(viewmats, np.float32).reshape(-1, 12), device=dev).contiguous()
+        self.target_rgb, self.target_depth = target_rgb, target_depth
+        self.keypoints = keypoints
+        self.twist = torch.zeros(V * 6, device=dev)
+        self.d_twist = torch.zeros(V * 6, device=dev)
+        self.m = torch.zeros(V * 6, device=dev)
+        self.v = torch.zeros(V * 6, device=dev)
+        self.step_count = torch.zeros(2, dtype=torch.int32, device=dev)
+        self.groups = []
+        for k in range(V):
+            self.groups += [(6 * k, 3, lr_rho), (6 * k + 3, 3, lr_phi)]
+        P = self.rast.n_pix
+        self.d_rgb = torch.zeros(P, 3, device=dev)
+        self.d_depth = torch.zeros(P, device=dev)
+        self.loss = torch.zeros(1, device=dev)
+        self.w_rpj, self.w_c, self.w_d, self.gamma = float(w_rpj), float(w_c), float(w_d), float(gamma)
+
+    def run(self, stream=None):
+        from . import gs_pose_update, gs_render_bwd
+        r = self.rast
+        self.d_twist.zero_()
+        self.loss.zero_()
+        r.forward(self.params, self.viewmats, stream)
+        gs_loss_l1(r.img["rgb"], r.img["depth"], r.img["alpha"], self.target_rgb, self.target_depth, self.w_c,
+                   self.w_d, True, self.gamma, self.loss, self.d_rgb, self.d_depth, stream)
+        gs_render_bwd(self.params, r.views, self.viewmats, r.proj, r.bins, r.img, self.d_rgb, self.d_depth, None,
+                      r.grad2d, None, self.d_twist, r.work_counter, r.near_z, r.blur, stream)
+        if self.keypoints is not None:
+            kp = self.keypoints
+            gs_reproj_loss_grad(kp["points"], kp["obs"], kp.get("view_ids"), r.views, self.viewmats, self.w_rpj,
+                                self.loss, self.d_twist, r.near_z, stream)
+        gs_adam_step(self.twist, self.d_twist, self.m, self.v, self.groups, self.step_count, stream=stream)
+        gs_pose_update(self.viewmats, self.twist, stream)
+
+
+GS_MAX_TRACK_VIEWS = 4
