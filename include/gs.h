@@ -147,6 +147,23 @@ size_t gs_bin_sort_workspace_size(int64_t n_records, int64_t pair_capacity, int6
 gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const gs_view_t *views, int32_t n_views,
                         gs_bins_t *bins, void *workspace, size_t workspace_bytes, void *stream);
 
+/* Allocation-free gs_bin_sort (the paper has no counterpart: this serves
+ * callers that cannot allocate device memory, such as code in the middle of a
+ * CUDA graph capture, fixed-rate tracking loops that cannot take the device
+ * synchronisation an allocation may cause, or host frameworks that own all
+ * device memory and pass a plugin only its inputs and outputs).  Same inputs,
+ * outputs and results as gs_bin_sort, but the scratch workspace is a 13 MiB
+ * static device array inside the library, held on every GPU that loads it
+ * until the process exits.  Limits: n_views * n <= 4,194,304 records and
+ * bins->capacity <= 1,048,576 pairs; larger calls return GS_ERR_CAPACITY and
+ * enqueue nothing.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * calls share the array and it keeps the last call's contents (what must
+ * start at zero is cleared inside each call); calls that may overlap on the
+ * GPU race on it and must not be issued. */
+gs_status_t gs_bin_sort_noalloc(const gs_projected_t *proj, int64_t n, const gs_view_t *views, int32_t n_views,
+                                gs_bins_t *bins, void *stream);
+
 /* a5. Forward compositing (Sec. 3.4: C(p) = sum c_i f_i prod_{j<i} (1 - f_j),
  * D(p) likewise with the depths d_i; Sec. 3.3: M_b(p) = sum f_i prod (1 - f_j)).
  * alpha_i = min(0.99, o_i exp(-1/2 d^T conic d)); entries with alpha < 1/255

@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import (GS_MAX_ADAM_GROUPS, GS_MAX_VIEWS, GS_TILE, GsAdamGroup, GsBins, GsError, GsImage, GsOptions,
                    GsParamGrads, GsParams, GsProjected, GsView, check)
 
-__all__ = ["gs_project", "gs_bin_sort", "gs_render_fwd", "gs_render_stats", "gs_loss_l1", "gs_render_bwd", "gs_render_bwd_splats",
+__all__ = ["gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd", "gs_render_stats", "gs_loss_l1", "gs_render_bwd", "gs_render_bwd_splats",
            "gs_project_bwd", "gs_reproj_loss_grad", "gs_adam_step", "gs_pose_update", "Rasterizer", "rasterize",
            "GsError", "lib"]
 
@@ -103,6 +103,16 @@ def gs_bin_sort_workspace_size(n_records, capacity, n_tiles):
 def gs_bin_sort(proj, n, views, bins, workspace, stream=None):
     check(lib().gs_bin_sort(ctypes.byref(_proj(proj)), n, views, len(views), ctypes.byref(_bins(bins)),
                             _ptr(workspace), workspace.numel(), _stream(stream)), "gs_bin_sort")
+
+
+def gs_bin_sort_noalloc(proj, n, views, bins, stream=None):
+    """gs_bin_sort without a caller workspace: for callers that cannot
+    allocate device memory (mid graph capture, fixed-rate loops, hosts that own
+    all device memory).  Uses a fixed 13 MiB scratch array inside the library;
+    at most 4,194,304 records and a pair capacity of 1,048,576.  Calls must not
+    overlap on the GPU."""
+    check(lib().gs_bin_sort_noalloc(ctypes.byref(_proj(proj)), n, views, len(views), ctypes.byref(_bins(bins)),
+                                    _stream(stream)), "gs_bin_sort_noalloc")
 
 
 def gs_render_fwd(proj, n, bins, views, img, work_counter, stream=None):

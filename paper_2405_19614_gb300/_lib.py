@@ -63,6 +63,7 @@ SIGNATURES = {
     "gs_project": ([P(GsParams), P(GsView), c_p, c_i32, P(GsOptions), P(GsProjected), c_p], c_i32),
     "gs_bin_sort_workspace_size": ([c_i64, c_i64, c_i64], c_sz),
     "gs_bin_sort": ([P(GsProjected), c_i64, P(GsView), c_i32, P(GsBins), c_p, c_sz, c_p], c_i32),
+    "gs_bin_sort_noalloc": ([P(GsProjected), c_i64, P(GsView), c_i32, P(GsBins), c_p], c_i32),
     "gs_render_fwd": ([P(GsProjected), c_i64, P(GsBins), P(GsView), c_i32, P(GsImage), c_p, c_p], c_i32),
     "gs_render_stats": ([P(GsProjected), c_i64, P(GsBins), P(GsView), c_i32, c_p, c_p, c_p, c_p], c_i32),
     "gs_loss_l1": ([c_p, c_p, c_p, c_p, c_p, c_i64, c_f, c_f, c_i32, c_f, c_p, c_p, c_p, c_p], c_i32),
