@@ -181,6 +181,18 @@ gs_status_t gs_render_stats(const gs_projected_t *proj, int64_t n, const gs_bins
                             const gs_view_t *views, int32_t n_views, uint32_t *n_eval, uint32_t *n_blend,
                             uint32_t *work_counter, void *stream);
 
+/* Kernel variants of the compositing (a5, a7): pixels per thread and the
+ * number of splat records staged per shared-memory batch, as indices into
+ * fwd: (1,256) (2,128) (2,256) (4,64) (4,128) (8,64) and
+ * bwd: (1,256) (2,128) (4,64) (4,128) (8,64).  All variants compute the same
+ * result; the autotuner times them on the workload and sets the fastest.  The
+ * setting is process-wide and read when a kernel is launched.
+ * GS_ERR_INVALID_ARG for an index out of range. */
+gs_status_t gs_set_render_variants(int32_t fwd, int32_t bwd);
+
+/* Current variants and the number of each (any pointer may be NULL). */
+gs_status_t gs_get_render_variants(int32_t *fwd, int32_t *bwd, int32_t *n_fwd, int32_t *n_bwd);
+
 /* a6. L1 rendering losses with the optional filter gate (Sec. 3.3
  * G(p) = [D_c > 0][D_g > 0][M_b > gamma]; Sec. 3.3 joint loss w2 L_c + w3 L_d;
  * Sec. 3.4 L_m L1 terms):  L = w_c/(3P) sum G |C - C^| + w_d/P sum G |D - D^|

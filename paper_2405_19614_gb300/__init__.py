@@ -19,7 +19,8 @@ from . import _lib
 from ._lib import (GS_MAX_ADAM_GROUPS, GS_MAX_VIEWS, GS_TILE, GsAdamGroup, GsBins, GsError, GsImage, GsOptions,
                    GsParamGrads, GsParams, GsProjected, GsView, check)
 
-__all__ = ["gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd", "gs_render_stats", "gs_loss_l1", "gs_render_bwd", "gs_render_bwd_splats",
+__all__ = ["gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd", "gs_render_stats", "gs_set_render_variants",
+           "gs_get_render_variants", "gs_loss_l1", "gs_render_bwd", "gs_render_bwd_splats",
            "gs_project_bwd", "gs_reproj_loss_grad", "gs_adam_step", "gs_pose_update", "Rasterizer", "rasterize",
            "GsError", "lib"]
 
@@ -123,6 +124,17 @@ def gs_render_fwd(proj, n, bins, views, img, work_counter, stream=None):
 def gs_render_stats(proj, n, bins, views, n_eval, n_blend, work_counter, stream=None):
     check(lib().gs_render_stats(ctypes.byref(_proj(proj)), n, ctypes.byref(_bins(bins)), views, len(views),
                                 _ptr(n_eval), _ptr(n_blend), _ptr(work_counter), _stream(stream)), "gs_render_stats")
+
+
+def gs_set_render_variants(fwd, bwd):
+    check(lib().gs_set_render_variants(int(fwd), int(bwd)), "gs_set_render_variants")
+
+
+def gs_get_render_variants():
+    """(fwd, bwd, n_fwd, n_bwd): variants in use and how many exist."""
+    out = [ctypes.c_int32() for _ in range(4)]
+    check(lib().gs_get_render_variants(*[ctypes.byref(o) for o in out]), "gs_get_render_variants")
+    return tuple(o.value for o in out)
 
 
 def gs_loss_l1(rgb, depth, alpha, target_rgb, target_depth, w_c, w_d, use_gate, gamma, loss, d_rgb, d_depth,

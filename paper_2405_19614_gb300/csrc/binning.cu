@@ -88,46 +88,72 @@ __global__ void __launch_bounds__(1024) scan_sums_kernel(uint64_t *sums, int64_t
     }
 }
 
+// Load-balanced emission: the block first scans its chunk's pair counts into
+// shared memory (with each record's depth bits, rectangle, view and index),
+// then its threads walk the chunk's output positions in order, each finding
+// its record by binary search, so consecutive threads write consecutive pairs.
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const float *__restrict__ rec, const uint32_t *__restrict__ tt,
                                                             int64_t n, int64_t total, ViewTable vt,
                                                             const uint64_t *__restrict__ block_off, uint64_t *keys,
                                                             uint32_t *vals, int64_t cap, uint32_t *status)
 {
     __shared__ uint64_t tmp[kEmitThreads / 32];
-    // each thread owns kEmitItems consecutive records, so its pairs are contiguous
-    const int64_t first = (int64_t)blockIdx.x * kEmitChunk + (int64_t)threadIdx.x * kEmitItems;
+    __shared__ uint32_t s_excl[kEmitChunk + 1];
+    __shared__ uint32_t s_z[kEmitChunk], s_r0[kEmitChunk], s_r1[kEmitChunk], s_g[kEmitChunk];
+    __shared__ uint16_t s_v[kEmitChunk];
+    const int64_t chunk = (int64_t)blockIdx.x * kEmitChunk;
+    const int64_t first = chunk + (int64_t)threadIdx.x * kEmitItems;
     uint32_t c[kEmitItems];
-    uint64_t s = 0;
+    uint64_t sum = 0;
     #pragma unroll
     for (int k = 0; k < kEmitItems; k++) {
-        const int64_t idx = first + k;
-        c[k] = idx < total ? tt[idx] : 0u;
-        s += c[k];
-    }
-    uint64_t off = block_off[blockIdx.x] + block_exclusive_scan_u64(s, tmp, nullptr);
-    bool overflow = false;
-    #pragma unroll 1
-    for (int k = 0; k < kEmitItems; k++) {
-        if (c[k] == 0) continue;
         const int64_t o = first + k;
-        const int v = (int)(o / n);
-        const uint32_t g = (uint32_t)(o - (int64_t)v * n);
-        const uint32_t zb = __float_as_uint(rec[12 * o + 2]);
-        const uint32_t r0 = __float_as_uint(rec[12 * o + 7]);
-        const uint32_t r1 = __float_as_uint(rec[12 * o + 11]);
-        const int x0 = r0 & 0xffff, y0 = r0 >> 16, x1 = r1 & 0xffff, y1 = r1 >> 16;
-        const int ntx = vt.v[v].tiles_x;
-        const uint32_t tbase = (uint32_t)vt.v[v].tile_base;
-        for (int ty = y0; ty <= y1; ty++)
-            for (int tx = x0; tx <= x1; tx++) {
-                if (off < (uint64_t)cap) {
-                    keys[off] = ((uint64_t)(tbase + (uint32_t)(ty * ntx + tx)) << 32) | zb;
-                    vals[off] = g;
-                } else {
-                    overflow = true;
-                }
-                off++;
-            }
+        c[k] = o < total ? tt[o] : 0u;
+        sum += c[k];
+    }
+    uint64_t block_total;
+    uint64_t run = block_exclusive_scan_u64(sum, tmp, &block_total);
+    #pragma unroll
+    for (int k = 0; k < kEmitItems; k++) {
+        const int r = threadIdx.x * kEmitItems + k;
+        s_excl[r] = (uint32_t)run;
+        run += c[k];
+        if (c[k]) {
+            const int64_t o = first + k;
+            const int v = (int)(o / n);
+            s_v[r] = (uint16_t)v;
+            s_g[r] = (uint32_t)(o - (int64_t)v * n);
+            s_z[r] = __float_as_uint(rec[12 * o + 2]);
+            s_r0[r] = __float_as_uint(rec[12 * o + 7]);
+            s_r1[r] = __float_as_uint(rec[12 * o + 11]);
+        }
+    }
+    if (threadIdx.x == 0) s_excl[kEmitChunk] = (uint32_t)block_total;
+    __syncthreads();
+    const uint64_t base = block_off[blockIdx.x];
+    const uint32_t nq = (uint32_t)block_total;
+    bool overflow = false;
+    for (uint32_t q = threadIdx.x; q < nq; q += kEmitThreads) {
+        // last record r with s_excl[r] <= q (records of zero count share their successor's offset)
+        int lo = 0, hi = kEmitChunk;  // invariant: s_excl[lo] <= q < s_excl[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_excl[mid] <= q) lo = mid; else hi = mid;
+        }
+        const int r = lo;
+        const uint32_t k = q - s_excl[r];
+        const uint32_t r0 = s_r0[r], r1 = s_r1[r];
+        const uint32_t x0 = r0 & 0xffff, y0 = r0 >> 16, x1 = r1 & 0xffff;
+        const uint32_t w = x1 - x0 + 1;
+        const uint32_t ty = y0 + k / w, tx = x0 + k % w;
+        const ViewInfo &V = vt.v[s_v[r]];
+        const uint64_t pos = base + q;
+        if (pos < (uint64_t)cap) {
+            keys[pos] = ((uint64_t)((uint32_t)V.tile_base + ty * (uint32_t)V.tiles_x + tx) << 32) | s_z[r];
+            vals[pos] = s_g[r];
+        } else {
+            overflow = true;
+        }
     }
     if (overflow) raise_status(status, GS_ERR_CAPACITY);
 }

@@ -2,10 +2,7 @@
 // gradient serves the Sec. 3.3 joint optimisation, the parameter gradients the
 // Sec. 3.4 mapping).
 //
-// One thread per Gaussian loops over all views, so the gradients summed over
-// views are written to HBM once.  Per view it reads the (view, Gaussian) 2D
-// gradients, clears them, recomputes the projection in FP32 and applies the
-// chain rule:
+// Forward map being differentiated, per view:
 //   conic = Sigma2D^-1,  Sigma2D = J Sc J^T + blur I,  Sc = W S W^T,
 //   S = M M^T,  M = R(q / |q|) diag(exp(log_scale)),
 //   mu2D = (fx x/z + cx, fy y/z + cy),  depth = z,  p = (x, y, z) = W mu + t,
@@ -14,6 +11,15 @@
 //   dir = (mu - c) / |mu - c|,  c = -W^T t.
 // Twist xi = (rho, phi) with pose Exp(xi) E at xi = 0: p -> p + rho + phi x p,
 // Sc -> Exp(phi) Sc Exp(phi)^T, c -> c - W^T rho.
+//
+// Two kernels, each looping over all views so that gradients summed over views
+// reach HBM once.  The colour kernel runs four lanes per Gaussian, one per
+// colour channel (the fourth idle), so each lane holds only its channel's SH
+// coefficients and gradients; it propagates the view-direction gradient to the
+// mean and to the twist.  The geometry kernel, one thread per Gaussian, then
+// does the mean, covariance, opacity and pose paths and clears the 2D gradient
+// entries it consumed.  Keeping the SH state out of the geometry kernel keeps
+// both at a register count that lets many warps hide latency.
 #include "common.cuh"
 #include "sh.cuh"
 
@@ -26,26 +32,141 @@ struct ProjectBwdArgs {
     float blur;
     const int32_t *radii;
     float4 *grad2d;
-    float *g_means, *g_log_scales, *g_quats, *g_opacity_logit, *g_sh;
+    float *g_means, *g_log_scales, *g_quats, *g_opacity_logit, *g_sh;  // all NULL: pose only
     float *d_twist;
 };
 
+__device__ __forceinline__ void load_views(const float *viewmats, int n_views, float (*s_E)[12], float (*s_c)[3],
+                                           float (*s_tw)[6])
+{
+    for (int k = threadIdx.x; k < n_views * 12; k += blockDim.x) s_E[k / 12][k % 12] = viewmats[k];
+    for (int k = threadIdx.x; k < n_views * 6; k += blockDim.x) s_tw[k / 6][k % 6] = 0.0f;
+    __syncthreads();
+    if (s_c) {
+        for (int v = threadIdx.x; v < n_views; v += blockDim.x) {
+            const float *E = s_E[v];
+            #pragma unroll
+            for (int i = 0; i < 3; i++) s_c[v][i] = -(E[i] * E[3] + E[4 + i] * E[7] + E[8 + i] * E[11]);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void flush_twist(float *d_twist, int n_views, float (*s_tw)[6])
+{
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_views * 6; k += blockDim.x) {
+        const float r = s_tw[k / 6][k % 6];
+        if (r != 0.0f) atomicAdd(d_twist + k, r);
+    }
+}
+
+// Colour path: lanes 4g .. 4g+3 of the grid handle Gaussian g, lane 4g+c its
+// colour channel c (c = 3 idle).
 template <int DEG>
-__global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a, ViewTable vt)
+__global__ void __launch_bounds__(128) project_bwd_color_kernel(ProjectBwdArgs a, ViewTable vt)
 {
     constexpr int K = ShCount<DEG>::value;
     __shared__ float s_E[GS_MAX_VIEWS][12];
     __shared__ float s_c[GS_MAX_VIEWS][3];
     __shared__ float s_tw[GS_MAX_VIEWS][6];
-    for (int k = threadIdx.x; k < vt.n_views * 12; k += blockDim.x) s_E[k / 12][k % 12] = a.viewmats[k];
-    for (int k = threadIdx.x; k < vt.n_views * 6; k += blockDim.x) s_tw[k / 6][k % 6] = 0.0f;
-    __syncthreads();
-    for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) {
-        const float *E = s_E[v];
-        #pragma unroll
-        for (int i = 0; i < 3; i++) s_c[v][i] = -(E[i] * E[3] + E[4 + i] * E[7] + E[8 + i] * E[11]);
+    load_views(a.viewmats, vt.n_views, s_E, s_c, s_tw);
+
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t >> 2;
+    const int ch = (int)(t & 3);
+    const int lane = threadIdx.x & 31;
+    const bool active = i < a.n;
+    const bool want_twist = a.d_twist != nullptr;
+    float sh[K], gsh[K];
+    float m[3] = {0.0f, 0.0f, 0.0f};
+    #pragma unroll
+    for (int k = 0; k < K; k++) {
+        sh[k] = (active && ch < 3) ? a.sh[((int64_t)K * i + k) * 3 + ch] : 0.0f;
+        gsh[k] = 0.0f;
     }
-    __syncthreads();
+    if (active) {
+        #pragma unroll
+        for (int k = 0; k < 3; k++) m[k] = a.means[3 * i + k];
+    }
+    float gm[3] = {0.0f, 0.0f, 0.0f};
+
+    #pragma unroll 1
+    for (int v = 0; v < vt.n_views; v++) {
+        const int64_t o = (int64_t)v * a.n + i;
+        float gdir[3] = {0.0f, 0.0f, 0.0f};
+        float dx = 0.0f, dy = 0.0f, dz = 0.0f, rn = 0.0f;
+        const bool vis = active && a.radii[o] > 0;
+        if (vis) {
+            const float vx = m[0] - s_c[v][0], vy = m[1] - s_c[v][1], vz = m[2] - s_c[v][2];
+            rn = rsqrtf(vx * vx + vy * vy + vz * vz);
+            dx = vx * rn;
+            dy = vy * rn;
+            dz = vz * rn;
+            if (ch < 3) {
+                const float gcol = reinterpret_cast<const float *>(a.grad2d)[12 * o + 6 + ch];
+                float Y[K];
+                sh_basis<DEG>(dx, dy, dz, Y);
+                float acc = 0.5f;
+                #pragma unroll
+                for (int k = 0; k < K; k++) acc += sh[k] * Y[k];
+                if (acc >= 0.0f && gcol != 0.0f) {
+                    float wk[K];
+                    #pragma unroll
+                    for (int k = 0; k < K; k++) {
+                        gsh[k] += Y[k] * gcol;
+                        wk[k] = sh[k] * gcol;
+                    }
+                    if (DEG > 0) sh_basis_grad<DEG>(dx, dy, dz, wk, gdir);
+                }
+            }
+        }
+        if (DEG == 0) continue;  // the colour does not depend on the view direction
+        // sum the channels' direction gradients over the quad
+        #pragma unroll
+        for (int k = 0; k < 3; k++) {
+            gdir[k] += __shfl_xor_sync(kFullMask, gdir[k], 1);
+            gdir[k] += __shfl_xor_sync(kFullMask, gdir[k], 2);
+        }
+        float tw[3] = {0.0f, 0.0f, 0.0f};
+        if (vis && ch == 0) {
+            const float dd = gdir[0] * dx + gdir[1] * dy + gdir[2] * dz;
+            const float gvx = (gdir[0] - dx * dd) * rn, gvy = (gdir[1] - dy * dd) * rn, gvz = (gdir[2] - dz * dd) * rn;
+            gm[0] += gvx;
+            gm[1] += gvy;
+            gm[2] += gvz;
+            const float *E = s_E[v];
+            tw[0] = E[0] * gvx + E[1] * gvy + E[2] * gvz;
+            tw[1] = E[4] * gvx + E[5] * gvy + E[6] * gvz;
+            tw[2] = E[8] * gvx + E[9] * gvy + E[10] * gvz;
+        }
+        if (want_twist) {
+            #pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float r = warp_sum(tw[k]);
+                if (lane == 0 && r != 0.0f) atomicAdd(&s_tw[v][k], r);
+            }
+        }
+    }
+    if (active && a.g_means) {
+        if (ch < 3) {
+            #pragma unroll
+            for (int k = 0; k < K; k++) a.g_sh[((int64_t)K * i + k) * 3 + ch] += gsh[k];
+        }
+        if (ch == 0 && DEG > 0) {
+            #pragma unroll
+            for (int k = 0; k < 3; k++) a.g_means[3 * i + k] += gm[k];
+        }
+    }
+    if (want_twist) flush_twist(a.d_twist, vt.n_views, s_tw);
+}
+
+// Geometry path: one thread per Gaussian.
+__global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a, ViewTable vt)
+{
+    __shared__ float s_E[GS_MAX_VIEWS][12];
+    __shared__ float s_tw[GS_MAX_VIEWS][6];
+    load_views(a.viewmats, vt.n_views, s_E, nullptr, s_tw);
 
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < a.n;
@@ -53,9 +174,6 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a, View
     const bool want_twist = a.d_twist != nullptr;
 
     float m[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, q[4] = {1, 0, 0, 0}, ol = 0.0f;
-    float sh[K * 3];
-    #pragma unroll
-    for (int k = 0; k < K * 3; k++) sh[k] = 0.0f;
     if (active) {
         #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -68,11 +186,7 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a, View
         q[2] = q4.z;
         q[3] = q4.w;
         ol = a.opacity_logit[i];
-        const float *shp = a.sh + (int64_t)K * 3 * i;
-        #pragma unroll
-        for (int k = 0; k < K * 3; k++) sh[k] = shp[k];
     }
-    // quantities that do not depend on the view
     const float qn2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     const float qinv = rsqrtf(fmaxf(qn2, 1e-30f));
     const float w = q[0] * qinv, qa = q[1] * qinv, qb = q[2] * qinv, qc = q[3] * qinv;
@@ -98,11 +212,7 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a, View
         for (int c = 0; c < 3; c++) S[r][c] = M[r][0] * M[c][0] + M[r][1] * M[c][1] + M[r][2] * M[c][2];
     const float opac = 1.0f / (1.0f + expf(-ol));
 
-    float gm[3] = {0, 0, 0}, gMacc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gol = 0.0f;
-    float gsh[K * 3];
-    #pragma unroll
-    for (int k = 0; k < K * 3; k++) gsh[k] = 0.0f;
-
+    float gm[3] = {0, 0, 0}, Gw[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gol = 0.0f;
     #pragma unroll 1
     for (int v = 0; v < vt.n_views; v++) {
         float tw[6] = {0, 0, 0, 0, 0, 0};
@@ -113,16 +223,13 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a, View
             a.grad2d[3 * o] = zero4;
             a.grad2d[3 * o + 1] = zero4;
             a.grad2d[3 * o + 2] = zero4;
-            const float gu = G0.x, gv = G0.y, gA = G0.z, gB = G0.w, gC = G1.x, gop = G1.y;
-            const float gcol[3] = {G1.z, G1.w, G2v.x};
-            const float gz = G2v.y;
+            const float gu = G0.x, gv = G0.y, gA = G0.z, gB = G0.w, gC = G1.x, gop = G1.y, gz = G2v.y;
             const float *E = s_E[v];
             const ViewInfo &V = vt.v[v];
             const float W[3][3] = {{E[0], E[1], E[2]}, {E[4], E[5], E[6]}, {E[8], E[9], E[10]}};
             const float x = W[0][0] * m[0] + W[0][1] * m[1] + W[0][2] * m[2] + E[3];
             const float y = W[1][0] * m[0] + W[1][1] * m[1] + W[1][2] * m[2] + E[7];
             const float z = W[2][0] * m[0] + W[2][1] * m[1] + W[2][2] * m[2] + E[11];
-            // camera-space covariance Sc = W S W^T
             float WS[3][3], Sc[3][3];
             #pragma unroll
             for (int r = 0; r < 3; r++)
@@ -140,7 +247,6 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a, View
             const float Lx = xz < 0.f ? -limx : limx, Ly = yz < 0.f ? -limy : limy;
             const float tx = (clx ? Lx : xz) * z, ty = (cly ? Ly : yz) * z;
             const float J00 = V.fx * rz, J02 = -V.fx * tx * rz2, J11 = V.fy * rz, J12 = -V.fy * ty * rz2;
-            // J Sc rows (J has zeros at [0][1] and [1][0])
             float JS0[3], JS1[3];
             #pragma unroll
             for (int c = 0; c < 3; c++) {
@@ -191,7 +297,7 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a, View
             }
             #pragma unroll
             for (int c = 0; c < 3; c++) gm[c] += W[0][c] * gpx + W[1][c] * gpy + W[2][c] * gpz;
-            // world covariance gradient Gw = W^T Gc W, accumulated over views
+            // world covariance gradient W^T Gc W, accumulated over views
             float GcW[3][3];
             #pragma unroll
             for (int r = 0; r < 3; r++)
@@ -200,40 +306,12 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a, View
             #pragma unroll
             for (int r = 0; r < 3; r++)
                 #pragma unroll
-                for (int c = 0; c < 3; c++)
-                    gMacc[r][c] += W[0][r] * GcW[0][c] + W[1][r] * GcW[1][c] + W[2][r] * GcW[2][c];
+                for (int c = 0; c < 3; c++) Gw[r][c] += W[0][r] * GcW[0][c] + W[1][r] * GcW[1][c] + W[2][r] * GcW[2][c];
             gol += gop * opac * (1.0f - opac);
-            // colour through the SH of the view direction
-            const float vx = m[0] - s_c[v][0], vy = m[1] - s_c[v][1], vz = m[2] - s_c[v][2];
-            const float rn = rsqrtf(vx * vx + vy * vy + vz * vz);
-            const float dx = vx * rn, dy = vy * rn, dz = vz * rn;
-            float Y[K], wk[K];
-            sh_basis<DEG>(dx, dy, dz, Y);
-            #pragma unroll
-            for (int k = 0; k < K; k++) wk[k] = 0.0f;
-            #pragma unroll
-            for (int ch = 0; ch < 3; ch++) {
-                float acc = 0.5f;
-                #pragma unroll
-                for (int k = 0; k < K; k++) acc += sh[3 * k + ch] * Y[k];
-                if (acc < 0.0f) continue;
-                #pragma unroll
-                for (int k = 0; k < K; k++) {
-                    gsh[3 * k + ch] += Y[k] * gcol[ch];
-                    wk[k] += sh[3 * k + ch] * gcol[ch];
-                }
-            }
-            float gdir[3];
-            sh_basis_grad<DEG>(dx, dy, dz, wk, gdir);
-            const float dd = gdir[0] * dx + gdir[1] * dy + gdir[2] * dz;
-            const float gvx = (gdir[0] - dx * dd) * rn, gvy = (gdir[1] - dy * dd) * rn, gvz = (gdir[2] - dz * dd) * rn;
-            gm[0] += gvx;
-            gm[1] += gvy;
-            gm[2] += gvz;
             if (want_twist) {
-                tw[0] = gpx + W[0][0] * gvx + W[0][1] * gvy + W[0][2] * gvz;
-                tw[1] = gpy + W[1][0] * gvx + W[1][1] * gvy + W[1][2] * gvz;
-                tw[2] = gpz + W[2][0] * gvx + W[2][1] * gvy + W[2][2] * gvz;
+                tw[0] = gpx;
+                tw[1] = gpy;
+                tw[2] = gpz;
                 // (Sc Gc - Gc Sc) entries (1,2), (2,0), (0,1)
                 float A12 = 0.f, A20 = 0.f, A01 = 0.f;
                 #pragma unroll
@@ -262,8 +340,7 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a, View
         #pragma unroll
         for (int r = 0; r < 3; r++)
             #pragma unroll
-            for (int c = 0; c < 3; c++)
-                gM[r][c] = 2.f * (gMacc[r][0] * M[0][c] + gMacc[r][1] * M[1][c] + gMacc[r][2] * M[2][c]);
+            for (int c = 0; c < 3; c++) gM[r][c] = 2.f * (Gw[r][0] * M[0][c] + Gw[r][1] * M[1][c] + Gw[r][2] * M[2][c]);
         float gR[3][3];
         #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -290,17 +367,8 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ProjectBwdArgs a, View
         #pragma unroll
         for (int k = 0; k < 3; k++) a.g_means[3 * i + k] += gm[k];
         a.g_opacity_logit[i] += gol;
-        float *gshp = a.g_sh + (int64_t)K * 3 * i;
-        #pragma unroll
-        for (int k = 0; k < K * 3; k++) gshp[k] += gsh[k];
     }
-    if (want_twist) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < vt.n_views * 6; k += blockDim.x) {
-            const float r = s_tw[k / 6][k % 6];
-            if (r != 0.0f) atomicAdd(a.d_twist + k, r);
-        }
-    }
+    if (want_twist) flush_twist(a.d_twist, vt.n_views, s_tw);
 }
 
 }  // namespace gs
@@ -343,14 +411,17 @@ extern "C" gs_status_t gs_project_bwd(const gs_params_t *params, const gs_view_t
     a.g_sh = grads ? grads->sh : nullptr;
     a.d_twist = d_twist;
     const int threads = 128;
-    const unsigned blocks = (unsigned)((params->n + threads - 1) / threads);
     cudaStream_t s = as_stream(stream);
+    // colour first: the geometry kernel clears the 2D gradients after use
+    const unsigned cblocks = (unsigned)((4 * params->n + threads - 1) / threads);
     switch (params->sh_degree) {
-    case 0: project_bwd_kernel<0><<<blocks, threads, 0, s>>>(a, vt); break;
-    case 1: project_bwd_kernel<1><<<blocks, threads, 0, s>>>(a, vt); break;
-    case 2: project_bwd_kernel<2><<<blocks, threads, 0, s>>>(a, vt); break;
-    default: project_bwd_kernel<3><<<blocks, threads, 0, s>>>(a, vt); break;
+    case 0: project_bwd_color_kernel<0><<<cblocks, threads, 0, s>>>(a, vt); break;
+    case 1: project_bwd_color_kernel<1><<<cblocks, threads, 0, s>>>(a, vt); break;
+    case 2: project_bwd_color_kernel<2><<<cblocks, threads, 0, s>>>(a, vt); break;
+    default: project_bwd_color_kernel<3><<<cblocks, threads, 0, s>>>(a, vt); break;
     }
+    const unsigned gblocks = (unsigned)((params->n + threads - 1) / threads);
+    project_bwd_geom_kernel<<<gblocks, threads, 0, s>>>(a, vt);
     return launch_status();
 }
 

@@ -10,11 +10,14 @@
 // and through alpha_i = min(0.99, o_i g_i), g_i = exp(power_i), to the
 // opacity, the 2D mean and the conic (no gradient where the clamp is active).
 //
-// Every thread of a block is at the same list entry at the same time, so the
-// per-Gaussian gradients are summed across the warp with shuffles, then
-// across the block's warps in shared memory, and only then added to HBM with
-// 16-byte vector atomics: at most three per (Gaussian, tile).
+// Every thread of a block is at the same list entry at the same time.  A
+// thread first sums the gradients of its PPT pixels in registers, the warp
+// then reduces the ten sums with a reduce-scatter butterfly (12 shuffles,
+// leaving one total per lane), the block adds its warps' totals in shared
+// memory, and only then are they added to HBM with vector atomics: at most
+// three per (Gaussian, tile).  PPT and BATCH are picked by the autotuner.
 #include "common.cuh"
+#include "render.cuh"
 
 namespace gs {
 
@@ -32,16 +35,22 @@ struct RenderBwdArgs {
 
 constexpr int kAcc = 10;
 
-__global__ void __launch_bounds__(kTilePix) render_bwd_kernel(RenderBwdArgs a, ViewTable vt)
+template <int PPT, int BATCH>
+__global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArgs a, ViewTable vt)
 {
-    __shared__ float4 s_pos[kTilePix];
-    __shared__ float4 s_con[kTilePix];
-    __shared__ float4 s_col[kTilePix];
-    __shared__ int64_t s_rid[kTilePix];
-    __shared__ float s_acc[kTilePix][kAcc + 1];
+    constexpr int THREADS = kTilePix / PPT;
+    constexpr int ROWS = kTile / PPT;
+    __shared__ float4 s_pos[BATCH];
+    __shared__ float4 s_con[BATCH];
+    __shared__ float4 s_col[BATCH];
+    __shared__ int64_t s_rid[BATCH];
+    __shared__ float s_acc[BATCH][kAcc + 1];
     __shared__ int s_item;
     __shared__ uint32_t s_maxlast;
     const int tid = threadIdx.x, lane = tid & 31;
+    int slot;
+    bool slot_valid;
+    reduce10_slot(lane, &slot, &slot_valid);
     for (;;) {
         if (tid == 0) {
             s_item = (int)atomicAdd(a.work_counter, 1u);
@@ -54,42 +63,49 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(RenderBwdArgs a, V
         const ViewInfo &V = vt.v[v];
         const int lt = item - V.tile_base;
         const int px = (lt % V.tiles_x) * kTile + (tid & (kTile - 1));
-        const int py = (lt / V.tiles_x) * kTile + (tid / kTile);
-        const bool inside = px < V.width && py < V.height;
-        const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
+        const int py0 = (lt / V.tiles_x) * kTile + (tid / kTile);
+        const float sx = (float)px + 0.5f;
         const uint32_t b = a.ranges[2 * item];
         const int64_t rbase = (int64_t)v * a.n;
 
-        float T = 1.0f, Tf = 1.0f, gC0 = 0.0f, gC1 = 0.0f, gC2 = 0.0f, gD = 0.0f, gA = 0.0f;
-        uint32_t last = 0;
-        if (inside) {
-            const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
-            Tf = T = a.final_T[pix];
-            last = a.n_contrib[pix];
-            if (a.d_rgb) {
-                gC0 = a.d_rgb[3 * pix];
-                gC1 = a.d_rgb[3 * pix + 1];
-                gC2 = a.d_rgb[3 * pix + 2];
+        float T[PPT], Tf[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gA[PPT], S[PPT];
+        uint32_t last[PPT];
+        uint32_t my_last = 0;
+        #pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            const int py = py0 + k * ROWS;
+            T[k] = Tf[k] = 1.0f;
+            gC0[k] = gC1[k] = gC2[k] = gD[k] = gA[k] = S[k] = 0.0f;
+            last[k] = 0;
+            if (px < V.width && py < V.height) {
+                const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
+                Tf[k] = T[k] = a.final_T[pix];
+                last[k] = a.n_contrib[pix];
+                if (a.d_rgb) {
+                    gC0[k] = a.d_rgb[3 * pix];
+                    gC1[k] = a.d_rgb[3 * pix + 1];
+                    gC2[k] = a.d_rgb[3 * pix + 2];
+                }
+                if (a.d_depth) gD[k] = a.d_depth[pix];
+                if (a.d_alpha) gA[k] = a.d_alpha[pix];
             }
-            if (a.d_depth) gD = a.d_depth[pix];
-            if (a.d_alpha) gA = a.d_alpha[pix];
+            my_last = max(my_last, last[k]);
         }
-        if (last) atomicMax(&s_maxlast, last);
+        if (my_last) atomicMax(&s_maxlast, my_last);
         __syncthreads();
         const uint32_t maxlast = s_maxlast;
-        float S = 0.0f;  // suffix sum of (c.gC + z gD) alpha T over later entries
 
         for (uint32_t bend = maxlast; bend > 0;) {
-            const uint32_t bstart = bend > (uint32_t)kTilePix ? bend - kTilePix : 0u;
+            const uint32_t bstart = bend > (uint32_t)BATCH ? bend - BATCH : 0u;
             const int cnt = (int)(bend - bstart);
-            if (tid < cnt) {
-                const int64_t r = rbase + a.vals[b + bstart + tid];
-                s_rid[tid] = r;
-                s_pos[tid] = a.rec[3 * r];
-                s_con[tid] = a.rec[3 * r + 1];
-                s_col[tid] = a.rec[3 * r + 2];
+            for (int r = tid; r < cnt; r += THREADS) {
+                const int64_t g = rbase + a.vals[b + bstart + r];
+                s_rid[r] = g;
+                s_pos[r] = a.rec[3 * g];
+                s_con[r] = a.rec[3 * g + 1];
+                s_col[r] = a.rec[3 * g + 2];
                 #pragma unroll
-                for (int k = 0; k < kAcc; k++) s_acc[tid][k] = 0.0f;
+                for (int k = 0; k < kAcc; k++) s_acc[r][k] = 0.0f;
             }
             __syncthreads();
             for (int j = cnt - 1; j >= 0; j--) {
@@ -98,63 +114,62 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(RenderBwdArgs a, V
                 #pragma unroll
                 for (int k = 0; k < kAcc; k++) gr[k] = 0.0f;
                 bool contrib = false;
-                if (pos < last) {
+                if (pos < my_last) {
                     const float4 p = s_pos[j];
                     const float4 c = s_con[j];
-                    float dx, dy;
-                    const float power = splat_power(p.x, p.y, c.x, c.y, c.z, sx, sy, &dx, &dy);
-                    const float g = __expf(power);
-                    const float araw = __fmul_rn(p.w, g);
-                    const float alpha = fminf(kAlphaMax, araw);
-                    if (alpha >= kAlphaMin) {
+                    const float4 col = s_col[j];
+                    #pragma unroll
+                    for (int k = 0; k < PPT; k++) {
+                        if (pos >= last[k]) continue;
+                        const float sy = (float)(py0 + k * ROWS) + 0.5f;
+                        float dx, dy;
+                        const float power = splat_power(p.x, p.y, c.x, c.y, c.z, sx, sy, &dx, &dy);
+                        const float g = __expf(power);
+                        const float araw = __fmul_rn(p.w, g);
+                        const float alpha = fminf(kAlphaMax, araw);
+                        if (alpha < kAlphaMin) continue;
                         contrib = true;
-                        const float om = 1.0f - alpha;
-                        const float inv_om = 1.0f / om;
-                        const float Tb = T * inv_om;
+                        const float inv_om = 1.0f / (1.0f - alpha);
+                        const float Tb = T[k] * inv_om;
                         const float w = alpha * Tb;
-                        const float4 col = s_col[j];
-                        gr[6] = gC0 * w;
-                        gr[7] = gC1 * w;
-                        gr[8] = gC2 * w;
-                        gr[9] = gD * w;
-                        const float wgt = col.x * gC0 + col.y * gC1 + col.z * gC2 + p.z * gD;
-                        const float dalpha = Tb * wgt + (gA * Tf - S) * inv_om;
-                        S += wgt * w;
-                        T = Tb;
+                        gr[6] += gC0[k] * w;
+                        gr[7] += gC1[k] * w;
+                        gr[8] += gC2[k] * w;
+                        gr[9] += gD[k] * w;
+                        const float wgt = col.x * gC0[k] + col.y * gC1[k] + col.z * gC2[k] + p.z * gD[k];
+                        const float dalpha = Tb * wgt + (gA[k] * Tf[k] - S[k]) * inv_om;
+                        S[k] += wgt * w;
+                        T[k] = Tb;
                         if (araw < kAlphaMax) {
-                            gr[5] = dalpha * g;
+                            gr[5] += dalpha * g;
                             const float dpow = dalpha * araw;
-                            gr[0] = dpow * (-c.x * dx - c.y * dy);
-                            gr[1] = dpow * (-c.z * dy - c.y * dx);
-                            gr[2] = -0.5f * dx * dx * dpow;
-                            gr[3] = -dx * dy * dpow;
-                            gr[4] = -0.5f * dy * dy * dpow;
+                            gr[0] += dpow * (-c.x * dx - c.y * dy);
+                            gr[1] += dpow * (-c.z * dy - c.y * dx);
+                            gr[2] += -0.5f * dx * dx * dpow;
+                            gr[3] += -dx * dy * dpow;
+                            gr[4] += -0.5f * dy * dy * dpow;
                         }
                     }
                 }
                 if (__any_sync(kFullMask, contrib)) {
-                    #pragma unroll
-                    for (int k = 0; k < kAcc; k++) gr[k] = warp_sum(gr[k]);
-                    if (lane == 0) {
-                        #pragma unroll
-                        for (int k = 0; k < kAcc; k++) atomicAdd(&s_acc[j][k], gr[k]);
-                    }
+                    const float r = warp_reduce_scatter10(gr, lane);
+                    if (slot_valid && r != 0.0f) atomicAdd(&s_acc[j][slot], r);
                 }
             }
             __syncthreads();
-            if (tid < cnt) {
-                float r[kAcc];
+            for (int r = tid; r < cnt; r += THREADS) {
+                float q[kAcc];
                 bool any = false;
                 #pragma unroll
                 for (int k = 0; k < kAcc; k++) {
-                    r[k] = s_acc[tid][k];
-                    any |= (r[k] != 0.0f);
+                    q[k] = s_acc[r][k];
+                    any |= (q[k] != 0.0f);
                 }
                 if (any) {
-                    float4 *dst = a.grad2d + 3 * s_rid[tid];
-                    atomicAdd(dst, make_float4(r[0], r[1], r[2], r[3]));
-                    atomicAdd(dst + 1, make_float4(r[4], r[5], r[6], r[7]));
-                    atomicAdd(reinterpret_cast<float2 *>(dst + 2), make_float2(r[8], r[9]));
+                    float4 *dst = a.grad2d + 3 * s_rid[r];
+                    atomicAdd(dst, make_float4(q[0], q[1], q[2], q[3]));
+                    atomicAdd(dst + 1, make_float4(q[4], q[5], q[6], q[7]));
+                    atomicAdd(reinterpret_cast<float2 *>(dst + 2), make_float2(q[8], q[9]));
                 }
             }
             __syncthreads();
@@ -162,6 +177,19 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(RenderBwdArgs a, V
         }
         __syncthreads();  // every thread has read s_item and s_maxlast before they are reset
     }
+}
+
+template <int PPT, int BATCH>
+static gs_status_t launch_bwd(const RenderBwdArgs &a, const ViewTable &vt, cudaStream_t s)
+{
+    auto kern = render_bwd_kernel<PPT, BATCH>;
+    constexpr int threads = kTilePix / PPT;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+    const int grid = (int)(slots < vt.n_tiles_total ? slots : vt.n_tiles_total);
+    kern<<<grid > 0 ? grid : 1, threads, 0, s>>>(a, vt);
+    return launch_status();
 }
 
 }  // namespace gs
@@ -200,10 +228,11 @@ extern "C" gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t 
     a.d_alpha = d_alpha;
     a.grad2d = reinterpret_cast<float4 *>(grad2d);
     a.work_counter = work_counter;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel, kTilePix, 0);
-    const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-    const int grid = (int)(slots < vt.n_tiles_total ? slots : vt.n_tiles_total);
-    render_bwd_kernel<<<grid > 0 ? grid : 1, kTilePix, 0, s>>>(a, vt);
-    return launch_status();
+    switch (render_variant_bwd()) {
+    case 0: return launch_bwd<1, 256>(a, vt, s);
+    case 1: return launch_bwd<2, 128>(a, vt, s);
+    case 2: return launch_bwd<4, 64>(a, vt, s);
+    case 3: return launch_bwd<4, 128>(a, vt, s);
+    default: return launch_bwd<8, 64>(a, vt, s);
+    }
 }

@@ -3,12 +3,15 @@
 // sum_i f_i prod_{j<i} (1 - f_j) = 1 - T_final).
 //
 // One persistent launch covers every (view, tile) work item of every view:
-// 256-thread blocks pull items from an atomic counter, so views of different
-// sizes share one launch and long tiles do not hold up a static schedule.
-// Each block stages its tile's sorted splat records in batches of 256 in
-// shared memory and each thread composites one pixel front to back, leaving
-// the batch loop once all 256 pixels have run out of transmittance.
+// blocks pull items from an atomic counter, so views of different sizes share
+// one launch and long tiles do not hold up a static schedule.  A block of
+// 256 / PPT threads owns one 16x16 tile at a time, each thread PPT pixels of
+// it (rows ty, ty + 16/PPT, ...), so every splat record staged in shared memory
+// serves PPT pixels per load.  Records are staged in batches of BATCH and the
+// block leaves the batch loop once all its pixels have run out of
+// transmittance.  PPT and BATCH are chosen per workload by the autotuner.
 #include "common.cuh"
+#include "render.cuh"
 
 namespace gs {
 
@@ -25,12 +28,14 @@ struct RenderFwdArgs {
 
 // STATS = true counts, per pixel, the list entries evaluated and blended (the
 // algorithmic work of the compositing) instead of writing the image.
-template <bool STATS>
-__global__ void __launch_bounds__(kTilePix) render_fwd_kernel(RenderFwdArgs a, ViewTable vt)
+template <int PPT, int BATCH, bool STATS>
+__global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArgs a, ViewTable vt)
 {
-    __shared__ float4 s_pos[kTilePix];  // (u, v, z, opacity)
-    __shared__ float4 s_con[kTilePix];  // (conicA, conicB, conicC, -)
-    __shared__ float4 s_col[kTilePix];  // (r, g, b, -)
+    constexpr int THREADS = kTilePix / PPT;
+    constexpr int ROWS = kTile / PPT;  // rows between a thread's pixels
+    __shared__ float4 s_pos[BATCH];    // (u, v, z, opacity)
+    __shared__ float4 s_con[BATCH];    // (conicA, conicB, conicC, -)
+    __shared__ float4 s_col[BATCH];    // (r, g, b, -)
     __shared__ int s_item;
     const int tid = threadIdx.x;
     for (;;) {
@@ -43,67 +48,113 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(RenderFwdArgs a, V
         const ViewInfo &V = vt.v[v];
         const int lt = item - V.tile_base;
         const int px = (lt % V.tiles_x) * kTile + (tid & (kTile - 1));
-        const int py = (lt / V.tiles_x) * kTile + (tid / kTile);
-        const bool inside = px < V.width && py < V.height;
-        const float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
+        const int py0 = (lt / V.tiles_x) * kTile + (tid / kTile);
+        const float sx = (float)px + 0.5f;
         const uint32_t b = a.ranges[2 * item], e = a.ranges[2 * item + 1];
         const int64_t rbase = (int64_t)v * a.n;
 
-        float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, D = 0.0f;
-        uint32_t last = 0, n_eval = 0, n_blend = 0;
-        bool done = !inside;
-        for (uint32_t start = b; start < e; start += kTilePix) {
-            if (__syncthreads_count(done) == kTilePix) break;
-            const uint32_t idx = start + tid;
-            if (idx < e) {
-                const int64_t r = rbase + a.vals[idx];
-                s_pos[tid] = a.rec[3 * r];
-                s_con[tid] = a.rec[3 * r + 1];
-                s_col[tid] = a.rec[3 * r + 2];
+        float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
+        uint32_t last[PPT], n_eval[PPT], n_blend[PPT];
+        bool live[PPT];
+        int alive = 0;
+        #pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            T[k] = 1.0f;
+            C0[k] = C1[k] = C2[k] = D[k] = 0.0f;
+            last[k] = n_eval[k] = n_blend[k] = 0;
+            live[k] = px < V.width && (py0 + k * ROWS) < V.height;
+            alive += live[k];
+        }
+        for (uint32_t start = b; start < e; start += BATCH) {
+            if (__syncthreads_count(alive > 0) == 0) break;
+            #pragma unroll
+            for (int r = tid; r < BATCH; r += THREADS) {
+                const uint32_t idx = start + r;
+                if (idx < e) {
+                    const int64_t g = rbase + a.vals[idx];
+                    s_pos[r] = a.rec[3 * g];
+                    s_con[r] = a.rec[3 * g + 1];
+                    s_col[r] = a.rec[3 * g + 2];
+                }
             }
             __syncthreads();
-            const int cnt = (int)min((uint32_t)kTilePix, e - start);
-            if (!done) {
+            const int cnt = (int)min((uint32_t)BATCH, e - start);
+            if (alive > 0) {
                 for (int j = 0; j < cnt; j++) {
                     const float4 p = s_pos[j];
                     const float4 c = s_con[j];
-                    float dx, dy;
-                    const float power = splat_power(p.x, p.y, c.x, c.y, c.z, sx, sy, &dx, &dy);
-                    const float alpha = fminf(kAlphaMax, __fmul_rn(p.w, __expf(power)));
-                    if (STATS) n_eval++;
-                    if (alpha < kAlphaMin) continue;
-                    const float tT = T * (1.0f - alpha);
-                    if (tT < kTMin) {
-                        done = true;
-                        break;
+                    #pragma unroll
+                    for (int k = 0; k < PPT; k++) {
+                        if (!live[k]) continue;
+                        const float sy = (float)(py0 + k * ROWS) + 0.5f;
+                        const float alpha = splat_alpha(p, c, sx, sy);
+                        if (STATS) n_eval[k]++;
+                        if (alpha < kAlphaMin) continue;
+                        const float tT = T[k] * (1.0f - alpha);
+                        if (tT < kTMin) {
+                            live[k] = false;
+                            alive--;
+                            continue;
+                        }
+                        if (STATS) n_blend[k]++;
+                        const float w = alpha * T[k];
+                        const float4 col = s_col[j];
+                        C0[k] += col.x * w;
+                        C1[k] += col.y * w;
+                        C2[k] += col.z * w;
+                        D[k] += p.z * w;
+                        T[k] = tT;
+                        last[k] = start - b + (uint32_t)j + 1u;
                     }
-                    if (STATS) n_blend++;
-                    const float w = alpha * T;
-                    const float4 col = s_col[j];
-                    C0 += col.x * w;
-                    C1 += col.y * w;
-                    C2 += col.z * w;
-                    D += p.z * w;
-                    T = tT;
-                    last = start - b + (uint32_t)j + 1u;
+                    if (alive == 0) break;
                 }
             }
             __syncthreads();
         }
-        if (STATS && inside) {
+        #pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            const int py = py0 + k * ROWS;
+            if (px >= V.width || py >= V.height) continue;
             const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
-            a.n_eval[pix] = n_eval;
-            a.n_blend[pix] = n_blend;
-        } else if (inside) {
-            const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
-            a.rgb[3 * pix + 0] = C0;
-            a.rgb[3 * pix + 1] = C1;
-            a.rgb[3 * pix + 2] = C2;
-            a.depth[pix] = D;
-            a.alpha[pix] = 1.0f - T;
-            a.final_T[pix] = T;
-            a.n_contrib[pix] = last;
+            if (STATS) {
+                a.n_eval[pix] = n_eval[k];
+                a.n_blend[pix] = n_blend[k];
+            } else {
+                a.rgb[3 * pix + 0] = C0[k];
+                a.rgb[3 * pix + 1] = C1[k];
+                a.rgb[3 * pix + 2] = C2[k];
+                a.depth[pix] = D[k];
+                a.alpha[pix] = 1.0f - T[k];
+                a.final_T[pix] = T[k];
+                a.n_contrib[pix] = last[k];
+            }
         }
+    }
+}
+
+template <int PPT, int BATCH, bool STATS>
+static gs_status_t launch_fwd(const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
+{
+    auto kern = render_fwd_kernel<PPT, BATCH, STATS>;
+    constexpr int threads = kTilePix / PPT;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
+    const int grid = (int)(slots < vt.n_tiles_total ? slots : vt.n_tiles_total);
+    kern<<<grid > 0 ? grid : 1, threads, 0, s>>>(a, vt);
+    return launch_status();
+}
+
+template <bool STATS>
+static gs_status_t dispatch_fwd(const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
+{
+    switch (render_variant_fwd()) {
+    case 0: return launch_fwd<1, 256, STATS>(a, vt, s);
+    case 1: return launch_fwd<2, 128, STATS>(a, vt, s);
+    case 2: return launch_fwd<2, 256, STATS>(a, vt, s);
+    case 3: return launch_fwd<4, 64, STATS>(a, vt, s);
+    case 4: return launch_fwd<4, 128, STATS>(a, vt, s);
+    default: return launch_fwd<8, 64, STATS>(a, vt, s);
     }
 }
 
@@ -124,7 +175,7 @@ extern "C" gs_status_t gs_render_fwd(const gs_projected_t *proj, int64_t n, cons
         return GS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     if (cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
-    RenderFwdArgs a;
+    RenderFwdArgs a = {};
     a.rec = reinterpret_cast<const float4 *>(proj->rec);
     a.n = n;
     a.vals = bins->vals;
@@ -134,14 +185,8 @@ extern "C" gs_status_t gs_render_fwd(const gs_projected_t *proj, int64_t n, cons
     a.alpha = img->alpha;
     a.final_T = img->final_T;
     a.n_contrib = img->n_contrib;
-    a.n_eval = a.n_blend = nullptr;
     a.work_counter = work_counter;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_fwd_kernel<false>, kTilePix, 0);
-    const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-    const int grid = (int)(slots < vt.n_tiles_total ? slots : vt.n_tiles_total);
-    render_fwd_kernel<false><<<grid > 0 ? grid : 1, kTilePix, 0, s>>>(a, vt);
-    return launch_status();
+    return dispatch_fwd<false>(a, vt, s);
 }
 
 extern "C" gs_status_t gs_render_stats(const gs_projected_t *proj, int64_t n, const gs_bins_t *bins,
@@ -163,7 +208,31 @@ extern "C" gs_status_t gs_render_stats(const gs_projected_t *proj, int64_t n, co
     a.n_eval = n_eval;
     a.n_blend = n_blend;
     a.work_counter = work_counter;
-    const int grid = (int)(num_sms() * 4 < vt.n_tiles_total ? num_sms() * 4 : vt.n_tiles_total);
-    render_fwd_kernel<true><<<grid > 0 ? grid : 1, kTilePix, 0, s>>>(a, vt);
-    return launch_status();
+    return launch_fwd<1, 256, true>(a, vt, s);
+}
+
+// Compositing kernel variants in use (pixels per thread x staged batch), set by
+// the autotuner; defaults suit 1200x680 views of room-scale scenes.
+namespace gs {
+static int g_variant_fwd = 1;
+static int g_variant_bwd = 3;
+int render_variant_fwd() { return g_variant_fwd; }
+int render_variant_bwd() { return g_variant_bwd; }
+}  // namespace gs
+
+extern "C" gs_status_t gs_set_render_variants(int32_t fwd, int32_t bwd)
+{
+    if (fwd < 0 || fwd >= kFwdVariants || bwd < 0 || bwd >= kBwdVariants) return GS_ERR_INVALID_ARG;
+    g_variant_fwd = fwd;
+    g_variant_bwd = bwd;
+    return GS_OK;
+}
+
+extern "C" gs_status_t gs_get_render_variants(int32_t *fwd, int32_t *bwd, int32_t *n_fwd, int32_t *n_bwd)
+{
+    if (fwd) *fwd = g_variant_fwd;
+    if (bwd) *bwd = g_variant_bwd;
+    if (n_fwd) *n_fwd = kFwdVariants;
+    if (n_bwd) *n_bwd = kBwdVariants;
+    return GS_OK;
 }

@@ -144,7 +144,8 @@ class MappingStep:
         import math
         n_bits = 32 + max(0, math.ceil(math.log2(max(self.rast.n_tiles, 1))))
         passes = (n_bits + 7) // 8
-        k = 1 + (3 + 1 + passes + 1) + 1 + 1 + 1 + 1  # project, bin (count, scan, emit, hist, passes, ranges), fwd, loss, bwd, pbwd
+        # project, bin (count, scan, emit, hist, passes, ranges), fwd, loss, bwd, pbwd colour + geometry
+        k = 1 + (3 + 1 + passes + 1) + 1 + 1 + 1 + 2
         k += 1 if self.keypoints is not None else 0
         k += 1 if self.optimise_params else 0
         return k

@@ -278,3 +278,29 @@ def test_capacity_overflow_is_reported_not_fatal():
     assert rast.n_pairs() == int(geom["tiles_touched"].sum()) > 500
     # the pipeline still completes with in-bounds output
     assert torch.isfinite(rast.img["rgb"]).all()
+
+
+def test_every_compositing_variant_matches():
+    """All forward variants give bit-identical images; every backward variant
+    meets the gradient bar against the oracle."""
+    name, scene, cams = CASES[1]
+    fwd0, bwd0, n_fwd, n_bwd = gs.gs_get_render_variants()
+    try:
+        ref_img = None
+        for fv in range(n_fwd):
+            gs.gs_set_render_variants(fv, bwd0)
+            rast, p, vm = _run(scene, cams)
+            img = {k: v.cpu().numpy() for k, v in rast.img.items()}
+            if ref_img is None:
+                ref_img = img
+            for k in img:
+                np.testing.assert_array_equal(img[k], ref_img[k], err_msg=f"fwd variant {fv} {k}")
+        for bv in range(n_bwd):
+            gs.gs_set_render_variants(fwd0, bv)
+            out, gref = _backward_case(scene, cams)
+            for k in (*PARAM_KEYS, "twist"):
+                e = rel_l2(out[k], gref[k])
+                assert e <= GRAD_TOL, (bv, k, e)
+            print(f"bwd variant {bv}: max rel-L2 {max(rel_l2(out[k], gref[k]) for k in out):.2e}")
+    finally:
+        gs.gs_set_render_variants(fwd0, bwd0)
