@@ -61,6 +61,24 @@ __device__ __forceinline__ void flush_twist(float *d_twist, int n_views, float (
     }
 }
 
+// Bit v of the result is set when Gaussian i is drawn in view v.  All radii are
+// loaded up front (independent loads, eight at a time), so the view loops that
+// follow carry no load whose address depends on an earlier load.
+__device__ __forceinline__ uint64_t visible_views(const int32_t *radii, int64_t n, int64_t i, bool active, int n_views)
+{
+    uint64_t mask = 0;
+    if (!active) return 0;
+    for (int v0 = 0; v0 < n_views; v0 += 8) {
+        int r[8];
+        #pragma unroll
+        for (int k = 0; k < 8; k++) r[k] = (v0 + k < n_views) ? __ldg(radii + (int64_t)(v0 + k) * n + i) : 0;
+        #pragma unroll
+        for (int k = 0; k < 8; k++)
+            if (r[k] > 0) mask |= 1ull << (v0 + k);
+    }
+    return mask;
+}
+
 // Colour path: lanes 4g .. 4g+3 of the grid handle Gaussian g, lane 4g+c its
 // colour channel c (c = 3 idle).
 template <int DEG>
@@ -90,13 +108,24 @@ __global__ void __launch_bounds__(128) project_bwd_color_kernel(ProjectBwdArgs a
         for (int k = 0; k < 3; k++) m[k] = a.means[3 * i + k];
     }
     float gm[3] = {0.0f, 0.0f, 0.0f};
+    const uint64_t vis_mask = visible_views(a.radii, a.n, i, active, vt.n_views);
+    const float *g2 = reinterpret_cast<const float *>(a.grad2d);
+    // this lane's colour gradient for the first visible view, then one view ahead
+    float gcol_next = 0.0f;
+    if (vis_mask && ch < 3) gcol_next = g2[12 * ((int64_t)(__ffsll((long long)vis_mask) - 1) * a.n + i) + 6 + ch];
 
     #pragma unroll 1
     for (int v = 0; v < vt.n_views; v++) {
-        const int64_t o = (int64_t)v * a.n + i;
+        const bool vis = (vis_mask >> v) & 1ull;
+        if (!__any_sync(kFullMask, vis)) continue;
+        float gcol = 0.0f;
+        if (vis) {
+            gcol = gcol_next;
+            const uint64_t rest = vis_mask & ~((2ull << v) - 1ull);
+            if (rest && ch < 3) gcol_next = g2[12 * ((int64_t)(__ffsll((long long)rest) - 1) * a.n + i) + 6 + ch];
+        }
         float gdir[3] = {0.0f, 0.0f, 0.0f};
         float dx = 0.0f, dy = 0.0f, dz = 0.0f, rn = 0.0f;
-        const bool vis = active && a.radii[o] > 0;
         if (vis) {
             const float vx = m[0] - s_c[v][0], vy = m[1] - s_c[v][1], vz = m[2] - s_c[v][2];
             rn = rsqrtf(vx * vx + vy * vy + vz * vz);
@@ -104,7 +133,6 @@ __global__ void __launch_bounds__(128) project_bwd_color_kernel(ProjectBwdArgs a
             dy = vy * rn;
             dz = vz * rn;
             if (ch < 3) {
-                const float gcol = reinterpret_cast<const float *>(a.grad2d)[12 * o + 6 + ch];
                 float Y[K];
                 sh_basis<DEG>(dx, dy, dz, Y);
                 float acc = 0.5f;
@@ -213,12 +241,30 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a,
     const float opac = 1.0f / (1.0f + expf(-ol));
 
     float gm[3] = {0, 0, 0}, Gw[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gol = 0.0f;
+    const uint64_t vis_mask = visible_views(a.radii, a.n, i, active, vt.n_views);
+    // 2D gradients of the first visible view, then always one visible view ahead
+    float4 N0 = make_float4(0.f, 0.f, 0.f, 0.f), N1 = N0, N2 = N0;
+    if (vis_mask) {
+        const int64_t o = (int64_t)(__ffsll((long long)vis_mask) - 1) * a.n + i;
+        N0 = a.grad2d[3 * o];
+        N1 = a.grad2d[3 * o + 1];
+        N2 = a.grad2d[3 * o + 2];
+    }
     #pragma unroll 1
     for (int v = 0; v < vt.n_views; v++) {
         float tw[6] = {0, 0, 0, 0, 0, 0};
-        const int64_t o = (int64_t)v * a.n + i;
-        if (active && a.radii[o] > 0) {
-            const float4 G0 = a.grad2d[3 * o], G1 = a.grad2d[3 * o + 1], G2v = a.grad2d[3 * o + 2];
+        const bool vis = (vis_mask >> v) & 1ull;
+        if (!__any_sync(kFullMask, vis)) continue;
+        if (vis) {
+            const int64_t o = (int64_t)v * a.n + i;
+            const float4 G0 = N0, G1 = N1, G2v = N2;
+            const uint64_t rest = vis_mask & ~((2ull << v) - 1ull);
+            if (rest) {
+                const int64_t on = (int64_t)(__ffsll((long long)rest) - 1) * a.n + i;
+                N0 = a.grad2d[3 * on];
+                N1 = a.grad2d[3 * on + 1];
+                N2 = a.grad2d[3 * on + 2];
+            }
             const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
             a.grad2d[3 * o] = zero4;
             a.grad2d[3 * o + 1] = zero4;

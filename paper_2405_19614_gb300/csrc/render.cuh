@@ -15,6 +15,24 @@ __device__ __forceinline__ float splat_alpha(const float4 &p, const float4 &c, f
     return fminf(kAlphaMax, __fmul_rn(p.w, __expf(power)));
 }
 
+// Conservative test that a splat cannot reach alpha >= 1/255 anywhere in a box
+// of pixel centres [x0, x1] x [y0, y1]: for every sample s in the box,
+//   power(s) = -1/2 (s - mu)^T Q (s - mu) <= -1/2 lambda_min(Q) dist(mu, box)^2,
+// so alpha <= o exp(-1/2 lambda_min dist^2).  The entry is dropped when that
+// bound is below 1/255 by a factor e^-0.001, a margin far larger than the FP32
+// rounding of the per-pixel evaluation, so a dropped entry is one the per-pixel
+// test would have skipped: results are unchanged, only work is saved.
+__device__ __forceinline__ bool splat_misses_box(const float4 &p, const float4 &c, float x0, float x1, float y0,
+                                                 float y1)
+{
+    const float dx = fmaxf(fmaxf(x0 - p.x, p.x - x1), 0.0f);
+    const float dy = fmaxf(fmaxf(y0 - p.y, p.y - y1), 0.0f);
+    const float h = 0.5f * (c.x - c.z);
+    const float lmin = fmaxf(0.5f * (c.x + c.z) - sqrtf(h * h + c.y * c.y), 0.0f);
+    // alpha bound < (1/255) e^-0.001  <=>  -1/2 lmin d^2 < -ln(255 o) - 0.001
+    return -0.5f * lmin * (dx * dx + dy * dy) < -__logf(255.0f * p.w) - 1e-3f;
+}
+
 // Kernel variants (pixels per thread x staged batch) the autotuner picks from.
 constexpr int kFwdVariants = 6;  // (1,256) (2,128) (2,256) (4,64) (4,128) (8,64)
 constexpr int kBwdVariants = 5;  // (1,256) (2,128) (4,64) (4,128) (8,64)

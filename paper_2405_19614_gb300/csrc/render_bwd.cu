@@ -10,12 +10,15 @@
 // and through alpha_i = min(0.99, o_i g_i), g_i = exp(power_i), to the
 // opacity, the 2D mean and the conic (no gradient where the clamp is active).
 //
-// Every thread of a block is at the same list entry at the same time.  A
-// thread first sums the gradients of its PPT pixels in registers, the warp
-// then reduces the ten sums with a reduce-scatter butterfly (12 shuffles,
-// leaving one total per lane), the block adds its warps' totals in shared
-// memory, and only then are they added to HBM with vector atomics: at most
-// three per (Gaussian, tile).  PPT and BATCH are picked by the autotuner.
+// Each warp owns a 16 x 2*PPT band of the tile and walks only the staged
+// entries that can reach alpha = 1/255 in that band (the same conservative
+// test as the forward, 32 entries at a time).  All threads of a warp are at
+// the same list entry at the same time: a thread first sums the gradients of
+// its PPT pixels in registers, the warp reduces the ten sums with a
+// reduce-scatter butterfly (12 shuffles, one total per lane), the block adds
+// its warps' totals in shared memory, and only then are they added to HBM with
+// vector atomics: at most three per (Gaussian, tile).  PPT and BATCH are
+// picked by the autotuner.
 #include "common.cuh"
 #include "render.cuh"
 
@@ -39,7 +42,7 @@ template <int PPT, int BATCH>
 __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArgs a, ViewTable vt)
 {
     constexpr int THREADS = kTilePix / PPT;
-    constexpr int ROWS = kTile / PPT;
+    constexpr int BAND = 2 * PPT;  // rows per warp
     __shared__ float4 s_pos[BATCH];
     __shared__ float4 s_con[BATCH];
     __shared__ float4 s_col[BATCH];
@@ -47,7 +50,8 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
     __shared__ float s_acc[BATCH][kAcc + 1];
     __shared__ int s_item;
     __shared__ uint32_t s_maxlast;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ly0 = warp * BAND + (lane >> 4);  // this thread's rows: ly0 + 2k
     int slot;
     bool slot_valid;
     reduce10_slot(lane, &slot, &slot_valid);
@@ -62,9 +66,12 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
         const int v = view_of_tile(vt, item);
         const ViewInfo &V = vt.v[v];
         const int lt = item - V.tile_base;
-        const int px = (lt % V.tiles_x) * kTile + (tid & (kTile - 1));
-        const int py0 = (lt / V.tiles_x) * kTile + (tid / kTile);
+        const int tx0 = (lt % V.tiles_x) * kTile, ty0 = (lt / V.tiles_x) * kTile;
+        const int px = tx0 + (lane & (kTile - 1));
+        const int py0 = ty0 + ly0;
         const float sx = (float)px + 0.5f;
+        const float bx0 = (float)tx0 + 0.5f, bx1 = (float)tx0 + (kTile - 0.5f);
+        const float by0 = (float)(ty0 + warp * BAND) + 0.5f, by1 = by0 + (float)(BAND - 1);
         const uint32_t b = a.ranges[2 * item];
         const int64_t rbase = (int64_t)v * a.n;
 
@@ -73,7 +80,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
         uint32_t my_last = 0;
         #pragma unroll
         for (int k = 0; k < PPT; k++) {
-            const int py = py0 + k * ROWS;
+            const int py = py0 + 2 * k;
             T[k] = Tf[k] = 1.0f;
             gC0[k] = gC1[k] = gC2[k] = gD[k] = gA[k] = S[k] = 0.0f;
             last[k] = 0;
@@ -92,6 +99,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
             my_last = max(my_last, last[k]);
         }
         if (my_last) atomicMax(&s_maxlast, my_last);
+        const uint32_t warp_last = __reduce_max_sync(kFullMask, my_last);
         __syncthreads();
         const uint32_t maxlast = s_maxlast;
 
@@ -108,7 +116,14 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
                 for (int k = 0; k < kAcc; k++) s_acc[r][k] = 0.0f;
             }
             __syncthreads();
-            for (int j = cnt - 1; j >= 0; j--) {
+            for (int m = ((cnt - 1) >> 5) << 5; m >= 0; m -= 32) {
+              const int jl = m + lane;
+              uint32_t todo = __ballot_sync(kFullMask, jl < cnt && (uint32_t)(bstart + jl) < warp_last &&
+                                                           !splat_misses_box(s_pos[jl], s_con[jl], bx0, bx1, by0, by1));
+              while (todo) {
+                const int bit = 31 - __clz(todo);
+                todo &= ~(1u << bit);
+                const int j = m + bit;
                 const uint32_t pos = bstart + (uint32_t)j;
                 float gr[kAcc];
                 #pragma unroll
@@ -121,7 +136,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
                     #pragma unroll
                     for (int k = 0; k < PPT; k++) {
                         if (pos >= last[k]) continue;
-                        const float sy = (float)(py0 + k * ROWS) + 0.5f;
+                        const float sy = (float)(py0 + 2 * k) + 0.5f;
                         float dx, dy;
                         const float power = splat_power(p.x, p.y, c.x, c.y, c.z, sx, sy, &dx, &dy);
                         const float g = __expf(power);
@@ -155,6 +170,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
                     const float r = warp_reduce_scatter10(gr, lane);
                     if (slot_valid && r != 0.0f) atomicAdd(&s_acc[j][slot], r);
                 }
+              }
             }
             __syncthreads();
             for (int r = tid; r < cnt; r += THREADS) {

@@ -5,11 +5,14 @@
 // One persistent launch covers every (view, tile) work item of every view:
 // blocks pull items from an atomic counter, so views of different sizes share
 // one launch and long tiles do not hold up a static schedule.  A block of
-// 256 / PPT threads owns one 16x16 tile at a time, each thread PPT pixels of
-// it (rows ty, ty + 16/PPT, ...), so every splat record staged in shared memory
-// serves PPT pixels per load.  Records are staged in batches of BATCH and the
-// block leaves the batch loop once all its pixels have run out of
-// transmittance.  PPT and BATCH are chosen per workload by the autotuner.
+// 256 / PPT threads owns one 16x16 tile at a time; each warp owns a 16 x 2*PPT
+// band of it and each thread PPT pixels of that band (rows r, r + 2, ...), so
+// every splat record staged in shared memory serves PPT pixels per load.
+// Records are staged in batches of BATCH; each warp first drops, 32 at a time
+// and in parallel, the records that provably cannot reach alpha = 1/255 in its
+// band (splat_misses_box), then walks the rest.  The block leaves the batch
+// loop once all its pixels have run out of transmittance.  PPT and BATCH are
+// chosen per workload by the autotuner.
 #include "common.cuh"
 #include "render.cuh"
 
@@ -32,12 +35,13 @@ template <int PPT, int BATCH, bool STATS>
 __global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArgs a, ViewTable vt)
 {
     constexpr int THREADS = kTilePix / PPT;
-    constexpr int ROWS = kTile / PPT;  // rows between a thread's pixels
+    constexpr int BAND = 2 * PPT;      // rows per warp
     __shared__ float4 s_pos[BATCH];    // (u, v, z, opacity)
     __shared__ float4 s_con[BATCH];    // (conicA, conicB, conicC, -)
     __shared__ float4 s_col[BATCH];    // (r, g, b, -)
     __shared__ int s_item;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ly0 = warp * BAND + (lane >> 4);  // this thread's rows: ly0 + 2k
     for (;;) {
         if (tid == 0) s_item = (int)atomicAdd(a.work_counter, 1u);
         __syncthreads();
@@ -47,9 +51,13 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArg
         const int v = view_of_tile(vt, item);
         const ViewInfo &V = vt.v[v];
         const int lt = item - V.tile_base;
-        const int px = (lt % V.tiles_x) * kTile + (tid & (kTile - 1));
-        const int py0 = (lt / V.tiles_x) * kTile + (tid / kTile);
+        const int tx0 = (lt % V.tiles_x) * kTile, ty0 = (lt / V.tiles_x) * kTile;
+        const int px = tx0 + (lane & (kTile - 1));
+        const int py0 = ty0 + ly0;
         const float sx = (float)px + 0.5f;
+        // the warp's band of pixel centres, for culling
+        const float bx0 = (float)tx0 + 0.5f, bx1 = (float)tx0 + (kTile - 0.5f);
+        const float by0 = (float)(ty0 + warp * BAND) + 0.5f, by1 = by0 + (float)(BAND - 1);
         const uint32_t b = a.ranges[2 * item], e = a.ranges[2 * item + 1];
         const int64_t rbase = (int64_t)v * a.n;
 
@@ -62,7 +70,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArg
             T[k] = 1.0f;
             C0[k] = C1[k] = C2[k] = D[k] = 0.0f;
             last[k] = n_eval[k] = n_blend[k] = 0;
-            live[k] = px < V.width && (py0 + k * ROWS) < V.height;
+            live[k] = px < V.width && (py0 + 2 * k) < V.height;
             alive += live[k];
         }
         for (uint32_t start = b; start < e; start += BATCH) {
@@ -79,14 +87,21 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArg
             }
             __syncthreads();
             const int cnt = (int)min((uint32_t)BATCH, e - start);
-            if (alive > 0) {
-                for (int j = 0; j < cnt; j++) {
+            for (int m = 0; m < cnt && __any_sync(kFullMask, alive > 0); m += 32) {
+                // entries of this chunk that may reach alpha = 1/255 in the warp's band
+                const int jl = m + lane;
+                uint32_t todo = __ballot_sync(
+                    kFullMask, jl < cnt && (STATS || !splat_misses_box(s_pos[jl], s_con[jl], bx0, bx1, by0, by1)));
+                if (alive == 0) todo = 0;
+                while (todo) {
+                    const int j = m + __ffs(todo) - 1;
+                    todo &= todo - 1;
                     const float4 p = s_pos[j];
                     const float4 c = s_con[j];
                     #pragma unroll
                     for (int k = 0; k < PPT; k++) {
                         if (!live[k]) continue;
-                        const float sy = (float)(py0 + k * ROWS) + 0.5f;
+                        const float sy = (float)(py0 + 2 * k) + 0.5f;
                         const float alpha = splat_alpha(p, c, sx, sy);
                         if (STATS) n_eval[k]++;
                         if (alpha < kAlphaMin) continue;
@@ -113,7 +128,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArg
         }
         #pragma unroll
         for (int k = 0; k < PPT; k++) {
-            const int py = py0 + k * ROWS;
+            const int py = py0 + 2 * k;
             if (px >= V.width || py >= V.height) continue;
             const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
             if (STATS) {
