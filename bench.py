@@ -186,7 +186,7 @@ def build_workload(idx, scale, device):
               view_ids=torch.as_tensor(np.concatenate(vid), device=device))
     step = MappingStep(scene, cams["intr"], cams["size"], cams["viewmats"], t_rgb, t_depth, w_c=c.get("w_c", 1.0),
                        w_d=c.get("w_d", 0.5), use_gate=c.get("gate", False), keypoints=kp, pair_capacity=cap,
-                       device=device)
+                       zeta=c.get("zeta", 0.0), device=device)
     return c, step, cap
 
 
@@ -213,10 +213,14 @@ def run_plain(c, step, rs):
         vm = step.viewmats[v:v + 1]
         P = r.n_pix
         r.forward(step.params, vm)
+        k1 = 1.0 - step.zeta
         gs.gs_loss_l1(r.img["rgb"], r.img["depth"], r.img["alpha"], step.target_rgb[base:base + P],
-                      step.target_depth[base:base + P], step.w_c * P / step.rast.n_pix,
-                      step.w_d * P / step.rast.n_pix, step.use_gate, step.gamma, step.loss,
+                      step.target_depth[base:base + P], k1 * step.w_c * P / step.rast.n_pix,
+                      k1 * step.w_d * P / step.rast.n_pix, step.use_gate, step.gamma, step.loss,
                       step.d_rgb[base:base + P], step.d_depth[base:base + P])
+        if step.zeta > 0:
+            gs.gs_loss_ssim(r.img["rgb"], step.target_rgb[base:base + P], r.views, step.zeta * P / step.rast.n_pix,
+                            step.loss, step.d_rgb[base:base + P], step.ssim_ws)
         r.backward(step.params, vm, step.d_rgb[base:base + P], step.d_depth[base:base + P], None, step.grads,
                    step.d_twist[v:v + 1])
         base += P
@@ -254,6 +258,8 @@ def stage_work(w):
         # per blended entry 14 more (transmittance, weight, three colour and one depth FMA)
         "render_fwd": ("alu", 14 * E + 14 * B),
         "loss": ("hbm", P * (12 + 4 + 12 + 4 + 12 + 4)),
+        # rendered + target RGB read twice, three partial maps written and read, d_rgb read and written
+        "ssim": ("hbm", P * (24 + 36 + 36 + 24 + 24)),
         # per entry up to the last blend 14 ops to recompute alpha; per blended
         # entry ~46 ops of reverse mode (T recovery, 10 partial derivatives)
         "render_bwd": ("alu", 14 * C + 46 * B),
@@ -273,10 +279,14 @@ def crop_cams(cams, v, y0, rows):
     return scenes.cams_from([intr], [[W, rows]], cams["viewmats"][v:v + 1])
 
 
-def oracle_step(scene, cams, t_rgb, t_depth, w_c, w_d):
+def oracle_step(scene, cams, t_rgb, t_depth, w_c, w_d, zeta=0.0):
     import oracle
+    from oracle import ssim
     f = oracle.forward(scene, cams)
-    L, dC, dD = oracle.loss_l1(f["img"], t_rgb, t_depth, w_c, w_d)
+    L, dC, dD = oracle.loss_l1(f["img"], t_rgb, t_depth, (1 - zeta) * w_c, (1 - zeta) * w_d)
+    if zeta > 0:
+        Ls, gs_ = ssim.loss_ssim(f["img"]["rgb"], t_rgb, cams["size"], zeta)
+        dC = dC + gs_
     oracle.backward(scene, cams, f, dC, dD)
     return f["bins"]["n_pix"]
 
@@ -295,7 +305,7 @@ def cpu_sample(c, target_seconds, rows=None):
         t_rgb = tgt_rng.uniform(0, 1, (P, 3))
         t_depth = tgt_rng.uniform(0, 4, P)
         t0 = time.perf_counter()
-        oracle_step(c["scene"], cc, t_rgb, t_depth, c.get("w_c", 1.0), c.get("w_d", 0.5))
+        oracle_step(c["scene"], cc, t_rgb, t_depth, c.get("w_c", 1.0), c.get("w_d", 0.5), c.get("zeta", 0.0))
         return time.perf_counter() - t0, P
 
     if rows is None:

@@ -74,14 +74,19 @@ typedef struct {
 } gs_options_t;
 
 /* Output of gs_project, one entry per (view, Gaussian) at [v * n + i]:
- *   rec [., 12] floats: (u, v, z, opacity), (conicA, conicB, conicC, r0),
- *                       (red, green, blue, r1) where r0 = x0 | y0 << 16 and
- *                       r1 = x1 | y1 << 16 (bit patterns) give the inclusive
- *                       tile rectangle; 16-byte aligned;
+ *   rec [., 12] floats: (u, v, z, opacity), (conicA, conicB, conicC, du),
+ *                       (red, green, blue, dv); u, v, z are the FP32 values of
+ *                       the binning contract and du, dv the remainders
+ *                       u* - u, v* - v of the 2D mean computed in double-FP32
+ *                       arithmetic, so the compositing sees the mean to
+ *                       ~1e-7 px; 16-byte aligned;
+ *   rect [., 2] uint32: x0 | y0 << 16 and x1 | y1 << 16, the inclusive tile
+ *                       rectangle;
  *   radii [.]   int32 support radius in pixels, 0 = not drawn in that view;
  *   tiles_touched [.] uint32 number of tiles of the rectangle. */
 typedef struct {
     float *rec;
+    uint32_t *rect;
     int32_t *radii;
     uint32_t *tiles_touched;
 } gs_projected_t;
@@ -203,6 +208,21 @@ gs_status_t gs_loss_l1(const float *rgb, const float *depth, const float *alpha,
                        int32_t use_gate, float gamma, float *loss, float *d_rgb, float *d_depth,
                        void *stream);
 
+/* Bytes of workspace gs_loss_ssim needs for n_pixels (9 floats per pixel). */
+size_t gs_ssim_workspace_size(int64_t n_pixels);
+
+/* SSIM term of the mapping loss (Sec. 3.4: L_m = (1 - zeta)(w4 L1(D) +
+ * w5 L1(C)) + zeta L_SSIM, zeta = 0.3).  The paper does not define its SSIM;
+ * this is the usual one: per colour channel, moments under an 11x11 Gaussian
+ * window (sigma 1.5, normalised, zero padding), C1 = 0.01^2, C2 = 0.03^2.
+ * Adds weight * (1 - mean SSIM) over all pixels and channels of the views to
+ * *loss and its gradient to d_rgb [P,3] (+=, so it sums with gs_loss_l1's).
+ * rgb, target_rgb [P,3] device; views host; workspace device, >=
+ * gs_ssim_workspace_size(P) bytes. */
+gs_status_t gs_loss_ssim(const float *rgb, const float *target_rgb, const gs_view_t *views, int32_t n_views,
+                         float weight, float *loss, float *d_rgb, void *workspace, size_t workspace_bytes,
+                         void *stream);
+
 /* Bytes of the per-(view, Gaussian) 2D gradient buffer: n_views * n * 12 floats. */
 size_t gs_grad2d_size(int64_t n, int32_t n_views);
 
@@ -268,6 +288,62 @@ gs_status_t gs_adam_step(float *param, const float *grad, float *m, float *v, co
 /* Pose update of the tracking loop: E_v <- Exp(xi_v) E_v, then xi_v <- 0, for
  * viewmats [n_views, 12] and twist [n_views, 6] (device). */
 gs_status_t gs_pose_update(float *viewmats, float *twist, int32_t n_views, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Map maintenance and keyframe choice                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of workspace of gs_densify / gs_prune_select for n_items pixels or
+ * Gaussians. */
+size_t gs_select_workspace_size(int64_t n_items);
+
+/* Densification (Sec. 3.4 "Densification", Eq. d: d = r f).  Every pixel of
+ * the views whose border mask alpha [P] is below threshold and whose sensor
+ * depth target_depth [P] is positive gets one new Gaussian, appended in pixel
+ * order at indices n_old, n_old + 1, ... of the parameter arrays (capacity
+ * rows each): mean = back-projection of the pixel centre at that depth through
+ * the view's pose viewmats [n_views,12]; log-scales = log(d / fx) on all axes
+ * (radius of one pixel on the image plane); quaternion (1,0,0,0); SH degree-0
+ * band = (rgb - 0.5) / C0 from target_rgb [P,3], higher bands 0; opacity logit
+ * as given.  *n_added (device) receives the number written; pixels beyond the
+ * capacity are dropped and flagged in *status (device, may be NULL).  The
+ * gs_param_grads_t struct is used here for its five writable pointers. */
+gs_status_t gs_densify(const float *alpha, const float *target_rgb, const float *target_depth,
+                       const gs_view_t *views, const float *viewmats, int32_t n_views, float threshold,
+                       float opacity_logit, gs_param_grads_t *params, int32_t sh_degree, int64_t n_old,
+                       int64_t capacity, uint32_t *n_added, uint32_t *status, void *workspace,
+                       size_t workspace_bytes, void *stream);
+
+/* Pruning (Sec. 3.4 "Gaussian Pruning", tau = 0.005 in Table hyper): a
+ * Gaussian is kept when its opacity sigmoid(logit) >= tau, decided on the
+ * logit against log(tau / (1 - tau)) rounded once to FP32.  Writes
+ * new_index [n] (its row after compaction, order kept, or -1) and *n_kept
+ * (device).  tau in (0, 1). */
+gs_status_t gs_prune_select(const float *opacity_logit, int64_t n, float tau, int32_t *new_index,
+                            uint32_t *n_kept, void *workspace, size_t workspace_bytes, void *stream);
+
+#define GS_MAX_COMPACT_ARRAYS 16
+
+/* One array of rows to compact: row i of src (row_floats floats) goes to row
+ * new_index[i] of dst when new_index[i] >= 0.  src and dst must not alias. */
+typedef struct {
+    const float *src;
+    float *dst;
+    int32_t row_floats;
+} gs_rows_t;
+
+/* Compacts up to GS_MAX_COMPACT_ARRAYS arrays (parameters and optimiser state)
+ * with the indices of gs_prune_select, in one launch.  arrays: host. */
+gs_status_t gs_compact_rows(const int32_t *new_index, int64_t n, const gs_rows_t *arrays, int32_t n_arrays,
+                            void *stream);
+
+/* View point selection (Sec. 3.3): keyframe i (i >= 1) is selected when
+ * beta <= matches[i] < alpha * totals[i], with matches[i] = M_{i-1,i} the
+ * feature matches between keyframes i-1 and i and totals[i] = T_{i-1,i} the
+ * total matches of keyframe i-1 (alpha = 0.75, beta = 20 in Table hyper); the
+ * first keyframe is always selected.  Host arrays; writes selected [n] as 0/1. */
+gs_status_t gs_select_views(const int32_t *matches, const int32_t *totals, int32_t n, float alpha, int32_t beta,
+                            int32_t *selected);
 
 #ifdef __cplusplus
 }

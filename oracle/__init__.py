@@ -192,7 +192,7 @@ def project64(params, cams, geom, blur=0.3):
     return out
 
 
-def render(cams, proj, bins, n, tile=(16, 16), margin_alpha=2e-5, margin_T=2e-4):
+def render(cams, proj, bins, n, tile=(16, 16), margin_alpha=2e-5, margin_T=2e-5):
     """FP64 compositing of RGB, depth and alpha (border mask) for all views."""
     L = _L()
     views = make_views(cams)

@@ -508,13 +508,44 @@ static void orc_view_tiles(const orc_view_t *V, int tw, int th, int *ntx, int *n
     *nty = (V->height + th - 1) / th;
 }
 
+/* One unit in the last place of x in FP32. */
+static double orc_ulp32(double x)
+{
+    int e;
+    if (x == 0.0) return ldexp(1.0, -149);
+    frexp(x, &e);
+    return ldexp(1.0, e - 24);
+}
+
+/* Bound on how far an FP32 evaluation of the exponent may be from this FP64
+ * one: the offset d = mean - pixel is rounded to FP32 (one ulp of dx, dy, plus
+ * 1e-6 px for a mean carried in double-FP32, moves the exponent by
+ * |dpower/dx| and |dpower/dy| times that), and the quadratic form is evaluated
+ * from an FP32 conic whose relative error grows with the eccentricity
+ * kappa = lambda_max / lambda_min of the 2D covariance (the determinant
+ * cancels), bounded by 1e-6 (4 + kappa) times the magnitude of its terms. */
+static double orc_power_uncertainty(const double *r, double dx, double dy)
+{
+    double A = r[3], B = r[4], C = r[5];
+    double gu = fabs(A * dx + B * dy), gv = fabs(B * dx + C * dy);
+    double mag = 0.5 * (A * dx * dx + C * dy * dy) + fabs(B * dx * dy);
+    double ca = r[10], cb = r[11], cc = r[12];
+    double mid = 0.5 * (ca + cc), rad = sqrt(0.25 * (ca - cc) * (ca - cc) + cb * cb);
+    double lmin = mid - rad > 1e-30 ? mid - rad : 1e-30;
+    double kappa = (mid + rad) / lmin;
+    return gu * (orc_ulp32(dx) + 1e-6) + gv * (orc_ulp32(dy) + 1e-6) + 1e-6 * (4.0 + kappa) * mag + 1e-6;
+}
+
 /* Composites every pixel of every view front to back over its tile's list:
  *   alpha_i = min(0.99, o_i exp(-1/2 d^T conic d)), skipped if < 1/255;
  *   stop before blending i when T (1 - alpha_i) < 1e-4;
  *   C += c_i alpha_i T, D += z_i alpha_i T, T *= (1 - alpha_i); A = 1 - T.
  * Pixel (px, py) is sampled at (px + 0.5, py + 0.5).  Images are stored per
  * view at pix_base[v] + py * width + px.  n_contrib = number of list entries
- * consumed up to and including the last blended one. */
+ * consumed up to and including the last blended one.
+ * A pixel is flagged when a decision's FP64 quantity lies within the margin
+ * plus the FP32 uncertainty (orc_power_uncertainty, accumulated along the ray
+ * for the transmittance) of its threshold. */
 void orc_render(int32_t n_views, const orc_view_t *views, int64_t n,
                 const double *proj, int32_t tw, int32_t th, const int32_t *tile_base,
                 const int64_t *pix_base, const uint32_t *vals, const uint32_t *ranges,
@@ -530,7 +561,7 @@ void orc_render(int32_t n_views, const orc_view_t *views, int64_t n,
                 int64_t pix = pix_base[v] + (int64_t)py * V->width + px;
                 int64_t tile = tile_base[v] + (py / th) * ntx + (px / tw);
                 uint32_t b = ranges[2 * tile], e = ranges[2 * tile + 1];
-                double T = 1.0, C[3] = {0, 0, 0}, D = 0.0;
+                double T = 1.0, C[3] = {0, 0, 0}, D = 0.0, lnT_unc = 0.0;
                 int32_t last = 0, fl = 0;
                 double sx = px + 0.5, sy = py + 0.5;
                 for (uint32_t k = b; k < e; k++) {
@@ -538,16 +569,20 @@ void orc_render(int32_t n_views, const orc_view_t *views, int64_t n,
                     double dx = r[0] - sx, dy = r[1] - sy;
                     double power = -0.5 * (r[3] * dx * dx + r[5] * dy * dy) - r[4] * dx * dy;
                     double araw = r[6] * exp(power);
-                    if (fabs(araw - ORC_ALPHA_MAX) <= mg.margin_alpha * ORC_ALPHA_MAX) fl |= ORC_FLAG_ALPHA_MAX;
+                    double unc = orc_power_uncertainty(r, dx, dy);
+                    if (fabs(log(araw / ORC_ALPHA_MAX)) <= mg.margin_alpha + unc) fl |= ORC_FLAG_ALPHA_MAX;
                     double a = araw < ORC_ALPHA_MAX ? araw : ORC_ALPHA_MAX;
-                    if (fabs(a - ORC_ALPHA_MIN) <= mg.margin_alpha * ORC_ALPHA_MIN) fl |= ORC_FLAG_ALPHA_MIN;
+                    if (fabs(log(a / ORC_ALPHA_MIN)) <= mg.margin_alpha + unc) fl |= ORC_FLAG_ALPHA_MIN;
                     if (a < ORC_ALPHA_MIN) continue;
                     double tT = T * (1.0 - a);
-                    if (fabs(tT - ORC_T_MIN) <= mg.margin_T * ORC_T_MIN) fl |= ORC_FLAG_T_MIN;
+                    /* FP32 error of the factor (1 - alpha) and of the product's rounding */
+                    double step_unc = a / (1.0 - a) * unc + 2.0e-7;
+                    if (fabs(log(tT / ORC_T_MIN)) <= mg.margin_T + lnT_unc + step_unc) fl |= ORC_FLAG_T_MIN;
                     if (tT < ORC_T_MIN) break;
                     for (int ch = 0; ch < 3; ch++) C[ch] += r[7 + ch] * a * T;
                     D += r[2] * a * T;
                     T = tT;
+                    lnT_unc += step_unc;
                     last = (int32_t)(k - b + 1);
                 }
                 for (int ch = 0; ch < 3; ch++) rgb[3 * pix + ch] = C[ch];

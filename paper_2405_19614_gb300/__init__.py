@@ -20,8 +20,9 @@ from ._lib import (GS_MAX_ADAM_GROUPS, GS_MAX_VIEWS, GS_TILE, GsAdamGroup, GsBin
                    GsParamGrads, GsParams, GsProjected, GsView, check)
 
 __all__ = ["gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd", "gs_render_stats", "gs_set_render_variants",
-           "gs_get_render_variants", "gs_loss_l1", "gs_render_bwd", "gs_render_bwd_splats",
-           "gs_project_bwd", "gs_reproj_loss_grad", "gs_adam_step", "gs_pose_update", "Rasterizer", "rasterize",
+           "gs_get_render_variants", "gs_loss_l1", "gs_loss_ssim", "gs_render_bwd", "gs_render_bwd_splats",
+           "gs_project_bwd", "gs_reproj_loss_grad", "gs_adam_step", "gs_pose_update", "gs_densify",
+           "gs_prune_select", "gs_compact_rows", "gs_select_views", "Rasterizer", "rasterize",
            "GsError", "lib"]
 
 
@@ -78,13 +79,13 @@ def _gref(grads):
 
 def gs_project(params, views, viewmats, proj, near_z=0.2, blur=0.3, stream=None):
     opt = GsOptions(near_z, blur)
-    pj = GsProjected(_ptr(proj["rec"]), _ptr(proj["radii"]), _ptr(proj["tiles_touched"]))
+    pj = _proj(proj)
     check(lib().gs_project(ctypes.byref(_params(params)), views, _ptr(viewmats), len(views), ctypes.byref(opt),
                            ctypes.byref(pj), _stream(stream)), "gs_project")
 
 
 def _proj(proj):
-    return GsProjected(_ptr(proj["rec"]), _ptr(proj["radii"]), _ptr(proj["tiles_touched"]))
+    return GsProjected(_ptr(proj["rec"]), _ptr(proj["rect"]), _ptr(proj["radii"]), _ptr(proj["tiles_touched"]))
 
 
 def _bins(bins):
@@ -144,6 +145,16 @@ def gs_loss_l1(rgb, depth, alpha, target_rgb, target_depth, w_c, w_d, use_gate, 
                            _stream(stream)), "gs_loss_l1")
 
 
+def gs_ssim_workspace_size(n_pixels):
+    return int(lib().gs_ssim_workspace_size(int(n_pixels)))
+
+
+def gs_loss_ssim(rgb, target_rgb, views, weight, loss, d_rgb, workspace, stream=None):
+    """Adds weight * (1 - mean SSIM) to loss and its gradient to d_rgb (+=)."""
+    check(lib().gs_loss_ssim(_ptr(rgb), _ptr(target_rgb), views, len(views), float(weight), _ptr(loss), _ptr(d_rgb),
+                             _ptr(workspace), workspace.numel(), _stream(stream)), "gs_loss_ssim")
+
+
 def gs_render_bwd_splats(proj, n, bins, views, img, d_rgb, d_depth, d_alpha, grad2d, work_counter, stream=None):
     check(lib().gs_render_bwd_splats(ctypes.byref(_proj(proj)), n, ctypes.byref(_bins(bins)), views, len(views),
                                      ctypes.byref(_img(img)), _ptr(d_rgb), _ptr(d_depth), _ptr(d_alpha),
@@ -185,6 +196,48 @@ def gs_pose_update(viewmats, twist, stream=None):
     check(lib().gs_pose_update(_ptr(viewmats), _ptr(twist), viewmats.shape[0], _stream(stream)), "gs_pose_update")
 
 
+def gs_select_workspace_size(n_items):
+    return int(lib().gs_select_workspace_size(int(n_items)))
+
+
+def gs_densify(alpha, target_rgb, target_depth, views, viewmats, threshold, opacity_logit, params, n_old, capacity,
+               n_added, workspace, status=None, stream=None):
+    """Appends one Gaussian per pixel with alpha < threshold and positive depth
+    (Sec. 3.4 densification); params: dict of arrays with room for capacity rows."""
+    pg = _grads(params)
+    check(lib().gs_densify(_ptr(alpha), _ptr(target_rgb), _ptr(target_depth), views, _ptr(viewmats), len(views),
+                           float(threshold), float(opacity_logit), ctypes.byref(pg), int(params["sh_degree"]),
+                           int(n_old), int(capacity), _ptr(n_added), _ptr(status), _ptr(workspace),
+                           workspace.numel(), _stream(stream)), "gs_densify")
+
+
+def gs_prune_select(opacity_logit, tau, new_index, n_kept, workspace, stream=None):
+    check(lib().gs_prune_select(_ptr(opacity_logit), opacity_logit.numel(), float(tau), _ptr(new_index),
+                                _ptr(n_kept), _ptr(workspace), workspace.numel(), _stream(stream)),
+          "gs_prune_select")
+
+
+def gs_compact_rows(new_index, pairs, stream=None):
+    """pairs: list of (src, dst) tensors with rows along dim 0."""
+    arr = (_lib.GsRows * len(pairs))()
+    for k, (src, dst) in enumerate(pairs):
+        arr[k].src = _ptr(src)
+        arr[k].dst = _ptr(dst)
+        arr[k].row_floats = int(src.numel() // max(src.shape[0], 1))
+    check(lib().gs_compact_rows(_ptr(new_index), new_index.numel(), arr, len(pairs), _stream(stream)),
+          "gs_compact_rows")
+
+
+def gs_select_views(matches, totals, alpha=0.75, beta=20):
+    """Host: 0/1 selection of keyframes (Sec. 3.3 view point selection)."""
+    n = len(matches)
+    M = (ctypes.c_int32 * n)(*[int(x) for x in matches])
+    T = (ctypes.c_int32 * n)(*[int(x) for x in totals])
+    out = (ctypes.c_int32 * n)()
+    check(lib().gs_select_views(M, T, n, float(alpha), int(beta), out), "gs_select_views")
+    return [int(x) for x in out]
+
+
 # --------------------------------------------------------------------------
 # buffer owner for one configuration
 # --------------------------------------------------------------------------
@@ -218,8 +271,8 @@ class Rasterizer:
         d = torch.device(device)
         R = self.V * self.n
         i32, f32 = torch.int32, torch.float32
-        self.proj = dict(rec=torch.empty(R * 12, dtype=f32, device=d), radii=torch.empty(R, dtype=i32, device=d),
-                         tiles_touched=torch.empty(R, dtype=i32, device=d))
+        self.proj = dict(rec=torch.empty(R * 12, dtype=f32, device=d), rect=torch.empty(R, 2, dtype=i32, device=d),
+                         radii=torch.empty(R, dtype=i32, device=d), tiles_touched=torch.empty(R, dtype=i32, device=d))
         self.bins = dict(keys=torch.empty(self.capacity, dtype=torch.int64, device=d),
                          vals=torch.empty(self.capacity, dtype=i32, device=d),
                          ranges=torch.zeros(self.n_tiles, 2, dtype=i32, device=d),

@@ -39,7 +39,7 @@ class GsOptions(ctypes.Structure):
 
 
 class GsProjected(ctypes.Structure):
-    _fields_ = [("rec", c_p), ("radii", c_p), ("tiles_touched", c_p)]
+    _fields_ = [("rec", c_p), ("rect", c_p), ("radii", c_p), ("tiles_touched", c_p)]
 
 
 class GsBins(ctypes.Structure):
@@ -49,6 +49,10 @@ class GsBins(ctypes.Structure):
 
 class GsImage(ctypes.Structure):
     _fields_ = [("rgb", c_p), ("depth", c_p), ("alpha", c_p), ("final_T", c_p), ("n_contrib", c_p)]
+
+
+class GsRows(ctypes.Structure):
+    _fields_ = [("src", c_p), ("dst", c_p), ("row_floats", c_i32)]
 
 
 class GsAdamGroup(ctypes.Structure):
@@ -69,6 +73,8 @@ SIGNATURES = {
     "gs_set_render_variants": ([c_i32, c_i32], c_i32),
     "gs_get_render_variants": ([P(c_i32), P(c_i32), P(c_i32), P(c_i32)], c_i32),
     "gs_loss_l1": ([c_p, c_p, c_p, c_p, c_p, c_i64, c_f, c_f, c_i32, c_f, c_p, c_p, c_p, c_p], c_i32),
+    "gs_ssim_workspace_size": ([c_i64], c_sz),
+    "gs_loss_ssim": ([c_p, c_p, P(GsView), c_i32, c_f, c_p, c_p, c_p, c_sz, c_p], c_i32),
     "gs_grad2d_size": ([c_i64, c_i32], c_sz),
     "gs_render_bwd_splats": ([P(GsProjected), c_i64, P(GsBins), P(GsView), c_i32, P(GsImage), c_p, c_p, c_p,
                               c_p, c_p, c_p], c_i32),
@@ -79,6 +85,12 @@ SIGNATURES = {
     "gs_reproj_loss_grad": ([c_p, c_p, c_p, c_i64, P(GsView), c_p, c_i32, c_f, c_f, c_p, c_p, c_p], c_i32),
     "gs_adam_step": ([c_p, c_p, c_p, c_p, P(GsAdamGroup), c_i32, c_f, c_f, c_f, c_p, c_p], c_i32),
     "gs_pose_update": ([c_p, c_p, c_i32, c_p], c_i32),
+    "gs_select_workspace_size": ([c_i64], c_sz),
+    "gs_densify": ([c_p, c_p, c_p, P(GsView), c_p, c_i32, c_f, c_f, P(GsParamGrads), c_i32, c_i64, c_i64, c_p, c_p,
+                    c_p, c_sz, c_p], c_i32),
+    "gs_prune_select": ([c_p, c_i64, c_f, c_p, c_p, c_p, c_sz, c_p], c_i32),
+    "gs_compact_rows": ([c_p, c_i64, P(GsRows), c_i32, c_p], c_i32),
+    "gs_select_views": ([c_p, c_p, c_i32, c_f, c_i32, c_p], c_i32),
 }
 
 _lib = None

@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(1024) scan_sums_kernel(uint64_t *sums, int64_t
 // shared memory (with each record's depth bits, rectangle, view and index),
 // then its threads walk the chunk's output positions in order, each finding
 // its record by binary search, so consecutive threads write consecutive pairs.
-__global__ void __launch_bounds__(kEmitThreads) emit_kernel(const float *__restrict__ rec, const uint32_t *__restrict__ tt,
+__global__ void __launch_bounds__(kEmitThreads) emit_kernel(const float *__restrict__ rec, const uint2 *__restrict__ rect,
+                                                            const uint32_t *__restrict__ tt,
                                                             int64_t n, int64_t total, ViewTable vt,
                                                             const uint64_t *__restrict__ block_off, uint64_t *keys,
                                                             uint32_t *vals, int64_t cap, uint32_t *status)
@@ -124,8 +125,9 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(const float *__restr
             s_v[r] = (uint16_t)v;
             s_g[r] = (uint32_t)(o - (int64_t)v * n);
             s_z[r] = __float_as_uint(rec[12 * o + 2]);
-            s_r0[r] = __float_as_uint(rec[12 * o + 7]);
-            s_r1[r] = __float_as_uint(rec[12 * o + 11]);
+            const uint2 rr = rect[o];
+            s_r0[r] = rr.x;
+            s_r1[r] = rr.y;
         }
     }
     if (threadIdx.x == 0) s_excl[kEmitChunk] = (uint32_t)block_total;
@@ -234,7 +236,7 @@ extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const 
         if (cudaMemsetAsync(bins->n_pairs, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
         return GS_OK;
     }
-    if (!proj->rec || !proj->tiles_touched) return GS_ERR_INVALID_ARG;
+    if (!proj->rec || !proj->rect || !proj->tiles_touched) return GS_ERR_INVALID_ARG;
 
     const int n_bits = 32 + ceil_log2(vt.n_tiles_total);
     const int P = sort_passes(n_bits);
@@ -247,7 +249,8 @@ extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const 
     const int64_t nb = (total + kEmitChunk - 1) / kEmitChunk;
     count_reduce_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(proj->tiles_touched, total, w.block_sums);
     scan_sums_kernel<<<1, 1024, 0, s>>>(w.block_sums, nb, cap, bins->n_pairs, bins->status);
-    emit_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(proj->rec, proj->tiles_touched, n, total, vt, w.block_sums,
+    emit_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(proj->rec, reinterpret_cast<const uint2 *>(proj->rect),
+                                                      proj->tiles_touched, n, total, vt, w.block_sums,
                                                       ek, ev, cap, bins->status);
     st = launch_status();
     if (st != GS_OK) return st;

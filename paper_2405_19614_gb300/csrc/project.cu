@@ -154,12 +154,59 @@ __device__ __forceinline__ bool geometry(const float m[3], const float ls[3], co
 #undef SUB
 #undef DIV
 
+// Error-free transformations for double-FP32 arithmetic (hi + lo).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// r0 m0 + r1 m1 + r2 m2 + t as hi + lo (compensated dot product).
+__device__ __forceinline__ void dot3_plus(const float *r, const float *m, float t, float &hi, float &lo)
+{
+    float p, e, s, es;
+    two_prod(r[0], m[0], s, lo);
+    two_prod(r[1], m[1], p, e);
+    two_sum(s, p, s, es);
+    lo += e + es;
+    two_prod(r[2], m[2], p, e);
+    two_sum(s, p, s, es);
+    lo += e + es;
+    two_sum(s, t, s, es);
+    lo += es;
+    hi = s;
+}
+
+// Remainder (f * x / z + c) - ref of the pixel coordinate, with x and z given
+// as hi + lo pairs, in double-FP32 arithmetic.
+__device__ __forceinline__ float pixel_remainder(float f, float xh, float xl, float zh, float zl, float c, float ref)
+{
+    const float q = __fdiv_rn(xh, zh);
+    // x - q z, exactly for the hi parts, then the lo parts
+    const float r = __fmaf_rn(-q, zh, xh) + (xl - q * zl);
+    const float ql = r / zh;
+    float m, me;
+    two_prod(f, q, m, me);
+    const float ml = me + f * ql;
+    float s, se;
+    two_sum(m, c, s, se);
+    return (s - ref) + (se + ml);
+}
+
 struct ProjectArgs {
     const float *means, *log_scales, *quats, *opacity_logit, *sh;
     const float *viewmats;
     int64_t n;
     float near_z, blur;
     float4 *rec;
+    uint2 *rect;
     int32_t *radii;
     uint32_t *tiles_touched;
 };
@@ -235,11 +282,21 @@ __global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable v
             for (int k = 0; k < K; k++) acc += sh[3 * k + ch] * Y[k];
             col[ch] = fmaxf(acc, 0.0f);
         }
+        // the 2D mean to ~1e-7 px: camera point and projection in double-FP32
+        const float *E = s_E[v];
+        float xh, xl, yh, yl, zh, zl;
+        dot3_plus(E + 0, m, E[3], xh, xl);
+        dot3_plus(E + 4, m, E[7], yh, yl);
+        dot3_plus(E + 8, m, E[11], zh, zl);
+        const ViewInfo &V = vt.v[v];
+        const float du = pixel_remainder(V.fx, xh, xl, zh, zl, V.cx, g.u);
+        const float dv = pixel_remainder(V.fy, yh, yl, zh, zl, V.cy, g.v);
         const uint32_t r0 = (uint32_t)g.x0 | ((uint32_t)g.y0 << 16);
         const uint32_t r1 = (uint32_t)g.x1 | ((uint32_t)g.y1 << 16);
         a.rec[3 * o + 0] = make_float4(g.u, g.v, g.z, opacity);
-        a.rec[3 * o + 1] = make_float4(g.cc * inv, -g.cb * inv, g.ca * inv, __uint_as_float(r0));
-        a.rec[3 * o + 2] = make_float4(col[0], col[1], col[2], __uint_as_float(r1));
+        a.rec[3 * o + 1] = make_float4(g.cc * inv, -g.cb * inv, g.ca * inv, du);
+        a.rec[3 * o + 2] = make_float4(col[0], col[1], col[2], dv);
+        a.rect[o] = make_uint2(r0, r1);
         a.radii[o] = g.radius;
         a.tiles_touched[o] = (uint32_t)((g.x1 - g.x0 + 1) * (g.y1 - g.y0 + 1));
     }
@@ -259,8 +316,9 @@ extern "C" gs_status_t gs_project(const gs_params_t *params, const gs_view_t *vi
     if (st != GS_OK) return st;
     if (params->n == 0) return GS_OK;
     if (!params->means || !params->log_scales || !params->quats || !params->opacity_logit || !params->sh ||
-        !out->rec || !out->radii || !out->tiles_touched)
+        !out->rec || !out->rect || !out->radii || !out->tiles_touched)
         return GS_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(out->rect) & 7) return GS_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(out->rec) & 15) || (reinterpret_cast<uintptr_t>(params->quats) & 15))
         return GS_ERR_INVALID_ARG;
     if ((params->sh_degree == 1 || params->sh_degree == 3) && (reinterpret_cast<uintptr_t>(params->sh) & 15))
@@ -276,6 +334,7 @@ extern "C" gs_status_t gs_project(const gs_params_t *params, const gs_view_t *vi
     a.near_z = opt->near_z;
     a.blur = opt->blur;
     a.rec = reinterpret_cast<float4 *>(out->rec);
+    a.rect = reinterpret_cast<uint2 *>(out->rect);
     a.radii = out->radii;
     a.tiles_touched = out->tiles_touched;
     const int threads = 128;

@@ -8,29 +8,48 @@ namespace gs {
 // alpha_i = min(0.99, o_i exp(power_i)) at the pixel centre (sx, sy).  The
 // forward and backward kernels both go through splat_power and this exact
 // expression, so they take the same skip decisions bit for bit.
-__device__ __forceinline__ float splat_alpha(const float4 &p, const float4 &c, float sx, float sy)
+__device__ __forceinline__ float splat_alpha(const float4 &p, const float4 &c, const float4 &col, float sx, float sy)
 {
     float dx, dy;
-    const float power = splat_power(p.x, p.y, c.x, c.y, c.z, sx, sy, &dx, &dy);
+    const float power = splat_power(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx, sy, &dx, &dy);
     return fminf(kAlphaMax, __fmul_rn(p.w, __expf(power)));
 }
 
+// Minimum over t in [t0, t1] of P s^2 + 2 B s t + Q t^2 for a fixed s (Q > 0):
+// the unconstrained minimiser t = -B s / Q clamped to the interval.  *mag
+// receives the sum of the magnitudes of the three terms at that point.
+__device__ __forceinline__ float edge_min(float P, float B, float Q, float s, float t0, float t1, float *mag)
+{
+    const float t = fminf(fmaxf(-B * s / Q, t0), t1);
+    const float a = P * s * s, b = 2.0f * B * s * t, c = Q * t * t;
+    *mag = fmaxf(*mag, a + fabsf(b) + c);
+    return a + b + c;
+}
+
 // Conservative test that a splat cannot reach alpha >= 1/255 anywhere in a box
-// of pixel centres [x0, x1] x [y0, y1]: for every sample s in the box,
-//   power(s) = -1/2 (s - mu)^T Q (s - mu) <= -1/2 lambda_min(Q) dist(mu, box)^2,
-// so alpha <= o exp(-1/2 lambda_min dist^2).  The entry is dropped when that
-// bound is below 1/255 by a factor e^-0.001, a margin far larger than the FP32
-// rounding of the per-pixel evaluation, so a dropped entry is one the per-pixel
-// test would have skipped: results are unchanged, only work is saved.
+// of pixel centres [x0, x1] x [y0, y1].  With d = pixel - mean, alpha at a
+// pixel is min(0.99, o exp(-q(d)/2)), q(d) = A dx^2 + 2 B dx dy + C dy^2 (the
+// conic is positive definite).  q is convex with minimum 0 at the mean, so over
+// a box not containing the mean its minimum lies on one of the four edges, where
+// it is a one-dimensional quadratic; the box minimum bounds q at every pixel
+// centre inside.  The entry is dropped when o exp(-q_min/2) is below 1/255 by a
+// factor e^-(0.001 + 2e-6 M), M the magnitude of the terms of q: more than the
+// FP32 rounding of this bound and of the per-pixel evaluation together, so a
+// dropped entry is one the per-pixel test would have skipped: results are
+// unchanged, only work is saved.  (A bound through the smallest eigenvalue of
+// the conic is weaker and, for elongated splats, cancels badly in FP32.)
 __device__ __forceinline__ bool splat_misses_box(const float4 &p, const float4 &c, float x0, float x1, float y0,
                                                  float y1)
 {
-    const float dx = fmaxf(fmaxf(x0 - p.x, p.x - x1), 0.0f);
-    const float dy = fmaxf(fmaxf(y0 - p.y, p.y - y1), 0.0f);
-    const float h = 0.5f * (c.x - c.z);
-    const float lmin = fmaxf(0.5f * (c.x + c.z) - sqrtf(h * h + c.y * c.y), 0.0f);
-    // alpha bound < (1/255) e^-0.001  <=>  -1/2 lmin d^2 < -ln(255 o) - 0.001
-    return -0.5f * lmin * (dx * dx + dy * dy) < -__logf(255.0f * p.w) - 1e-3f;
+    const float ex0 = x0 - p.x, ex1 = x1 - p.x, ey0 = y0 - p.y, ey1 = y1 - p.y;
+    float q = 0.0f, mag = 0.0f;
+    if (!(ex0 <= 0.0f && ex1 >= 0.0f && ey0 <= 0.0f && ey1 >= 0.0f)) {
+        const float A = c.x, B = c.y, C = c.z;
+        q = fminf(fminf(edge_min(A, B, C, ex0, ey0, ey1, &mag), edge_min(A, B, C, ex1, ey0, ey1, &mag)),
+                  fminf(edge_min(C, B, A, ey0, ex0, ex1, &mag), edge_min(C, B, A, ey1, ex0, ex1, &mag)));
+    }
+    // alpha bound < (1/255) e^-margin  <=>  -q/2 < -ln(255 o) - margin
+    return -0.5f * q < -__logf(255.0f * p.w) - (1e-3f + 2e-6f * mag);
 }
 
 // Kernel variants (pixels per thread x staged batch) the autotuner picks from.

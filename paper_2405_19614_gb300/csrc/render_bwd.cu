@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
                         if (pos >= last[k]) continue;
                         const float sy = (float)(py0 + 2 * k) + 0.5f;
                         float dx, dy;
-                        const float power = splat_power(p.x, p.y, c.x, c.y, c.z, sx, sy, &dx, &dy);
+                        const float power = splat_power(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx, sy, &dx, &dy);
                         const float g = __expf(power);
                         const float araw = __fmul_rn(p.w, g);
                         const float alpha = fminf(kAlphaMax, araw);

@@ -98,11 +98,12 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArg
                     todo &= todo - 1;
                     const float4 p = s_pos[j];
                     const float4 c = s_con[j];
+                    const float4 col = s_col[j];
                     #pragma unroll
                     for (int k = 0; k < PPT; k++) {
                         if (!live[k]) continue;
                         const float sy = (float)(py0 + 2 * k) + 0.5f;
-                        const float alpha = splat_alpha(p, c, sx, sy);
+                        const float alpha = splat_alpha(p, c, col, sx, sy);
                         if (STATS) n_eval[k]++;
                         if (alpha < kAlphaMin) continue;
                         const float tT = T[k] * (1.0f - alpha);
@@ -113,7 +114,6 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArg
                         }
                         if (STATS) n_blend[k]++;
                         const float w = alpha * T[k];
-                        const float4 col = s_col[j];
                         C0[k] += col.x * w;
                         C1[k] += col.y * w;
                         C2[k] += col.z * w;

@@ -1,10 +1,11 @@
 """One mapping / pose-refinement iteration over a batch of keyframes, built from
 the C-ABI calls (Sec. 3.4 online mapping; Sec. 3.3 joint optimisation).
 
-A step is: project (a1) -> bin + sort (a2-a4) -> composite (a5) -> L1 loss and
-gate (a6) -> backward of the compositing and projection, with per-view twist
-gradients (a7, a8) -> keypoint re-projection term (a9) -> Adam on all Gaussian
-parameters (a10).  Everything is enqueued on one stream without a host
+A step is: project (a1) -> bin + sort (a2-a4) -> composite (a5) -> mapping
+loss L_m = (1 - zeta)(w4 L1(D) + w5 L1(C)) + zeta L_SSIM with the optional gate
+(a6 and the SSIM term) -> backward of the compositing and projection, with
+per-view twist gradients (a7, a8) -> keypoint re-projection term (a9) -> Adam on
+all Gaussian parameters (a10).  Everything is enqueued on one stream without a host
 synchronisation, so a step can be captured in a CUDA graph and replayed.
 """
 from __future__ import annotations
@@ -12,7 +13,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (Rasterizer, gs_adam_step, gs_loss_l1, gs_reproj_loss_grad)
+from . import (Rasterizer, gs_adam_step, gs_loss_l1, gs_loss_ssim, gs_reproj_loss_grad, gs_ssim_workspace_size)
 
 PARAM_ORDER = ("means", "log_scales", "quats", "opacity_logit", "sh")
 DEFAULT_LR = dict(means=1.6e-4, log_scales=5e-3, quats=1e-3, opacity_logit=5e-2, sh=2.5e-3)
@@ -58,7 +59,7 @@ class MappingStep:
 
     def __init__(self, scene, intr, size, viewmats, target_rgb, target_depth, w_c=1.0, w_d=0.5,
                  use_gate=False, gamma=0.99, keypoints=None, w_rpj=1.5, lrs=None, pair_capacity=None,
-                 device="cuda"):
+                 zeta=0.0, device="cuda"):
         dev = torch.device(device)
         self.flat = FlatParams(scene, dev)
         self.params = self.flat.views()
@@ -79,6 +80,9 @@ class MappingStep:
         self.loss = torch.zeros(1, device=dev)
         self.d_twist = torch.zeros(self.rast.V, 6, device=dev)
         self.w_c, self.w_d, self.use_gate, self.gamma = float(w_c), float(w_d), bool(use_gate), float(gamma)
+        self.zeta = float(zeta)
+        self.ssim_ws = (torch.empty(gs_ssim_workspace_size(P), dtype=torch.uint8, device=dev)
+                        if self.zeta > 0 else None)
         self.keypoints = keypoints  # dict(points [n,3], obs [n,2], view_ids [n]) on the device
         self.w_rpj = float(w_rpj)
         self.optimise_params = True
@@ -117,9 +121,15 @@ class MappingStep:
         gs_render_fwd(r.proj, r.n, r.bins, r.views, r.img, r.work_counter, stream)
         close(tok)
         tok = mark("loss")
-        gs_loss_l1(r.img["rgb"], r.img["depth"], r.img["alpha"], self.target_rgb, self.target_depth, self.w_c,
-                   self.w_d, self.use_gate, self.gamma, self.loss, self.d_rgb, self.d_depth, stream)
+        k1 = 1.0 - self.zeta
+        gs_loss_l1(r.img["rgb"], r.img["depth"], r.img["alpha"], self.target_rgb, self.target_depth, k1 * self.w_c,
+                   k1 * self.w_d, self.use_gate, self.gamma, self.loss, self.d_rgb, self.d_depth, stream)
         close(tok)
+        if self.zeta > 0:
+            tok = mark("ssim")
+            gs_loss_ssim(r.img["rgb"], self.target_rgb, r.views, self.zeta, self.loss, self.d_rgb, self.ssim_ws,
+                         stream)
+            close(tok)
         tok = mark("render_bwd")
         gs_render_bwd_splats(r.proj, r.n, r.bins, r.views, r.img, self.d_rgb, self.d_depth, None, r.grad2d,
                              r.work_counter, stream)
@@ -146,6 +156,7 @@ class MappingStep:
         passes = (n_bits + 7) // 8
         # project, bin (count, scan, emit, hist, passes, ranges), fwd, loss, bwd, pbwd colour + geometry
         k = 1 + (3 + 1 + passes + 1) + 1 + 1 + 1 + 2
+        k += 2 if self.zeta > 0 else 0
         k += 1 if self.keypoints is not None else 0
         k += 1 if self.optimise_params else 0
         return k

@@ -305,7 +305,7 @@ def config(idx: int, scale: float = 1.0):
         intr = np.tile([600.0, 600.0, 600.0, 340.0], (8, 1))
         cams = cams_from(intr, np.tile([1200, 680], (8, 1)), vm)
         return dict(name=CONFIG_NAMES[4], scene=scene, cams=cams, target_scene=target_scene,
-                    w_c=1.0, w_d=0.5, gate=False, iters=20)
+                    w_c=1.0, w_d=0.5, zeta=0.3, gate=False, iters=20)
     if idx == 5:
         n = max(1, int(4_000_000 * scale))
         lay = multi_room_layout(5)
@@ -316,7 +316,7 @@ def config(idx: int, scale: float = 1.0):
         intr = [[0.5 * w, 0.5 * w, 0.5 * w, 0.5 * h] for (w, h) in sizes]
         cams = cams_from(intr, sizes, vm)
         return dict(name=CONFIG_NAMES[5], scene=scene, cams=cams, target_scene=target_scene,
-                    w_c=1.0, w_d=0.5, gate=False, iters=20)
+                    w_c=1.0, w_d=0.5, zeta=0.3, gate=False, iters=20)
     raise ValueError(f"unknown workload {idx}")
 
 

@@ -47,8 +47,8 @@ def gpu_geom(rast):
     rec = rast.proj["rec"].view(-1, 12).cpu().numpy()
     radii = rast.proj["radii"].cpu().numpy()
     tt = rast.proj["tiles_touched"].cpu().numpy().view(np.uint32)
-    r0 = rec[:, 7].view(np.uint32)
-    r1 = rec[:, 11].view(np.uint32)
+    rr = rast.proj["rect"].cpu().numpy().view(np.uint32)
+    r0, r1 = rr[:, 0], rr[:, 1]
     rect = np.stack([r0 & 0xFFFF, r0 >> 16, r1 & 0xFFFF, r1 >> 16], 1).astype(np.int32)
     return rec, radii, tt, rect
 

@@ -82,13 +82,17 @@ def test_render_forward_parity(name, scene, cams):
     rast, p, vm = _run(scene, cams)
     ref = oracle.forward(scene, cams)["img"]
     keep = ref["flags"] == 0
-    print(f"{name}: {(~keep).sum()} of {keep.size} pixels near a threshold, left out")
-    assert keep.mean() > 0.995
+    print(f"{name}: {(~keep).sum()} of {keep.size} pixels near a threshold, compared loosely")
+    assert keep.mean() > 0.99
     img = {k: v.cpu().numpy() for k, v in rast.img.items()}
+    zmax = max(float(ref["depth"].max()), 1.0)
     for k in ("rgb", "depth", "alpha", "final_T"):
-        err = np.abs(img[k][keep] - ref[k][keep]).max()
+        diff = np.abs(img[k] - ref[k])
+        err = diff[keep].max()
         print(f"{name}: max |{k} err| = {err:.3e}")
         assert err <= IMG_TOL, k
+        if (~keep).any():
+            assert diff[~keep].max() <= 0.02 * (zmax if k == "depth" else 1.0), k
     np.testing.assert_array_equal(img["n_contrib"][keep], ref["n_contrib"][keep])
 
 
@@ -304,3 +308,26 @@ def test_every_compositing_variant_matches():
             print(f"bwd variant {bv}: max rel-L2 {max(rel_l2(out[k], gref[k]) for k in out):.2e}")
     finally:
         gs.gs_set_render_variants(fwd0, bwd0)
+
+
+def test_ssim_term_parity():
+    """The SSIM term of L_m against the FP64 oracle on uneven views, added on
+    top of an existing gradient."""
+    from oracle import ssim as S
+    rng = np.random.default_rng(7)
+    size = np.array([[45, 37], [64, 48], [19, 23]])
+    P = int((size[:, 0] * size[:, 1]).sum())
+    x = rng.uniform(0, 1, (P, 3)).astype(np.float32)
+    y = np.clip(x + rng.normal(0, 0.15, x.shape), 0, 1).astype(np.float32)
+    L, g = S.loss_ssim(x.astype(np.float64), y.astype(np.float64), size, weight=0.3)
+    views = gs.make_views([[50, 50, 20, 20]] * 3, size)
+    loss = torch.full((1,), 0.25, device="cuda")
+    base = rng.normal(0, 1e-5, (P, 3)).astype(np.float32)
+    d_rgb = t(base)
+    ws = torch.empty(gs.gs_ssim_workspace_size(P), dtype=torch.uint8, device="cuda")
+    gs.gs_loss_ssim(t(x), t(y), views, 0.3, loss, d_rgb, ws)
+    torch.cuda.synchronize()
+    assert abs(float(loss) - 0.25 - L) <= 2e-6 * max(1.0, L)
+    e = rel_l2(d_rgb.cpu().numpy() - base, g)
+    print(f"SSIM gradient rel-L2 err = {e:.3e}, loss {float(loss) - 0.25:.6f} vs {L:.6f}")
+    assert e <= GRAD_TOL

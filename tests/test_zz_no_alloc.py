@@ -60,7 +60,8 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     cams = c["cams"]
     views = gs.make_views(cams["intr"], cams["size"])
     big = 5_000_000  # records beyond the 4,194,304 limit; nothing is enqueued
-    proj = dict(rec=torch.zeros(16, device="cuda"), radii=torch.zeros(4, dtype=torch.int32, device="cuda"),
+    proj = dict(rec=torch.zeros(16, device="cuda"), rect=torch.zeros(4, 2, dtype=torch.int32, device="cuda"),
+                radii=torch.zeros(4, dtype=torch.int32, device="cuda"),
                 tiles_touched=torch.zeros(4, dtype=torch.int32, device="cuda"))
     bins = dict(keys=torch.zeros(4, dtype=torch.int64, device="cuda"),
                 vals=torch.zeros(4, dtype=torch.int32, device="cuda"),
