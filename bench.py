@@ -2,7 +2,7 @@
 """Throughput of the differentiable Gaussian-splatting hot path on one GB300.
 
 A step is one joint mapping iteration over a batch of keyframes through the C
-ABI: project -> bin + onesweep sort -> composite -> L1 loss -> backward
+ABI: project -> bin + per-tile sort -> composite -> L1 loss -> backward
 (compositing + projection, with per-view SE(3) twist gradients) -> keypoint
 re-projection term -> Adam on all Gaussian parameters.  Default workload:
 1M Gaussians (SH degree 3) on synthetic room surfaces, 8 keyframes of
@@ -250,10 +250,11 @@ def stage_work(w):
     """Per-stage algorithmic bytes (HBM-bound stages) or FP32 flops (compositing)."""
     N, V, P, K, Vv, E, B, C, S = (w[k] for k in ("N", "V", "P", "K", "V_vis", "E", "B", "C", "sh_floats"))
     param_b = 4 * (3 + 3 + 4 + 1 + S)
-    passes = math.ceil((32 + math.ceil(math.log2(max(w["T"], 2)))) / 8)
     return {
         "project": ("hbm", param_b * N + 8 * V * N + 48 * Vv),
-        "bin_sort": ("hbm", 8 * V * N + 12 * Vv + 12 * K + 8 * K + passes * 24 * K + 8 * K + 8 * w["T"]),
+        # tile counts and rectangles read, depth of the drawn records, sorted keys and values and
+        # the tile ranges written (the per-tile buckets in between are not counted)
+        "bin_sort": ("hbm", 4 * V * N + 12 * Vv + 12 * K + 8 * w["T"]),
         # per evaluation 14 FP32 ops (offset, quadratic form, exp, opacity, clamp, test);
         # per blended entry 14 more (transmittance, weight, three colour and one depth FMA)
         "render_fwd": ("alu", 14 * E + 14 * B),

@@ -12,9 +12,9 @@
  *    Work is only enqueued; results are ready when the stream is.
  *  - Synchronous argument errors return a gs_status_t and enqueue nothing.
  *    Asynchronous errors (pair capacity exceeded, bounded wait expired) are
- *    OR-ed into a device status word (bit 1 << GS_ERR_CAPACITY, 1 << GS_ERR_TIMEOUT)
- *    that the caller reads after the stream; outputs are then incomplete but
- *    every access stays in bounds.
+ *    OR-ed into a device status word (bit 1 << GS_ERR_CAPACITY,
+ *    1 << GS_ERR_TIMEOUT) that the caller reads after the stream; outputs are
+ *    then incomplete but every access stays in bounds.
  *  - Views: up to GS_MAX_VIEWS cameras per call, possibly of different sizes.
  *    Per-view arrays are concatenated: projected records and radii at
  *    [v * n + i]; pixels at pix_base[v] + y * width + x with pix_base the
@@ -139,15 +139,21 @@ gs_status_t gs_project(const gs_params_t *params, const gs_view_t *views, const 
                        int32_t n_views, const gs_options_t *opt, gs_projected_t *out, void *stream);
 
 /* Bytes of workspace gs_bin_sort needs for n_records = n_views * n and the
- * given pair capacity and total tile count. */
+ * given pair capacity (about 8 bytes per pair of capacity and 16 per record;
+ * n_tiles_total does not enter); 0 for invalid sizes. */
 size_t gs_bin_sort_workspace_size(int64_t n_records, int64_t pair_capacity, int64_t n_tiles_total);
 
 /* a2-a4. Binning in front-to-back order (Sec. 3.4 "Differentiable
  * Rasterization": Gaussians arranged front to back before alpha blending).
- * Scans tiles_touched, emits one (key, value) per (Gaussian, tile), sorts the
- * keys with a stable onesweep LSD radix sort over their 32 + ceil(log2 tiles)
- * significant bits, and writes each tile's [start, end).  Ties keep the
- * Gaussian index order.  Pairs beyond bins->capacity are dropped and flagged.
+ * Produces exactly the pairs a stable sort of the keys (global tile << 32) |
+ * bits(depth), values = Gaussian index, would: per tile, entries by depth,
+ * equal depths in index order, and each tile's [start, end) ([0, 0) when
+ * empty).  Built by sorting the drawn records by depth, emitting their pairs
+ * in that order and sorting the pairs stably by tile id (onesweep radix
+ * passes over 32-bit keys).  n_views * n must be below 2^32.  When the pair
+ * total exceeds bins->capacity, n_pairs still reports the total, the
+ * capacity bit is set in the status word and only the pairs of the nearest
+ * records that fit are binned.
  * workspace: device, >= gs_bin_sort_workspace_size bytes, 256-byte aligned. */
 gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const gs_view_t *views, int32_t n_views,
                         gs_bins_t *bins, void *workspace, size_t workspace_bytes, void *stream);
@@ -157,12 +163,13 @@ gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const gs_view_t *
  * CUDA graph capture, fixed-rate tracking loops that cannot take the device
  * synchronisation an allocation may cause, or host frameworks that own all
  * device memory and pass a plugin only its inputs and outputs).  Same inputs,
- * outputs and results as gs_bin_sort, but the scratch workspace is a 13 MiB
+ * outputs and results as gs_bin_sort, but the scratch workspace is an 80 MiB
  * static device array inside the library, held on every GPU that loads it
  * until the process exits.  Limits: n_views * n <= 4,194,304 records and
  * bins->capacity <= 1,048,576 pairs; larger calls return GS_ERR_CAPACITY and
- * enqueue nothing.  The first call on a device looks up the array's address
- * (cudaGetSymbolAddress) and should come before any stream capture.  All
+ * enqueue nothing.  The first call on a device looks up
+ * the array's address (cudaGetSymbolAddress) and should come before any
+ * stream capture.  All
  * calls share the array and it keeps the last call's contents (what must
  * start at zero is cleared inside each call); calls that may overlap on the
  * GPU race on it and must not be issued. */

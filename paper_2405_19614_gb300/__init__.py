@@ -110,7 +110,7 @@ def gs_bin_sort(proj, n, views, bins, workspace, stream=None):
 def gs_bin_sort_noalloc(proj, n, views, bins, stream=None):
     """gs_bin_sort without a caller workspace: for callers that cannot
     allocate device memory (mid graph capture, fixed-rate loops, hosts that own
-    all device memory).  Uses a fixed 13 MiB scratch array inside the library;
+    all device memory).  Uses a fixed 80 MiB scratch array inside the library;
     at most 4,194,304 records and a pair capacity of 1,048,576.  Calls must not
     overlap on the GPU."""
     check(lib().gs_bin_sort_noalloc(ctypes.byref(_proj(proj)), n, views, len(views), ctypes.byref(_bins(bins)),

@@ -1,8 +1,24 @@
-// a2 + a4. Binning of projected Gaussians into 16x16 tiles in front-to-back
-// order (Sec. 3.4 "Differentiable Rasterization"): an exclusive scan of the
-// number of tiles each (view, Gaussian) touches, emission of one
-// (key = (global tile << 32) | bits(depth), value = Gaussian index) pair per
-// touched tile, the onesweep radix sort (sort.cu), and each tile's [start, end).
+// a2 - a4. Binning of projected Gaussians into 16x16 tiles in front-to-back
+// order (Sec. 3.4 "Differentiable Rasterization": the Gaussians of each tile
+// are arranged by depth before alpha blending).
+//
+// The result is the list a stable sort of the 64-bit keys (global tile << 32)
+// | bits(depth), values = Gaussian index, would give: per tile, entries by
+// depth, equal depths in index order.  It is built in two small sorts instead
+// of one wide one:
+//   1. the drawn (view, Gaussian) records are compacted and sorted by depth
+//      (four 8-bit passes over 32-bit keys; ties stay in record order);
+//   2. every record emits one (tile id, depth rank) pair per tile it touches,
+//      in depth order, so the pair list is already in front-to-back order;
+//   3. a stable sort of the pairs by tile id alone (ceil(log2 tiles / 8)
+//      passes over 32-bit keys, two for up to 65,536 tiles) gives the final
+//      order; its last pass writes the 64-bit keys and the values from the
+//      depth rank;
+//   4. each tile's [start, end) from the sorted keys.
+// Steps 1 and 2 build the digit histograms of the passes that follow, so no
+// pass needs a histogram kernel.  Emission is load-balanced: a block scans its
+// records' tile counts in shared memory and consecutive threads take
+// consecutive pairs, finding their record by binary search.
 #include "common.cuh"
 #include "sort.cuh"
 
@@ -10,7 +26,11 @@ namespace gs {
 
 constexpr int kEmitThreads = 256;
 constexpr int kEmitItems = 8;
-constexpr int kEmitChunk = kEmitThreads * kEmitItems;
+constexpr int kEmitChunk = kEmitThreads * kEmitItems;  // records per block, compaction
+constexpr int kPairItems = 2;
+constexpr int kPairChunk = kEmitThreads * kPairItems;  // sorted records per block, pair emission
+constexpr int kDepthPasses = 4;
+constexpr int kMaxTilePasses = 4;
 
 __device__ __forceinline__ uint64_t block_exclusive_scan_u64(uint64_t x, uint64_t *tmp /* [8] */, uint64_t *total)
 {
@@ -34,35 +54,57 @@ __device__ __forceinline__ uint64_t block_exclusive_scan_u64(uint64_t x, uint64_
     return wbase + inc - x;
 }
 
-__global__ void __launch_bounds__(kEmitThreads) count_reduce_kernel(const uint32_t *__restrict__ tt, int64_t total,
-                                                                    uint64_t *block_sums)
+__device__ __forceinline__ void clear_hist(uint32_t (*h)[kRadix], int n_passes)
+{
+    for (int k = threadIdx.x; k < n_passes * kRadix; k += blockDim.x) (&h[0][0])[k] = 0;
+}
+
+__device__ __forceinline__ void flush_hist(uint32_t (*h)[kRadix], int n_passes, uint32_t *global)
+{
+    for (int k = threadIdx.x; k < n_passes * kRadix; k += blockDim.x) {
+        const uint32_t c = (&h[0][0])[k];
+        if (c) atomicAdd(global + k, c);
+    }
+}
+
+// 1a. Drawn records (tiles_touched > 0) of each block of kEmitChunk records.
+__global__ void __launch_bounds__(kEmitThreads) vis_count_kernel(const uint32_t *__restrict__ tt, int64_t total,
+                                                                 uint64_t *block_sums)
 {
     __shared__ uint64_t tmp[kEmitThreads / 32];
     const int64_t first = (int64_t)blockIdx.x * kEmitChunk + threadIdx.x;
     uint64_t s = 0;
     #pragma unroll
     for (int k = 0; k < kEmitItems; k++) {
-        const int64_t idx = first + k * kEmitThreads;
-        if (idx < total) s += tt[idx];
+        const int64_t o = first + k * kEmitThreads;
+        if (o < total && tt[o] > 0) s++;
     }
     uint64_t all;
     block_exclusive_scan_u64(s, tmp, &all);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = all;
 }
 
-// One block: exclusive scan of the block sums in place; the grand total is the
-// pair count.
-__global__ void __launch_bounds__(1024) scan_sums_kernel(uint64_t *sums, int64_t nb, int64_t cap,
-                                                         uint32_t *n_pairs, uint32_t *status)
+// One block: exclusive scan of the block sums in place, 16 consecutive sums
+// per thread per round (all loads in flight at once); the grand total goes to
+// *count, flagged when it exceeds cap.
+constexpr int kScanPer = 16;
+
+__global__ void __launch_bounds__(1024) scan_sums_kernel(uint64_t *sums, int64_t nb, int64_t cap, uint32_t *count,
+                                                         uint32_t *status)
 {
     __shared__ uint64_t tmp[32];
     __shared__ uint64_t carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int64_t base = 0; base < nb; base += 1024) {
-        const int64_t i = base + threadIdx.x;
-        const uint64_t x = i < nb ? sums[i] : 0ull;
+    for (int64_t base = 0; base < nb; base += 1024 * kScanPer) {
+        const int64_t first = base + (int64_t)threadIdx.x * kScanPer;
+        uint64_t v[kScanPer], x = 0;
+        #pragma unroll
+        for (int k = 0; k < kScanPer; k++) {
+            v[k] = first + k < nb ? sums[first + k] : 0ull;
+            x += v[k];
+        }
         uint64_t inc = x;
         #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -76,130 +118,227 @@ __global__ void __launch_bounds__(1024) scan_sums_kernel(uint64_t *sums, int64_t
             wbase += (w < warp) ? tmp[w] : 0ull;
             all += tmp[w];
         }
-        if (i < nb) sums[i] = carry + wbase + inc - x;
+        uint64_t run = carry + wbase + inc - x;
+        #pragma unroll
+        for (int k = 0; k < kScanPer; k++) {
+            if (first + k < nb) sums[first + k] = run;
+            run += v[k];
+        }
         __syncthreads();
         if (threadIdx.x == 0) carry += all;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         const uint64_t total = carry;
-        *n_pairs = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
+        *count = total > 0xffffffffull ? 0xffffffffu : (uint32_t)total;
         if (total > (uint64_t)cap) raise_status(status, GS_ERR_CAPACITY);
     }
 }
 
-// Load-balanced emission: the block first scans its chunk's pair counts into
-// shared memory (with each record's depth bits, rectangle, view and index),
-// then its threads walk the chunk's output positions in order, each finding
-// its record by binary search, so consecutive threads write consecutive pairs.
-__global__ void __launch_bounds__(kEmitThreads) emit_kernel(const float *__restrict__ rec, const uint2 *__restrict__ rect,
-                                                            const uint32_t *__restrict__ tt,
-                                                            int64_t n, int64_t total, ViewTable vt,
-                                                            const uint64_t *__restrict__ block_off, uint64_t *keys,
-                                                            uint32_t *vals, int64_t cap, uint32_t *status)
+// 1b. Compaction of the drawn records in record order: (depth bits, record
+// id), and the histograms of the four depth digits.
+__global__ void __launch_bounds__(kEmitThreads) vis_compact_kernel(const float *__restrict__ rec,
+                                                                   const uint32_t *__restrict__ tt, int64_t total,
+                                                                   const uint64_t *__restrict__ block_off,
+                                                                   uint32_t *rz, uint32_t *rid, uint32_t *hist)
 {
     __shared__ uint64_t tmp[kEmitThreads / 32];
-    __shared__ uint32_t s_excl[kEmitChunk + 1];
-    __shared__ uint32_t s_z[kEmitChunk], s_r0[kEmitChunk], s_r1[kEmitChunk], s_g[kEmitChunk];
-    __shared__ uint16_t s_v[kEmitChunk];
-    const int64_t chunk = (int64_t)blockIdx.x * kEmitChunk;
-    const int64_t first = chunk + (int64_t)threadIdx.x * kEmitItems;
-    uint32_t c[kEmitItems];
-    uint64_t sum = 0;
+    __shared__ uint32_t h[kDepthPasses][kRadix];
+    clear_hist(h, kDepthPasses);
+    // records first + 8 t .. first + 8 t + 7 belong to thread t, so the
+    // compacted order is the record order
+    const int64_t first = (int64_t)blockIdx.x * kEmitChunk + (int64_t)threadIdx.x * kEmitItems;
+    bool vis[kEmitItems];
+    uint64_t s = 0;
     #pragma unroll
     for (int k = 0; k < kEmitItems; k++) {
         const int64_t o = first + k;
-        c[k] = o < total ? tt[o] : 0u;
-        sum += c[k];
+        vis[k] = o < total && tt[o] > 0;
+        s += vis[k];
     }
+    uint32_t z[kEmitItems];
+    #pragma unroll
+    for (int k = 0; k < kEmitItems; k++) z[k] = vis[k] ? __float_as_uint(rec[12 * (first + k) + 2]) : 0u;
+    uint64_t pos = block_off[blockIdx.x] + block_exclusive_scan_u64(s, tmp, nullptr);
+    #pragma unroll
+    for (int k = 0; k < kEmitItems; k++) {
+        if (vis[k]) {
+            rz[pos] = z[k];
+            rid[pos] = (uint32_t)(first + k);
+            pos++;
+        }
+        count_digits_warp(h, z[k], vis[k], kDepthPasses);
+    }
+    __syncthreads();
+    flush_hist(h, kDepthPasses, hist);
+}
+
+// Record ids and tile counts of the depth-sorted records j < n_vis of a
+// block's chunk (thread t holds j = first + 2 t, first + 2 t + 1); recs holds
+// (depth bits, record id) pairs.
+__device__ __forceinline__ void chunk_counts(const uint2 *__restrict__ recs, const uint32_t *__restrict__ tt,
+                                             uint32_t n_vis, uint32_t (&r)[kPairItems], uint32_t (&c)[kPairItems])
+{
+    const int64_t first = (int64_t)blockIdx.x * kPairChunk + (int64_t)threadIdx.x * kPairItems;
+    #pragma unroll
+    for (int k = 0; k < kPairItems; k++) {
+        const int64_t j = first + k;
+        r[k] = j < n_vis ? recs[j].y : 0u;
+        c[k] = j < n_vis ? tt[r[k]] : 0u;
+    }
+}
+
+// 2a. Pairs of each block of kPairChunk depth-sorted records.
+__global__ void __launch_bounds__(kEmitThreads) pair_count_kernel(const uint2 *__restrict__ recs,
+                                                                  const uint32_t *__restrict__ tt,
+                                                                  const uint32_t *n_vis_p, uint64_t *block_sums)
+{
+    __shared__ uint64_t tmp[kEmitThreads / 32];
+    uint32_t r[kPairItems], c[kPairItems];
+    chunk_counts(recs, tt, *n_vis_p, r, c);
+    uint64_t s = 0;
+    #pragma unroll
+    for (int k = 0; k < kPairItems; k++) s += c[k];
+    uint64_t all;
+    block_exclusive_scan_u64(s, tmp, &all);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = all;
+}
+
+// 2b. Emission of (tile id, depth rank) pairs in depth order, and the
+// histograms of the tile-id digits.
+__global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__restrict__ recs,
+                                                                 const uint2 *__restrict__ rect,
+                                                                 const uint32_t *__restrict__ tt,
+                                                                 const uint32_t *n_vis_p, uint32_t n, ViewTable vt,
+                                                                 const uint64_t *__restrict__ block_off, int64_t cap,
+                                                                 uint32_t *tk, uint32_t *tv, uint32_t *hist,
+                                                                 int tile_passes)
+{
+    __shared__ uint64_t tmp[kEmitThreads / 32];
+    __shared__ uint32_t s_excl[kPairChunk + 1];
+    __shared__ uint32_t s_r0[kPairChunk], s_r1[kPairChunk];
+    __shared__ uint16_t s_v[kPairChunk];
+    __shared__ uint32_t h[kMaxTilePasses][kRadix];
+    clear_hist(h, tile_passes);
+    uint32_t r[kPairItems], c[kPairItems];
+    chunk_counts(recs, tt, *n_vis_p, r, c);
+    uint64_t sum = 0;
+    #pragma unroll
+    for (int k = 0; k < kPairItems; k++) sum += c[k];
     uint64_t block_total;
     uint64_t run = block_exclusive_scan_u64(sum, tmp, &block_total);
     #pragma unroll
-    for (int k = 0; k < kEmitItems; k++) {
-        const int r = threadIdx.x * kEmitItems + k;
-        s_excl[r] = (uint32_t)run;
+    for (int k = 0; k < kPairItems; k++) {
+        const int q = threadIdx.x * kPairItems + k;
+        s_excl[q] = (uint32_t)run;
         run += c[k];
         if (c[k]) {
-            const int64_t o = first + k;
-            const int v = (int)(o / n);
-            s_v[r] = (uint16_t)v;
-            s_g[r] = (uint32_t)(o - (int64_t)v * n);
-            s_z[r] = __float_as_uint(rec[12 * o + 2]);
-            const uint2 rr = rect[o];
-            s_r0[r] = rr.x;
-            s_r1[r] = rr.y;
+            const uint2 rr = rect[r[k]];
+            s_r0[q] = rr.x;
+            s_r1[q] = rr.y;
+            s_v[q] = (uint16_t)(r[k] / n);
         }
     }
-    if (threadIdx.x == 0) s_excl[kEmitChunk] = (uint32_t)block_total;
+    if (threadIdx.x == 0) s_excl[kPairChunk] = (uint32_t)block_total;
     __syncthreads();
     const uint64_t base = block_off[blockIdx.x];
+    const uint32_t j0 = blockIdx.x * kPairChunk;
     const uint32_t nq = (uint32_t)block_total;
-    bool overflow = false;
-    for (uint32_t q = threadIdx.x; q < nq; q += kEmitThreads) {
-        // last record r with s_excl[r] <= q (records of zero count share their successor's offset)
-        int lo = 0, hi = kEmitChunk;  // invariant: s_excl[lo] <= q < s_excl[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_excl[mid] <= q) lo = mid; else hi = mid;
-        }
-        const int r = lo;
-        const uint32_t k = q - s_excl[r];
-        const uint32_t r0 = s_r0[r], r1 = s_r1[r];
-        const uint32_t x0 = r0 & 0xffff, y0 = r0 >> 16, x1 = r1 & 0xffff;
-        const uint32_t w = x1 - x0 + 1;
-        const uint32_t ty = y0 + k / w, tx = x0 + k % w;
-        const ViewInfo &V = vt.v[s_v[r]];
+    for (uint32_t q0 = 0; q0 < nq; q0 += kEmitThreads) {  // block-uniform trip count
+        const uint32_t q = q0 + threadIdx.x;
         const uint64_t pos = base + q;
-        if (pos < (uint64_t)cap) {
-            keys[pos] = ((uint64_t)((uint32_t)V.tile_base + ty * (uint32_t)V.tiles_x + tx) << 32) | s_z[r];
-            vals[pos] = s_g[r];
-        } else {
-            overflow = true;
+        // pairs past the capacity are dropped (the capacity bit is already set)
+        const bool valid = q < nq && pos < (uint64_t)cap;
+        uint32_t tile = 0;
+        if (valid) {
+            // last record i with s_excl[i] <= q (records of zero count share their successor's offset)
+            int lo = 0, hi = kPairChunk;  // invariant: s_excl[lo] <= q < s_excl[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_excl[mid] <= q) lo = mid; else hi = mid;
+            }
+            const uint32_t k = q - s_excl[lo];
+            const uint32_t r0 = s_r0[lo], r1 = s_r1[lo];
+            const uint32_t x0 = r0 & 0xffff, y0 = r0 >> 16, x1 = r1 & 0xffff;
+            const uint32_t w = x1 - x0 + 1;
+            const uint32_t ty = y0 + k / w, tx = x0 + k % w;
+            const ViewInfo &V = vt.v[s_v[lo]];
+            tile = (uint32_t)V.tile_base + ty * (uint32_t)V.tiles_x + tx;
+            tk[pos] = tile;
+            tv[pos] = j0 + (uint32_t)lo;
         }
+        count_digits_warp(h, tile, valid, tile_passes);
     }
-    if (overflow) raise_status(status, GS_ERR_CAPACITY);
+    __syncthreads();
+    flush_hist(h, tile_passes, hist);
 }
 
-__global__ void ranges_kernel(const uint64_t *__restrict__ keys, const uint32_t *n_pairs_p, uint32_t cap,
-                              uint32_t *ranges)
+// 4. Each tile's [start, end) from the sorted keys (tiles without pairs keep
+// the [0, 0) they were cleared to).
+__global__ void __launch_bounds__(256) ranges_kernel(const uint64_t *__restrict__ keys, const uint32_t *n_pairs_p,
+                                                     uint32_t cap, uint32_t *ranges)
 {
     const uint32_t n = min(*n_pairs_p, cap);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    #pragma unroll 4
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint32_t t = (uint32_t)(keys[i] >> 32);
-        if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[2 * t] = i;
-        if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[2 * t + 1] = i + 1;
+        const uint32_t tp = i > 0 ? (uint32_t)(keys[i - 1] >> 32) : ~0u;
+        if (tp != t) {
+            ranges[2 * t] = i;
+            if (i > 0) ranges[2 * tp + 1] = i;
+        }
+        if (i == n - 1) ranges[2 * t + 1] = n;
     }
 }
 
-static int ceil_log2(int64_t x)
+static int bits_for(int64_t x)  // bits needed to represent x >= 0
 {
     int b = 0;
-    while ((int64_t(1) << b) < x) b++;
+    while (b < 63 && (int64_t(1) << b) <= x) b++;
     return b;
 }
 
 struct BinWorkspace {
     uint64_t *block_sums;
-    uint64_t *alt_keys;
-    uint32_t *alt_vals;
-    void *sort_ws;
-    size_t bytes;
+    uint32_t *small;  // n_vis, pass counters, depth and tile histograms (cleared together)
+    uint32_t *rz[2], *rid[2];
+    uint2 *recs;  // depth-sorted (depth bits, record id)
+    uint32_t *lb[2];
+    uint32_t *pk, *pv;  // pair buffer
+    size_t lb_bytes, small_bytes, bytes;
 };
+
+constexpr int kSmallWords = 1 + kDepthPasses + kMaxTilePasses + (kDepthPasses + kMaxTilePasses) * kRadix;
 
 static BinWorkspace carve(void *base, int64_t n_records, int64_t cap)
 {
     BinWorkspace w;
-    const int64_t nb = (n_records + kEmitChunk - 1) / kEmitChunk + 1;
+    const int64_t nb = (n_records + kPairChunk - 1) / kPairChunk + 1;  // the larger of the two block counts
     unsigned char *p = static_cast<unsigned char *>(base);
     size_t off = 0;
     w.block_sums = reinterpret_cast<uint64_t *>(p + off);
     off += align256(sizeof(uint64_t) * (size_t)nb);
-    w.alt_keys = reinterpret_cast<uint64_t *>(p + off);
-    off += align256(sizeof(uint64_t) * (size_t)cap);
-    w.alt_vals = reinterpret_cast<uint32_t *>(p + off);
+    w.small = reinterpret_cast<uint32_t *>(p + off);
+    w.small_bytes = sizeof(uint32_t) * kSmallWords;
+    off += align256(w.small_bytes);
+    for (int i = 0; i < 2; i++) {
+        w.rz[i] = reinterpret_cast<uint32_t *>(p + off);
+        off += align256(sizeof(uint32_t) * (size_t)n_records);
+        w.rid[i] = reinterpret_cast<uint32_t *>(p + off);
+        off += align256(sizeof(uint32_t) * (size_t)n_records);
+    }
+    w.recs = reinterpret_cast<uint2 *>(p + off);
+    off += align256(sizeof(uint2) * (size_t)n_records);
+    w.lb_bytes = onesweep_lookback_bytes(n_records > cap ? n_records : cap);
+    for (int i = 0; i < 2; i++) {
+        w.lb[i] = reinterpret_cast<uint32_t *>(p + off);
+        off += w.lb_bytes;
+    }
+    w.pk = reinterpret_cast<uint32_t *>(p + off);
     off += align256(sizeof(uint32_t) * (size_t)cap);
-    w.sort_ws = p + off;
-    off += sort_workspace_bytes(cap);
+    w.pv = reinterpret_cast<uint32_t *>(p + off);
+    off += align256(sizeof(uint32_t) * (size_t)cap);
     w.bytes = off;
     return w;
 }
@@ -212,7 +351,7 @@ extern "C" size_t gs_bin_sort_workspace_size(int64_t n_records, int64_t pair_cap
 {
     (void)n_tiles_total;
     if (n_records < 0 || pair_capacity < 1) return 0;
-    return carve(nullptr, n_records, pair_capacity).bytes;
+    return carve(nullptr, n_records > 0 ? n_records : 1, pair_capacity).bytes;
 }
 
 extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const gs_view_t *views, int32_t n_views,
@@ -227,8 +366,11 @@ extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const 
     if (!bins->keys || !bins->vals || !bins->ranges || !bins->n_pairs || !bins->status || !workspace)
         return GS_ERR_INVALID_ARG;
     const int64_t total = (int64_t)n_views * n;
-    BinWorkspace w = carve(workspace, total, cap);
+    if (total >= (int64_t(1) << 32)) return GS_ERR_INVALID_ARG;  // record ids are 32-bit
+    BinWorkspace w = carve(workspace, total > 0 ? total : 1, cap);
     if (workspace_bytes < w.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255)) return GS_ERR_INVALID_ARG;
+    const int tile_passes = (bits_for(vt.n_tiles_total - 1) + 7) / 8 > 0 ? (bits_for(vt.n_tiles_total - 1) + 7) / 8 : 1;
+    if (tile_passes > kMaxTilePasses) return GS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     if (cudaMemsetAsync(bins->ranges, 0, sizeof(uint32_t) * 2 * (size_t)vt.n_tiles_total, s) != cudaSuccess)
         return GS_ERR_CUDA;
@@ -238,24 +380,59 @@ extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const 
     }
     if (!proj->rec || !proj->rect || !proj->tiles_touched) return GS_ERR_INVALID_ARG;
 
-    const int n_bits = 32 + ceil_log2(vt.n_tiles_total);
-    const int P = sort_passes(n_bits);
-    // emit where an odd or even number of passes leaves the result in bins
-    uint64_t *ek = (P & 1) ? w.alt_keys : bins->keys;
-    uint32_t *ev = (P & 1) ? w.alt_vals : bins->vals;
-    uint64_t *ok = (P & 1) ? bins->keys : w.alt_keys;
-    uint32_t *ov = (P & 1) ? bins->vals : w.alt_vals;
+    uint32_t *n_vis = w.small;
+    uint32_t *counters = w.small + 1;  // one per pass
+    uint32_t *hist_depth = counters + kDepthPasses + kMaxTilePasses;
+    uint32_t *hist_tile = hist_depth + kDepthPasses * kRadix;
+    if (cudaMemsetAsync(w.small, 0, w.small_bytes, s) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaMemsetAsync(w.lb[0], 0, w.lb_bytes, s) != cudaSuccess) return GS_ERR_CUDA;
 
-    const int64_t nb = (total + kEmitChunk - 1) / kEmitChunk;
-    count_reduce_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(proj->tiles_touched, total, w.block_sums);
-    scan_sums_kernel<<<1, 1024, 0, s>>>(w.block_sums, nb, cap, bins->n_pairs, bins->status);
-    emit_kernel<<<(unsigned)nb, kEmitThreads, 0, s>>>(proj->rec, reinterpret_cast<const uint2 *>(proj->rect),
-                                                      proj->tiles_touched, n, total, vt, w.block_sums,
-                                                      ek, ev, cap, bins->status);
+    // 1. drawn records sorted by depth
+    const unsigned nb = (unsigned)((total + kEmitChunk - 1) / kEmitChunk);
+    vis_count_kernel<<<nb, kEmitThreads, 0, s>>>(proj->tiles_touched, total, w.block_sums);
+    scan_sums_kernel<<<1, 1024, 0, s>>>(w.block_sums, nb, total, n_vis, bins->status);
+    vis_compact_kernel<<<nb, kEmitThreads, 0, s>>>(proj->rec, proj->tiles_touched, total, w.block_sums, w.rz[0],
+                                                   w.rid[0], hist_depth);
+    for (int p = 0; p < kDepthPasses; p++) {
+        const int a = p & 1;
+        const bool last = p + 1 == kDepthPasses;  // writes (depth bits, record id) pairs
+        st = onesweep_pass(w.rz[a], w.rid[a], last ? reinterpret_cast<uint32_t *>(w.recs) : w.rz[a ^ 1],
+                           w.rid[a ^ 1], n_vis, total, hist_depth + p * kRadix, w.lb[a], last ? nullptr : w.lb[a ^ 1],
+                           counters + p, 8 * p, last ? kSortPaired : kSortPlain, nullptr, bins->status, s);
+        if (st != GS_OK) return st;
+    }
+
+    // 2. pairs in depth order; the last tile pass reads the workspace buffer,
+    // so emission goes where the pass count puts it (the key array doubles
+    // as the other buffer)
+    uint32_t *buf_k[2] = {w.pk, reinterpret_cast<uint32_t *>(bins->keys)};
+    uint32_t *buf_v[2] = {w.pv, reinterpret_cast<uint32_t *>(bins->keys) + cap};
+    const int e = (tile_passes & 1) ? 0 : 1;
+    const unsigned np = (unsigned)((total + kPairChunk - 1) / kPairChunk);
+    pair_count_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, proj->tiles_touched, n_vis, w.block_sums);
+    scan_sums_kernel<<<1, 1024, 0, s>>>(w.block_sums, np, cap, bins->n_pairs, bins->status);
+    pair_emit_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, reinterpret_cast<const uint2 *>(proj->rect),
+                                                 proj->tiles_touched, n_vis, (uint32_t)n, vt, w.block_sums, cap,
+                                                 buf_k[e], buf_v[e], hist_tile, tile_passes);
     st = launch_status();
     if (st != GS_OK) return st;
-    st = radix_sort_pairs(ek, ev, ok, ov, bins->n_pairs, cap, n_bits, w.sort_ws, bins->status, s);
-    if (st != GS_OK) return st;
-    ranges_kernel<<<num_sms() * 4, 256, 0, s>>>(bins->keys, bins->n_pairs, (uint32_t)cap, bins->ranges);
+
+    // 3. stable passes over the tile id; the last writes keys and values
+    if (cudaMemsetAsync(w.lb[0], 0, w.lb_bytes, s) != cudaSuccess) return GS_ERR_CUDA;
+    const SortExpand ex = {bins->keys, bins->vals, w.recs, (uint32_t)n};
+    int src = e;
+    for (int p = 0; p < tile_passes; p++) {
+        const bool last = p + 1 == tile_passes;
+        const int a = p & 1;
+        st = onesweep_pass(buf_k[src], buf_v[src], buf_k[src ^ 1], buf_v[src ^ 1], bins->n_pairs, cap,
+                           hist_tile + p * kRadix, w.lb[a], last ? nullptr : w.lb[a ^ 1],
+                           counters + kDepthPasses + p, 8 * p, last ? kSortExpand : kSortPlain, &ex, bins->status, s);
+        if (st != GS_OK) return st;
+        src ^= 1;
+    }
+
+    // 4. tile ranges
+    const int64_t rb = (cap + 255) / 256, rmax = (int64_t)num_sms() * 16;
+    ranges_kernel<<<(unsigned)(rb < rmax ? rb : rmax), 256, 0, s>>>(bins->keys, bins->n_pairs, (uint32_t)cap, bins->ranges);
     return launch_status();
 }

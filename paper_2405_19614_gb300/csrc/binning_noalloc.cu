@@ -1,20 +1,20 @@
 // Allocation-free variant of gs_bin_sort (the paper has no counterpart; this is
 // a service for callers that cannot allocate device memory).
 //
-// gs_bin_sort needs a scratch workspace (the scan's block sums, the second
-// key/value buffer the radix sort ping-pongs with, the digit histograms and the
-// look-back flags).  Normally the caller allocates it.  Some callers cannot:
-// code that is capturing a CUDA graph cannot call cudaMalloc in the middle of
-// the capture, a fixed-rate tracking loop on a robot cannot afford the device
+// gs_bin_sort needs a scratch workspace (the scans' block sums, the drawn
+// records' depth keys and ids with their second sort buffer, the look-back
+// flags and histograms of the radix passes, and the second pair buffer).  Normally the caller allocates
+// it.  Some callers cannot: code that is capturing a CUDA graph cannot call
+// cudaMalloc in the middle of the capture, a fixed-rate tracking loop on a robot cannot afford the device
 // synchronisation an allocation may cause, and some host frameworks own every
 // byte of device memory and hand a plugin only its inputs and outputs.  For
 // them this file keeps the scratch in one file-scope device array of fixed
 // size, reserved when the library is loaded on a GPU and held until the
 // process exits.
 //
-// Limits: at most kMaxRecords (view, Gaussian) records (n_views * n) and a pair
-// capacity of at most kMaxPairs; larger calls are rejected with
-// GS_ERR_CAPACITY before anything is enqueued.
+// Limits: at most kNoAllocMaxRecords (view, Gaussian) records (n_views * n)
+// and a pair capacity of at most kNoAllocMaxPairs; larger calls are rejected
+// with GS_ERR_CAPACITY before anything is enqueued.
 //
 // Sharing: every call uses the same array and it keeps the previous call's
 // contents.  Everything the sort needs at zero is cleared inside the call, so
@@ -34,7 +34,7 @@ namespace gs {
 
 constexpr int64_t kNoAllocMaxRecords = int64_t(1) << 22;  // 4,194,304 records
 constexpr int64_t kNoAllocMaxPairs = int64_t(1) << 20;    // 1,048,576 pairs
-constexpr size_t kNoAllocScratchBytes = size_t(13) << 20; // 13 MiB >= workspace at the limits
+constexpr size_t kNoAllocScratchBytes = size_t(80) << 20; // 80 MiB >= workspace at the limits (~75 MiB)
 
 static __device__ __align__(256) unsigned char g_bin_scratch[kNoAllocScratchBytes];
 
@@ -67,11 +67,14 @@ extern "C" gs_status_t gs_bin_sort_noalloc(const gs_projected_t *proj, int64_t n
     if (!proj || !bins || n < 0 || n_views < 1 || n_views > GS_MAX_VIEWS) return GS_ERR_INVALID_ARG;
     const int64_t records = (int64_t)n_views * n;
     if (records > kNoAllocMaxRecords || bins->capacity > kNoAllocMaxPairs) return GS_ERR_CAPACITY;
-    const size_t need = gs_bin_sort_workspace_size(records, bins->capacity, 0);
+    ViewTable vt;
+    gs_status_t st = make_view_table(views, n_views, &vt);
+    if (st != GS_OK) return st;
+    const size_t need = gs_bin_sort_workspace_size(records, bins->capacity, vt.n_tiles_total);
     if (need == 0) return GS_ERR_INVALID_ARG;
     if (need > kNoAllocScratchBytes) return GS_ERR_CAPACITY;
     void *scratch = nullptr;
-    gs_status_t st = scratch_for_current_device(&scratch);
+    st = scratch_for_current_device(&scratch);
     if (st != GS_OK) return st;
     return gs_bin_sort(proj, n, views, n_views, bins, scratch, kNoAllocScratchBytes, stream);
 }

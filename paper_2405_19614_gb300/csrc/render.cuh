@@ -15,12 +15,46 @@ __device__ __forceinline__ float splat_alpha(const float4 &p, const float4 &c, c
     return fminf(kAlphaMax, __fmul_rn(p.w, __expf(power)));
 }
 
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// splat_power at two pixel centres of one column, (sx, sy.x) and (sx, sy.y):
+// the same IEEE operations in the same order, two at a time in packed FP32x2
+// instructions, so each component equals splat_power bit for bit.  dx is
+// shared by both pixels.
+__device__ __forceinline__ float2 splat_power2(float mx, float my, float dmx, float dmy, float A, float B, float C,
+                                               float sx, float2 sy, float *dx_out, float2 *dy_out)
+{
+    const float dx = __fadd_rn(__fsub_rn(mx, sx), dmx);
+    const float2 dy = __fadd2_rn(__fadd2_rn(f2(my), f2(-sy.x, -sy.y)), f2(dmy));
+    const float adx2 = __fmul_rn(__fmul_rn(A, dx), dx);
+    const float2 q = __ffma2_rn(__fmul2_rn(f2(C), dy), dy, f2(adx2));
+    const float2 bdy = __fmul2_rn(f2(B), dy);
+    const float2 p = __ffma2_rn(f2(-bdy.x, -bdy.y), f2(dx), __fmul2_rn(f2(-0.5f), q));
+    *dx_out = dx;
+    *dy_out = dy;
+    return p;
+}
+
+// splat_alpha at two pixel centres of one column; each component equals
+// splat_alpha at that pixel bit for bit.
+__device__ __forceinline__ float2 splat_alpha2(const float4 &p, const float4 &c, const float4 &col, float sx, float2 sy)
+{
+    float dx;
+    float2 dy;
+    const float2 power = splat_power2(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx, sy, &dx, &dy);
+    const float2 araw = __fmul2_rn(f2(p.w), f2(__expf(power.x), __expf(power.y)));
+    return f2(fminf(kAlphaMax, araw.x), fminf(kAlphaMax, araw.y));
+}
+
 // Minimum over t in [t0, t1] of P s^2 + 2 B s t + Q t^2 for a fixed s (Q > 0):
 // the unconstrained minimiser t = -B s / Q clamped to the interval.  *mag
 // receives the sum of the magnitudes of the three terms at that point.
 __device__ __forceinline__ float edge_min(float P, float B, float Q, float s, float t0, float t1, float *mag)
 {
-    const float t = fminf(fmaxf(-B * s / Q, t0), t1);
+    // t only has to be near the minimiser: q(t) - q_min = Q (t - t*)^2 is far
+    // below the margin of splat_misses_box for a 2-ulp quotient
+    const float t = fminf(fmaxf(__fdividef(-B * s, Q), t0), t1);
     const float a = P * s * s, b = 2.0f * B * s * t, c = Q * t * t;
     *mag = fmaxf(*mag, a + fabsf(b) + c);
     return a + b + c;
@@ -54,7 +88,7 @@ __device__ __forceinline__ bool splat_misses_box(const float4 &p, const float4 &
 
 // Kernel variants (pixels per thread x staged batch) the autotuner picks from.
 constexpr int kFwdVariants = 6;  // (1,256) (2,128) (2,256) (4,64) (4,128) (8,64)
-constexpr int kBwdVariants = 5;  // (1,256) (2,128) (4,64) (4,128) (8,64)
+constexpr int kBwdVariants = 5;  // (1,64) (2,128) (4,64) (4,128) (8,64)
 int render_variant_fwd();
 int render_variant_bwd();
 

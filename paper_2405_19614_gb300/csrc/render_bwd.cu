@@ -38,16 +38,30 @@ struct RenderBwdArgs {
 
 constexpr int kAcc = 10;
 
+// Blocks per SM asked of the register allocator: 64 registers a thread for
+// one and two pixels a thread, 80 for four, 128 for eight (no spills inside
+// the entry loop at these budgets).
+template <int PPT>
+struct BwdOccupancy {
+    static constexpr int value = PPT == 1 ? 4 : PPT == 2 ? 8 : PPT == 4 ? 12 : 16;
+};
+
 template <int PPT, int BATCH>
-__global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArgs a, ViewTable vt)
+__global__ void __launch_bounds__(kTilePix / PPT, BwdOccupancy<PPT>::value)
+    render_bwd_kernel(RenderBwdArgs a, ViewTable vt)
 {
     constexpr int THREADS = kTilePix / PPT;
+    constexpr int WARPS = THREADS / 32;
     constexpr int BAND = 2 * PPT;  // rows per warp
+    constexpr int WORDS = BATCH / 32;
     __shared__ float4 s_pos[BATCH];
     __shared__ float4 s_con[BATCH];
     __shared__ float4 s_col[BATCH];
     __shared__ int64_t s_rid[BATCH];
-    __shared__ float s_acc[BATCH][kAcc + 1];
+    // per-warp gradient totals of the staged entries; s_hit marks the entries
+    // a warp has written, so nothing needs clearing between batches
+    __shared__ float s_acc[WARPS][BATCH][kAcc + 1];
+    __shared__ uint32_t s_hit[WARPS][WORDS];
     __shared__ int s_item;
     __shared__ uint32_t s_maxlast;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -75,18 +89,20 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
         const uint32_t b = a.ranges[2 * item];
         const int64_t rbase = (int64_t)v * a.n;
 
-        float T[PPT], Tf[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gA[PPT], S[PPT];
+        // per pixel: T running transmittance, gC/gD upstream gradients,
+        // R = gA T_final - (sum over later blended entries of (c.gC + z gD) alpha T)
+        float T[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], R[PPT];
         uint32_t last[PPT];
         uint32_t my_last = 0;
         #pragma unroll
         for (int k = 0; k < PPT; k++) {
             const int py = py0 + 2 * k;
-            T[k] = Tf[k] = 1.0f;
-            gC0[k] = gC1[k] = gC2[k] = gD[k] = gA[k] = S[k] = 0.0f;
+            T[k] = 1.0f;
+            gC0[k] = gC1[k] = gC2[k] = gD[k] = R[k] = 0.0f;
             last[k] = 0;
             if (px < V.width && py < V.height) {
                 const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
-                Tf[k] = T[k] = a.final_T[pix];
+                T[k] = a.final_T[pix];
                 last[k] = a.n_contrib[pix];
                 if (a.d_rgb) {
                     gC0[k] = a.d_rgb[3 * pix];
@@ -94,7 +110,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
                     gC2[k] = a.d_rgb[3 * pix + 2];
                 }
                 if (a.d_depth) gD[k] = a.d_depth[pix];
-                if (a.d_alpha) gA[k] = a.d_alpha[pix];
+                if (a.d_alpha) R[k] = a.d_alpha[pix] * T[k];
             }
             my_last = max(my_last, last[k]);
         }
@@ -112,14 +128,13 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
                 s_pos[r] = a.rec[3 * g];
                 s_con[r] = a.rec[3 * g + 1];
                 s_col[r] = a.rec[3 * g + 2];
-                #pragma unroll
-                for (int k = 0; k < kAcc; k++) s_acc[r][k] = 0.0f;
             }
             __syncthreads();
             for (int m = ((cnt - 1) >> 5) << 5; m >= 0; m -= 32) {
               const int jl = m + lane;
               uint32_t todo = __ballot_sync(kFullMask, jl < cnt && (uint32_t)(bstart + jl) < warp_last &&
                                                            !splat_misses_box(s_pos[jl], s_con[jl], bx0, bx1, by0, by1));
+              uint32_t hit = 0;
               while (todo) {
                 const int bit = 31 - __clz(todo);
                 todo &= ~(1u << bit);
@@ -133,18 +148,34 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
                     const float4 p = s_pos[j];
                     const float4 c = s_con[j];
                     const float4 col = s_col[j];
+                    // exponents (and offsets) of this thread's pixels, two per packed evaluation
+                    float pw[PPT], dyk[PPT], dx;
+                    if (PPT == 1) {
+                        pw[0] = splat_power(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx, (float)py0 + 0.5f, &dx, &dyk[0]);
+                    } else {
+                        #pragma unroll
+                        for (int k = 0; k < PPT; k += 2) {
+                            float2 dy2;
+                            const float2 p2 = splat_power2(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx,
+                                                           f2((float)(py0 + 2 * k) + 0.5f, (float)(py0 + 2 * k + 2) + 0.5f),
+                                                           &dx, &dy2);
+                            pw[k] = p2.x;
+                            pw[(k + 1) % PPT] = p2.y;
+                            dyk[k] = dy2.x;
+                            dyk[(k + 1) % PPT] = dy2.y;
+                        }
+                    }
                     #pragma unroll
                     for (int k = 0; k < PPT; k++) {
                         if (pos >= last[k]) continue;
-                        const float sy = (float)(py0 + 2 * k) + 0.5f;
-                        float dx, dy;
-                        const float power = splat_power(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx, sy, &dx, &dy);
-                        const float g = __expf(power);
+                        const float dy = dyk[k];
+                        const float g = __expf(pw[k]);
                         const float araw = __fmul_rn(p.w, g);
                         const float alpha = fminf(kAlphaMax, araw);
                         if (alpha < kAlphaMin) continue;
                         contrib = true;
-                        const float inv_om = 1.0f / (1.0f - alpha);
+                        // 1 - alpha >= 0.01: the fast reciprocal is within 2 ulp
+                        const float inv_om = __fdividef(1.0f, 1.0f - alpha);
                         const float Tb = T[k] * inv_om;
                         const float w = alpha * Tb;
                         gr[6] += gC0[k] * w;
@@ -152,8 +183,8 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
                         gr[8] += gC2[k] * w;
                         gr[9] += gD[k] * w;
                         const float wgt = col.x * gC0[k] + col.y * gC1[k] + col.z * gC2[k] + p.z * gD[k];
-                        const float dalpha = Tb * wgt + (gA[k] * Tf[k] - S[k]) * inv_om;
-                        S[k] += wgt * w;
+                        const float dalpha = Tb * wgt + R[k] * inv_om;
+                        R[k] -= wgt * w;
                         T[k] = Tb;
                         if (araw < kAlphaMax) {
                             gr[5] += dalpha * g;
@@ -168,18 +199,24 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_bwd_kernel(RenderBwdArg
                 }
                 if (__any_sync(kFullMask, contrib)) {
                     const float r = warp_reduce_scatter10(gr, lane);
-                    if (slot_valid && r != 0.0f) atomicAdd(&s_acc[j][slot], r);
+                    if (slot_valid) s_acc[warp][j][slot] = r;
+                    hit |= 1u << bit;
                 }
               }
+              if (lane == 0) s_hit[warp][m >> 5] = hit;
             }
             __syncthreads();
             for (int r = tid; r < cnt; r += THREADS) {
                 float q[kAcc];
+                #pragma unroll
+                for (int k = 0; k < kAcc; k++) q[k] = 0.0f;
                 bool any = false;
                 #pragma unroll
-                for (int k = 0; k < kAcc; k++) {
-                    q[k] = s_acc[r][k];
-                    any |= (q[k] != 0.0f);
+                for (int w = 0; w < WARPS; w++) {
+                    if (!((s_hit[w][r >> 5] >> (r & 31)) & 1u)) continue;
+                    any = true;
+                    #pragma unroll
+                    for (int k = 0; k < kAcc; k++) q[k] += s_acc[w][r][k];
                 }
                 if (any) {
                     float4 *dst = a.grad2d + 3 * s_rid[r];
@@ -245,7 +282,7 @@ extern "C" gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t 
     a.grad2d = reinterpret_cast<float4 *>(grad2d);
     a.work_counter = work_counter;
     switch (render_variant_bwd()) {
-    case 0: return launch_bwd<1, 256>(a, vt, s);
+    case 0: return launch_bwd<1, 64>(a, vt, s);
     case 1: return launch_bwd<2, 128>(a, vt, s);
     case 2: return launch_bwd<4, 64>(a, vt, s);
     case 3: return launch_bwd<4, 128>(a, vt, s);

@@ -99,11 +99,23 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArg
                     const float4 p = s_pos[j];
                     const float4 c = s_con[j];
                     const float4 col = s_col[j];
+                    // alphas of this thread's pixels, two per packed evaluation
+                    float al[PPT];
+                    if (PPT == 1) {
+                        al[0] = splat_alpha(p, c, col, sx, (float)py0 + 0.5f);
+                    } else {
+                        #pragma unroll
+                        for (int k = 0; k < PPT; k += 2) {
+                            const float2 a2 = splat_alpha2(p, c, col, sx,
+                                                           f2((float)(py0 + 2 * k) + 0.5f, (float)(py0 + 2 * k + 2) + 0.5f));
+                            al[k] = a2.x;
+                            al[(k + 1) % PPT] = a2.y;
+                        }
+                    }
                     #pragma unroll
                     for (int k = 0; k < PPT; k++) {
                         if (!live[k]) continue;
-                        const float sy = (float)(py0 + 2 * k) + 0.5f;
-                        const float alpha = splat_alpha(p, c, col, sx, sy);
+                        const float alpha = al[k];
                         if (STATS) n_eval[k]++;
                         if (alpha < kAlphaMin) continue;
                         const float tT = T[k] * (1.0f - alpha);

@@ -6,23 +6,72 @@
 //   s = (2 mx my + C1)(2 sxy + C2) / ((mx^2 + my^2 + C1)(sx^2 + sy^2 + C2)),
 // L_SSIM = weight (1 - mean s) over all pixels and channels of all views.
 //
-// Two kernels over 32 x 16 output tiles of all views.  The first stages each
-// tile plus a 5-pixel halo in shared memory, filters the five moments
-// separably (rows, then columns), sums s into the loss and writes, per pixel
-// and channel, the three partial derivatives of s with respect to the moments
-// that depend on the rendered image:
+// Two kernels over 32 x 48 output tiles of all views.  The first stages the
+// tile plus a 5-pixel halo of both images (all three channels, coalesced) in
+// shared memory, filters the moments x, y, x^2 + y^2 and x y separably (s
+// needs the two variances only through their sum) and sums s into the loss;
+// per pixel and channel it writes the three partial derivatives of s with
+// respect to the moments that depend on the rendered image,
 //   ds/dmx = (2 my (a2 - a1) - 2 mx s (b2 - b1)) / (b1 b2),
-//   ds/dE[x^2] = -s / b2,  ds/dE[xy] = 2 a1 / (b1 b2).
-// The second filters those maps with the same (symmetric) window and forms
-//   dL/dx = g (G*ds/dmx + 2 x G*ds/dE[x^2] + y G*ds/dE[xy]),  g = -weight/(3P),
-// which it adds to d_rgb.
+//   ds/dE[x^2] = -s / b2,  ds/dE[xy] = 2 a1 / (b1 b2),
+// as nine planar maps.  The second filters those maps with the same
+// (symmetric) window and adds
+//   dL/dx = g (G*ds/dmx + 2 x G*ds/dE[x^2] + y G*ds/dE[xy]),  g = -weight/(3P)
+// to d_rgb.
+//
+// The gradient kernel double-buffers the staging, so one channel's maps are
+// copied while the previous channel is filtered.  Both filters are done with
+// each value read once from shared memory: the
+// horizontal pass gives each thread one halo row and eight output columns
+// (lanes are consecutive rows, so row pitches are odd for conflict-free
+// access); the vertical pass gives each thread one column and six output rows
+// and keeps the 16 input rows it needs in registers.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace gs {
 
-constexpr int kSsimTW = 32, kSsimTH = 16, kSsimR = 5, kSsimWin = 2 * kSsimR + 1;
-constexpr int kSsimHW = kSsimTW + 2 * kSsimR, kSsimHH = kSsimTH + 2 * kSsimR;  // 42 x 26 with halo
+constexpr int kSsimTW = 32, kSsimTH = 48, kSsimR = 5, kSsimWin = 2 * kSsimR + 1;
+constexpr int kSsimRows = kSsimTH + 2 * kSsimR;  // 58 halo rows
+constexpr int kSsimCols = kSsimTW + 2 * kSsimR;  // 42 halo columns
+constexpr int kSsimSeg = 8;                      // output columns per thread, horizontal pass
+constexpr int kSsimGrp = 6;                      // output rows per thread, vertical pass
+constexpr int kSsimThreads = 256;
+constexpr int kSsimInPitchXY = 3 * kSsimCols + 1;  // 127: interleaved RGB halo row
+constexpr int kSsimInPitch = kSsimCols + 1;        // 43: one map's halo row
+constexpr int kSsimHPitch = kSsimTW + 1;           // 33: horizontally filtered row
+constexpr int kSsimOutPitch = 3 * kSsimTW + 1;     // 97: interleaved RGB output row
 constexpr float kSsimC1 = 0.01f * 0.01f, kSsimC2 = 0.03f * 0.03f;
+
+static_assert(kSsimTW == 4 * kSsimSeg, "four column segments per halo row");
+static_assert(kSsimRows <= 64, "two 32-row groups cover the halo rows");
+static_assert(kSsimTH == 8 * kSsimGrp, "eight warps of row groups cover the tile");
+static_assert(kSsimSeg % 2 == 0 && kSsimGrp % 2 == 0, "outputs are filtered in pairs");
+
+constexpr size_t kSsimStatsSmem =
+    sizeof(float) * (2 * kSsimRows * kSsimInPitchXY + 4 * kSsimRows * kSsimHPitch);
+constexpr size_t kSsimGradSmem =
+    sizeof(float) * (2 * 3 * kSsimRows * kSsimInPitch + 3 * kSsimRows * kSsimHPitch + kSsimTH * kSsimOutPitch);
+
+// 4-byte asynchronous copy global -> shared (Ampere-style cp.async); a
+// source size of 0 writes a zero instead (the zero padding of the window).
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// Waits until at most N of this thread's committed copy groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 struct SsimTiles {
     int32_t n_views;
@@ -30,7 +79,11 @@ struct SsimTiles {
     int32_t tiles_x[GS_MAX_VIEWS];
     int32_t width[GS_MAX_VIEWS], height[GS_MAX_VIEWS];
     int64_t pix_base[GS_MAX_VIEWS];
+    int64_t n_pix;
     float g[kSsimWin];
+    // gp[t] = (g[t], g[t - 1]) for t = 0 .. 11, zero outside the window: the
+    // weights of two neighbouring outputs for one input, for packed FMAs
+    float2 gp[kSsimWin + 1];
 };
 
 __device__ __forceinline__ void ssim_tile_of(const SsimTiles &T, int item, int *v, int *x0, int *y0)
@@ -45,151 +98,255 @@ __device__ __forceinline__ void ssim_tile_of(const SsimTiles &T, int item, int *
     *y0 = (lt / T.tiles_x[vv]) * kSsimTH;
 }
 
-__global__ void __launch_bounds__(256) ssim_stats_kernel(const float *__restrict__ x, const float *__restrict__ y,
-                                                         SsimTiles T, float *__restrict__ partial, float *loss,
-                                                         float scale, float constant)
+// Both passes accumulate two neighbouring outputs (o, o + 1) per packed
+// FP32x2 FMA: output o takes g[t] and output o + 1 takes g[t - 1] from input
+// o + t, i.e. the weight pair gp[t].  Each output still sums its inputs in
+// ascending order with single-rounded FMAs, exactly as one FMA at a time.
+
+// Horizontal pass for NM maps: acc[p][m] = (out(2p), out(2p + 1)) with
+// out(o) = sum_t g[t] f_m(column o + t), for the eight output columns of this
+// thread's segment; load(i, f) gives the NM map values at the segment's halo
+// column i = 0..17 of this thread's row.
+template <int NM, typename Load>
+__device__ __forceinline__ void ssim_hpass(const SsimTiles &T, Load load, float2 (&acc)[kSsimSeg / 2][NM])
 {
-    __shared__ float sx[kSsimHH][kSsimHW], sy[kSsimHH][kSsimHW];
-    __shared__ float hs[5][kSsimHH][kSsimTW];
-    __shared__ float red[8];
+    #pragma unroll
+    for (int p = 0; p < kSsimSeg / 2; p++)
+        #pragma unroll
+        for (int m = 0; m < NM; m++) acc[p][m] = make_float2(0.0f, 0.0f);
+    #pragma unroll
+    for (int i = 0; i < kSsimSeg + kSsimWin - 1; i++) {
+        float f[NM];
+        load(i, f);
+        #pragma unroll
+        for (int p = 0; p < kSsimSeg / 2; p++) {
+            const int t = i - 2 * p;
+            if (t < 0 || t > kSsimWin) continue;
+            #pragma unroll
+            for (int m = 0; m < NM; m++) acc[p][m] = __ffma2_rn(T.gp[t], make_float2(f[m], f[m]), acc[p][m]);
+        }
+    }
+}
+
+// Vertical pass for NM maps: thread column c, output rows r0 .. r0+5 (as pairs
+// out[p] = rows (2p, 2p + 1)) from filtered rows r0 .. r0+15 of h[m][row][c].
+template <int NM>
+__device__ __forceinline__ void ssim_vpass(const SsimTiles &T, const float *h, int c, int r0,
+                                           float2 (&out)[kSsimGrp / 2][NM])
+{
+    #pragma unroll
+    for (int p = 0; p < kSsimGrp / 2; p++)
+        #pragma unroll
+        for (int m = 0; m < NM; m++) out[p][m] = make_float2(0.0f, 0.0f);
+    #pragma unroll
+    for (int i = 0; i < kSsimGrp + kSsimWin - 1; i++) {
+        float f[NM];
+        #pragma unroll
+        for (int m = 0; m < NM; m++) f[m] = h[(m * kSsimRows + r0 + i) * kSsimHPitch + c];
+        #pragma unroll
+        for (int p = 0; p < kSsimGrp / 2; p++) {
+            const int t = i - 2 * p;
+            if (t < 0 || t > kSsimWin) continue;
+            #pragma unroll
+            for (int m = 0; m < NM; m++) out[p][m] = __ffma2_rn(T.gp[t], make_float2(f[m], f[m]), out[p][m]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSsimThreads) ssim_stats_kernel(const float *__restrict__ x,
+                                                                  const float *__restrict__ y, SsimTiles T,
+                                                                  float *__restrict__ partial, float *loss,
+                                                                  float scale, float constant)
+{
+    extern __shared__ float smem[];
+    float *s_in = smem;                                   // [2][rows][127]: x, y halo, RGB interleaved
+    float *s_h = smem + 2 * kSsimRows * kSsimInPitchXY;  // [4][rows][33]
+    __shared__ float red[kSsimThreads / 32];
     int v, x0, y0;
     ssim_tile_of(T, blockIdx.x, &v, &x0, &y0);
     const int W = T.width[v], H = T.height[v];
     const int64_t pb = T.pix_base[v];
-    const int tid = threadIdx.x;
-    float acc = 0.0f;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // stage: halo rows of 42 pixels x 3 channels are contiguous in both
+    // images; every copy is in flight at once
+    for (int e = tid; e < kSsimRows * 3 * kSsimCols; e += kSsimThreads) {
+        const int r = e / (3 * kSsimCols), q = e - r * (3 * kSsimCols);
+        const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + q / 3;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const int64_t idx = in ? 3 * (pb + (int64_t)gy * W + (x0 - kSsimR)) + q : 0;
+        cp_async4(s_in + r * kSsimInPitchXY + q, x + idx, in);
+        cp_async4(s_in + (kSsimRows + r) * kSsimInPitchXY + q, y + idx, in);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    float acc_s = 0.0f;
+    const int hrow = (warp >> 2) * 32 + lane, hseg = warp & 3;  // horizontal pass: row, column segment
+    const int vc = lane, vr0 = warp * kSsimGrp;                // vertical pass: column, first output row
     for (int ch = 0; ch < 3; ch++) {
-        for (int k = tid; k < kSsimHH * kSsimHW; k += 256) {
-            const int r = k / kSsimHW, c = k % kSsimHW;
-            const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + c;
-            float xv = 0.0f, yv = 0.0f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-                const int64_t p = pb + (int64_t)gy * W + gx;
-                xv = x[3 * p + ch];
-                yv = y[3 * p + ch];
-            }
-            sx[r][c] = xv;
-            sy[r][c] = yv;
+        if (hrow < kSsimRows) {
+            const float *rx = s_in + hrow * kSsimInPitchXY + 3 * hseg * kSsimSeg + ch;
+            const float *ry = rx + kSsimRows * kSsimInPitchXY;
+            // s needs the two variances only through their sum, so four maps do:
+            // x, y, x^2 + y^2 and x y
+            float2 acc[kSsimSeg / 2][4];
+            ssim_hpass<4>(T, [&](int i, float (&f)[4]) {
+                const float a = rx[3 * i], b = ry[3 * i];
+                f[0] = a;
+                f[1] = b;
+                f[2] = fmaf(a, a, b * b);
+                f[3] = a * b;
+            }, acc);
+            #pragma unroll
+            for (int p = 0; p < kSsimSeg / 2; p++)
+                #pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    float *dst = s_h + (m * kSsimRows + hrow) * kSsimHPitch + hseg * kSsimSeg + 2 * p;
+                    dst[0] = acc[p][m].x;
+                    dst[1] = acc[p][m].y;
+                }
         }
         __syncthreads();
-        for (int k = tid; k < kSsimHH * kSsimTW; k += 256) {
-            const int r = k / kSsimTW, c = k % kSsimTW;
-            float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
-            #pragma unroll
-            for (int t = 0; t < kSsimWin; t++) {
-                const float w = T.g[t], a = sx[r][c + t], b = sy[r][c + t];
-                m0 += w * a;
-                m1 += w * b;
-                m2 += w * a * a;
-                m3 += w * b * b;
-                m4 += w * a * b;
-            }
-            hs[0][r][c] = m0;
-            hs[1][r][c] = m1;
-            hs[2][r][c] = m2;
-            hs[3][r][c] = m3;
-            hs[4][r][c] = m4;
-        }
-        __syncthreads();
-        for (int k = tid; k < kSsimTH * kSsimTW; k += 256) {
-            const int r = k / kSsimTW, c = k % kSsimTW;
-            const int gy = y0 + r, gx = x0 + c;
-            float mx = 0.f, my = 0.f, ex2 = 0.f, ey2 = 0.f, exy = 0.f;
-            #pragma unroll
-            for (int t = 0; t < kSsimWin; t++) {
-                const float w = T.g[t];
-                mx += w * hs[0][r + t][c];
-                my += w * hs[1][r + t][c];
-                ex2 += w * hs[2][r + t][c];
-                ey2 += w * hs[3][r + t][c];
-                exy += w * hs[4][r + t][c];
-            }
+        float2 mp[kSsimGrp / 2][4];
+        ssim_vpass<4>(T, s_h, vc, vr0, mp);
+        const int gx = x0 + vc;
+        #pragma unroll
+        for (int o = 0; o < kSsimGrp; o++) {
+            const int gy = y0 + vr0 + o;
             if (gx >= W || gy >= H) continue;
-            const float sx2 = ex2 - mx * mx, sy2 = ey2 - my * my, sxy = exy - mx * my;
+            float mo[4];
+            #pragma unroll
+            for (int m = 0; m < 4; m++) mo[m] = (o & 1) ? mp[o >> 1][m].y : mp[o >> 1][m].x;
+            const float mx = mo[0], my = mo[1];
+            const float m2 = mx * mx + my * my, sxy = mo[3] - mx * my;
             const float a1 = 2.f * mx * my + kSsimC1, a2 = 2.f * sxy + kSsimC2;
-            const float b1 = mx * mx + my * my + kSsimC1, b2 = sx2 + sy2 + kSsimC2;
-            const float ib = 1.0f / (b1 * b2);
+            const float b1 = m2 + kSsimC1, b2 = (mo[2] - m2) + kSsimC2;
+            const float ib = __fdividef(1.0f, b1 * b2);  // b1 b2 >= C1 C2: in the fast quotient's range
             const float s = a1 * a2 * ib;
-            acc += s;
+            acc_s += s;
             const int64_t p = pb + (int64_t)gy * W + gx;
-            partial[9 * p + 3 * ch + 0] = (2.f * my * (a2 - a1) - 2.f * mx * s * (b2 - b1)) * ib;
-            partial[9 * p + 3 * ch + 1] = -s / b2;
-            partial[9 * p + 3 * ch + 2] = 2.f * a1 * ib;
+            float *pl = partial + (int64_t)(3 * ch) * T.n_pix + p;
+            pl[0] = (2.f * my * (a2 - a1) - 2.f * mx * s * (b2 - b1)) * ib;
+            pl[T.n_pix] = -s * b1 * ib;
+            pl[2 * T.n_pix] = 2.f * a1 * ib;
         }
         __syncthreads();
     }
-    acc = warp_sum(acc);
-    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    acc_s = warp_sum(acc_s);
+    if (lane == 0) red[warp] = acc_s;
     __syncthreads();
     if (tid == 0) {
         float s = 0.f;
-        for (int w = 0; w < 8; w++) s += red[w];
+        for (int w = 0; w < kSsimThreads / 32; w++) s += red[w];
         atomicAdd(loss, scale * s + (blockIdx.x == 0 ? constant : 0.0f));
     }
 }
 
-__global__ void __launch_bounds__(256) ssim_grad_kernel(const float *__restrict__ x, const float *__restrict__ y,
-                                                        SsimTiles T, const float *__restrict__ partial,
-                                                        float *__restrict__ d_rgb, float gsc)
+__global__ void __launch_bounds__(kSsimThreads) ssim_grad_kernel(const float *__restrict__ x,
+                                                                 const float *__restrict__ y, SsimTiles T,
+                                                                 const float *__restrict__ partial,
+                                                                 float *__restrict__ d_rgb, float gsc)
 {
-    __shared__ float sp[3][kSsimHH][kSsimHW];
-    __shared__ float hs[3][kSsimHH][kSsimTW];
+    extern __shared__ float smem[];
+    constexpr int kBuf = 3 * kSsimRows * kSsimInPitch;
+    float *s_in = smem;                                 // [2][3][rows][43]: a channel's three maps, double-buffered
+    float *s_h = smem + 2 * kBuf;                       // [3][rows][33]
+    float *s_out = s_h + 3 * kSsimRows * kSsimHPitch;  // [48][97]: dL/dx, RGB interleaved
     int v, x0, y0;
     ssim_tile_of(T, blockIdx.x, &v, &x0, &y0);
     const int W = T.width[v], H = T.height[v];
     const int64_t pb = T.pix_base[v];
-    const int tid = threadIdx.x;
-    for (int ch = 0; ch < 3; ch++) {
-        for (int k = tid; k < kSsimHH * kSsimHW; k += 256) {
-            const int r = k / kSsimHW, c = k % kSsimHW;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int hrow = (warp >> 2) * 32 + lane, hseg = warp & 3;
+    const int vc = lane, vr0 = warp * kSsimGrp;
+    // copies of channel ch's three maps (halo included) into buffer ch & 1
+    auto stage = [&](int ch) {
+        float *dst = s_in + (ch & 1) * kBuf;
+        for (int e = tid; e < 3 * kSsimRows * kSsimCols; e += kSsimThreads) {
+            const int m = e / (kSsimRows * kSsimCols), rem = e - m * (kSsimRows * kSsimCols);
+            const int r = rem / kSsimCols, c = rem - r * kSsimCols;
             const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + c;
-            float a = 0.f, b = 0.f, d = 0.f;
-            if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
+            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+            const int64_t idx = in ? (int64_t)(3 * ch + m) * T.n_pix + pb + (int64_t)gy * W + gx : 0;
+            cp_async4(dst + (m * kSsimRows + r) * kSsimInPitch + c, partial + idx, in);
+        }
+        cp_async_commit();
+    };
+    stage(0);
+    for (int ch = 0; ch < 3; ch++) {
+        if (ch < 2) {
+            stage(ch + 1);  // in flight while this channel is filtered
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        // this channel's image values for the output pixels, loaded ahead of the filtering
+        const int gx = x0 + vc;
+        float xs[kSsimGrp], ys[kSsimGrp];
+        #pragma unroll
+        for (int o = 0; o < kSsimGrp; o++) {
+            const int gy = y0 + vr0 + o;
+            xs[o] = ys[o] = 0.0f;
+            if (gx < W && gy < H) {
                 const int64_t p = pb + (int64_t)gy * W + gx;
-                a = partial[9 * p + 3 * ch + 0];
-                b = partial[9 * p + 3 * ch + 1];
-                d = partial[9 * p + 3 * ch + 2];
+                xs[o] = x[3 * p + ch];
+                ys[o] = y[3 * p + ch];
             }
-            sp[0][r][c] = a;
-            sp[1][r][c] = b;
-            sp[2][r][c] = d;
+        }
+        if (hrow < kSsimRows) {
+            const float *r0 = s_in + (ch & 1) * kBuf + hrow * kSsimInPitch + hseg * kSsimSeg;
+            float2 acc[kSsimSeg / 2][3];
+            ssim_hpass<3>(T, [&](int i, float (&f)[3]) {
+                f[0] = r0[i];
+                f[1] = r0[kSsimRows * kSsimInPitch + i];
+                f[2] = r0[2 * kSsimRows * kSsimInPitch + i];
+            }, acc);
+            #pragma unroll
+            for (int p = 0; p < kSsimSeg / 2; p++)
+                #pragma unroll
+                for (int m = 0; m < 3; m++) {
+                    float *dst = s_h + (m * kSsimRows + hrow) * kSsimHPitch + hseg * kSsimSeg + 2 * p;
+                    dst[0] = acc[p][m].x;
+                    dst[1] = acc[p][m].y;
+                }
         }
         __syncthreads();
-        for (int k = tid; k < kSsimHH * kSsimTW; k += 256) {
-            const int r = k / kSsimTW, c = k % kSsimTW;
-            float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+        float2 fp[kSsimGrp / 2][3];
+        ssim_vpass<3>(T, s_h, vc, vr0, fp);
+        #pragma unroll
+        for (int o = 0; o < kSsimGrp; o++) {
+            float f[3];
             #pragma unroll
-            for (int t = 0; t < kSsimWin; t++) {
-                const float w = T.g[t];
-                m0 += w * sp[0][r][c + t];
-                m1 += w * sp[1][r][c + t];
-                m2 += w * sp[2][r][c + t];
-            }
-            hs[0][r][c] = m0;
-            hs[1][r][c] = m1;
-            hs[2][r][c] = m2;
-        }
-        __syncthreads();
-        for (int k = tid; k < kSsimTH * kSsimTW; k += 256) {
-            const int r = k / kSsimTW, c = k % kSsimTW;
-            const int gy = y0 + r, gx = x0 + c;
-            if (gx >= W || gy >= H) continue;
-            float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-            #pragma unroll
-            for (int t = 0; t < kSsimWin; t++) {
-                const float w = T.g[t];
-                f0 += w * hs[0][r + t][c];
-                f1 += w * hs[1][r + t][c];
-                f2 += w * hs[2][r + t][c];
-            }
-            const int64_t p = pb + (int64_t)gy * W + gx;
-            d_rgb[3 * p + ch] += gsc * (f0 + 2.f * x[3 * p + ch] * f1 + y[3 * p + ch] * f2);
+            for (int m = 0; m < 3; m++) f[m] = (o & 1) ? fp[o >> 1][m].y : fp[o >> 1][m].x;
+            s_out[(vr0 + o) * kSsimOutPitch + 3 * vc + ch] = f[0] + 2.f * xs[o] * f[1] + ys[o] * f[2];
         }
         __syncthreads();
     }
+    // the tile's rows of d_rgb are contiguous runs of 3 * 32 floats; all
+    // reads are issued before the writes
+    constexpr int kPer = kSsimTH * 3 * kSsimTW / kSsimThreads;
+    static_assert(kPer * kSsimThreads == kSsimTH * 3 * kSsimTW, "whole rounds");
+    int64_t idx[kPer];
+    float cur[kPer];
+    #pragma unroll
+    for (int i = 0; i < kPer; i++) {
+        const int e = tid + i * kSsimThreads;
+        const int r = e / (3 * kSsimTW), q = e - r * (3 * kSsimTW);
+        const int gy = y0 + r, gx = x0 + q / 3;
+        idx[i] = (gx < W && gy < H) ? 3 * (pb + (int64_t)gy * W + x0) + q : -1;
+        cur[i] = idx[i] >= 0 ? d_rgb[idx[i]] : 0.0f;
+    }
+    #pragma unroll
+    for (int i = 0; i < kPer; i++) {
+        const int e = tid + i * kSsimThreads;
+        const int r = e / (3 * kSsimTW), q = e - r * (3 * kSsimTW);
+        if (idx[i] >= 0) d_rgb[idx[i]] = cur[i] + gsc * s_out[r * kSsimOutPitch + q];
+    }
 }
 
-static gs_status_t make_ssim_tiles(const gs_view_t *views, int32_t n_views, SsimTiles *T, int64_t *n_pix)
+static gs_status_t make_ssim_tiles(const gs_view_t *views, int32_t n_views, SsimTiles *T)
 {
     ViewTable vt;
     gs_status_t st = make_view_table(views, n_views, &vt);
@@ -206,6 +363,7 @@ static gs_status_t make_ssim_tiles(const gs_view_t *views, int32_t n_views, Ssim
     }
     if (tiles >= (int64_t(1) << 31)) return GS_ERR_INVALID_ARG;
     T->base[n_views] = (int32_t)tiles;
+    T->n_pix = vt.n_pix_total;
     // window: exp(-i^2 / (2 * 1.5^2)), i = -5..5, normalised to sum 1
     double g[kSsimWin], sum = 0.0;
     for (int i = 0; i < kSsimWin; i++) {
@@ -214,7 +372,27 @@ static gs_status_t make_ssim_tiles(const gs_view_t *views, int32_t n_views, Ssim
         sum += g[i];
     }
     for (int i = 0; i < kSsimWin; i++) T->g[i] = (float)(g[i] / sum);
-    *n_pix = vt.n_pix_total;
+    for (int t = 0; t <= kSsimWin; t++)
+        T->gp[t] = make_float2(t < kSsimWin ? T->g[t] : 0.0f, t >= 1 ? T->g[t - 1] : 0.0f);
+    return GS_OK;
+}
+
+// Both kernels take more than 48 KB of dynamic shared memory, which has to be
+// allowed once per device.
+static gs_status_t ssim_set_smem_limits()
+{
+    static std::mutex mu;
+    static bool done[256] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return GS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return GS_OK;
+    if (cudaFuncSetAttribute(ssim_stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSsimStatsSmem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(ssim_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSsimGradSmem) !=
+            cudaSuccess)
+        return GS_ERR_CUDA;
+    done[dev] = true;
     return GS_OK;
 }
 
@@ -233,16 +411,17 @@ extern "C" gs_status_t gs_loss_ssim(const float *rgb, const float *target_rgb, c
 {
     if (!rgb || !target_rgb || !loss || !d_rgb || !workspace) return GS_ERR_INVALID_ARG;
     SsimTiles T;
-    int64_t P = 0;
-    gs_status_t st = make_ssim_tiles(views, n_views, &T, &P);
+    gs_status_t st = make_ssim_tiles(views, n_views, &T);
     if (st != GS_OK) return st;
+    const int64_t P = T.n_pix;
     if (workspace_bytes < gs_ssim_workspace_size(P)) return GS_ERR_INVALID_ARG;
+    if (ssim_set_smem_limits() != GS_OK) return GS_ERR_CUDA;
     cudaStream_t s = as_stream(stream);
     const int blocks = T.base[n_views];
     float *partial = static_cast<float *>(workspace);
     const float scale = (float)(-(double)weight / (3.0 * (double)P));
     // weight * (1 - mean s): block 0 adds the constant weight, every block -weight/(3P) times its sum of s
-    ssim_stats_kernel<<<blocks, 256, 0, s>>>(rgb, target_rgb, T, partial, loss, scale, weight);
-    ssim_grad_kernel<<<blocks, 256, 0, s>>>(rgb, target_rgb, T, partial, d_rgb, scale);
+    ssim_stats_kernel<<<blocks, kSsimThreads, kSsimStatsSmem, s>>>(rgb, target_rgb, T, partial, loss, scale, weight);
+    ssim_grad_kernel<<<blocks, kSsimThreads, kSsimGradSmem, s>>>(rgb, target_rgb, T, partial, d_rgb, scale);
     return launch_status();
 }

@@ -151,11 +151,12 @@ class MappingStep:
 
     def kernels_per_step(self):
         """Kernels of this library launched by one run() (memsets excluded)."""
-        import math
-        n_bits = 32 + max(0, math.ceil(math.log2(max(self.rast.n_tiles, 1))))
-        passes = (n_bits + 7) // 8
-        # project, bin (count, scan, emit, hist, passes, ranges), fwd, loss, bwd, pbwd colour + geometry
-        k = 1 + (3 + 1 + passes + 1) + 1 + 1 + 1 + 2
+        # bin: record count, scan, compaction, 4 depth passes, pair count, scan, emission, the tile-id
+        # passes (8 bits each) and the ranges
+        tile_passes = max(1, (max(self.rast.n_tiles - 1, 0).bit_length() + 7) // 8)
+        k_bin = 3 + 4 + 3 + tile_passes + 1
+        # project, bin, fwd, loss, bwd, pbwd colour + geometry
+        k = 1 + k_bin + 1 + 1 + 1 + 2
         k += 2 if self.zeta > 0 else 0
         k += 1 if self.keypoints is not None else 0
         k += 1 if self.optimise_params else 0

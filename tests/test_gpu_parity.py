@@ -315,12 +315,12 @@ def test_ssim_term_parity():
     top of an existing gradient."""
     from oracle import ssim as S
     rng = np.random.default_rng(7)
-    size = np.array([[45, 37], [64, 48], [19, 23]])
+    size = np.array([[45, 37], [64, 48], [19, 23], [131, 101]])  # several tiles and ragged edges
     P = int((size[:, 0] * size[:, 1]).sum())
     x = rng.uniform(0, 1, (P, 3)).astype(np.float32)
     y = np.clip(x + rng.normal(0, 0.15, x.shape), 0, 1).astype(np.float32)
     L, g = S.loss_ssim(x.astype(np.float64), y.astype(np.float64), size, weight=0.3)
-    views = gs.make_views([[50, 50, 20, 20]] * 3, size)
+    views = gs.make_views([[50, 50, 20, 20]] * len(size), size)
     loss = torch.full((1,), 0.25, device="cuda")
     base = rng.normal(0, 1e-5, (P, 3)).astype(np.float32)
     d_rgb = t(base)
