@@ -86,9 +86,9 @@ __device__ __forceinline__ bool splat_misses_box(const float4 &p, const float4 &
     return -0.5f * q < -__logf(255.0f * p.w) - (1e-3f + 2e-6f * mag);
 }
 
-// Kernel variants (pixels per thread x staged batch) the autotuner picks from.
-constexpr int kFwdVariants = 6;  // (1,256) (2,128) (2,256) (4,64) (4,128) (8,64)
-constexpr int kBwdVariants = 5;  // (1,64) (2,128) (4,64) (4,128) (8,64)
+// Kernel variants (pixels per thread 1, 2, 4, 8) the autotuner picks from.
+constexpr int kFwdVariants = 4;
+constexpr int kBwdVariants = 4;
 int render_variant_fwd();
 int render_variant_bwd();
 

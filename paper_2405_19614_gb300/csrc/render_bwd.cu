@@ -9,16 +9,23 @@
 //   dL/dalpha_i = T_i (c_i.gC + z_i gD) - s / (1 - alpha_i) + gA T_final / (1 - alpha_i),
 // and through alpha_i = min(0.99, o_i g_i), g_i = exp(power_i), to the
 // opacity, the 2D mean and the conic (no gradient where the clamp is active).
+// With t = dL/dalpha g (0 where the clamp is active) and d = mean - pixel,
+// power = -1/2 (A dx^2 + 2 B dx dy + C dy^2), so over a thread's pixels (one
+// column: dx is common) the mean and conic gradients need only
+// G = sum t, S1 = sum t dy, S2 = sum t dy^2:
+//   dL/du = -o (A dx G + B S1),  dL/dv = -o (B dx G + C S1),
+//   dL/dA = -o dx^2 G / 2,  dL/dB = -o dx S1,  dL/dC = -o S2 / 2,  dL/do = G.
 //
-// Each warp owns a 16 x 2*PPT band of the tile and walks only the staged
-// entries that can reach alpha = 1/255 in that band (the same conservative
-// test as the forward, 32 entries at a time).  All threads of a warp are at
-// the same list entry at the same time: a thread first sums the gradients of
-// its PPT pixels in registers, the warp reduces the ten sums with a
-// reduce-scatter butterfly (12 shuffles, one total per lane), the block adds
-// its warps' totals in shared memory, and only then are they added to HBM with
-// vector atomics: at most three per (Gaussian, tile).  PPT and BATCH are
-// picked by the autotuner.
+// Each warp owns a 16 x 2*PPT band of the tile and walks, independently of
+// the other warps, the entries up to its pixels' last blend backwards in
+// chunks of 32 (next chunk prefetched), keeping only the entries that can reach
+// alpha = 1/255 in its band (the same conservative test as the forward).  All
+// threads of a warp are at the same entry at the same time: a thread sums its
+// PPT pixels' terms in registers, the warp reduces the ten gradients with a
+// reduce-scatter butterfly (12 shuffles, one total per lane) and the ten lanes
+// holding a total add it to HBM in one predicated atomic instruction.  Per
+// warp band rather than per tile costs few extra atomics: after culling an
+// entry rarely reaches more than one band.  PPT is picked by the autotuner.
 #include "common.cuh"
 #include "render.cuh"
 
@@ -32,7 +39,7 @@ struct RenderBwdArgs {
     const float *final_T;
     const uint32_t *n_contrib;
     const float *d_rgb, *d_depth, *d_alpha;
-    float4 *grad2d;
+    float *grad2d;
     uint32_t *work_counter;
 };
 
@@ -46,34 +53,39 @@ struct BwdOccupancy {
     static constexpr int value = PPT == 1 ? 4 : PPT == 2 ? 8 : PPT == 4 ? 12 : 16;
 };
 
-template <int PPT, int BATCH>
+// Record and index of list entry idx (zeros past the end of the walk).
+__device__ __forceinline__ void load_bwd_entry(const RenderBwdArgs &a, int64_t rbase, uint32_t idx, bool valid,
+                                               float4 &r0, float4 &r1, float4 &r2, uint32_t &g)
+{
+    if (valid) {
+        g = a.vals[idx];
+        const int64_t o = rbase + g;
+        r0 = __ldg(a.rec + 3 * o);
+        r1 = __ldg(a.rec + 3 * o + 1);
+        r2 = __ldg(a.rec + 3 * o + 2);
+    } else {
+        g = 0;
+        r0 = r1 = r2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+template <int PPT>
 __global__ void __launch_bounds__(kTilePix / PPT, BwdOccupancy<PPT>::value)
     render_bwd_kernel(RenderBwdArgs a, ViewTable vt)
 {
-    constexpr int THREADS = kTilePix / PPT;
-    constexpr int WARPS = THREADS / 32;
+    constexpr int WARPS = kTilePix / PPT / 32;
     constexpr int BAND = 2 * PPT;  // rows per warp
-    constexpr int WORDS = BATCH / 32;
-    __shared__ float4 s_pos[BATCH];
-    __shared__ float4 s_con[BATCH];
-    __shared__ float4 s_col[BATCH];
-    __shared__ int64_t s_rid[BATCH];
-    // per-warp gradient totals of the staged entries; s_hit marks the entries
-    // a warp has written, so nothing needs clearing between batches
-    __shared__ float s_acc[WARPS][BATCH][kAcc + 1];
-    __shared__ uint32_t s_hit[WARPS][WORDS];
+    __shared__ float4 s_rec[WARPS][3][32];
+    __shared__ uint32_t s_gid[WARPS][32];
     __shared__ int s_item;
-    __shared__ uint32_t s_maxlast;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ly0 = warp * BAND + (lane >> 4);  // this thread's rows: ly0 + 2k
     int slot;
     bool slot_valid;
     reduce10_slot(lane, &slot, &slot_valid);
     for (;;) {
-        if (tid == 0) {
-            s_item = (int)atomicAdd(a.work_counter, 1u);
-            s_maxlast = 0;
-        }
+        __syncthreads();  // every warp is done with the previous tile
+        if (tid == 0) s_item = (int)atomicAdd(a.work_counter, 1u);
         __syncthreads();
         const int item = s_item;
         if (item >= vt.n_tiles_total) break;
@@ -114,42 +126,40 @@ __global__ void __launch_bounds__(kTilePix / PPT, BwdOccupancy<PPT>::value)
             }
             my_last = max(my_last, last[k]);
         }
-        if (my_last) atomicMax(&s_maxlast, my_last);
         const uint32_t warp_last = __reduce_max_sync(kFullMask, my_last);
-        __syncthreads();
-        const uint32_t maxlast = s_maxlast;
 
-        for (uint32_t bend = maxlast; bend > 0;) {
-            const uint32_t bstart = bend > (uint32_t)BATCH ? bend - BATCH : 0u;
-            const int cnt = (int)(bend - bstart);
-            for (int r = tid; r < cnt; r += THREADS) {
-                const int64_t g = rbase + a.vals[b + bstart + r];
-                s_rid[r] = g;
-                s_pos[r] = a.rec[3 * g];
-                s_con[r] = a.rec[3 * g + 1];
-                s_col[r] = a.rec[3 * g + 2];
-            }
-            __syncthreads();
-            for (int m = ((cnt - 1) >> 5) << 5; m >= 0; m -= 32) {
-              const int jl = m + lane;
-              uint32_t todo = __ballot_sync(kFullMask, jl < cnt && (uint32_t)(bstart + jl) < warp_last &&
-                                                           !splat_misses_box(s_pos[jl], s_con[jl], bx0, bx1, by0, by1));
-              uint32_t hit = 0;
-              while (todo) {
+        // chunks [lo, hi) of the list, from the warp's last blend down to 0
+        uint32_t hi = warp_last;
+        uint32_t lo = hi > 32u ? hi - 32u : 0u;
+        float4 n0, n1, n2;
+        uint32_t ng;
+        load_bwd_entry(a, rbase, b + lo + lane, lo + lane < hi, n0, n1, n2, ng);
+        while (hi > 0) {
+            const float4 r0 = n0, r1 = n1, r2 = n2;
+            const uint32_t g_self = ng;
+            const bool have = lo + lane < hi;
+            const uint32_t nlo = lo > 32u ? lo - 32u : 0u;
+            if (lo > 0) load_bwd_entry(a, rbase, b + nlo + lane, nlo + lane < lo, n0, n1, n2, ng);
+            uint32_t todo = __ballot_sync(kFullMask, have && !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
+            __syncwarp();  // the previous chunk's records have been read
+            s_rec[warp][0][lane] = r0;
+            s_rec[warp][1][lane] = r1;
+            s_rec[warp][2][lane] = r2;
+            s_gid[warp][lane] = g_self;
+            __syncwarp();
+            while (todo) {
                 const int bit = 31 - __clz(todo);
                 todo &= ~(1u << bit);
-                const int j = m + bit;
-                const uint32_t pos = bstart + (uint32_t)j;
-                float gr[kAcc];
-                #pragma unroll
-                for (int k = 0; k < kAcc; k++) gr[k] = 0.0f;
+                const uint32_t pos = lo + (uint32_t)bit;
+                float gc[4] = {0.f, 0.f, 0.f, 0.f};  // colour (3) and depth gradients
+                float G = 0.f, S1 = 0.f, S2 = 0.f, dx = 0.f;
                 bool contrib = false;
+                const float4 p = s_rec[warp][0][bit];
+                const float4 c = s_rec[warp][1][bit];
+                const float4 col = s_rec[warp][2][bit];
                 if (pos < my_last) {
-                    const float4 p = s_pos[j];
-                    const float4 c = s_con[j];
-                    const float4 col = s_col[j];
                     // exponents (and offsets) of this thread's pixels, two per packed evaluation
-                    float pw[PPT], dyk[PPT], dx;
+                    float pw[PPT], dyk[PPT];
                     if (PPT == 1) {
                         pw[0] = splat_power(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx, (float)py0 + 0.5f, &dx, &dyk[0]);
                     } else {
@@ -168,74 +178,58 @@ __global__ void __launch_bounds__(kTilePix / PPT, BwdOccupancy<PPT>::value)
                     #pragma unroll
                     for (int k = 0; k < PPT; k++) {
                         if (pos >= last[k]) continue;
-                        const float dy = dyk[k];
                         const float g = __expf(pw[k]);
                         const float araw = __fmul_rn(p.w, g);
+                        if (araw < kAlphaMin) continue;  // alpha = min(0.99, araw) < 1/255 exactly when araw is
                         const float alpha = fminf(kAlphaMax, araw);
-                        if (alpha < kAlphaMin) continue;
                         contrib = true;
                         // 1 - alpha >= 0.01: the fast reciprocal is within 2 ulp
                         const float inv_om = __fdividef(1.0f, 1.0f - alpha);
                         const float Tb = T[k] * inv_om;
                         const float w = alpha * Tb;
-                        gr[6] += gC0[k] * w;
-                        gr[7] += gC1[k] * w;
-                        gr[8] += gC2[k] * w;
-                        gr[9] += gD[k] * w;
+                        gc[0] += gC0[k] * w;
+                        gc[1] += gC1[k] * w;
+                        gc[2] += gC2[k] * w;
+                        gc[3] += gD[k] * w;
                         const float wgt = col.x * gC0[k] + col.y * gC1[k] + col.z * gC2[k] + p.z * gD[k];
                         const float dalpha = Tb * wgt + R[k] * inv_om;
                         R[k] -= wgt * w;
                         T[k] = Tb;
-                        if (araw < kAlphaMax) {
-                            gr[5] += dalpha * g;
-                            const float dpow = dalpha * araw;
-                            gr[0] += dpow * (-c.x * dx - c.y * dy);
-                            gr[1] += dpow * (-c.z * dy - c.y * dx);
-                            gr[2] += -0.5f * dx * dx * dpow;
-                            gr[3] += -dx * dy * dpow;
-                            gr[4] += -0.5f * dy * dy * dpow;
-                        }
+                        const float t = araw < kAlphaMax ? dalpha * g : 0.0f;
+                        const float u = t * dyk[k];
+                        G += t;
+                        S1 += u;
+                        S2 = fmaf(u, dyk[k], S2);
                     }
                 }
                 if (__any_sync(kFullMask, contrib)) {
+                    const float o = p.w, odx = o * dx;
+                    float gr[kAcc];
+                    gr[0] = -(c.x * odx * G + c.y * o * S1);
+                    gr[1] = -(c.y * odx * G + c.z * o * S1);
+                    gr[2] = -0.5f * odx * dx * G;
+                    gr[3] = -odx * S1;
+                    gr[4] = -0.5f * o * S2;
+                    gr[5] = G;
+                    gr[6] = gc[0];
+                    gr[7] = gc[1];
+                    gr[8] = gc[2];
+                    gr[9] = gc[3];
                     const float r = warp_reduce_scatter10(gr, lane);
-                    if (slot_valid) s_acc[warp][j][slot] = r;
-                    hit |= 1u << bit;
-                }
-              }
-              if (lane == 0) s_hit[warp][m >> 5] = hit;
-            }
-            __syncthreads();
-            for (int r = tid; r < cnt; r += THREADS) {
-                float q[kAcc];
-                #pragma unroll
-                for (int k = 0; k < kAcc; k++) q[k] = 0.0f;
-                bool any = false;
-                #pragma unroll
-                for (int w = 0; w < WARPS; w++) {
-                    if (!((s_hit[w][r >> 5] >> (r & 31)) & 1u)) continue;
-                    any = true;
-                    #pragma unroll
-                    for (int k = 0; k < kAcc; k++) q[k] += s_acc[w][r][k];
-                }
-                if (any) {
-                    float4 *dst = a.grad2d + 3 * s_rid[r];
-                    atomicAdd(dst, make_float4(q[0], q[1], q[2], q[3]));
-                    atomicAdd(dst + 1, make_float4(q[4], q[5], q[6], q[7]));
-                    atomicAdd(reinterpret_cast<float2 *>(dst + 2), make_float2(q[8], q[9]));
+                    if (slot_valid && r != 0.0f)
+                        atomicAdd(a.grad2d + 12 * (rbase + s_gid[warp][bit]) + slot, r);
                 }
             }
-            __syncthreads();
-            bend = bstart;
+            hi = lo;
+            lo = nlo;
         }
-        __syncthreads();  // every thread has read s_item and s_maxlast before they are reset
     }
 }
 
-template <int PPT, int BATCH>
+template <int PPT>
 static gs_status_t launch_bwd(const RenderBwdArgs &a, const ViewTable &vt, cudaStream_t s)
 {
-    auto kern = render_bwd_kernel<PPT, BATCH>;
+    auto kern = render_bwd_kernel<PPT>;
     constexpr int threads = kTilePix / PPT;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
@@ -279,13 +273,12 @@ extern "C" gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t 
     a.d_rgb = d_rgb;
     a.d_depth = d_depth;
     a.d_alpha = d_alpha;
-    a.grad2d = reinterpret_cast<float4 *>(grad2d);
+    a.grad2d = grad2d;
     a.work_counter = work_counter;
     switch (render_variant_bwd()) {
-    case 0: return launch_bwd<1, 64>(a, vt, s);
-    case 1: return launch_bwd<2, 128>(a, vt, s);
-    case 2: return launch_bwd<4, 64>(a, vt, s);
-    case 3: return launch_bwd<4, 128>(a, vt, s);
-    default: return launch_bwd<8, 64>(a, vt, s);
+    case 0: return launch_bwd<1>(a, vt, s);
+    case 1: return launch_bwd<2>(a, vt, s);
+    case 2: return launch_bwd<4>(a, vt, s);
+    default: return launch_bwd<8>(a, vt, s);
     }
 }

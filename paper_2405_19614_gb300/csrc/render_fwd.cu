@@ -3,16 +3,17 @@
 // sum_i f_i prod_{j<i} (1 - f_j) = 1 - T_final).
 //
 // One persistent launch covers every (view, tile) work item of every view:
-// blocks pull items from an atomic counter, so views of different sizes share
+// blocks pull tiles from an atomic counter, so views of different sizes share
 // one launch and long tiles do not hold up a static schedule.  A block of
 // 256 / PPT threads owns one 16x16 tile at a time; each warp owns a 16 x 2*PPT
-// band of it and each thread PPT pixels of that band (rows r, r + 2, ...), so
-// every splat record staged in shared memory serves PPT pixels per load.
-// Records are staged in batches of BATCH; each warp first drops, 32 at a time
-// and in parallel, the records that provably cannot reach alpha = 1/255 in its
-// band (splat_misses_box), then walks the rest.  The block leaves the batch
-// loop once all its pixels have run out of transmittance.  PPT and BATCH are
-// chosen per workload by the autotuner.
+// band of it and each thread PPT pixels of that band (one column, rows r,
+// r + 2, ...).  The warps of a tile run independently: each walks the tile's
+// list in chunks of 32 entries, one per lane, loading the next chunk's records
+// while it works on the current one, drops (in parallel) the entries that
+// provably cannot reach alpha = 1/255 in its band (splat_misses_box), stages
+// the rest in its own shared-memory slot and walks them; it stops once all its
+// pixels have run out of transmittance.  The only block barrier is between
+// tiles.  PPT is chosen per workload by the autotuner.
 #include "common.cuh"
 #include "render.cuh"
 
@@ -29,24 +30,37 @@ struct RenderFwdArgs {
     uint32_t *work_counter;
 };
 
+// The three float4 of list entry idx of a tile (zeros past the end).
+__device__ __forceinline__ void load_entry(const RenderFwdArgs &a, int64_t rbase, uint32_t idx, uint32_t e,
+                                           float4 &r0, float4 &r1, float4 &r2)
+{
+    if (idx < e) {
+        const int64_t g = rbase + a.vals[idx];
+        r0 = __ldg(a.rec + 3 * g);
+        r1 = __ldg(a.rec + 3 * g + 1);
+        r2 = __ldg(a.rec + 3 * g + 2);
+    } else {
+        r0 = r1 = r2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 // STATS = true counts, per pixel, the list entries evaluated and blended (the
-// algorithmic work of the compositing) instead of writing the image.
-template <int PPT, int BATCH, bool STATS>
+// algorithmic work of the compositing, without culling) instead of writing the
+// image.
+template <int PPT, bool STATS>
 __global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArgs a, ViewTable vt)
 {
-    constexpr int THREADS = kTilePix / PPT;
-    constexpr int BAND = 2 * PPT;      // rows per warp
-    __shared__ float4 s_pos[BATCH];    // (u, v, z, opacity)
-    __shared__ float4 s_con[BATCH];    // (conicA, conicB, conicC, -)
-    __shared__ float4 s_col[BATCH];    // (r, g, b, -)
+    constexpr int WARPS = kTilePix / PPT / 32;
+    constexpr int BAND = 2 * PPT;  // rows per warp
+    __shared__ float4 s_rec[WARPS][3][32];  // (u, v, z, opacity), (conic, du), (rgb, dv) of a chunk
     __shared__ int s_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ly0 = warp * BAND + (lane >> 4);  // this thread's rows: ly0 + 2k
     for (;;) {
+        __syncthreads();  // every warp is done with the previous tile
         if (tid == 0) s_item = (int)atomicAdd(a.work_counter, 1u);
         __syncthreads();
         const int item = s_item;
-        __syncthreads();
         if (item >= vt.n_tiles_total) break;
         const int v = view_of_tile(vt, item);
         const ViewInfo &V = vt.v[v];
@@ -73,70 +87,63 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArg
             live[k] = px < V.width && (py0 + 2 * k) < V.height;
             alive += live[k];
         }
-        for (uint32_t start = b; start < e; start += BATCH) {
-            if (__syncthreads_count(alive > 0) == 0) break;
-            #pragma unroll
-            for (int r = tid; r < BATCH; r += THREADS) {
-                const uint32_t idx = start + r;
-                if (idx < e) {
-                    const int64_t g = rbase + a.vals[idx];
-                    s_pos[r] = a.rec[3 * g];
-                    s_con[r] = a.rec[3 * g + 1];
-                    s_col[r] = a.rec[3 * g + 2];
-                }
-            }
-            __syncthreads();
-            const int cnt = (int)min((uint32_t)BATCH, e - start);
-            for (int m = 0; m < cnt && __any_sync(kFullMask, alive > 0); m += 32) {
-                // entries of this chunk that may reach alpha = 1/255 in the warp's band
-                const int jl = m + lane;
-                uint32_t todo = __ballot_sync(
-                    kFullMask, jl < cnt && (STATS || !splat_misses_box(s_pos[jl], s_con[jl], bx0, bx1, by0, by1)));
-                if (alive == 0) todo = 0;
-                while (todo) {
-                    const int j = m + __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    const float4 p = s_pos[j];
-                    const float4 c = s_con[j];
-                    const float4 col = s_col[j];
-                    // alphas of this thread's pixels, two per packed evaluation
-                    float al[PPT];
-                    if (PPT == 1) {
-                        al[0] = splat_alpha(p, c, col, sx, (float)py0 + 0.5f);
-                    } else {
-                        #pragma unroll
-                        for (int k = 0; k < PPT; k += 2) {
-                            const float2 a2 = splat_alpha2(p, c, col, sx,
-                                                           f2((float)(py0 + 2 * k) + 0.5f, (float)(py0 + 2 * k + 2) + 0.5f));
-                            al[k] = a2.x;
-                            al[(k + 1) % PPT] = a2.y;
-                        }
-                    }
+        float4 n0, n1, n2;  // this lane's entry of the next chunk
+        load_entry(a, rbase, b + lane, e, n0, n1, n2);
+        for (uint32_t m = b; m < e; m += 32) {
+            if (!__any_sync(kFullMask, alive > 0)) break;
+            const float4 r0 = n0, r1 = n1, r2 = n2;
+            const bool have = m + lane < e;
+            if (m + 32 < e) load_entry(a, rbase, m + 32 + lane, e, n0, n1, n2);
+            const bool keep = have && (STATS || !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
+            uint32_t todo = __ballot_sync(kFullMask, keep);
+            if (alive == 0) todo = 0;
+            __syncwarp();  // the previous chunk's records have been read
+            s_rec[warp][0][lane] = r0;
+            s_rec[warp][1][lane] = r1;
+            s_rec[warp][2][lane] = r2;
+            __syncwarp();
+            while (todo) {
+                const int j = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const float4 p = s_rec[warp][0][j];
+                const float4 c = s_rec[warp][1][j];
+                const float4 col = s_rec[warp][2][j];
+                // alphas of this thread's pixels, two per packed evaluation
+                float al[PPT];
+                if (PPT == 1) {
+                    al[0] = splat_alpha(p, c, col, sx, (float)py0 + 0.5f);
+                } else {
                     #pragma unroll
-                    for (int k = 0; k < PPT; k++) {
-                        if (!live[k]) continue;
-                        const float alpha = al[k];
-                        if (STATS) n_eval[k]++;
-                        if (alpha < kAlphaMin) continue;
-                        const float tT = T[k] * (1.0f - alpha);
-                        if (tT < kTMin) {
-                            live[k] = false;
-                            alive--;
-                            continue;
-                        }
-                        if (STATS) n_blend[k]++;
-                        const float w = alpha * T[k];
-                        C0[k] += col.x * w;
-                        C1[k] += col.y * w;
-                        C2[k] += col.z * w;
-                        D[k] += p.z * w;
-                        T[k] = tT;
-                        last[k] = start - b + (uint32_t)j + 1u;
+                    for (int k = 0; k < PPT; k += 2) {
+                        const float2 a2 = splat_alpha2(p, c, col, sx,
+                                                       f2((float)(py0 + 2 * k) + 0.5f, (float)(py0 + 2 * k + 2) + 0.5f));
+                        al[k] = a2.x;
+                        al[(k + 1) % PPT] = a2.y;
                     }
-                    if (alive == 0) break;
                 }
+                #pragma unroll
+                for (int k = 0; k < PPT; k++) {
+                    if (!live[k]) continue;
+                    const float alpha = al[k];
+                    if (STATS) n_eval[k]++;
+                    if (alpha < kAlphaMin) continue;
+                    const float tT = T[k] * (1.0f - alpha);
+                    if (tT < kTMin) {
+                        live[k] = false;
+                        alive--;
+                        continue;
+                    }
+                    if (STATS) n_blend[k]++;
+                    const float w = alpha * T[k];
+                    C0[k] += col.x * w;
+                    C1[k] += col.y * w;
+                    C2[k] += col.z * w;
+                    D[k] += p.z * w;
+                    T[k] = tT;
+                    last[k] = m - b + (uint32_t)j + 1u;
+                }
+                if (alive == 0) break;
             }
-            __syncthreads();
         }
         #pragma unroll
         for (int k = 0; k < PPT; k++) {
@@ -159,10 +166,10 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArg
     }
 }
 
-template <int PPT, int BATCH, bool STATS>
+template <int PPT, bool STATS>
 static gs_status_t launch_fwd(const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
 {
-    auto kern = render_fwd_kernel<PPT, BATCH, STATS>;
+    auto kern = render_fwd_kernel<PPT, STATS>;
     constexpr int threads = kTilePix / PPT;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
@@ -176,12 +183,10 @@ template <bool STATS>
 static gs_status_t dispatch_fwd(const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
 {
     switch (render_variant_fwd()) {
-    case 0: return launch_fwd<1, 256, STATS>(a, vt, s);
-    case 1: return launch_fwd<2, 128, STATS>(a, vt, s);
-    case 2: return launch_fwd<2, 256, STATS>(a, vt, s);
-    case 3: return launch_fwd<4, 64, STATS>(a, vt, s);
-    case 4: return launch_fwd<4, 128, STATS>(a, vt, s);
-    default: return launch_fwd<8, 64, STATS>(a, vt, s);
+    case 0: return launch_fwd<1, STATS>(a, vt, s);
+    case 1: return launch_fwd<2, STATS>(a, vt, s);
+    case 2: return launch_fwd<4, STATS>(a, vt, s);
+    default: return launch_fwd<8, STATS>(a, vt, s);
     }
 }
 
@@ -235,14 +240,14 @@ extern "C" gs_status_t gs_render_stats(const gs_projected_t *proj, int64_t n, co
     a.n_eval = n_eval;
     a.n_blend = n_blend;
     a.work_counter = work_counter;
-    return launch_fwd<1, 256, true>(a, vt, s);
+    return launch_fwd<1, true>(a, vt, s);
 }
 
-// Compositing kernel variants in use (pixels per thread x staged batch), set by
+// Compositing kernel variants in use (pixels per thread: 1, 2, 4, 8), set by
 // the autotuner; defaults suit 1200x680 views of room-scale scenes.
 namespace gs {
 static int g_variant_fwd = 1;
-static int g_variant_bwd = 3;
+static int g_variant_bwd = 2;
 int render_variant_fwd() { return g_variant_fwd; }
 int render_variant_bwd() { return g_variant_bwd; }
 }  // namespace gs
