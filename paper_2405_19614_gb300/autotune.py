@@ -1,5 +1,5 @@
-"""Autotuner for the compositing kernels (a5, a7): pixels per thread and splat
-records per shared-memory batch.
+"""Autotuner for the compositing kernels (a5, a7): pixels per thread (1, 2, 4
+or 8; a warp's band of a tile is 16 x 2 * that many rows).
 
 Every variant computes the same result (the forward bit for bit, the backward
 up to the order of floating-point additions); this times each one on the

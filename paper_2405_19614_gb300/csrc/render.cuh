@@ -86,6 +86,17 @@ __device__ __forceinline__ bool splat_misses_box(const float4 &p, const float4 &
     return -0.5f * q < -__logf(255.0f * p.w) - (1e-3f + 2e-6f * mag);
 }
 
+// Threads per block of the compositing kernels (each warp works alone).
+constexpr int kRenderThreads = 128;
+
+// Blocks per SM asked of the register allocator, per pixels per thread:
+// 64 registers a thread up to two pixels, 80 for four, 128 for eight.
+template <int PPT>
+struct RenderOccupancy {
+    static constexpr int fwd = PPT <= 2 ? 8 : PPT == 4 ? 6 : 4;
+    static constexpr int bwd = PPT <= 2 ? 8 : PPT == 4 ? 6 : 4;
+};
+
 // Kernel variants (pixels per thread 1, 2, 4, 8) the autotuner picks from.
 constexpr int kFwdVariants = 4;
 constexpr int kBwdVariants = 4;

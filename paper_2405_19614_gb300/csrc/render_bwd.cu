@@ -16,10 +16,11 @@
 //   dL/du = -o (A dx G + B S1),  dL/dv = -o (B dx G + C S1),
 //   dL/dA = -o dx^2 G / 2,  dL/dB = -o dx S1,  dL/dC = -o S2 / 2,  dL/do = G.
 //
-// Each warp owns a 16 x 2*PPT band of the tile and walks, independently of
-// the other warps, the entries up to its pixels' last blend backwards in
-// chunks of 32 (next chunk prefetched), keeping only the entries that can reach
-// alpha = 1/255 in its band (the same conservative test as the forward).  All
+// Work items are (view, tile, band) with a band of 16 x 2*PPT pixels, pulled
+// by warps from an atomic counter.  A warp walks the entries up to its
+// pixels' last blend backwards in chunks of 32 (next chunk prefetched),
+// keeping only the entries that can reach alpha = 1/255 in its band (the same
+// conservative test as the forward); warps never wait for one another.  All
 // threads of a warp are at the same entry at the same time: a thread sums its
 // PPT pixels' terms in registers, the warp reduces the ten gradients with a
 // reduce-scatter butterfly (12 shuffles, one total per lane) and the ten lanes
@@ -45,14 +46,6 @@ struct RenderBwdArgs {
 
 constexpr int kAcc = 10;
 
-// Blocks per SM asked of the register allocator: 64 registers a thread for
-// one and two pixels a thread, 80 for four, 128 for eight (no spills inside
-// the entry loop at these budgets).
-template <int PPT>
-struct BwdOccupancy {
-    static constexpr int value = PPT == 1 ? 4 : PPT == 2 ? 8 : PPT == 4 ? 12 : 16;
-};
-
 // Record and index of list entry idx (zeros past the end of the walk).
 __device__ __forceinline__ void load_bwd_entry(const RenderBwdArgs &a, int64_t rbase, uint32_t idx, bool valid,
                                                float4 &r0, float4 &r1, float4 &r2, uint32_t &g)
@@ -70,25 +63,26 @@ __device__ __forceinline__ void load_bwd_entry(const RenderBwdArgs &a, int64_t r
 }
 
 template <int PPT>
-__global__ void __launch_bounds__(kTilePix / PPT, BwdOccupancy<PPT>::value)
+__global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
     render_bwd_kernel(RenderBwdArgs a, ViewTable vt)
 {
-    constexpr int WARPS = kTilePix / PPT / 32;
-    constexpr int BAND = 2 * PPT;  // rows per warp
+    constexpr int WARPS = kRenderThreads / 32;
+    constexpr int BAND = 2 * PPT;         // rows per band
+    constexpr int BANDS = kTile / BAND;  // bands per tile
     __shared__ float4 s_rec[WARPS][3][32];
     __shared__ uint32_t s_gid[WARPS][32];
-    __shared__ int s_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ly0 = warp * BAND + (lane >> 4);  // this thread's rows: ly0 + 2k
+    const uint32_t n_items = (uint32_t)vt.n_tiles_total * BANDS;
     int slot;
     bool slot_valid;
     reduce10_slot(lane, &slot, &slot_valid);
     for (;;) {
-        __syncthreads();  // every warp is done with the previous tile
-        if (tid == 0) s_item = (int)atomicAdd(a.work_counter, 1u);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= vt.n_tiles_total) break;
+        uint32_t wi = 0;
+        if (lane == 0) wi = atomicAdd(a.work_counter, 1u);
+        wi = __shfl_sync(kFullMask, wi, 0);
+        if (wi >= n_items) break;
+        const int item = (int)(wi / BANDS), band = (int)(wi % BANDS);
+        const int ly0 = band * BAND + (lane >> 4);  // this thread's rows: ly0 + 2k
         const int v = view_of_tile(vt, item);
         const ViewInfo &V = vt.v[v];
         const int lt = item - V.tile_base;
@@ -97,7 +91,7 @@ __global__ void __launch_bounds__(kTilePix / PPT, BwdOccupancy<PPT>::value)
         const int py0 = ty0 + ly0;
         const float sx = (float)px + 0.5f;
         const float bx0 = (float)tx0 + 0.5f, bx1 = (float)tx0 + (kTile - 0.5f);
-        const float by0 = (float)(ty0 + warp * BAND) + 0.5f, by1 = by0 + (float)(BAND - 1);
+        const float by0 = (float)(ty0 + band * BAND) + 0.5f, by1 = by0 + (float)(BAND - 1);
         const uint32_t b = a.ranges[2 * item];
         const int64_t rbase = (int64_t)v * a.n;
 
@@ -230,12 +224,13 @@ template <int PPT>
 static gs_status_t launch_bwd(const RenderBwdArgs &a, const ViewTable &vt, cudaStream_t s)
 {
     auto kern = render_bwd_kernel<PPT>;
-    constexpr int threads = kTilePix / PPT;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, 0);
     const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-    const int grid = (int)(slots < vt.n_tiles_total ? slots : vt.n_tiles_total);
-    kern<<<grid > 0 ? grid : 1, threads, 0, s>>>(a, vt);
+    const int64_t warps_needed = (int64_t)vt.n_tiles_total * (kTile / (2 * PPT));
+    const int64_t blocks_needed = (warps_needed + kRenderThreads / 32 - 1) / (kRenderThreads / 32);
+    const int grid = (int)(slots < blocks_needed ? slots : blocks_needed);
+    kern<<<grid > 0 ? grid : 1, kRenderThreads, 0, s>>>(a, vt);
     return launch_status();
 }
 

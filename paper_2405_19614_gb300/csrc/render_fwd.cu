@@ -2,18 +2,17 @@
 // and D(p) likewise with the depths d_i; Sec. 3.3: border mask M_b(p) =
 // sum_i f_i prod_{j<i} (1 - f_j) = 1 - T_final).
 //
-// One persistent launch covers every (view, tile) work item of every view:
-// blocks pull tiles from an atomic counter, so views of different sizes share
-// one launch and long tiles do not hold up a static schedule.  A block of
-// 256 / PPT threads owns one 16x16 tile at a time; each warp owns a 16 x 2*PPT
-// band of it and each thread PPT pixels of that band (one column, rows r,
-// r + 2, ...).  The warps of a tile run independently: each walks the tile's
-// list in chunks of 32 entries, one per lane, loading the next chunk's records
-// while it works on the current one, drops (in parallel) the entries that
-// provably cannot reach alpha = 1/255 in its band (splat_misses_box), stages
-// the rest in its own shared-memory slot and walks them; it stops once all its
-// pixels have run out of transmittance.  The only block barrier is between
-// tiles.  PPT is chosen per workload by the autotuner.
+// One persistent launch covers every (view, tile, band) work item of every
+// view: warps pull items from an atomic counter, so views of different sizes
+// share one launch and long tiles do not hold up a static schedule.  A band is
+// 16 x 2*PPT pixels of a 16x16 tile and each thread owns PPT pixels of it (one
+// column, rows r, r + 2, ...).  A warp walks its tile's list in chunks of 32
+// entries, one per lane, loading the next chunk's records while it works on
+// the current one, drops (in parallel) the entries that provably cannot reach
+// alpha = 1/255 in its band (splat_misses_box), stages the rest in its own
+// shared-memory slot and walks them; it stops once all its pixels have run out
+// of transmittance.  Warps never wait for one another.  PPT is chosen per
+// workload by the autotuner.
 #include "common.cuh"
 #include "render.cuh"
 
@@ -48,20 +47,22 @@ __device__ __forceinline__ void load_entry(const RenderFwdArgs &a, int64_t rbase
 // algorithmic work of the compositing, without culling) instead of writing the
 // image.
 template <int PPT, bool STATS>
-__global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArgs a, ViewTable vt)
+__global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) render_fwd_kernel(RenderFwdArgs a,
+                                                                                             ViewTable vt)
 {
-    constexpr int WARPS = kTilePix / PPT / 32;
-    constexpr int BAND = 2 * PPT;  // rows per warp
+    constexpr int WARPS = kRenderThreads / 32;
+    constexpr int BAND = 2 * PPT;         // rows per band
+    constexpr int BANDS = kTile / BAND;  // bands per tile
     __shared__ float4 s_rec[WARPS][3][32];  // (u, v, z, opacity), (conic, du), (rgb, dv) of a chunk
-    __shared__ int s_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ly0 = warp * BAND + (lane >> 4);  // this thread's rows: ly0 + 2k
+    const uint32_t n_items = (uint32_t)vt.n_tiles_total * BANDS;
     for (;;) {
-        __syncthreads();  // every warp is done with the previous tile
-        if (tid == 0) s_item = (int)atomicAdd(a.work_counter, 1u);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= vt.n_tiles_total) break;
+        uint32_t wi = 0;
+        if (lane == 0) wi = atomicAdd(a.work_counter, 1u);
+        wi = __shfl_sync(kFullMask, wi, 0);
+        if (wi >= n_items) break;
+        const int item = (int)(wi / BANDS), band = (int)(wi % BANDS);
+        const int ly0 = band * BAND + (lane >> 4);  // this thread's rows: ly0 + 2k
         const int v = view_of_tile(vt, item);
         const ViewInfo &V = vt.v[v];
         const int lt = item - V.tile_base;
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(kTilePix / PPT) render_fwd_kernel(RenderFwdArg
         const float sx = (float)px + 0.5f;
         // the warp's band of pixel centres, for culling
         const float bx0 = (float)tx0 + 0.5f, bx1 = (float)tx0 + (kTile - 0.5f);
-        const float by0 = (float)(ty0 + warp * BAND) + 0.5f, by1 = by0 + (float)(BAND - 1);
+        const float by0 = (float)(ty0 + band * BAND) + 0.5f, by1 = by0 + (float)(BAND - 1);
         const uint32_t b = a.ranges[2 * item], e = a.ranges[2 * item + 1];
         const int64_t rbase = (int64_t)v * a.n;
 
@@ -170,12 +171,13 @@ template <int PPT, bool STATS>
 static gs_status_t launch_fwd(const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
 {
     auto kern = render_fwd_kernel<PPT, STATS>;
-    constexpr int threads = kTilePix / PPT;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, 0);
     const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-    const int grid = (int)(slots < vt.n_tiles_total ? slots : vt.n_tiles_total);
-    kern<<<grid > 0 ? grid : 1, threads, 0, s>>>(a, vt);
+    const int64_t warps_needed = (int64_t)vt.n_tiles_total * (kTile / (2 * PPT));
+    const int64_t blocks_needed = (warps_needed + kRenderThreads / 32 - 1) / (kRenderThreads / 32);
+    const int grid = (int)(slots < blocks_needed ? slots : blocks_needed);
+    kern<<<grid > 0 ? grid : 1, kRenderThreads, 0, s>>>(a, vt);
     return launch_status();
 }
 
