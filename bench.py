@@ -187,6 +187,10 @@ def build_workload(idx, scale, device):
     step = MappingStep(scene, cams["intr"], cams["size"], cams["viewmats"], t_rgb, t_depth, w_c=c.get("w_c", 1.0),
                        w_d=c.get("w_d", 0.5), use_gate=c.get("gate", False), keypoints=kp, pair_capacity=cap,
                        zeta=c.get("zeta", 0.0), device=device)
+    # map maintenance as densification leaves it: Gaussians in the spatial
+    # (Morton) order of their means (setup, not timed)
+    step.reorder_spatially()
+    torch.cuda.synchronize()
     return c, step, cap
 
 
@@ -507,7 +511,8 @@ def main_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": c["name"], "gaussians": w["N"], "views": w["V"], "pixels_per_step": px_per_step,
                    "pairs": w["K"], "visible": w["V_vis"], "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (params 236 MB + pair arrays), no flush"},
+                   "l2": "inputs larger than L2 (params 236 MB + pair arrays), no flush",
+                   "gaussian_order": "Morton order of the means (map maintenance at setup)"},
         "iters_per_s": 1e3 / ms,
         "graph": None if graph_ms is None else {"ms_per_step": graph_ms, "value": world * px_per_step / graph_ms / 1e3},
         "plain": plain,

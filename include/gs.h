@@ -344,6 +344,23 @@ typedef struct {
 gs_status_t gs_compact_rows(const int32_t *new_index, int64_t n, const gs_rows_t *arrays, int32_t n_arrays,
                             void *stream);
 
+/* Bytes of workspace of gs_spatial_order for n Gaussians (0 for n < 1). */
+size_t gs_spatial_order_workspace_size(int64_t n);
+
+/* Spatial order of the map (a layout service; the paper has no counterpart):
+ * new_index [n] (device) receives each Gaussian's rank in the Morton (Z-order)
+ * sequence of its mean, quantised to 1024 cells per axis of the means'
+ * bounding box in correctly rounded FP32 (q = min(1023, floor((m - lo) *
+ * (1024 / (hi - lo)))), 0 on a flat axis; x in the lowest bit); equal codes
+ * keep index order.  Applied with gs_compact_rows to every per-Gaussian array
+ * it stores Gaussians that are close in space next to each other, as a map
+ * grown by densification is, so that the 32 Gaussians of a warp are drawn in
+ * the same views.  means [n,3] device; workspace >= the size above, 256-byte
+ * aligned; status (device, may be NULL) receives GS_ERR_TIMEOUT if a bounded
+ * wait of the sort expires.  n < 2^31. */
+gs_status_t gs_spatial_order(const float *means, int64_t n, int32_t *new_index, void *workspace,
+                             size_t workspace_bytes, uint32_t *status, void *stream);
+
 /* View point selection (Sec. 3.3): keyframe i (i >= 1) is selected when
  * beta <= matches[i] < alpha * totals[i], with matches[i] = M_{i-1,i} the
  * feature matches between keyframes i-1 and i and totals[i] = T_{i-1,i} the

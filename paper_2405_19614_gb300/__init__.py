@@ -22,7 +22,8 @@ from ._lib import (GS_MAX_ADAM_GROUPS, GS_MAX_VIEWS, GS_TILE, GsAdamGroup, GsBin
 __all__ = ["gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd", "gs_render_stats", "gs_set_render_variants",
            "gs_get_render_variants", "gs_loss_l1", "gs_loss_ssim", "gs_render_bwd", "gs_render_bwd_splats",
            "gs_project_bwd", "gs_reproj_loss_grad", "gs_adam_step", "gs_pose_update", "gs_densify",
-           "gs_prune_select", "gs_compact_rows", "gs_select_views", "Rasterizer", "rasterize",
+           "gs_prune_select", "gs_compact_rows", "gs_spatial_order_workspace_size", "gs_spatial_order",
+           "gs_select_views", "Rasterizer", "rasterize",
            "GsError", "lib"]
 
 
@@ -226,6 +227,16 @@ def gs_compact_rows(new_index, pairs, stream=None):
         arr[k].row_floats = int(src.numel() // max(src.shape[0], 1))
     check(lib().gs_compact_rows(_ptr(new_index), new_index.numel(), arr, len(pairs), _stream(stream)),
           "gs_compact_rows")
+
+
+def gs_spatial_order_workspace_size(n):
+    return int(lib().gs_spatial_order_workspace_size(int(n)))
+
+
+def gs_spatial_order(means, new_index, workspace, status=None, stream=None):
+    """Rank of every Gaussian in the Morton order of its mean (int32 [n])."""
+    check(lib().gs_spatial_order(_ptr(means), means.shape[0], _ptr(new_index), _ptr(workspace), workspace.numel(),
+                                 _ptr(status), _stream(stream)), "gs_spatial_order")
 
 
 def gs_select_views(matches, totals, alpha=0.75, beta=20):

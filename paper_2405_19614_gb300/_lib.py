@@ -90,6 +90,8 @@ SIGNATURES = {
                     c_p, c_sz, c_p], c_i32),
     "gs_prune_select": ([c_p, c_i64, c_f, c_p, c_p, c_p, c_sz, c_p], c_i32),
     "gs_compact_rows": ([c_p, c_i64, P(GsRows), c_i32, c_p], c_i32),
+    "gs_spatial_order_workspace_size": ([c_i64], c_sz),
+    "gs_spatial_order": ([c_p, c_i64, c_p, c_p, c_sz, c_p, c_p], c_i32),
     "gs_select_views": ([c_p, c_p, c_i32, c_f, c_i32, c_p], c_i32),
 }
 

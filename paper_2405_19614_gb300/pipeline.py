@@ -149,6 +149,27 @@ class MappingStep:
             gs_adam_step(self.flat.buf, self.grad_buf, self.m, self.v, self.groups, self.step_count, stream=stream)
             close(tok)
 
+    def reorder_spatially(self, stream=None):
+        """Stores the Gaussians (parameters and Adam state) in the Morton order
+        of their means, as a map grown by densification is stored; rendering
+        results do not depend on the order.  Map maintenance, not part of a
+        step."""
+        from . import gs_compact_rows, gs_spatial_order, gs_spatial_order_workspace_size
+        n = self.flat.n
+        new_index = torch.empty(n, dtype=torch.int32, device=self.flat.buf.device)
+        ws = torch.empty(gs_spatial_order_workspace_size(n), dtype=torch.uint8, device=self.flat.buf.device)
+        gs_spatial_order(self.params["means"], new_index, ws, stream=stream)
+        bufs = [self.flat.buf, self.m, self.v]
+        news = [torch.empty_like(b) for b in bufs]
+        pairs = []
+        for b, nb in zip(bufs, news):
+            src, dst = self.flat.views(b), self.flat.views(nb)
+            pairs += [(src[k].reshape(n, -1), dst[k].reshape(n, -1)) for k in PARAM_ORDER]
+        gs_compact_rows(new_index, pairs, stream=stream)
+        self.flat.buf.copy_(news[0])
+        self.m.copy_(news[1])
+        self.v.copy_(news[2])
+
     def kernels_per_step(self):
         """Kernels of this library launched by one run() (memsets excluded)."""
         # bin: record count, scan, compaction, 4 depth passes, pair count, scan, emission, the tile-id

@@ -82,3 +82,72 @@ def test_view_selection_matches_oracle():
     M = rng.integers(0, 200, 500).tolist()
     T = rng.integers(1, 250, 500).tolist()
     assert gs.gs_select_views(M, T, 0.75, 20) == MU.select_views(M, T, 0.75, 20)
+
+
+def _spread10(v):
+    v = v.astype(np.uint32) & np.uint32(0x3FF)
+    out = np.zeros_like(v)
+    for b in range(10):
+        out |= ((v >> np.uint32(b)) & np.uint32(1)) << np.uint32(3 * b)
+    return out
+
+
+def _morton_ranks(means):
+    """Ranks by the Morton code of the FP32-quantised means (1024 cells per
+    axis of the bounding box), ties in index order: the definition, in numpy
+    float32 arithmetic (each operation correctly rounded, as on the GPU)."""
+    m = np.asarray(means, np.float32)
+    lo, hi = m.min(0), m.max(0)
+    q = np.zeros(m.shape, np.uint32)
+    for a in range(3):
+        ext = np.float32(hi[a] - lo[a])
+        if ext > 0:
+            t = (m[:, a] - lo[a]).astype(np.float32) * (np.float32(1024.0) / ext)
+            q[:, a] = np.where(t >= np.float32(1023.0), 1023, np.floor(t)).astype(np.uint32)
+    code = _spread10(q[:, 0]) | (_spread10(q[:, 1]) << np.uint32(1)) | (_spread10(q[:, 2]) << np.uint32(2))
+    order = np.argsort(code, kind="stable")
+    rank = np.empty(len(m), np.int32)
+    rank[order] = np.arange(len(m), dtype=np.int32)
+    return rank
+
+
+@pytest.mark.parametrize("n", [1, 37, 5000, 100003])
+def test_spatial_order_is_the_morton_rank(n):
+    sc = scenes.cube_scene(n, seed=11, sh_degree=0)
+    means = sc["means"].copy()
+    if n > 40:
+        means[5] = means[6]  # equal codes keep index order
+        means[:7, 2] = means[0, 2]
+    new_index = torch.empty(n, dtype=torch.int32, device="cuda")
+    ws = torch.empty(gs.gs_spatial_order_workspace_size(n), dtype=torch.uint8, device="cuda")
+    gs.gs_spatial_order(t(means), new_index, ws)
+    got = new_index.cpu().numpy()
+    assert sorted(got.tolist()) == list(range(n))
+    np.testing.assert_array_equal(got, _morton_ranks(means))
+
+
+def test_spatial_order_leaves_the_render_unchanged():
+    """Reordering the Gaussians changes no image (list order within a tile is
+    by depth; only exactly equal depths could swap)."""
+    from gpu_util import make_rast, params_on_device, viewmats_on_device
+    c = scenes.config(2, 0.02)
+    sc, cams = c["scene"], c["cams"]
+    n = sc["means"].shape[0]
+    rast = make_rast(sc, cams)
+    vm = viewmats_on_device(cams)
+    rast.forward(params_on_device(sc), vm)
+    ref = {k: rast.img[k].clone() for k in ("rgb", "depth", "alpha")}
+    new_index = torch.empty(n, dtype=torch.int32, device="cuda")
+    ws = torch.empty(gs.gs_spatial_order_workspace_size(n), dtype=torch.uint8, device="cuda")
+    gs.gs_spatial_order(t(sc["means"]), new_index, ws)
+    perm = new_index.cpu().numpy()
+    assert not np.array_equal(perm, np.arange(n))
+    sc2 = dict(sc)
+    for k in ("means", "log_scales", "quats", "opacity_logit", "sh"):
+        a = np.empty_like(sc[k])
+        a[perm] = sc[k]
+        sc2[k] = a
+    rast.forward(params_on_device(sc2), vm)
+    torch.cuda.synchronize()
+    for k in ref:
+        np.testing.assert_allclose(rast.img[k].cpu().numpy(), ref[k].cpu().numpy(), atol=1e-6, err_msg=k)
