@@ -250,6 +250,39 @@ def work_counts(step):
                 C=int(r.img["n_contrib"].sum(dtype=torch.int64)), sh_floats=3 * (r.sh_degree + 1) ** 2)
 
 
+TRAFFIC_SOURCES = {"render_bwd": ("render_bwd.cu", "render.cuh", "common.cuh")}
+
+
+def kernel_traffic(stage, workload, rast):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu
+    summary (profiles/traffic_<workload>.md), or None when there is none for
+    this kernel, variant and workload, or when the kernel's sources have
+    changed since the counters were taken."""
+    import hashlib
+    import re
+
+    import paper_2405_19614_gb300 as gs
+    files = TRAFFIC_SOURCES.get(stage)
+    if files is None:
+        return None
+    try:
+        text = open(os.path.join(ROOT, "profiles", f"traffic_{workload}.md")).read()
+    except OSError:
+        return None
+    m = re.search(rf"traffic {stage} variant=(\d+) workload={re.escape(workload)} bytes_per_launch=(\d+) "
+                  r"sources_sha256=([0-9a-f]+)", text)
+    if m is None:
+        return None
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2405_19614_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    _, bwd_variant, _, _ = gs.gs_get_render_variants()
+    if h.hexdigest() != m.group(3) or int(m.group(1)) != bwd_variant:
+        return None
+    return int(m.group(2))
+
+
 def stage_work(w):
     """Per-stage algorithmic bytes (HBM-bound stages) or FP32 flops (compositing)."""
     N, V, P, K, Vv, E, B, C, S = (w[k] for k in ("N", "V", "P", "K", "V_vis", "E", "B", "C", "sh_floats"))
@@ -493,7 +526,7 @@ def main_ours(args):
         return {"bound": "alu", "achieved": amount / sec / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": amount / sec / 1e12 / alu_peak, "algorithmic_flops": amount}
 
-    roofline = dict(roof(dom), kernel=dom, traffic=None)
+    roofline = dict(roof(dom), kernel=dom, traffic=kernel_traffic(dom, c["name"], step.rast))
     stages = {k: {"ms": stage_ms[k], **({"frac": roof(k)["frac"], "bound": roof(k)["bound"]} if k in works else {})}
               for k in stage_ms}
 
