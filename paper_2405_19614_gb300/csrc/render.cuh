@@ -97,9 +97,12 @@ struct RenderOccupancy {
     static constexpr int bwd = PPT <= 2 ? 8 : PPT == 4 ? 6 : 4;
 };
 
-// Kernel variants (pixels per thread 1, 2, 4, 8) the autotuner picks from.
-constexpr int kFwdVariants = 4;
-constexpr int kBwdVariants = 4;
+// Kernel variants the autotuner picks from, as (pixels per thread, band
+// width): (1, 8) (2, 8) (2, 16) (4, 8) (4, 16) (8, 16).  A warp's band is
+// BW x PPT * 32 / BW pixels; a thread's pixels share a column, 32 / BW rows
+// apart.
+constexpr int kFwdVariants = 6;
+constexpr int kBwdVariants = 6;
 int render_variant_fwd();
 int render_variant_bwd();
 

@@ -62,13 +62,15 @@ __device__ __forceinline__ void load_bwd_entry(const RenderBwdArgs &a, int64_t r
     }
 }
 
-template <int PPT>
+template <int PPT, int BW>
 __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
     render_bwd_kernel(RenderBwdArgs a, ViewTable vt)
 {
     constexpr int WARPS = kRenderThreads / 32;
-    constexpr int BAND = 2 * PPT;         // rows per band
-    constexpr int BANDS = kTile / BAND;  // bands per tile
+    constexpr int RS = 32 / BW;                  // rows between a thread's pixels
+    constexpr int BH = PPT * RS;                 // band height (width BW)
+    constexpr int BANDS_X = kTile / BW;
+    constexpr int BANDS = BANDS_X * (kTile / BH);  // bands per tile
     __shared__ float4 s_rec[WARPS][3][32];
     __shared__ uint32_t s_gid[WARPS][32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -82,16 +84,16 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
         wi = __shfl_sync(kFullMask, wi, 0);
         if (wi >= n_items) break;
         const int item = (int)(wi / BANDS), band = (int)(wi % BANDS);
-        const int ly0 = band * BAND + (lane >> 4);  // this thread's rows: ly0 + 2k
+        const int bxo = (band % BANDS_X) * BW, byo = (band / BANDS_X) * BH;  // band origin in the tile
         const int v = view_of_tile(vt, item);
         const ViewInfo &V = vt.v[v];
         const int lt = item - V.tile_base;
         const int tx0 = (lt % V.tiles_x) * kTile, ty0 = (lt / V.tiles_x) * kTile;
-        const int px = tx0 + (lane & (kTile - 1));
-        const int py0 = ty0 + ly0;
+        const int px = tx0 + bxo + lane % BW;
+        const int py0 = ty0 + byo + lane / BW;  // this thread's rows: py0 + RS k
         const float sx = (float)px + 0.5f;
-        const float bx0 = (float)tx0 + 0.5f, bx1 = (float)tx0 + (kTile - 0.5f);
-        const float by0 = (float)(ty0 + band * BAND) + 0.5f, by1 = by0 + (float)(BAND - 1);
+        const float bx0 = (float)(tx0 + bxo) + 0.5f, bx1 = bx0 + (float)(BW - 1);
+        const float by0 = (float)(ty0 + byo) + 0.5f, by1 = by0 + (float)(BH - 1);
         const uint32_t b = a.ranges[2 * item];
         const int64_t rbase = (int64_t)v * a.n;
 
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
         uint32_t my_last = 0;
         #pragma unroll
         for (int k = 0; k < PPT; k++) {
-            const int py = py0 + 2 * k;
+            const int py = py0 + RS * k;
             T[k] = 1.0f;
             gC0[k] = gC1[k] = gC2[k] = gD[k] = R[k] = 0.0f;
             last[k] = 0;
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
                         for (int k = 0; k < PPT; k += 2) {
                             float2 dy2;
                             const float2 p2 = splat_power2(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx,
-                                                           f2((float)(py0 + 2 * k) + 0.5f, (float)(py0 + 2 * k + 2) + 0.5f),
+                                                           f2((float)(py0 + RS * k) + 0.5f, (float)(py0 + RS * (k + 1)) + 0.5f),
                                                            &dx, &dy2);
                             pw[k] = p2.x;
                             pw[(k + 1) % PPT] = p2.y;
@@ -220,14 +222,14 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
     }
 }
 
-template <int PPT>
+template <int PPT, int BW>
 static gs_status_t launch_bwd(const RenderBwdArgs &a, const ViewTable &vt, cudaStream_t s)
 {
-    auto kern = render_bwd_kernel<PPT>;
+    auto kern = render_bwd_kernel<PPT, BW>;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, 0);
     const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-    const int64_t warps_needed = (int64_t)vt.n_tiles_total * (kTile / (2 * PPT));
+    const int64_t warps_needed = (int64_t)vt.n_tiles_total * (kTile / BW) * (kTile / (PPT * (32 / BW)));
     const int64_t blocks_needed = (warps_needed + kRenderThreads / 32 - 1) / (kRenderThreads / 32);
     const int grid = (int)(slots < blocks_needed ? slots : blocks_needed);
     kern<<<grid > 0 ? grid : 1, kRenderThreads, 0, s>>>(a, vt);
@@ -271,9 +273,11 @@ extern "C" gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t 
     a.grad2d = grad2d;
     a.work_counter = work_counter;
     switch (render_variant_bwd()) {
-    case 0: return launch_bwd<1>(a, vt, s);
-    case 1: return launch_bwd<2>(a, vt, s);
-    case 2: return launch_bwd<4>(a, vt, s);
-    default: return launch_bwd<8>(a, vt, s);
+    case 0: return launch_bwd<1, 8>(a, vt, s);
+    case 1: return launch_bwd<2, 8>(a, vt, s);
+    case 2: return launch_bwd<2, 16>(a, vt, s);
+    case 3: return launch_bwd<4, 8>(a, vt, s);
+    case 4: return launch_bwd<4, 16>(a, vt, s);
+    default: return launch_bwd<8, 16>(a, vt, s);
     }
 }

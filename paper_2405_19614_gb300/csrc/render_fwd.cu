@@ -46,13 +46,15 @@ __device__ __forceinline__ void load_entry(const RenderFwdArgs &a, int64_t rbase
 // STATS = true counts, per pixel, the list entries evaluated and blended (the
 // algorithmic work of the compositing, without culling) instead of writing the
 // image.
-template <int PPT, bool STATS>
+template <int PPT, int BW, bool STATS>
 __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) render_fwd_kernel(RenderFwdArgs a,
                                                                                              ViewTable vt)
 {
     constexpr int WARPS = kRenderThreads / 32;
-    constexpr int BAND = 2 * PPT;         // rows per band
-    constexpr int BANDS = kTile / BAND;  // bands per tile
+    constexpr int RS = 32 / BW;                  // rows between a thread's pixels
+    constexpr int BH = PPT * RS;                 // band height (width BW)
+    constexpr int BANDS_X = kTile / BW;
+    constexpr int BANDS = BANDS_X * (kTile / BH);  // bands per tile
     __shared__ float4 s_rec[WARPS][3][32];  // (u, v, z, opacity), (conic, du), (rgb, dv) of a chunk
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n_items = (uint32_t)vt.n_tiles_total * BANDS;
@@ -62,17 +64,17 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
         wi = __shfl_sync(kFullMask, wi, 0);
         if (wi >= n_items) break;
         const int item = (int)(wi / BANDS), band = (int)(wi % BANDS);
-        const int ly0 = band * BAND + (lane >> 4);  // this thread's rows: ly0 + 2k
+        const int bxo = (band % BANDS_X) * BW, byo = (band / BANDS_X) * BH;  // band origin in the tile
         const int v = view_of_tile(vt, item);
         const ViewInfo &V = vt.v[v];
         const int lt = item - V.tile_base;
         const int tx0 = (lt % V.tiles_x) * kTile, ty0 = (lt / V.tiles_x) * kTile;
-        const int px = tx0 + (lane & (kTile - 1));
-        const int py0 = ty0 + ly0;
+        const int px = tx0 + bxo + lane % BW;
+        const int py0 = ty0 + byo + lane / BW;  // this thread's rows: py0 + RS k
         const float sx = (float)px + 0.5f;
         // the warp's band of pixel centres, for culling
-        const float bx0 = (float)tx0 + 0.5f, bx1 = (float)tx0 + (kTile - 0.5f);
-        const float by0 = (float)(ty0 + band * BAND) + 0.5f, by1 = by0 + (float)(BAND - 1);
+        const float bx0 = (float)(tx0 + bxo) + 0.5f, bx1 = bx0 + (float)(BW - 1);
+        const float by0 = (float)(ty0 + byo) + 0.5f, by1 = by0 + (float)(BH - 1);
         const uint32_t b = a.ranges[2 * item], e = a.ranges[2 * item + 1];
         const int64_t rbase = (int64_t)v * a.n;
 
@@ -85,7 +87,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
             T[k] = 1.0f;
             C0[k] = C1[k] = C2[k] = D[k] = 0.0f;
             last[k] = n_eval[k] = n_blend[k] = 0;
-            live[k] = px < V.width && (py0 + 2 * k) < V.height;
+            live[k] = px < V.width && (py0 + RS * k) < V.height;
             alive += live[k];
         }
         float4 n0, n1, n2;  // this lane's entry of the next chunk
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
                     #pragma unroll
                     for (int k = 0; k < PPT; k += 2) {
                         const float2 a2 = splat_alpha2(p, c, col, sx,
-                                                       f2((float)(py0 + 2 * k) + 0.5f, (float)(py0 + 2 * k + 2) + 0.5f));
+                                                       f2((float)(py0 + RS * k) + 0.5f, (float)(py0 + RS * (k + 1)) + 0.5f));
                         al[k] = a2.x;
                         al[(k + 1) % PPT] = a2.y;
                     }
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
         }
         #pragma unroll
         for (int k = 0; k < PPT; k++) {
-            const int py = py0 + 2 * k;
+            const int py = py0 + RS * k;
             if (px >= V.width || py >= V.height) continue;
             const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
             if (STATS) {
@@ -167,14 +169,14 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
     }
 }
 
-template <int PPT, bool STATS>
+template <int PPT, int BW, bool STATS>
 static gs_status_t launch_fwd(const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
 {
-    auto kern = render_fwd_kernel<PPT, STATS>;
+    auto kern = render_fwd_kernel<PPT, BW, STATS>;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, 0);
     const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-    const int64_t warps_needed = (int64_t)vt.n_tiles_total * (kTile / (2 * PPT));
+    const int64_t warps_needed = (int64_t)vt.n_tiles_total * (kTile / BW) * (kTile / (PPT * (32 / BW)));
     const int64_t blocks_needed = (warps_needed + kRenderThreads / 32 - 1) / (kRenderThreads / 32);
     const int grid = (int)(slots < blocks_needed ? slots : blocks_needed);
     kern<<<grid > 0 ? grid : 1, kRenderThreads, 0, s>>>(a, vt);
@@ -185,10 +187,12 @@ template <bool STATS>
 static gs_status_t dispatch_fwd(const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
 {
     switch (render_variant_fwd()) {
-    case 0: return launch_fwd<1, STATS>(a, vt, s);
-    case 1: return launch_fwd<2, STATS>(a, vt, s);
-    case 2: return launch_fwd<4, STATS>(a, vt, s);
-    default: return launch_fwd<8, STATS>(a, vt, s);
+    case 0: return launch_fwd<1, 8, STATS>(a, vt, s);
+    case 1: return launch_fwd<2, 8, STATS>(a, vt, s);
+    case 2: return launch_fwd<2, 16, STATS>(a, vt, s);
+    case 3: return launch_fwd<4, 8, STATS>(a, vt, s);
+    case 4: return launch_fwd<4, 16, STATS>(a, vt, s);
+    default: return launch_fwd<8, 16, STATS>(a, vt, s);
     }
 }
 
@@ -242,14 +246,14 @@ extern "C" gs_status_t gs_render_stats(const gs_projected_t *proj, int64_t n, co
     a.n_eval = n_eval;
     a.n_blend = n_blend;
     a.work_counter = work_counter;
-    return launch_fwd<1, true>(a, vt, s);
+    return launch_fwd<1, 16, true>(a, vt, s);
 }
 
-// Compositing kernel variants in use (pixels per thread: 1, 2, 4, 8), set by
-// the autotuner; defaults suit 1200x680 views of room-scale scenes.
+// Compositing kernel variants in use (see kFwdVariants), set by the
+// autotuner; defaults suit 1200x680 views of room-scale scenes.
 namespace gs {
 static int g_variant_fwd = 1;
-static int g_variant_bwd = 2;
+static int g_variant_bwd = 3;
 int render_variant_fwd() { return g_variant_fwd; }
 int render_variant_bwd() { return g_variant_bwd; }
 }  // namespace gs
