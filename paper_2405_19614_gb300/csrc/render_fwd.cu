@@ -124,26 +124,28 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
                         al[(k + 1) % PPT] = a2.y;
                     }
                 }
+                // branch-free per pixel (a skipped pixel adds exactly zero), so
+                // the pixels' independent chains can interleave
                 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
-                    if (!live[k]) continue;
                     const float alpha = al[k];
-                    if (STATS) n_eval[k]++;
-                    if (alpha < kAlphaMin) continue;
+                    const bool hit = live[k] && alpha >= kAlphaMin;
                     const float tT = T[k] * (1.0f - alpha);
-                    if (tT < kTMin) {
-                        live[k] = false;
-                        alive--;
-                        continue;
+                    const bool stop = hit && tT < kTMin;  // stops before this entry
+                    const bool blend = hit && !stop;
+                    if (STATS) {
+                        n_eval[k] += live[k];
+                        n_blend[k] += blend;
                     }
-                    if (STATS) n_blend[k]++;
-                    const float w = alpha * T[k];
+                    const float w = blend ? alpha * T[k] : 0.0f;
                     C0[k] += col.x * w;
                     C1[k] += col.y * w;
                     C2[k] += col.z * w;
                     D[k] += p.z * w;
-                    T[k] = tT;
-                    last[k] = m - b + (uint32_t)j + 1u;
+                    T[k] = blend ? tT : T[k];
+                    last[k] = blend ? m - b + (uint32_t)j + 1u : last[k];
+                    live[k] = live[k] && !stop;
+                    alive -= stop;
                 }
                 if (alive == 0) break;
             }
