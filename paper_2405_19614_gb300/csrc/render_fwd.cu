@@ -78,16 +78,23 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
         const uint32_t b = a.ranges[2 * item], e = a.ranges[2 * item + 1];
         const int64_t rbase = (int64_t)v * a.n;
 
-        float T[PPT], C0[PPT], C1[PPT], C2[PPT], D[PPT];
-        uint32_t last[PPT], n_eval[PPT], n_blend[PPT];
-        bool live[PPT];
+        // pixel state in pairs (pixels 2i, 2i + 1 of the thread), updated with
+        // packed FP32x2 instructions; with one pixel a thread the second of
+        // the pair is never live
+        constexpr int NP = (PPT + 1) / 2;
+        float2 T[NP], C0[NP], C1[NP], C2[NP], D[NP];
+        uint32_t last[2 * NP], n_eval[2 * NP], n_blend[2 * NP];
+        bool live[2 * NP];
         int alive = 0;
         #pragma unroll
-        for (int k = 0; k < PPT; k++) {
-            T[k] = 1.0f;
-            C0[k] = C1[k] = C2[k] = D[k] = 0.0f;
+        for (int i = 0; i < NP; i++) {
+            T[i] = f2(1.0f);
+            C0[i] = C1[i] = C2[i] = D[i] = f2(0.0f);
+        }
+        #pragma unroll
+        for (int k = 0; k < 2 * NP; k++) {
             last[k] = n_eval[k] = n_blend[k] = 0;
-            live[k] = px < V.width && (py0 + RS * k) < V.height;
+            live[k] = k < PPT && px < V.width && (py0 + RS * k) < V.height;
             alive += live[k];
         }
         float4 n0, n1, n2;  // this lane's entry of the next chunk
@@ -111,41 +118,35 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
                 const float4 p = s_rec[warp][0][j];
                 const float4 c = s_rec[warp][1][j];
                 const float4 col = s_rec[warp][2][j];
-                // alphas of this thread's pixels, two per packed evaluation
-                float al[PPT];
-                if (PPT == 1) {
-                    al[0] = splat_alpha(p, c, col, sx, (float)py0 + 0.5f);
-                } else {
-                    #pragma unroll
-                    for (int k = 0; k < PPT; k += 2) {
-                        const float2 a2 = splat_alpha2(p, c, col, sx,
-                                                       f2((float)(py0 + RS * k) + 0.5f, (float)(py0 + RS * (k + 1)) + 0.5f));
-                        al[k] = a2.x;
-                        al[(k + 1) % PPT] = a2.y;
-                    }
-                }
-                // branch-free per pixel (a skipped pixel adds exactly zero), so
-                // the pixels' independent chains can interleave
+                // two pixels per packed evaluation and update; branch-free per
+                // pixel (a skipped pixel adds exactly zero), so the chains interleave
                 #pragma unroll
-                for (int k = 0; k < PPT; k++) {
-                    const float alpha = al[k];
-                    const bool hit = live[k] && alpha >= kAlphaMin;
-                    const float tT = T[k] * (1.0f - alpha);
-                    const bool stop = hit && tT < kTMin;  // stops before this entry
-                    const bool blend = hit && !stop;
-                    if (STATS) {
-                        n_eval[k] += live[k];
-                        n_blend[k] += blend;
+                for (int i = 0; i < NP; i++) {
+                    const float2 al = splat_alpha2(p, c, col, sx,
+                                                   f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f));
+                    const float2 tT = __fmul2_rn(T[i], __fadd2_rn(f2(1.0f), f2(-al.x, -al.y)));  // T (1 - alpha)
+                    const float2 aT = __fmul2_rn(al, T[i]);
+                    bool blend[2];
+                    #pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const int k = 2 * i + h;
+                        const bool hit = live[k] && (h ? al.y : al.x) >= kAlphaMin;
+                        const bool stop = hit && (h ? tT.y : tT.x) < kTMin;  // stops before this entry
+                        blend[h] = hit && !stop;
+                        if (STATS) {
+                            n_eval[k] += live[k];
+                            n_blend[k] += blend[h];
+                        }
+                        last[k] = blend[h] ? m - b + (uint32_t)j + 1u : last[k];
+                        live[k] = live[k] && !stop;
+                        alive -= stop;
                     }
-                    const float w = blend ? alpha * T[k] : 0.0f;
-                    C0[k] += col.x * w;
-                    C1[k] += col.y * w;
-                    C2[k] += col.z * w;
-                    D[k] += p.z * w;
-                    T[k] = blend ? tT : T[k];
-                    last[k] = blend ? m - b + (uint32_t)j + 1u : last[k];
-                    live[k] = live[k] && !stop;
-                    alive -= stop;
+                    const float2 w = f2(blend[0] ? aT.x : 0.0f, blend[1] ? aT.y : 0.0f);
+                    C0[i] = __ffma2_rn(f2(col.x), w, C0[i]);
+                    C1[i] = __ffma2_rn(f2(col.y), w, C1[i]);
+                    C2[i] = __ffma2_rn(f2(col.z), w, C2[i]);
+                    D[i] = __ffma2_rn(f2(p.z), w, D[i]);
+                    T[i] = f2(blend[0] ? tT.x : T[i].x, blend[1] ? tT.y : T[i].y);
                 }
                 if (alive == 0) break;
             }
@@ -155,16 +156,19 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
             const int py = py0 + RS * k;
             if (px >= V.width || py >= V.height) continue;
             const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
+            const int i = k >> 1;
+            const bool hi = k & 1;
             if (STATS) {
                 a.n_eval[pix] = n_eval[k];
                 a.n_blend[pix] = n_blend[k];
             } else {
-                a.rgb[3 * pix + 0] = C0[k];
-                a.rgb[3 * pix + 1] = C1[k];
-                a.rgb[3 * pix + 2] = C2[k];
-                a.depth[pix] = D[k];
-                a.alpha[pix] = 1.0f - T[k];
-                a.final_T[pix] = T[k];
+                const float t = hi ? T[i].y : T[i].x;
+                a.rgb[3 * pix + 0] = hi ? C0[i].y : C0[i].x;
+                a.rgb[3 * pix + 1] = hi ? C1[i].y : C1[i].x;
+                a.rgb[3 * pix + 2] = hi ? C2[i].y : C2[i].x;
+                a.depth[pix] = hi ? D[i].y : D[i].x;
+                a.alpha[pix] = 1.0f - t;
+                a.final_T[pix] = t;
                 a.n_contrib[pix] = last[k];
             }
         }
