@@ -90,11 +90,15 @@ __device__ __forceinline__ bool splat_misses_box(const float4 &p, const float4 &
 constexpr int kRenderThreads = 128;
 
 // Blocks per SM asked of the register allocator, per pixels per thread:
-// 64 registers a thread up to two pixels, 80 for four, 128 for eight.
+// 64 registers a thread up to two pixels, 80 for four (128 for the backward,
+// whose packed gradient state spills at 80), 128 for eight.
+#ifndef GS_BWD_BLOCKS_PPT4
+#define GS_BWD_BLOCKS_PPT4 4
+#endif
 template <int PPT>
 struct RenderOccupancy {
     static constexpr int fwd = PPT <= 2 ? 8 : PPT == 4 ? 6 : 4;
-    static constexpr int bwd = PPT <= 2 ? 8 : PPT == 4 ? 6 : 4;
+    static constexpr int bwd = PPT <= 2 ? 8 : PPT == 4 ? GS_BWD_BLOCKS_PPT4 : 4;
 };
 
 // Kernel variants the autotuner picks from, as (pixels per thread, band

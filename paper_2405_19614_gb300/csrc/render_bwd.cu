@@ -99,28 +99,41 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
 
         // per pixel: T running transmittance, gC/gD upstream gradients,
         // R = gA T_final - (sum over later blended entries of (c.gC + z gD) alpha T)
-        float T[PPT], gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], R[PPT];
-        uint32_t last[PPT];
+        // pixel state in pairs (pixels 2i, 2i + 1 of the thread) for packed
+        // FP32x2 updates; with one pixel a thread the second is never blended
+        constexpr int NP = (PPT + 1) / 2;
+        float2 T[NP], gC0[NP], gC1[NP], gC2[NP], gD[NP], R[NP];
+        uint32_t last[2 * NP];
         uint32_t my_last = 0;
         #pragma unroll
-        for (int k = 0; k < PPT; k++) {
-            const int py = py0 + RS * k;
-            T[k] = 1.0f;
-            gC0[k] = gC1[k] = gC2[k] = gD[k] = R[k] = 0.0f;
-            last[k] = 0;
-            if (px < V.width && py < V.height) {
-                const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
-                T[k] = a.final_T[pix];
-                last[k] = a.n_contrib[pix];
-                if (a.d_rgb) {
-                    gC0[k] = a.d_rgb[3 * pix];
-                    gC1[k] = a.d_rgb[3 * pix + 1];
-                    gC2[k] = a.d_rgb[3 * pix + 2];
+        for (int i = 0; i < NP; i++) {
+            float t[2] = {1.0f, 1.0f}, c0[2] = {0.f, 0.f}, c1[2] = {0.f, 0.f}, c2[2] = {0.f, 0.f}, d[2] = {0.f, 0.f},
+                  r[2] = {0.f, 0.f};
+            #pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int k = 2 * i + h;
+                const int py = py0 + RS * k;
+                last[k] = 0;
+                if (k < PPT && px < V.width && py < V.height) {
+                    const int64_t pix = V.pix_base + (int64_t)py * V.width + px;
+                    t[h] = a.final_T[pix];
+                    last[k] = a.n_contrib[pix];
+                    if (a.d_rgb) {
+                        c0[h] = a.d_rgb[3 * pix];
+                        c1[h] = a.d_rgb[3 * pix + 1];
+                        c2[h] = a.d_rgb[3 * pix + 2];
+                    }
+                    if (a.d_depth) d[h] = a.d_depth[pix];
+                    if (a.d_alpha) r[h] = a.d_alpha[pix] * t[h];
                 }
-                if (a.d_depth) gD[k] = a.d_depth[pix];
-                if (a.d_alpha) R[k] = a.d_alpha[pix] * T[k];
+                my_last = max(my_last, last[k]);
             }
-            my_last = max(my_last, last[k]);
+            T[i] = f2(t[0], t[1]);
+            gC0[i] = f2(c0[0], c0[1]);
+            gC1[i] = f2(c1[0], c1[1]);
+            gC2[i] = f2(c2[0], c2[1]);
+            gD[i] = f2(d[0], d[1]);
+            R[i] = f2(r[0], r[1]);
         }
         const uint32_t warp_last = __reduce_max_sync(kFullMask, my_last);
 
@@ -147,58 +160,59 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
                 const int bit = 31 - __clz(todo);
                 todo &= ~(1u << bit);
                 const uint32_t pos = lo + (uint32_t)bit;
-                float gc[4] = {0.f, 0.f, 0.f, 0.f};  // colour (3) and depth gradients
-                float G = 0.f, S1 = 0.f, S2 = 0.f, dx = 0.f;
+                // per pixel pair: colour (3) and depth gradients, and the sums
+                // G, S1, S2, accumulated two pixels at a time
+                float2 gc[4] = {f2(0.f), f2(0.f), f2(0.f), f2(0.f)};
+                float2 G2 = f2(0.f), S12 = f2(0.f), S22 = f2(0.f);
+                float dx = 0.f;
                 bool contrib = false;
                 const float4 p = s_rec[warp][0][bit];
                 const float4 c = s_rec[warp][1][bit];
                 const float4 col = s_rec[warp][2][bit];
                 if (pos < my_last) {
-                    // exponents (and offsets) of this thread's pixels, two per packed evaluation
-                    float pw[PPT], dyk[PPT];
-                    if (PPT == 1) {
-                        pw[0] = splat_power(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx, (float)py0 + 0.5f, &dx, &dyk[0]);
-                    } else {
-                        #pragma unroll
-                        for (int k = 0; k < PPT; k += 2) {
-                            float2 dy2;
-                            const float2 p2 = splat_power2(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx,
-                                                           f2((float)(py0 + RS * k) + 0.5f, (float)(py0 + RS * (k + 1)) + 0.5f),
-                                                           &dx, &dy2);
-                            pw[k] = p2.x;
-                            pw[(k + 1) % PPT] = p2.y;
-                            dyk[k] = dy2.x;
-                            dyk[(k + 1) % PPT] = dy2.y;
-                        }
-                    }
                     #pragma unroll
-                    for (int k = 0; k < PPT; k++) {
-                        if (pos >= last[k]) continue;
-                        const float g = __expf(pw[k]);
-                        const float araw = __fmul_rn(p.w, g);
-                        if (araw < kAlphaMin) continue;  // alpha = min(0.99, araw) < 1/255 exactly when araw is
-                        const float alpha = fminf(kAlphaMax, araw);
+                    for (int i = 0; i < NP; i++) {
+                        float2 dy;
+                        const float2 pw = splat_power2(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx,
+                                                       f2((float)(py0 + RS * 2 * i) + 0.5f,
+                                                          (float)(py0 + RS * (2 * i + 1)) + 0.5f),
+                                                       &dx, &dy);
+                        const float2 g = f2(__expf(pw.x), __expf(pw.y));
+                        const float2 araw = __fmul2_rn(f2(p.w), g);
+                        // alpha = min(0.99, araw) < 1/255 exactly when araw is
+                        const bool hx = pos < last[2 * i] && araw.x >= kAlphaMin;
+                        const bool hy = pos < last[2 * i + 1] && araw.y >= kAlphaMin;
+                        if (!(hx || hy)) continue;
                         contrib = true;
+                        // a pixel of the pair that does not blend this entry adds exactly zero
+                        const float2 al = f2(fminf(kAlphaMax, araw.x), fminf(kAlphaMax, araw.y));
+                        const float2 om = __fadd2_rn(f2(1.0f), f2(-al.x, -al.y));
                         // 1 - alpha >= 0.01: the fast reciprocal is within 2 ulp
-                        const float inv_om = __fdividef(1.0f, 1.0f - alpha);
-                        const float Tb = T[k] * inv_om;
-                        const float w = alpha * Tb;
-                        gc[0] += gC0[k] * w;
-                        gc[1] += gC1[k] * w;
-                        gc[2] += gC2[k] * w;
-                        gc[3] += gD[k] * w;
-                        const float wgt = col.x * gC0[k] + col.y * gC1[k] + col.z * gC2[k] + p.z * gD[k];
-                        const float dalpha = Tb * wgt + R[k] * inv_om;
-                        R[k] -= wgt * w;
-                        T[k] = Tb;
-                        const float t = araw < kAlphaMax ? dalpha * g : 0.0f;
-                        const float u = t * dyk[k];
-                        G += t;
-                        S1 += u;
-                        S2 = fmaf(u, dyk[k], S2);
+                        const float2 inv = f2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
+                        const float2 Tb = __fmul2_rn(T[i], inv);
+                        const float2 aTb = __fmul2_rn(al, Tb);
+                        const float2 w = f2(hx ? aTb.x : 0.0f, hy ? aTb.y : 0.0f);
+                        gc[0] = __ffma2_rn(gC0[i], w, gc[0]);
+                        gc[1] = __ffma2_rn(gC1[i], w, gc[1]);
+                        gc[2] = __ffma2_rn(gC2[i], w, gc[2]);
+                        gc[3] = __ffma2_rn(gD[i], w, gc[3]);
+                        float2 wgt = __fmul2_rn(f2(col.x), gC0[i]);
+                        wgt = __ffma2_rn(f2(col.y), gC1[i], wgt);
+                        wgt = __ffma2_rn(f2(col.z), gC2[i], wgt);
+                        wgt = __ffma2_rn(f2(p.z), gD[i], wgt);
+                        const float2 dalpha = __ffma2_rn(Tb, wgt, __fmul2_rn(R[i], inv));
+                        R[i] = __ffma2_rn(f2(-wgt.x, -wgt.y), w, R[i]);
+                        T[i] = f2(hx ? Tb.x : T[i].x, hy ? Tb.y : T[i].y);
+                        const float2 tg = __fmul2_rn(dalpha, g);
+                        const float2 t = f2(hx && araw.x < kAlphaMax ? tg.x : 0.0f, hy && araw.y < kAlphaMax ? tg.y : 0.0f);
+                        const float2 u = __fmul2_rn(t, dy);
+                        G2 = __fadd2_rn(G2, t);
+                        S12 = __fadd2_rn(S12, u);
+                        S22 = __ffma2_rn(u, dy, S22);
                     }
                 }
                 if (__any_sync(kFullMask, contrib)) {
+                    const float G = G2.x + G2.y, S1 = S12.x + S12.y, S2 = S22.x + S22.y;
                     const float o = p.w, odx = o * dx;
                     float gr[kAcc];
                     gr[0] = -(c.x * odx * G + c.y * o * S1);
@@ -207,10 +221,10 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
                     gr[3] = -odx * S1;
                     gr[4] = -0.5f * o * S2;
                     gr[5] = G;
-                    gr[6] = gc[0];
-                    gr[7] = gc[1];
-                    gr[8] = gc[2];
-                    gr[9] = gc[3];
+                    gr[6] = gc[0].x + gc[0].y;
+                    gr[7] = gc[1].x + gc[1].y;
+                    gr[8] = gc[2].x + gc[2].y;
+                    gr[9] = gc[3].x + gc[3].y;
                     const float r = warp_reduce_scatter10(gr, lane);
                     if (slot_valid && r != 0.0f)
                         atomicAdd(a.grad2d + 12 * (rbase + s_gid[warp][bit]) + slot, r);
