@@ -472,17 +472,41 @@ def main_ours(args):
         step.run()
     torch.cuda.synchronize()
     barrier(world)
+    # keyframes are double-buffered: the copy of step i + 1's keyframes (on a
+    # copy stream) overlaps step i; every step's copy is inside the timed region
+    compute = torch.cuda.current_stream()
+    copier = torch.cuda.Stream()
+    bufs = [(step.target_rgb, step.target_depth), (torch.empty_like(step.target_rgb), torch.empty_like(step.target_depth))]
+    ready = [torch.cuda.Event(), torch.cuda.Event()]
+    free = [torch.cuda.Event(), torch.cuda.Event()]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        step.target_rgb.copy_(h_rgb, non_blocking=True)
-        step.target_depth.copy_(h_depth, non_blocking=True)
+
+    def upload(k):
+        with torch.cuda.stream(copier):
+            bufs[k][0].copy_(h_rgb, non_blocking=True)
+            bufs[k][1].copy_(h_depth, non_blocking=True)
+            ready[k].record(copier)
+
+    for k in range(2):
+        free[k].record(compute)
+    e0.record(compute)
+    copier.wait_event(e0)
+    upload(0)
+    for i in range(args.steps):
+        cur = i % 2
+        if i + 1 < args.steps:
+            copier.wait_event(free[1 - cur])  # the step that last read that buffer is done
+            upload(1 - cur)
+        compute.wait_event(ready[cur])
+        step.target_rgb, step.target_depth = bufs[cur]
         step.viewmats.copy_(h_vm, non_blocking=True)
         step.run()
+        free[cur].record(compute)
         h_loss.copy_(step.loss, non_blocking=True)
-    e1.record()
+    e1.record(compute)
     torch.cuda.synchronize()
+    step.target_rgb, step.target_depth = bufs[0]
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     h2d = h_rgb.numel() * 4 + h_depth.numel() * 4 + h_vm.numel() * 4
 
