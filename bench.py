@@ -551,6 +551,12 @@ def main_ours(args):
                 "frac": amount / sec / 1e12 / alu_peak, "algorithmic_flops": amount}
 
     roofline = dict(roof(dom), kernel=dom, traffic=kernel_traffic(dom, c["name"], step.rast))
+    # combined roofline of the step: sum over stages of the time its algorithmic
+    # work needs at the bounding peak, against the measured step
+    def floor_ms(stage):
+        kind, amount = works[stage]
+        return amount / (hbm_peak * 1e9) * 1e3 if kind == "hbm" else amount / (alu_peak * 1e12) * 1e3
+    step_floor = sum(floor_ms(k) for k in stage_ms if k in works)
     stages = {k: {"ms": stage_ms[k], **({"frac": roof(k)["frac"], "bound": roof(k)["bound"]} if k in works else {})}
               for k in stage_ms}
 
@@ -581,6 +587,8 @@ def main_ours(args):
         "stages": stages,
         "work": w,
         "roofline": roofline,
+        "roofline_step": {"floor_ms": step_floor, "ms": ms, "frac": step_floor / ms,
+                          "stages": {k: floor_ms(k) for k in stage_ms if k in works}},
         "clocks": clk,
         "cpu_baseline": cpu,
     }
