@@ -219,6 +219,8 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
     __shared__ uint32_t s_r0[kPairChunk], s_r1[kPairChunk];
     __shared__ uint16_t s_v[kPairChunk];
     __shared__ uint32_t h[kMaxTilePasses][kRadix];
+    constexpr int kRun = 8;  // consecutive pairs a thread emits per round
+    __shared__ uint32_t s_tk[kEmitThreads * kRun], s_tv[kEmitThreads * kRun];
     clear_hist(h, tile_passes);
     uint32_t r[kPairItems], c[kPairItems];
     chunk_counts(recs, tt, *n_vis_p, r, c);
@@ -244,30 +246,69 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
     const uint64_t base = block_off[blockIdx.x];
     const uint32_t j0 = blockIdx.x * kPairChunk;
     const uint32_t nq = (uint32_t)block_total;
-    for (uint32_t q0 = 0; q0 < nq; q0 += kEmitThreads) {  // block-uniform trip count
-        const uint32_t q = q0 + threadIdx.x;
-        const uint64_t pos = base + q;
-        // pairs past the capacity are dropped (the capacity bit is already set)
-        const bool valid = q < nq && pos < (uint64_t)cap;
-        uint32_t tile = 0;
-        if (valid) {
-            // last record i with s_excl[i] <= q (records of zero count share their successor's offset)
-            int lo = 0, hi = kPairChunk;  // invariant: s_excl[lo] <= q < s_excl[hi]
+    // each thread makes kRun consecutive pairs: one search for the first, then
+    // a walk along the rectangle's rows (and on to the next records); the
+    // round's pairs go out through shared memory so the writes are coalesced
+    for (uint32_t q0 = 0; q0 < nq; q0 += kEmitThreads * kRun) {  // block-uniform trip count
+        const uint32_t qs = q0 + threadIdx.x * kRun;
+        uint32_t tile[kRun];
+        bool valid[kRun];
+        #pragma unroll
+        for (int j = 0; j < kRun; j++) {
+            tile[j] = 0;
+            valid[j] = false;
+        }
+        if (qs < nq) {
+            // last record i with s_excl[i] <= qs (records of zero count share their successor's offset)
+            int lo = 0, hi = kPairChunk;  // invariant: s_excl[lo] <= qs < s_excl[hi]
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
-                if (s_excl[mid] <= q) lo = mid; else hi = mid;
+                if (s_excl[mid] <= qs) lo = mid; else hi = mid;
             }
-            const uint32_t k = q - s_excl[lo];
-            const uint32_t r0 = s_r0[lo], r1 = s_r1[lo];
-            const uint32_t x0 = r0 & 0xffff, y0 = r0 >> 16, x1 = r1 & 0xffff;
-            const uint32_t w = x1 - x0 + 1;
-            const uint32_t ty = y0 + k / w, tx = x0 + k % w;
-            const ViewInfo &V = vt.v[s_v[lo]];
-            tile = (uint32_t)V.tile_base + ty * (uint32_t)V.tiles_x + tx;
-            tk[pos] = tile;
-            tv[pos] = j0 + (uint32_t)lo;
+            uint32_t x0, x1, tx, row, tiles_x;
+            auto enter = [&](int rec, uint32_t k) {  // record rec, its k-th tile
+                const uint32_t r0 = s_r0[rec], r1 = s_r1[rec];
+                x0 = r0 & 0xffff;
+                x1 = r1 & 0xffff;
+                const uint32_t w = x1 - x0 + 1, ky = k / w;
+                const ViewInfo &V = vt.v[s_v[rec]];
+                tiles_x = (uint32_t)V.tiles_x;
+                tx = x0 + (k - ky * w);
+                row = (uint32_t)V.tile_base + ((r0 >> 16) + ky) * tiles_x;
+            };
+            enter(lo, qs - s_excl[lo]);
+            #pragma unroll
+            for (int j = 0; j < kRun; j++) {
+                const uint32_t q = qs + j;
+                if (q >= nq) break;
+                if (base + q >= (uint64_t)cap) break;  // dropped: the capacity bit is already set
+                if (q >= s_excl[lo + 1]) {  // on to the next record with pairs
+                    do {
+                        lo++;
+                    } while (q >= s_excl[lo + 1]);
+                    enter(lo, 0);
+                }
+                tile[j] = row + tx;
+                valid[j] = true;
+                s_tk[threadIdx.x * kRun + j] = tile[j];
+                s_tv[threadIdx.x * kRun + j] = j0 + (uint32_t)lo;
+                if (++tx > x1) {
+                    tx = x0;
+                    row += tiles_x;
+                }
+            }
         }
-        count_digits_warp(h, tile, valid, tile_passes);
+        #pragma unroll
+        for (int j = 0; j < kRun; j++) count_digits_warp(h, tile[j], valid[j], tile_passes);
+        __syncthreads();
+        const uint32_t m = min((uint32_t)(kEmitThreads * kRun), nq - q0);
+        for (uint32_t i = threadIdx.x; i < m; i += kEmitThreads) {
+            const uint64_t pos = base + q0 + i;
+            if (pos >= (uint64_t)cap) break;
+            tk[pos] = s_tk[i];
+            tv[pos] = s_tv[i];
+        }
+        __syncthreads();
     }
     __syncthreads();
     flush_hist(h, tile_passes, hist);
