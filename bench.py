@@ -43,7 +43,9 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="Gaussian count scale (1 = full size)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="wall time of each CPU oracle sample")
+    ap.add_argument("--cpu-workers", type=int, default=0, help="oracle processes of the all-cores baseline "
+                    "(0 = every host core, as memory allows)")
     ap.add_argument("--profile-steps", type=int, default=0, help="run N untimed steps and exit (for ncu)")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default kernel variants")
     return ap.parse_args()
@@ -329,29 +331,140 @@ def oracle_step(scene, cams, t_rgb, t_depth, w_c, w_d, zeta=0.0):
     return f["bins"]["n_pix"]
 
 
-def cpu_sample(c, target_seconds, rows=None):
-    """Times the oracle's fwd+bwd on a crop of view 0 (rows starting at a
-    multiple of 16, so tiles are those of the full view)."""
+# Environment variables that cap the BLAS / OpenMP threads numpy may start:
+# each oracle worker is one thread, so `cores` counts the threads used.
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+                "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")
+_WORKER = {}
+GB_PER_WORKER = 3.0  # peak RSS of one worker on a full 1200x680 view of 1M Gaussians is ~1.8 GB
+
+
+def _oracle_init(workload, scale, ready):
+    _WORKER["c"] = scenes.config(workload, scale)
+    ready.wait(timeout=900)  # every worker holds its scene before the first timed strip
+
+
+def _oracle_strip(job):
+    """One oracle fwd+bwd over rows [y0, y0 + rows) of view v (y0 a multiple
+    of 16, so the tiles are those of the full view); returns (seconds, pixels)."""
+    v, y0, rows, seed = job
+    c = _WORKER["c"]
     cams = c["cams"]
-    W, H = (int(x) for x in cams["size"][0])
-    y0 = (H // 2) // 16 * 16
-    tgt_rng = np.random.default_rng(7)
+    P = int(cams["size"][v][0]) * rows
+    rng = np.random.default_rng(seed)
+    t_rgb = rng.uniform(0, 1, (P, 3))
+    t_depth = rng.uniform(0, 4, P)
+    cc = crop_cams(cams, v, y0, rows)
+    t0 = time.perf_counter()
+    oracle_step(c["scene"], cc, t_rgb, t_depth, c.get("w_c", 1.0), c.get("w_d", 0.5), c.get("zeta", 0.0))
+    return time.perf_counter() - t0, P
 
-    def run(r):
-        cc = crop_cams(cams, 0, y0, r)
-        P = W * r
-        t_rgb = tgt_rng.uniform(0, 1, (P, 3))
-        t_depth = tgt_rng.uniform(0, 4, P)
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def mem_available_gb():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return None
+
+
+class OraclePool:
+    """The oracle on `cores` spawned worker processes, one thread each, each
+    with its own copy of the workload's scene.  A sample is a set of strips
+    (tile-aligned row ranges of the keyframes) dealt out one per task; its
+    throughput is the pixels of all strips over the wall time of the batch."""
+
+    def __init__(self, workload, scale, cams, cores):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.cores = cores
+        self.V = len(cams["size"])
+        self.W, self.H = (int(x) for x in cams["size"][0])
+        saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+        os.environ.update({k: "1" for k in _THREAD_VARS})
+        try:
+            ready = ctx.Barrier(cores)
+            self.pool = ctx.Pool(cores, initializer=_oracle_init, initargs=(workload, scale, ready))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.seed = 0
+        self.fixed = self.per_row = None
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _jobs(self, rows, n):
+        strips = [(v, y0, min(rows, self.H - y0)) for v in range(self.V) for y0 in range(0, self.H, rows)]
+        jobs = []
+        for i in range(n):
+            v, y0, r = strips[i % len(strips)]
+            jobs.append((v, y0, r, 1000 + self.seed))
+            self.seed += 1
+        return jobs
+
+    def run(self, rows, per_core):
+        """Times per_core strips of `rows` rows on every worker."""
+        jobs = self._jobs(rows, self.cores * per_core)
         t0 = time.perf_counter()
-        oracle_step(c["scene"], cc, t_rgb, t_depth, c.get("w_c", 1.0), c.get("w_d", 0.5), c.get("zeta", 0.0))
-        return time.perf_counter() - t0, P
+        res = self.pool.map(_oracle_strip, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+        return dict(seconds=wall, pixels=sum(p for _, p in res), rows=rows, strips=len(jobs))
 
-    if rows is None:
-        dt, P = run(16)
-        per_row = dt / 16
-        rows = int(max(16, min(H - y0, target_seconds / max(per_row, 1e-6))) // 16 * 16)
-    dt, P = run(rows)
-    return dict(seconds=dt, pixels=P, rows=rows, width=W)
+    def plan(self, target_seconds):
+        """Strip height and strips per worker for a sample of about
+        target_seconds.  A strip costs a fixed part (mostly projecting every
+        Gaussian) plus a part per row that varies down the image, so the fit
+        takes a 16-row strip from the middle of each view and the full view."""
+        if self.fixed is None:
+            mid = (self.H // 2) // 16 * 16
+            probe = lambda y0, r: statistics.median(t for t, _ in self.pool.map(
+                _oracle_strip, [(i % self.V, y0, r, i) for i in range(self.cores)], chunksize=1))
+            t16, t_all = probe(mid, 16), probe(0, self.H)
+            self.per_row = max((t_all - t16) / max(self.H - 16, 1), 1e-5)
+            self.fixed = max(t16 - 16 * self.per_row, 0.0)
+        fit = (target_seconds - self.fixed) / self.per_row
+        rows = self.H if fit >= self.H else int(max(16, fit) // 16 * 16)
+        per_core = max(1, round(target_seconds / (self.fixed + rows * self.per_row)))
+        return rows, per_core
+
+    def sample(self, target_seconds):
+        rows, per_core = self.plan(target_seconds)
+        s = self.run(rows, per_core)
+        s["text"] = (f"oracle fwd+bwd of {s['strips']} strips of {self.W}x{rows} (tile-aligned rows of the "
+                     f"{self.V} keyframes, all Gaussians projected per strip) on {self.cores} worker "
+                     f"process(es) of one thread, {s['seconds']:.1f} s wall")
+        return s
+
+
+def oracle_workers(want):
+    """Workers for the all-cores baseline: every host core, as far as memory
+    allows each its own scene."""
+    n = host_cores() if want <= 0 else want
+    mem = mem_available_gb()
+    if mem is not None:
+        n = min(n, max(1, int(0.6 * mem / GB_PER_WORKER)))
+    return max(1, n)
 
 
 # --------------------------------------------------------------------------
@@ -364,23 +477,26 @@ def main_reference(args):
         return
     c = scenes.config(args.workload, args.scale)
     per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
-    probe = cpu_sample(c, per_step)
-    rows = probe["rows"]
-    for _ in range(args.warmup):
-        cpu_sample(c, per_step, rows)
-    tot, pix = 0.0, 0
-    for _ in range(args.steps):
-        s = cpu_sample(c, per_step, rows)
-        tot += s["seconds"]
-        pix += s["pixels"]
+    with OraclePool(args.workload, args.scale, c["cams"], oracle_workers(args.cpu_workers)) as pool:
+        rows, per_core = pool.plan(per_step)
+        for _ in range(args.warmup):
+            pool.run(rows, per_core)
+        tot, pix, text = 0.0, 0, ""
+        for _ in range(args.steps):
+            s = pool.run(rows, per_core)
+            tot += s["seconds"]
+            pix += s["pixels"]
+        text = (f"per step, oracle fwd+bwd of {s['strips']} strips of {pool.W}x{rows} (tile-aligned rows of "
+                f"the {pool.V} keyframes, all Gaussians projected per strip) on {pool.cores} worker "
+                f"process(es) of one thread")
+        cores = pool.cores
     v = pix / tot / 1e6
-    sample = f"oracle fwd+bwd of a {probe['width']}x{rows} crop of view 0 (all Gaussians projected)"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "Mpix/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": c["name"], "sample": sample},
-        "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": c["name"], "sample": text},
+        "cpu_baseline": {"value": v, "unit": "Mpix/s", "cores": cores, "kind": "oracle", "sample": text},
         "e2e": {"value": v, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -560,12 +676,17 @@ def main_ours(args):
     stages = {k: {"ms": stage_ms[k], **({"frac": roof(k)["frac"], "bound": roof(k)["bound"]} if k in works else {})}
               for k in stage_ms}
 
-    cpu = None
+    cpu = cpu_all = None
     if not args.no_cpu and rank == 0:
-        s = cpu_sample(c, args.cpu_seconds)
-        cpu = {"value": s["pixels"] / s["seconds"] / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
-               "sample": f"oracle fwd+bwd of a {s['width']}x{s['rows']} crop of view 0 "
-                         f"({s['seconds']:.1f} s, all Gaussians projected)"}
+        def line(s, cores):
+            return {"value": s["pixels"] / s["seconds"] / 1e6, "unit": "Mpix/s", "cores": cores,
+                    "kind": "oracle", "sample": s["text"]}
+        with OraclePool(args.workload, args.scale, c["cams"], 1) as pool:
+            cpu = line(pool.sample(args.cpu_seconds), 1)
+        n_all = oracle_workers(args.cpu_workers)
+        if n_all > 1:
+            with OraclePool(args.workload, args.scale, c["cams"], n_all) as pool:
+                cpu_all = line(pool.sample(args.cpu_seconds), n_all)
 
     value = world * px_per_step / ms / 1e3
     out = {
@@ -591,6 +712,7 @@ def main_ours(args):
                           "stages": {k: floor_ms(k) for k in stage_ms if k in works}},
         "clocks": clk,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
     }
     if rank == 0:
         print(json.dumps(out))
