@@ -98,22 +98,6 @@ __device__ __forceinline__ float warp_sum(float x)
     return x;
 }
 
-// Exponent of one splat at a pixel centre (sx, sy): power = -1/2 (A dx^2 +
-// C dy^2) - B dx dy with d = mean - pixel centre.  The mean is u + du: u - sx
-// is exact (both are close FP32 numbers) and the remainder du restores the
-// mean's precision.  Shared by the forward and backward passes so that both
-// take the same skip decisions bit for bit.
-__device__ __forceinline__ float splat_power(float mx, float my, float dmx, float dmy, float A, float B, float C,
-                                             float sx, float sy, float *dx_out, float *dy_out)
-{
-    const float dx = __fadd_rn(__fsub_rn(mx, sx), dmx), dy = __fadd_rn(__fsub_rn(my, sy), dmy);
-    const float q = __fmaf_rn(__fmul_rn(C, dy), dy, __fmul_rn(__fmul_rn(A, dx), dx));
-    const float p = __fmaf_rn(-__fmul_rn(B, dy), dx, __fmul_rn(-0.5f, q));
-    *dx_out = dx;
-    *dy_out = dy;
-    return p;
-}
-
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kTMin = 1e-4f;

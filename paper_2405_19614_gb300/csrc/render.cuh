@@ -5,46 +5,67 @@
 
 namespace gs {
 
-// alpha_i = min(0.99, o_i exp(power_i)) at the pixel centre (sx, sy).  The
-// forward and backward kernels both go through splat_power and this exact
-// expression, so they take the same skip decisions bit for bit.
-__device__ __forceinline__ float splat_alpha(const float4 &p, const float4 &c, const float4 &col, float sx, float sy)
-{
-    float dx, dy;
-    const float power = splat_power(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx, sy, &dx, &dy);
-    return fminf(kAlphaMax, __fmul_rn(p.w, __expf(power)));
-}
-
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-// splat_power at two pixel centres of one column, (sx, sy.x) and (sx, sy.y):
-// the same IEEE operations in the same order, two at a time in packed FP32x2
-// instructions, so each component equals splat_power bit for bit.  dx is
-// shared by both pixels.
-__device__ __forceinline__ float2 splat_power2(float mx, float my, float dmx, float dmy, float A, float B, float C,
-                                               float sx, float2 sy, float *dx_out, float2 *dy_out)
+// 2^x by the approximate base-2 exponential instruction (a relative error of
+// a few units in the last place; results below 2^-126 flush to zero).
+__device__ __forceinline__ float ex2_approx(float x)
 {
-    const float dx = __fadd_rn(__fsub_rn(mx, sx), dmx);
-    const float2 dy = __fadd2_rn(__fadd2_rn(f2(my), f2(-sy.x, -sy.y)), f2(dmy));
-    const float adx2 = __fmul_rn(__fmul_rn(A, dx), dx);
-    const float2 q = __ffma2_rn(__fmul2_rn(f2(C), dy), dy, f2(adx2));
-    const float2 bdy = __fmul2_rn(f2(B), dy);
-    const float2 p = __ffma2_rn(f2(-bdy.x, -bdy.y), f2(dx), __fmul2_rn(f2(-0.5f), q));
-    *dx_out = dx;
-    *dy_out = dy;
-    return p;
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
-// splat_alpha at two pixel centres of one column; each component equals
-// splat_alpha at that pixel bit for bit.
-__device__ __forceinline__ float2 splat_alpha2(const float4 &p, const float4 &c, const float4 &col, float sx, float2 sy)
+// The compositing evaluates alpha_i = min(0.99, o_i exp(power_i)) in base 2:
+// with power = -1/2 (A dx^2 + C dy^2) - B dx dy and d = mean - pixel centre,
+//   log2(o exp(power)) = log2(o) + A' dx^2 + dy (B' dx + C' dy),
+//   A' = -log2(e)/2 A, B' = -log2(e) B, C' = -log2(e)/2 C,
+// so an entry costs two packed FMAs per pixel pair up to the blend test, which
+// compares this logarithm with log2(1/255); the exponential is taken only
+// where the entry is blended.  The forward and backward kernels go through the
+// same helpers with the same explicitly rounded operations, so both take the
+// same skip decisions and the same alphas bit for bit.
+constexpr float kLog2e = 1.442695041f;
+constexpr float kLn2 = 0.6931471806f;
+constexpr float kLog2AlphaMin = -7.994353294f;  // FP32 value nearest log2(1/255), within 1e-7 relative of it
+
+// Turns a record, as staged in shared memory for the per-pixel walk, into the
+// base-2 form: p.w = log2(o), c.xyz = (A', B', C').  The mean remainders (c.w,
+// col.w), depth and colour are unchanged.
+__device__ __forceinline__ void stage_log2(float4 &p, float4 &c)
 {
-    float dx;
-    float2 dy;
-    const float2 power = splat_power2(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx, sy, &dx, &dy);
-    const float2 araw = __fmul2_rn(f2(p.w), f2(__expf(power.x), __expf(power.y)));
-    return f2(fminf(kAlphaMax, araw.x), fminf(kAlphaMax, araw.y));
+    p.w = __log2f(p.w);
+    c.x = __fmul_rn(c.x, -0.5f * kLog2e);
+    c.y = __fmul_rn(c.y, -kLog2e);
+    c.z = __fmul_rn(c.z, -0.5f * kLog2e);
+}
+
+// The part of log2(raw alpha) that a thread's pixels share (they lie in one
+// column sx): dx, log2(o) + A' dx^2 and B' dx.  The mean is u + du: u - sx is
+// exact (both are close FP32 numbers) and the remainder du restores the
+// mean's precision.
+struct SplatColumn {
+    float dx, base, bdx;
+};
+
+__device__ __forceinline__ SplatColumn splat_column(const float4 &p, const float4 &c, float sx)
+{
+    SplatColumn k;
+    k.dx = __fadd_rn(__fsub_rn(p.x, sx), c.w);
+    k.base = __fmaf_rn(__fmul_rn(c.x, k.dx), k.dx, p.w);
+    k.bdx = __fmul_rn(c.y, k.dx);
+    return k;
+}
+
+// log2(raw alpha) of a staged record at the two pixel centres (sx, sy.x) and
+// (sx, sy.y), with dy = mean - pixel centre per pixel.
+__device__ __forceinline__ float2 splat_log2a2(const SplatColumn &k, const float4 &p, const float4 &c,
+                                               const float4 &col, float2 sy, float2 *dy_out)
+{
+    const float2 dy = __fadd2_rn(__fadd2_rn(f2(p.y), f2(-sy.x, -sy.y)), f2(col.w));
+    *dy_out = dy;
+    return __ffma2_rn(dy, __ffma2_rn(f2(c.z), dy, f2(k.bdx)), f2(k.base));
 }
 
 // Minimum over t in [t0, t1] of P s^2 + 2 B s t + Q t^2 for a fixed s (Q > 0):

@@ -9,15 +9,17 @@
 //   dL/dalpha_i = T_i (c_i.gC + z_i gD) - s / (1 - alpha_i) + gA T_final / (1 - alpha_i),
 // and through alpha_i = min(0.99, o_i g_i), g_i = exp(power_i), to the
 // opacity, the 2D mean and the conic (no gradient where the clamp is active).
-// With t = dL/dalpha g (0 where the clamp is active) and d = mean - pixel,
+// With t = dL/dalpha o g (0 where the clamp is active; o g is the raw alpha
+// the walk computes) and d = mean - pixel,
 // power = -1/2 (A dx^2 + 2 B dx dy + C dy^2), so over a thread's pixels (one
 // column: dx is common) the mean and conic gradients need only
 // G = sum t, S1 = sum t dy, S2 = sum t dy^2:
-//   dL/du = -o (A dx G + B S1),  dL/dv = -o (B dx G + C S1),
-//   dL/dA = -o dx^2 G / 2,  dL/dB = -o dx S1,  dL/dC = -o S2 / 2,  dL/do = G.
+//   dL/du = -(A dx G + B S1),  dL/dv = -(B dx G + C S1),
+//   dL/dA = -dx^2 G / 2,  dL/dB = -dx S1,  dL/dC = -S2 / 2,  dL/do = G / o.
 //
-// Work items are (view, tile, band) with a band of 16 x 2*PPT pixels, pulled
-// by warps from an atomic counter.  A warp walks the entries up to its
+// Work items are (view, tile, band) with a band of BW x PPT * 32 / BW pixels
+// (a thread's PPT pixels share a column), pulled by warps from an atomic
+// counter.  A warp walks the entries up to its
 // pixels' last blend backwards in chunks of 32 (next chunk prefetched),
 // keeping only the entries that can reach alpha = 1/255 in its band (the same
 // conservative test as the forward); warps never wait for one another.  All
@@ -150,9 +152,11 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
             const uint32_t nlo = lo > 32u ? lo - 32u : 0u;
             if (lo > 0) load_bwd_entry(a, rbase, b + nlo + lane, nlo + lane < lo, n0, n1, n2, ng);
             uint32_t todo = __ballot_sync(kFullMask, have && !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
+            float4 q0 = r0, q1 = r1;
+            stage_log2(q0, q1);
             __syncwarp();  // the previous chunk's records have been read
-            s_rec[warp][0][lane] = r0;
-            s_rec[warp][1][lane] = r1;
+            s_rec[warp][0][lane] = q0;
+            s_rec[warp][1][lane] = q1;
             s_rec[warp][2][lane] = r2;
             s_gid[warp][lane] = g_self;
             __syncwarp();
@@ -161,30 +165,27 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
                 todo &= ~(1u << bit);
                 const uint32_t pos = lo + (uint32_t)bit;
                 // per pixel pair: colour (3) and depth gradients, and the sums
-                // G, S1, S2, accumulated two pixels at a time
+                // G, S1, S2 (of t = dL/dalpha o g), accumulated two pixels at a time
                 float2 gc[4] = {f2(0.f), f2(0.f), f2(0.f), f2(0.f)};
                 float2 G2 = f2(0.f), S12 = f2(0.f), S22 = f2(0.f);
-                float dx = 0.f;
                 bool contrib = false;
                 const float4 p = s_rec[warp][0][bit];
                 const float4 c = s_rec[warp][1][bit];
                 const float4 col = s_rec[warp][2][bit];
+                const SplatColumn kc = splat_column(p, c, sx);
                 if (pos < my_last) {
                     #pragma unroll
                     for (int i = 0; i < NP; i++) {
                         float2 dy;
-                        const float2 pw = splat_power2(p.x, p.y, c.w, col.w, c.x, c.y, c.z, sx,
-                                                       f2((float)(py0 + RS * 2 * i) + 0.5f,
-                                                          (float)(py0 + RS * (2 * i + 1)) + 0.5f),
-                                                       &dx, &dy);
-                        const float2 g = f2(__expf(pw.x), __expf(pw.y));
-                        const float2 araw = __fmul2_rn(f2(p.w), g);
-                        // alpha = min(0.99, araw) < 1/255 exactly when araw is
-                        const bool hx = pos < last[2 * i] && araw.x >= kAlphaMin;
-                        const bool hy = pos < last[2 * i + 1] && araw.y >= kAlphaMin;
+                        const float2 l2 = splat_log2a2(
+                            kc, p, c, col, f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f),
+                            &dy);
+                        const bool hx = pos < last[2 * i] && l2.x >= kLog2AlphaMin;
+                        const bool hy = pos < last[2 * i + 1] && l2.y >= kLog2AlphaMin;
                         if (!(hx || hy)) continue;
                         contrib = true;
                         // a pixel of the pair that does not blend this entry adds exactly zero
+                        const float2 araw = f2(ex2_approx(l2.x), ex2_approx(l2.y));  // o g
                         const float2 al = f2(fminf(kAlphaMax, araw.x), fminf(kAlphaMax, araw.y));
                         const float2 om = __fadd2_rn(f2(1.0f), f2(-al.x, -al.y));
                         // 1 - alpha >= 0.01: the fast reciprocal is within 2 ulp
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
                         const float2 dalpha = __ffma2_rn(Tb, wgt, __fmul2_rn(R[i], inv));
                         R[i] = __ffma2_rn(f2(-wgt.x, -wgt.y), w, R[i]);
                         T[i] = f2(hx ? Tb.x : T[i].x, hy ? Tb.y : T[i].y);
-                        const float2 tg = __fmul2_rn(dalpha, g);
+                        const float2 tg = __fmul2_rn(dalpha, araw);
                         const float2 t = f2(hx && araw.x < kAlphaMax ? tg.x : 0.0f, hy && araw.y < kAlphaMax ? tg.y : 0.0f);
                         const float2 u = __fmul2_rn(t, dy);
                         G2 = __fadd2_rn(G2, t);
@@ -212,15 +213,16 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
                     }
                 }
                 if (__any_sync(kFullMask, contrib)) {
+                    // staged conic (A', B', C') = -log2(e) (A/2, B, C/2)
                     const float G = G2.x + G2.y, S1 = S12.x + S12.y, S2 = S22.x + S22.y;
-                    const float o = p.w, odx = o * dx;
+                    const float dx = kc.dx, dxG = dx * G;
                     float gr[kAcc];
-                    gr[0] = -(c.x * odx * G + c.y * o * S1);
-                    gr[1] = -(c.y * odx * G + c.z * o * S1);
-                    gr[2] = -0.5f * odx * dx * G;
-                    gr[3] = -odx * S1;
-                    gr[4] = -0.5f * o * S2;
-                    gr[5] = G;
+                    gr[0] = (2.0f * kLn2) * c.x * dxG + kLn2 * c.y * S1;  // -(A dx G + B S1)
+                    gr[1] = kLn2 * c.y * dxG + (2.0f * kLn2) * c.z * S1;  // -(B dx G + C S1)
+                    gr[2] = -0.5f * dx * dxG;
+                    gr[3] = -dx * S1;
+                    gr[4] = -0.5f * S2;
+                    gr[5] = G * ex2_approx(-p.w);  // dL/do = G / o
                     gr[6] = gc[0].x + gc[0].y;
                     gr[7] = gc[1].x + gc[1].y;
                     gr[8] = gc[2].x + gc[2].y;

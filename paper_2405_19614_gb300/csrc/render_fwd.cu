@@ -5,14 +5,14 @@
 // One persistent launch covers every (view, tile, band) work item of every
 // view: warps pull items from an atomic counter, so views of different sizes
 // share one launch and long tiles do not hold up a static schedule.  A band is
-// 16 x 2*PPT pixels of a 16x16 tile and each thread owns PPT pixels of it (one
-// column, rows r, r + 2, ...).  A warp walks its tile's list in chunks of 32
+// BW x PPT * 32 / BW pixels of a 16x16 tile and each thread owns PPT pixels of
+// it (one column, rows r, r + 32 / BW, ...).  A warp walks its tile's list in chunks of 32
 // entries, one per lane, loading the next chunk's records while it works on
 // the current one, drops (in parallel) the entries that provably cannot reach
 // alpha = 1/255 in its band (splat_misses_box), stages the rest in its own
-// shared-memory slot and walks them; it stops once all its pixels have run out
+// shared-memory slot (in the base-2 form of render.cuh) and walks them; it stops once all its pixels have run out
 // of transmittance.  Warps never wait for one another.  PPT is chosen per
-// workload by the autotuner.
+// workload by the autotuner, with the band width BW.
 #include "common.cuh"
 #include "render.cuh"
 
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
     constexpr int BH = PPT * RS;                 // band height (width BW)
     constexpr int BANDS_X = kTile / BW;
     constexpr int BANDS = BANDS_X * (kTile / BH);  // bands per tile
-    __shared__ float4 s_rec[WARPS][3][32];  // (u, v, z, opacity), (conic, du), (rgb, dv) of a chunk
+    __shared__ float4 s_rec[WARPS][3][32];  // (u, v, z, log2 o), (base-2 conic, du), (rgb, dv) of a chunk
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n_items = (uint32_t)vt.n_tiles_total * BANDS;
     for (;;) {
@@ -107,9 +107,11 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
             const bool keep = have && (STATS || !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
             uint32_t todo = __ballot_sync(kFullMask, keep);
             if (alive == 0) todo = 0;
+            float4 q0 = r0, q1 = r1;
+            stage_log2(q0, q1);
             __syncwarp();  // the previous chunk's records have been read
-            s_rec[warp][0][lane] = r0;
-            s_rec[warp][1][lane] = r1;
+            s_rec[warp][0][lane] = q0;
+            s_rec[warp][1][lane] = q1;
             s_rec[warp][2][lane] = r2;
             __syncwarp();
             while (todo) {
@@ -118,19 +120,22 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
                 const float4 p = s_rec[warp][0][j];
                 const float4 c = s_rec[warp][1][j];
                 const float4 col = s_rec[warp][2][j];
+                const SplatColumn kc = splat_column(p, c, sx);
                 // two pixels per packed evaluation and update; branch-free per
                 // pixel (a skipped pixel adds exactly zero), so the chains interleave
                 #pragma unroll
                 for (int i = 0; i < NP; i++) {
-                    const float2 al = splat_alpha2(p, c, col, sx,
-                                                   f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f));
+                    float2 dy;
+                    const float2 l2 = splat_log2a2(
+                        kc, p, c, col, f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f), &dy);
+                    const float2 al = f2(fminf(kAlphaMax, ex2_approx(l2.x)), fminf(kAlphaMax, ex2_approx(l2.y)));
                     const float2 tT = __fmul2_rn(T[i], __fadd2_rn(f2(1.0f), f2(-al.x, -al.y)));  // T (1 - alpha)
                     const float2 aT = __fmul2_rn(al, T[i]);
                     bool blend[2];
                     #pragma unroll
                     for (int h = 0; h < 2; h++) {
                         const int k = 2 * i + h;
-                        const bool hit = live[k] && (h ? al.y : al.x) >= kAlphaMin;
+                        const bool hit = live[k] && (h ? l2.y : l2.x) >= kLog2AlphaMin;
                         const bool stop = hit && (h ? tT.y : tT.x) < kTMin;  // stops before this entry
                         blend[h] = hit && !stop;
                         if (STATS) {
