@@ -131,50 +131,4 @@ constexpr int kBwdVariants = 6;
 int render_variant_fwd();
 int render_variant_bwd();
 
-// Sums ten values over the 32 lanes of a warp by recursive halving: at each
-// step a lane keeps half of its values, sends the other half to the partner
-// lane and adds what the partner sent (12 shuffles in all).  On return lane L
-// holds the warp total of value index reduce10_index(L), valid where
-// reduce10_valid(L).
-__device__ __forceinline__ float warp_reduce_scatter10(const float (&g)[10], int lane)
-{
-    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4, u2 = lane & 2;
-    float a5[5], a3[3], a2[2];
-    #pragma unroll
-    for (int i = 0; i < 5; i++) {
-        const float lo = g[i], hi = g[i + 5];
-        a5[i] = (u16 ? hi : lo) + __shfl_xor_sync(kFullMask, u16 ? lo : hi, 16);
-    }
-    #pragma unroll
-    for (int i = 0; i < 3; i++) {
-        const float lo = a5[i], hi = (i + 3 < 5) ? a5[i + 3] : 0.0f;
-        a3[i] = (u8 ? hi : lo) + __shfl_xor_sync(kFullMask, u8 ? lo : hi, 8);
-    }
-    #pragma unroll
-    for (int i = 0; i < 2; i++) {
-        const float lo = a3[i], hi = (i + 2 < 3) ? a3[i + 2] : 0.0f;
-        a2[i] = (u4 ? hi : lo) + __shfl_xor_sync(kFullMask, u4 ? lo : hi, 4);
-    }
-    float a1 = (u2 ? a2[1] : a2[0]) + __shfl_xor_sync(kFullMask, u2 ? a2[0] : a2[1], 2);
-    return a1 + __shfl_xor_sync(kFullMask, a1, 1);
-}
-
-__host__ __device__ __forceinline__ void reduce10_slot(int lane, int *index, bool *valid)
-{
-    int base = 0, cnt = 10;
-    const int H[4] = {5, 3, 2, 1};
-    const int bit[4] = {16, 8, 4, 2};
-    #pragma unroll
-    for (int s = 0; s < 4; s++) {
-        if (lane & bit[s]) {
-            base += H[s];
-            cnt = cnt - H[s] > 0 ? cnt - H[s] : 0;
-        } else {
-            cnt = cnt < H[s] ? cnt : H[s];
-        }
-    }
-    *index = base;
-    *valid = cnt >= 1 && (lane & 1) == 0;
-}
-
 }  // namespace gs

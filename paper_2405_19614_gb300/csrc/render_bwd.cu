@@ -24,9 +24,11 @@
 // keeping only the entries that can reach alpha = 1/255 in its band (the same
 // conservative test as the forward); warps never wait for one another.  All
 // threads of a warp are at the same entry at the same time: a thread sums its
-// PPT pixels' terms in registers, the warp reduces the ten gradients with a
-// reduce-scatter butterfly (12 shuffles, one total per lane) and the ten lanes
-// holding a total add it to HBM in one predicated atomic instruction.  Per
+// PPT pixels' terms in registers, and the warp reduces the ten gradients of
+// three entries at a time through a transposed table in shared memory (ten
+// column stores a lane per entry, then one 32-value row sum a lane per three
+// entries); the 30 lanes holding a total add them to HBM in one predicated
+// atomic instruction.  Per
 // warp band rather than per tile costs few extra atomics: after culling an
 // entry rarely reaches more than one band.  PPT is picked by the autotuner.
 #include "common.cuh"
@@ -47,6 +49,16 @@ struct RenderBwdArgs {
 };
 
 constexpr int kAcc = 10;
+// The ten sums of kBatch consecutive entries are reduced over the warp
+// together: every lane stores its values as one column of a kBatch * 10 x 32
+// table in shared memory (rows padded to kRedPitch floats: column stores and
+// the 16-byte row loads below are free of bank conflicts), then lane j adds up
+// row j and the 30 lanes holding a total add them to HBM in one predicated
+// atomic instruction.
+constexpr int kBatch = 3;
+constexpr int kRedRows = kBatch * kAcc;
+constexpr int kRedPitch = 36;
+static_assert(kRedRows <= 32, "one row per lane");
 
 // Record and index of list entry idx (zeros past the end of the walk).
 __device__ __forceinline__ void load_bwd_entry(const RenderBwdArgs &a, int64_t rbase, uint32_t idx, bool valid,
@@ -75,11 +87,11 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
     constexpr int BANDS = BANDS_X * (kTile / BH);  // bands per tile
     __shared__ float4 s_rec[WARPS][3][32];
     __shared__ uint32_t s_gid[WARPS][32];
+    __shared__ __align__(16) float s_red[WARPS][kRedRows][kRedPitch];
+    __shared__ uint32_t s_bgid[WARPS][kBatch];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t n_items = (uint32_t)vt.n_tiles_total * BANDS;
-    int slot;
-    bool slot_valid;
-    reduce10_slot(lane, &slot, &slot_valid);
+    const int red_entry = lane / kAcc, red_value = lane % kAcc;  // the row this lane adds up
     for (;;) {
         uint32_t wi = 0;
         if (lane == 0) wi = atomicAdd(a.work_counter, 1u);
@@ -98,6 +110,26 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
         const float by0 = (float)(ty0 + byo) + 0.5f, by1 = by0 + (float)(BH - 1);
         const uint32_t b = a.ranges[2 * item];
         const int64_t rbase = (int64_t)v * a.n;
+        // entries waiting in s_red, and their reduction
+        int nb = 0;
+        auto flush = [&]() {
+            __syncwarp();  // every lane's columns (and lane 0's ids) are written
+            if (red_entry < nb) {
+                const float4 *row = reinterpret_cast<const float4 *>(&s_red[warp][lane][0]);
+                float4 q = row[0];
+                float2 lo = make_float2(q.x, q.y), hi = make_float2(q.z, q.w);
+                #pragma unroll
+                for (int c = 1; c < 8; c++) {
+                    q = row[c];
+                    lo = __fadd2_rn(lo, make_float2(q.x, q.y));
+                    hi = __fadd2_rn(hi, make_float2(q.z, q.w));
+                }
+                const float r = (lo.x + lo.y) + (hi.x + hi.y);
+                if (r != 0.0f) atomicAdd(a.grad2d + 12 * (rbase + s_bgid[warp][red_entry]) + red_value, r);
+            }
+            __syncwarp();  // the table may be written again
+            nb = 0;
+        };
 
         // per pixel: T running transmittance, gC/gD upstream gradients,
         // R = gA T_final - (sum over later blended entries of (c.gC + z gD) alpha T)
@@ -227,14 +259,16 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
                     gr[7] = gc[1].x + gc[1].y;
                     gr[8] = gc[2].x + gc[2].y;
                     gr[9] = gc[3].x + gc[3].y;
-                    const float r = warp_reduce_scatter10(gr, lane);
-                    if (slot_valid && r != 0.0f)
-                        atomicAdd(a.grad2d + 12 * (rbase + s_gid[warp][bit]) + slot, r);
+                    #pragma unroll
+                    for (int k = 0; k < kAcc; k++) s_red[warp][nb * kAcc + k][lane] = gr[k];
+                    if (lane == 0) s_bgid[warp][nb] = s_gid[warp][bit];
+                    if (++nb == kBatch) flush();
                 }
             }
             hi = lo;
             lo = nlo;
         }
+        if (nb > 0) flush();
     }
 }
 
