@@ -168,15 +168,31 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_stats_kernel(const float *_
     const int64_t pb = T.pix_base[v];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // stage: halo rows of 42 pixels x 3 channels are contiguous in both
-    // images; every copy is in flight at once
-    for (int e = tid; e < kSsimRows * 3 * kSsimCols; e += kSsimThreads) {
-        const int r = e / (3 * kSsimCols), q = e - r * (3 * kSsimCols);
-        const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + q / 3;
-        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-        const int64_t idx = in ? 3 * (pb + (int64_t)gy * W + (x0 - kSsimR)) + q : 0;
-        cp_async4(s_in + r * kSsimInPitchXY + q, x + idx, in);
-        cp_async4(s_in + (kSsimRows + r) * kSsimInPitchXY + q, y + idx, in);
+    // stage: halo rows of 42 pixels x 3 channels (126 floats) are contiguous
+    // in both images; a warp copies whole rows and a lane the same four
+    // positions of every row, whose column bounds are tested once; every copy
+    // is in flight at once
+    constexpr int kRowFloats = 3 * kSsimCols;
+    bool col_in[4];
+    #pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int q = lane + 32 * j, gx = x0 - kSsimR + q / 3;
+        col_in[j] = q < kRowFloats && gx >= 0 && gx < W;
+    }
+    for (int r = warp; r < kSsimRows; r += kSsimThreads / 32) {
+        const int gy = y0 - kSsimR + r;
+        const bool row_in = gy >= 0 && gy < H;
+        const int64_t row = 3 * (pb + (int64_t)(row_in ? gy : 0) * W + (x0 - kSsimR));
+        #pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int q = lane + 32 * j;
+            if (q < kRowFloats) {
+                const bool in = row_in && col_in[j];
+                const int64_t idx = in ? row + q : 0;
+                cp_async4(s_in + r * kSsimInPitchXY + q, x + idx, in);
+                cp_async4(s_in + (kSsimRows + r) * kSsimInPitchXY + q, y + idx, in);
+            }
+        }
     }
     cp_async_wait_all();
     __syncthreads();
@@ -260,16 +276,30 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_grad_kernel(const float *__
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int hrow = (warp >> 2) * 32 + lane, hseg = warp & 3;
     const int vc = lane, vr0 = warp * kSsimGrp;
-    // copies of channel ch's three maps (halo included) into buffer ch & 1
+    // copies of channel ch's three maps (halo included) into buffer ch & 1: a
+    // warp copies whole halo rows of 42 values, a lane the same two columns of
+    // every row (bounds tested once)
+    bool col_in[2];
+    #pragma unroll
+    for (int j = 0; j < 2; j++) {
+        const int c = lane + 32 * j, gx = x0 - kSsimR + c;
+        col_in[j] = c < kSsimCols && gx >= 0 && gx < W;
+    }
     auto stage = [&](int ch) {
         float *dst = s_in + (ch & 1) * kBuf;
-        for (int e = tid; e < 3 * kSsimRows * kSsimCols; e += kSsimThreads) {
-            const int m = e / (kSsimRows * kSsimCols), rem = e - m * (kSsimRows * kSsimCols);
-            const int r = rem / kSsimCols, c = rem - r * kSsimCols;
-            const int gy = y0 - kSsimR + r, gx = x0 - kSsimR + c;
-            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-            const int64_t idx = in ? (int64_t)(3 * ch + m) * T.n_pix + pb + (int64_t)gy * W + gx : 0;
-            cp_async4(dst + (m * kSsimRows + r) * kSsimInPitch + c, partial + idx, in);
+        for (int mr = warp; mr < 3 * kSsimRows; mr += kSsimThreads / 32) {
+            const int m = mr / kSsimRows, r = mr - m * kSsimRows;
+            const int gy = y0 - kSsimR + r;
+            const bool row_in = gy >= 0 && gy < H;
+            const int64_t row = (int64_t)(3 * ch + m) * T.n_pix + pb + (int64_t)(row_in ? gy : 0) * W + (x0 - kSsimR);
+            #pragma unroll
+            for (int j = 0; j < 2; j++) {
+                const int c = lane + 32 * j;
+                if (c < kSsimCols) {
+                    const bool in = row_in && col_in[j];
+                    cp_async4(dst + (m * kSsimRows + r) * kSsimInPitch + c, partial + (in ? row + c : 0), in);
+                }
+            }
         }
         cp_async_commit();
     };
