@@ -236,8 +236,9 @@ size_t gs_grad2d_size(int64_t n, int32_t n_views);
 /* a7. Backward of the compositing for upstream gradients d_rgb [P,3],
  * d_depth [P], d_alpha [P] (each may be NULL = zero).  Recomputes each
  * pixel's blend state from final_T and n_contrib, reduces per-Gaussian
- * gradients within each warp by shuffles, then within the block, and adds
- * them with vector atomics into grad2d [n_views * n, 12] laid out as
+ * gradients over each warp (three list entries at a time, through a table in
+ * shared memory) and adds them with atomics into grad2d [n_views * n, 12]
+ * laid out as
  * (du, dv, dconicA, dconicB), (dconicC, dopacity, dred, dgreen),
  * (dblue, dz, 0, 0).  grad2d is accumulated (+=). */
 gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t n, const gs_bins_t *bins,
