@@ -211,7 +211,6 @@ def plain_steps(c, step, cap, device):
 
 def run_plain(c, step, rs):
     import paper_2405_19614_gb300 as gs
-    step.grad_buf.zero_()
     step.loss.zero_()
     step.d_twist.zero_()
     base = 0
@@ -227,8 +226,9 @@ def run_plain(c, step, rs):
         if step.zeta > 0:
             gs.gs_loss_ssim(r.img["rgb"], step.target_rgb[base:base + P], r.views, step.zeta * P / step.rast.n_pix,
                             step.loss, step.d_rgb[base:base + P], step.ssim_ws)
+        # the first view writes the parameter gradients, the others add to them
         r.backward(step.params, vm, step.d_rgb[base:base + P], step.d_depth[base:base + P], None, step.grads,
-                   step.d_twist[v:v + 1])
+                   step.d_twist[v:v + 1], overwrite_grads=(v == 0))
         base += P
     kp = step.keypoints
     gs.gs_reproj_loss_grad(kp["points"], kp["obs"], kp["view_ids"], step.rast.views, step.viewmats, step.w_rpj,

@@ -63,7 +63,8 @@ typedef struct {
     int32_t sh_degree; /* 0..3 */
 } gs_params_t;
 
-/* Gradients with the same layouts as gs_params_t; accumulated (+=). */
+/* Gradients with the same layouts as gs_params_t; accumulated (+=), or
+ * written (=) where gs_options_t.overwrite_grads is set. */
 typedef struct {
     float *means, *log_scales, *quats, *opacity_logit, *sh;
 } gs_param_grads_t;
@@ -71,6 +72,8 @@ typedef struct {
 typedef struct {
     float near_z; /* cull if camera z <= near_z (0.2) */
     float blur;   /* low-pass variance added to the 2D covariance (0.3 px^2) */
+    int32_t overwrite_grads; /* gs_project_bwd: 0 adds to grads (+=); 1 writes every
+                              * Gaussian's gradients (=), so grads need no zeroing */
 } gs_options_t;
 
 /* Output of gs_project, one entry per (view, Gaussian) at [v * n + i]:
@@ -248,7 +251,8 @@ gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t n, const gs
 
 /* a8. Backward of the projection: chains grad2d to the parameter gradients
  * (summed over views, accumulated into grads) and to each view's twist
- * gradient d_twist [n_views, 6] (+=; NULL to skip).  grads = NULL selects the
+ * gradient d_twist [n_views, 6] (+=; NULL to skip); with opt->overwrite_grads
+ * set, grads are written (=) instead of accumulated.  grads = NULL selects the
  * pose-only mode of tracking (Sec. 3.3: the pose is refined, the map is not):
  * only d_twist is written.  Entries of grad2d it reads are set back to zero,
  * so a buffer that starts zeroed is zero again when the call completes. */

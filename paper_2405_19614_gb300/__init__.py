@@ -162,16 +162,17 @@ def gs_render_bwd_splats(proj, n, bins, views, img, d_rgb, d_depth, d_alpha, gra
                                      _ptr(grad2d), _ptr(work_counter), _stream(stream)), "gs_render_bwd_splats")
 
 
-def gs_project_bwd(params, views, viewmats, proj, grad2d, grads, d_twist, near_z=0.2, blur=0.3, stream=None):
-    opt = GsOptions(near_z, blur)
+def gs_project_bwd(params, views, viewmats, proj, grad2d, grads, d_twist, near_z=0.2, blur=0.3, stream=None,
+                   overwrite_grads=False):
+    opt = GsOptions(near_z, blur, int(bool(overwrite_grads)))
     check(lib().gs_project_bwd(ctypes.byref(_params(params)), views, _ptr(viewmats), len(views), ctypes.byref(opt),
                                ctypes.byref(_proj(proj)), _ptr(grad2d), _gref(grads), _ptr(d_twist),
                                _stream(stream)), "gs_project_bwd")
 
 
 def gs_render_bwd(params, views, viewmats, proj, bins, img, d_rgb, d_depth, d_alpha, grad2d, grads, d_twist,
-                  work_counter, near_z=0.2, blur=0.3, stream=None):
-    opt = GsOptions(near_z, blur)
+                  work_counter, near_z=0.2, blur=0.3, stream=None, overwrite_grads=False):
+    opt = GsOptions(near_z, blur, int(bool(overwrite_grads)))
     check(lib().gs_render_bwd(ctypes.byref(_params(params)), views, _ptr(viewmats), len(views), ctypes.byref(opt),
                               ctypes.byref(_proj(proj)), ctypes.byref(_bins(bins)), ctypes.byref(_img(img)),
                               _ptr(d_rgb), _ptr(d_depth), _ptr(d_alpha), _ptr(grad2d), _gref(grads),
@@ -304,11 +305,14 @@ class Rasterizer:
         gs_render_fwd(self.proj, self.n, self.bins, self.views, self.img, self.work_counter, stream)
         return self.img
 
-    def backward(self, params, viewmats, d_rgb, d_depth, d_alpha, grads, d_twist=None, stream=None):
-        """Accumulate parameter gradients (and per-view twist gradients) for
-        upstream image gradients; self.grad2d is left zeroed."""
+    def backward(self, params, viewmats, d_rgb, d_depth, d_alpha, grads, d_twist=None, stream=None,
+                 overwrite_grads=False):
+        """Accumulate parameter gradients (or write them, with
+        overwrite_grads) and per-view twist gradients for upstream image
+        gradients; self.grad2d is left zeroed."""
         gs_render_bwd(params, self.views, viewmats, self.proj, self.bins, self.img, d_rgb, d_depth, d_alpha,
-                      self.grad2d, grads, d_twist, self.work_counter, self.near_z, self.blur, stream)
+                      self.grad2d, grads, d_twist, self.work_counter, self.near_z, self.blur, stream,
+                      overwrite_grads)
 
     def status(self):
         """Host read of the asynchronous error word (synchronises)."""
@@ -335,12 +339,12 @@ class _RasterizeFn(torch.autograd.Function):
         viewmats, means, log_scales, quats, opacity_logit, sh = ctx.saved_tensors
         params = dict(means=means, log_scales=log_scales, quats=quats, opacity_logit=opacity_logit, sh=sh,
                       sh_degree=ctx.sh_degree)
-        grads = dict(means=torch.zeros_like(means), log_scales=torch.zeros_like(log_scales),
-                     quats=torch.zeros_like(quats), opacity_logit=torch.zeros_like(opacity_logit),
-                     sh=torch.zeros_like(sh))
+        grads = dict(means=torch.empty_like(means), log_scales=torch.empty_like(log_scales),
+                     quats=torch.empty_like(quats), opacity_logit=torch.empty_like(opacity_logit),
+                     sh=torch.empty_like(sh))
         d_twist = torch.zeros(viewmats.shape[0], 6, device=means.device) if ctx.want_twist else None
         c = lambda t: None if t is None else t.contiguous()
-        ctx.rast.backward(params, viewmats, c(g_rgb), c(g_depth), c(g_alpha), grads, d_twist)
+        ctx.rast.backward(params, viewmats, c(g_rgb), c(g_depth), c(g_alpha), grads, d_twist, overwrite_grads=True)
         return (None, None, None, d_twist, grads["means"], grads["log_scales"], grads["quats"],
                 grads["opacity_logit"], grads["sh"])
 

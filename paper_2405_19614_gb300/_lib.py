@@ -35,7 +35,7 @@ class GsParamGrads(ctypes.Structure):
 
 
 class GsOptions(ctypes.Structure):
-    _fields_ = [("near_z", c_f), ("blur", c_f)]
+    _fields_ = [("near_z", c_f), ("blur", c_f), ("overwrite_grads", c_i32)]
 
 
 class GsProjected(ctypes.Structure):

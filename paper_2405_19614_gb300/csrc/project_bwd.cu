@@ -34,7 +34,12 @@ struct ProjectBwdArgs {
     float4 *grad2d;
     float *g_means, *g_log_scales, *g_quats, *g_opacity_logit, *g_sh;  // all NULL: pose only
     float *d_twist;
+    bool overwrite;          // write (=) the parameter gradients instead of adding (+=)
+    bool color_wrote_means;  // the colour kernel has written g_means (SH degree > 0)
 };
+
+// dst = v (overwrite) or dst += v
+__device__ __forceinline__ void put_grad(float *dst, float v, bool overwrite) { *dst = overwrite ? v : *dst + v; }
 
 __device__ __forceinline__ void load_views(const float *viewmats, int n_views, float (*s_E)[12], float (*s_c)[3],
                                            float (*s_tw)[6])
@@ -179,11 +184,11 @@ __global__ void __launch_bounds__(128) project_bwd_color_kernel(ProjectBwdArgs a
     if (active && a.g_means) {
         if (ch < 3) {
             #pragma unroll
-            for (int k = 0; k < K; k++) a.g_sh[((int64_t)K * i + k) * 3 + ch] += gsh[k];
+            for (int k = 0; k < K; k++) put_grad(a.g_sh + ((int64_t)K * i + k) * 3 + ch, gsh[k], a.overwrite);
         }
         if (ch == 0 && DEG > 0) {
             #pragma unroll
-            for (int k = 0; k < 3; k++) a.g_means[3 * i + k] += gm[k];
+            for (int k = 0; k < 3; k++) put_grad(a.g_means + 3 * i + k, gm[k], a.overwrite);
         }
     }
     if (want_twist) flush_twist(a.d_twist, vt.n_views, s_tw);
@@ -396,7 +401,7 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a,
                 gsv += gM[r][c] * Rq[r][c];
                 gR[r][c] = gM[r][c] * s[c];
             }
-            a.g_log_scales[3 * i + c] += gsv * s[c];
+            put_grad(a.g_log_scales + 3 * i + c, gsv * s[c], a.overwrite);
         }
         float gq[4];
         gq[0] = 2.f * (-qc * gR[0][1] + qb * gR[0][2] + qc * gR[1][0] - qa * gR[1][2] - qb * gR[2][0] + qa * gR[2][1]);
@@ -409,10 +414,10 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a,
         const float qd = gq[0] * w + gq[1] * qa + gq[2] * qb + gq[3] * qc;
         const float qn[4] = {w, qa, qb, qc};
         #pragma unroll
-        for (int k = 0; k < 4; k++) a.g_quats[4 * i + k] += (gq[k] - qn[k] * qd) * qinv;
+        for (int k = 0; k < 4; k++) put_grad(a.g_quats + 4 * i + k, (gq[k] - qn[k] * qd) * qinv, a.overwrite);
         #pragma unroll
-        for (int k = 0; k < 3; k++) a.g_means[3 * i + k] += gm[k];
-        a.g_opacity_logit[i] += gol;
+        for (int k = 0; k < 3; k++) put_grad(a.g_means + 3 * i + k, gm[k], a.overwrite && !a.color_wrote_means);
+        put_grad(a.g_opacity_logit + i, gol, a.overwrite);
     }
     if (want_twist) flush_twist(a.d_twist, vt.n_views, s_tw);
 }
@@ -456,6 +461,8 @@ extern "C" gs_status_t gs_project_bwd(const gs_params_t *params, const gs_view_t
     a.g_opacity_logit = grads ? grads->opacity_logit : nullptr;
     a.g_sh = grads ? grads->sh : nullptr;
     a.d_twist = d_twist;
+    a.overwrite = opt->overwrite_grads != 0;
+    a.color_wrote_means = params->sh_degree > 0;
     const int threads = 128;
     cudaStream_t s = as_stream(stream);
     // colour first: the geometry kernel clears the 2D gradients after use

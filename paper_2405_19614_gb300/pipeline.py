@@ -106,7 +106,7 @@ class MappingStep:
 
         r = self.rast
         tok = mark("zero")
-        self.grad_buf.zero_()
+        # grad_buf needs no clearing: the projection backward writes every entry
         self.loss.zero_()
         self.d_twist.zero_()
         close(tok)
@@ -136,7 +136,7 @@ class MappingStep:
         close(tok)
         tok = mark("project_bwd")
         gs_project_bwd(self.params, r.views, self.viewmats, r.proj, r.grad2d, self.grads, self.d_twist, r.near_z,
-                       r.blur, stream)
+                       r.blur, stream, overwrite_grads=True)
         close(tok)
         if self.keypoints is not None:
             tok = mark("reproj")

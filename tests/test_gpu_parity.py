@@ -158,6 +158,31 @@ def test_splat_gradients_parity():
         assert e <= GRAD_TOL, nm
 
 
+@pytest.mark.parametrize("name,scene,cams", CASES, ids=[c[0] for c in CASES])
+def test_overwrite_grads_equals_accumulating_into_zeros(name, scene, cams):
+    """With overwrite_grads the projection backward writes every Gaussian's
+    gradients: a buffer full of garbage ends equal to zeros plus the
+    accumulated gradients (SH degrees with and without view dependence).  Both
+    calls chain the same 2D gradients (the compositing backward adds with
+    atomics, so two runs of it may differ in the last bit)."""
+    rast, p, vm = _run(scene, cams)
+    rng = np.random.default_rng(9)
+    P = rast.n_pix
+    gs.gs_render_bwd_splats(rast.proj, rast.n, rast.bins, rast.views, rast.img, t(rng.normal(0, 1, (P, 3))),
+                            t(rng.normal(0, 1, P)), None, rast.grad2d, rast.work_counter)
+    g2d = rast.grad2d.clone()
+    out = {}
+    for mode in ("add", "overwrite"):
+        rast.grad2d.copy_(g2d)
+        g = zero_grads(p) if mode == "add" else {k: torch.full_like(p[k], 1e30) for k in PARAM_KEYS}
+        gs.gs_project_bwd(p, rast.views, vm, rast.proj, rast.grad2d, g, None, overwrite_grads=(mode == "overwrite"))
+        torch.cuda.synchronize()
+        out[mode] = {k: g[k].cpu().numpy() for k in PARAM_KEYS}
+    for k in PARAM_KEYS:
+        assert np.abs(out["add"][k]).max() > 0, k
+        np.testing.assert_array_equal(out["overwrite"][k], out["add"][k], err_msg=k)
+
+
 def test_batched_views_equal_plain_views():
     """Rendering several views in one launch gives the same images as one view per launch."""
     name, scene, cams = CASES[1]
