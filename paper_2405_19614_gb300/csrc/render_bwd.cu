@@ -206,25 +206,31 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
                 const float4 col = s_rec[warp][2][bit];
                 const SplatColumn kc = splat_column(p, c, sx);
                 if (pos < my_last) {
+                    // the blend tests of all the thread's pixels first, then the
+                    // pairs with a blended pixel (independent chains interleave)
+                    float2 l2[NP], dy[NP];
+                    bool hx[NP], hy[NP];
                     #pragma unroll
                     for (int i = 0; i < NP; i++) {
-                        float2 dy;
-                        const float2 l2 = splat_log2a2(
-                            kc, p, c, col, f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f),
-                            &dy);
-                        const bool hx = pos < last[2 * i] && l2.x >= kLog2AlphaMin;
-                        const bool hy = pos < last[2 * i + 1] && l2.y >= kLog2AlphaMin;
-                        if (!(hx || hy)) continue;
+                        l2[i] = splat_log2a2(kc, p, c, col,
+                                             f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f),
+                                             &dy[i]);
+                        hx[i] = pos < last[2 * i] && l2[i].x >= kLog2AlphaMin;
+                        hy[i] = pos < last[2 * i + 1] && l2[i].y >= kLog2AlphaMin;
+                    }
+                    #pragma unroll
+                    for (int i = 0; i < NP; i++) {
+                        if (!(hx[i] || hy[i])) continue;
                         contrib = true;
-                        // a pixel of the pair that does not blend this entry adds exactly zero
-                        const float2 araw = f2(ex2_approx(l2.x), ex2_approx(l2.y));  // o g
+                        // a pixel of the pair that does not blend this entry takes
+                        // raw alpha 0, so its w, t and sums are exactly zero
+                        const float2 araw = f2(hx[i] ? ex2_approx(l2[i].x) : 0.0f, hy[i] ? ex2_approx(l2[i].y) : 0.0f);
                         const float2 al = f2(fminf(kAlphaMax, araw.x), fminf(kAlphaMax, araw.y));
-                        const float2 om = __fadd2_rn(f2(1.0f), f2(-al.x, -al.y));
+                        const float2 om = __ffma2_rn(al, f2(-1.0f), f2(1.0f));
                         // 1 - alpha >= 0.01: the fast reciprocal is within 2 ulp
                         const float2 inv = f2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
                         const float2 Tb = __fmul2_rn(T[i], inv);
-                        const float2 aTb = __fmul2_rn(al, Tb);
-                        const float2 w = f2(hx ? aTb.x : 0.0f, hy ? aTb.y : 0.0f);
+                        const float2 w = __fmul2_rn(al, Tb);
                         gc[0] = __ffma2_rn(gC0[i], w, gc[0]);
                         gc[1] = __ffma2_rn(gC1[i], w, gc[1]);
                         gc[2] = __ffma2_rn(gC2[i], w, gc[2]);
@@ -235,13 +241,14 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
                         wgt = __ffma2_rn(f2(p.z), gD[i], wgt);
                         const float2 dalpha = __ffma2_rn(Tb, wgt, __fmul2_rn(R[i], inv));
                         R[i] = __ffma2_rn(f2(-wgt.x, -wgt.y), w, R[i]);
-                        T[i] = f2(hx ? Tb.x : T[i].x, hy ? Tb.y : T[i].y);
+                        // T of a pixel that does not blend stays exact
+                        T[i] = f2(hx[i] ? Tb.x : T[i].x, hy[i] ? Tb.y : T[i].y);
                         const float2 tg = __fmul2_rn(dalpha, araw);
-                        const float2 t = f2(hx && araw.x < kAlphaMax ? tg.x : 0.0f, hy && araw.y < kAlphaMax ? tg.y : 0.0f);
-                        const float2 u = __fmul2_rn(t, dy);
+                        const float2 t = f2(araw.x < kAlphaMax ? tg.x : 0.0f, araw.y < kAlphaMax ? tg.y : 0.0f);
+                        const float2 u = __fmul2_rn(t, dy[i]);
                         G2 = __fadd2_rn(G2, t);
                         S12 = __fadd2_rn(S12, u);
-                        S22 = __ffma2_rn(u, dy, S22);
+                        S22 = __ffma2_rn(u, dy[i], S22);
                     }
                 }
                 if (__any_sync(kFullMask, contrib)) {
