@@ -66,6 +66,42 @@ __device__ __forceinline__ void flush_twist(float *d_twist, int n_views, float (
     }
 }
 
+// Twist terms of a warp, reduced once per kTwGroup views instead of one warp
+// reduction per view and term: lane l stores its NV terms of view v in column
+// l of rows (v mod kTwGroup) * NV + k of the warp's table; after the group's
+// last view each lane sums whole rows (32 terms, 16-byte loads; the 36-float
+// pitch keeps both access patterns free of bank conflicts) into the block's
+// s_tw.  Every view of a group stores its rows, zeros included.
+constexpr int kTwGroup = 8;
+constexpr int kTwPitch = 36;
+constexpr int kPbwdWarps = 4;  // 128-thread blocks
+
+template <int NV>
+__device__ __forceinline__ void twist_put(float (*tab)[kTwPitch], int v, const float (&tw)[NV], int lane, int n_views,
+                                          float (*s_tw)[6])
+{
+    const int slot = v % kTwGroup;
+    #pragma unroll
+    for (int k = 0; k < NV; k++) tab[slot * NV + k][lane] = tw[k];
+    if (slot != kTwGroup - 1 && v != n_views - 1) return;
+    __syncwarp();
+    const int v0 = v - slot;
+    for (int r = lane; r < (slot + 1) * NV; r += 32) {
+        const float4 *row = reinterpret_cast<const float4 *>(tab[r]);
+        float4 q = row[0];
+        float2 lo = make_float2(q.x, q.y), hi = make_float2(q.z, q.w);
+        #pragma unroll
+        for (int c = 1; c < 8; c++) {
+            q = row[c];
+            lo = __fadd2_rn(lo, make_float2(q.x, q.y));
+            hi = __fadd2_rn(hi, make_float2(q.z, q.w));
+        }
+        const float sum = (lo.x + lo.y) + (hi.x + hi.y);
+        if (sum != 0.0f) atomicAdd(&s_tw[v0 + r / NV][r % NV], sum);
+    }
+    __syncwarp();
+}
+
 // Bit v of the result is set when Gaussian i is drawn in view v.  All radii are
 // loaded up front (independent loads, eight at a time), so the view loops that
 // follow carry no load whose address depends on an earlier load.
@@ -93,6 +129,7 @@ __global__ void __launch_bounds__(128) project_bwd_color_kernel(ProjectBwdArgs a
     __shared__ float s_E[GS_MAX_VIEWS][12];
     __shared__ float s_c[GS_MAX_VIEWS][3];
     __shared__ float s_tw[GS_MAX_VIEWS][6];
+    __shared__ __align__(16) float s_twt[kPbwdWarps][kTwGroup * 3][kTwPitch];
     load_views(a.viewmats, vt.n_views, s_E, s_c, s_tw);
 
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -119,10 +156,18 @@ __global__ void __launch_bounds__(128) project_bwd_color_kernel(ProjectBwdArgs a
     float gcol_next = 0.0f;
     if (vis_mask && ch < 3) gcol_next = g2[12 * ((int64_t)(__ffsll((long long)vis_mask) - 1) * a.n + i) + 6 + ch];
 
+    float(*twt)[kTwPitch] = s_twt[threadIdx.x >> 5];
+    const bool put_twist = want_twist && DEG > 0;  // the colour depends on the view direction
     #pragma unroll 1
     for (int v = 0; v < vt.n_views; v++) {
         const bool vis = (vis_mask >> v) & 1ull;
-        if (!__any_sync(kFullMask, vis)) continue;
+        if (!__any_sync(kFullMask, vis)) {
+            if (put_twist) {
+                const float zero[3] = {0.0f, 0.0f, 0.0f};
+                twist_put<3>(twt, v, zero, lane, vt.n_views, s_tw);
+            }
+            continue;
+        }
         float gcol = 0.0f;
         if (vis) {
             gcol = gcol_next;
@@ -173,13 +218,7 @@ __global__ void __launch_bounds__(128) project_bwd_color_kernel(ProjectBwdArgs a
             tw[1] = E[4] * gvx + E[5] * gvy + E[6] * gvz;
             tw[2] = E[8] * gvx + E[9] * gvy + E[10] * gvz;
         }
-        if (want_twist) {
-            #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                const float r = warp_sum(tw[k]);
-                if (lane == 0 && r != 0.0f) atomicAdd(&s_tw[v][k], r);
-            }
-        }
+        if (put_twist) twist_put<3>(twt, v, tw, lane, vt.n_views, s_tw);
     }
     if (active && a.g_means) {
         if (ch < 3) {
@@ -199,6 +238,7 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a,
 {
     __shared__ float s_E[GS_MAX_VIEWS][12];
     __shared__ float s_tw[GS_MAX_VIEWS][6];
+    __shared__ __align__(16) float s_twt[kPbwdWarps][kTwGroup * 6][kTwPitch];
     load_views(a.viewmats, vt.n_views, s_E, nullptr, s_tw);
 
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -255,11 +295,15 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a,
         N1 = a.grad2d[3 * o + 1];
         N2 = a.grad2d[3 * o + 2];
     }
+    float(*twt)[kTwPitch] = s_twt[threadIdx.x >> 5];
     #pragma unroll 1
     for (int v = 0; v < vt.n_views; v++) {
         float tw[6] = {0, 0, 0, 0, 0, 0};
         const bool vis = (vis_mask >> v) & 1ull;
-        if (!__any_sync(kFullMask, vis)) continue;
+        if (!__any_sync(kFullMask, vis)) {
+            if (want_twist) twist_put<6>(twt, v, tw, lane, vt.n_views, s_tw);
+            continue;
+        }
         if (vis) {
             const int64_t o = (int64_t)v * a.n + i;
             const float4 G0 = N0, G1 = N1, G2v = N2;
@@ -376,13 +420,7 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a,
                 tw[5] = x * gpy - y * gpx + 2.f * A01;
             }
         }
-        if (want_twist) {
-            #pragma unroll
-            for (int k = 0; k < 6; k++) {
-                const float r = warp_sum(tw[k]);
-                if (lane == 0 && r != 0.0f) atomicAdd(&s_tw[v][k], r);
-            }
-        }
+        if (want_twist) twist_put<6>(twt, v, tw, lane, vt.n_views, s_tw);
     }
 
     if (active && a.g_means) {
