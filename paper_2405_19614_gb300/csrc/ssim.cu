@@ -110,6 +110,9 @@ __device__ __forceinline__ void ssim_tile_of(const SsimTiles &T, int item, int *
 template <int NM, typename Load>
 __device__ __forceinline__ void ssim_hpass(const SsimTiles &T, Load load, float2 (&acc)[kSsimSeg / 2][NM])
 {
+    float2 w[kSsimWin + 1];  // weight pairs held in registers for the packed FMAs
+    #pragma unroll
+    for (int t = 0; t <= kSsimWin; t++) w[t] = T.gp[t];
     #pragma unroll
     for (int p = 0; p < kSsimSeg / 2; p++)
         #pragma unroll
@@ -123,7 +126,7 @@ __device__ __forceinline__ void ssim_hpass(const SsimTiles &T, Load load, float2
             const int t = i - 2 * p;
             if (t < 0 || t > kSsimWin) continue;
             #pragma unroll
-            for (int m = 0; m < NM; m++) acc[p][m] = __ffma2_rn(T.gp[t], make_float2(f[m], f[m]), acc[p][m]);
+            for (int m = 0; m < NM; m++) acc[p][m] = __ffma2_rn(w[t], make_float2(f[m], f[m]), acc[p][m]);
         }
     }
 }
@@ -134,6 +137,9 @@ template <int NM>
 __device__ __forceinline__ void ssim_vpass(const SsimTiles &T, const float *h, int c, int r0,
                                            float2 (&out)[kSsimGrp / 2][NM])
 {
+    float2 w[kSsimWin + 1];
+    #pragma unroll
+    for (int t = 0; t <= kSsimWin; t++) w[t] = T.gp[t];
     #pragma unroll
     for (int p = 0; p < kSsimGrp / 2; p++)
         #pragma unroll
@@ -148,7 +154,7 @@ __device__ __forceinline__ void ssim_vpass(const SsimTiles &T, const float *h, i
             const int t = i - 2 * p;
             if (t < 0 || t > kSsimWin) continue;
             #pragma unroll
-            for (int m = 0; m < NM; m++) out[p][m] = __ffma2_rn(T.gp[t], make_float2(f[m], f[m]), out[p][m]);
+            for (int m = 0; m < NM; m++) out[p][m] = __ffma2_rn(w[t], make_float2(f[m], f[m]), out[p][m]);
         }
     }
 }
