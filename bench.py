@@ -578,10 +578,16 @@ def main_ours(args):
         graph_ms = None
         print(f"graph capture failed: {exc}", file=sys.stderr)
 
-    # end to end through the public API: host keyframes in, loss out, every step
-    import paper_2405_19614_gb300  # noqa: F401
-    h_rgb = step.target_rgb.cpu().pin_memory()
-    h_depth = step.target_depth.cpu().pin_memory()
+    # end to end through the public API: host keyframes in, loss out, every
+    # step.  The keyframes travel in their sensor format (8-bit colour, 16-bit
+    # depth in units of DEPTH_UNIT metres, as TUM RGB-D stores them) and are
+    # decoded to the FP32 loss targets on the device.
+    import paper_2405_19614_gb300 as gs_api
+    DEPTH_UNIT = 1.0 / 5000.0
+    h_rgb = (step.target_rgb * 255.0).round().clamp(0, 255).to(torch.uint8).cpu().pin_memory()
+    h_depth = ((step.target_depth / DEPTH_UNIT).round().clamp(0, 65535).to(torch.int32).cpu().numpy()
+               .astype(np.uint16).view(np.int16))
+    h_depth = torch.from_numpy(h_depth).pin_memory()
     h_vm = step.viewmats.cpu().pin_memory()
     h_loss = torch.empty(1, dtype=torch.float32).pin_memory()
     for _ in range(2):
@@ -593,6 +599,7 @@ def main_ours(args):
     compute = torch.cuda.current_stream()
     copier = torch.cuda.Stream()
     bufs = [(step.target_rgb, step.target_depth), (torch.empty_like(step.target_rgb), torch.empty_like(step.target_depth))]
+    raw = [(torch.empty_like(h_rgb, device=device), torch.empty_like(h_depth, device=device)) for _ in range(2)]
     ready = [torch.cuda.Event(), torch.cuda.Event()]
     free = [torch.cuda.Event(), torch.cuda.Event()]
     e0 = torch.cuda.Event(enable_timing=True)
@@ -600,8 +607,9 @@ def main_ours(args):
 
     def upload(k):
         with torch.cuda.stream(copier):
-            bufs[k][0].copy_(h_rgb, non_blocking=True)
-            bufs[k][1].copy_(h_depth, non_blocking=True)
+            raw[k][0].copy_(h_rgb, non_blocking=True)
+            raw[k][1].copy_(h_depth, non_blocking=True)
+            gs_api.gs_decode_keyframes(raw[k][0], raw[k][1], DEPTH_UNIT, bufs[k][0], bufs[k][1], stream=copier)
             ready[k].record(copier)
 
     for k in range(2):
@@ -624,7 +632,7 @@ def main_ours(args):
     torch.cuda.synchronize()
     step.target_rgb, step.target_depth = bufs[0]
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
-    h2d = h_rgb.numel() * 4 + h_depth.numel() * 4 + h_vm.numel() * 4
+    h2d = h_rgb.numel() * h_rgb.element_size() + h_depth.numel() * h_depth.element_size() + h_vm.numel() * 4
 
     # plain path: one view per launch, same scene, same step contents
     plain = None

@@ -218,6 +218,15 @@ gs_status_t gs_loss_l1(const float *rgb, const float *depth, const float *alpha,
                        int32_t use_gate, float gamma, float *loss, float *d_rgb, float *d_depth,
                        void *stream);
 
+/* Keyframe decoding (Sec. 4: RGB-D frames of TUM RGB-D, 8-bit colour and
+ * 16-bit depth): rgb8 [P,3] bytes and depth16 [P] (device, as uploaded from
+ * the sensor) to the FP32 loss targets rgb [P,3] = c / 255 and depth [P] =
+ * d * depth_scale (metres per depth unit, e.g. 1/5000 for TUM RGB-D; 0 stays
+ * 0), each one correctly rounded FP32 operation.  Alignment: rgb8 4 bytes,
+ * depth16 8 bytes, rgb and depth 16 bytes, else GS_ERR_INVALID_ARG. */
+gs_status_t gs_decode_keyframes(const uint8_t *rgb8, const uint16_t *depth16, int64_t n_pixels, float depth_scale,
+                                float *rgb, float *depth, void *stream);
+
 /* Bytes of workspace gs_loss_ssim needs for n_pixels (9 floats per pixel). */
 size_t gs_ssim_workspace_size(int64_t n_pixels);
 

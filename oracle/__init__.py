@@ -260,6 +260,15 @@ def reproj(points, obs, cams, weight=1.0, view_ids=None, near_z=0.2):
     return Lv, g
 
 
+def decode_keyframes(rgb8, depth16, depth_scale):
+    """Sec. 4 keyframes (TUM RGB-D: 8-bit colour, 16-bit depth) to the FP32
+    loss targets by their definition: colour c / 255 and depth d * scale, each
+    one IEEE FP32 operation (numpy float32 arithmetic is correctly rounded)."""
+    rgb = np.asarray(rgb8, np.uint8).astype(np.float32) / np.float32(255.0)
+    depth = np.asarray(depth16, np.uint16).astype(np.float32) * np.float32(depth_scale)
+    return rgb.astype(np.float32), depth.astype(np.float32)
+
+
 def adam(param, grad, m, v, lr, b1=0.9, b2=0.999, eps=1e-15, t=1):
     """One FP64 Adam step in place on float64 arrays."""
     for a in (param, grad, m, v):

@@ -21,7 +21,7 @@ from ._lib import (GS_MAX_ADAM_GROUPS, GS_MAX_VIEWS, GS_TILE, GsAdamGroup, GsBin
 
 __all__ = ["gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd", "gs_render_stats", "gs_set_render_variants",
            "gs_get_render_variants", "gs_loss_l1", "gs_loss_ssim", "gs_render_bwd", "gs_render_bwd_splats",
-           "gs_project_bwd", "gs_reproj_loss_grad", "gs_adam_step", "gs_pose_update", "gs_densify",
+           "gs_project_bwd", "gs_decode_keyframes", "gs_reproj_loss_grad", "gs_adam_step", "gs_pose_update", "gs_densify",
            "gs_prune_select", "gs_compact_rows", "gs_spatial_order_workspace_size", "gs_spatial_order",
            "gs_select_views", "Rasterizer", "rasterize",
            "GsError", "lib"]
@@ -137,6 +137,18 @@ def gs_get_render_variants():
     out = [ctypes.c_int32() for _ in range(4)]
     check(lib().gs_get_render_variants(*[ctypes.byref(o) for o in out]), "gs_get_render_variants")
     return tuple(o.value for o in out)
+
+
+def gs_decode_keyframes(rgb8, depth16, depth_scale, rgb, depth, stream=None):
+    """Sensor-format keyframes (uint8 [P,3] colour, 16-bit [P] depth, as
+    uint16 or int16 storage) to the FP32 targets rgb [P,3] and depth [P]."""
+    if rgb8.dtype != torch.uint8 or depth16.dtype not in (torch.int16, getattr(torch, "uint16", torch.int16)):
+        raise GsError("rgb8 must be uint8 and depth16 16-bit")
+    P = depth16.numel()
+    if rgb8.numel() != 3 * P or rgb.numel() != 3 * P or depth.numel() != P:
+        raise GsError("keyframe sizes disagree")
+    check(lib().gs_decode_keyframes(_ptr(rgb8), _ptr(depth16), P, float(depth_scale), _ptr(rgb), _ptr(depth),
+                                    _stream(stream)), "gs_decode_keyframes")
 
 
 def gs_loss_l1(rgb, depth, alpha, target_rgb, target_depth, w_c, w_d, use_gate, gamma, loss, d_rgb, d_depth,

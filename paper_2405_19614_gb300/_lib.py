@@ -72,6 +72,7 @@ SIGNATURES = {
     "gs_render_stats": ([P(GsProjected), c_i64, P(GsBins), P(GsView), c_i32, c_p, c_p, c_p, c_p], c_i32),
     "gs_set_render_variants": ([c_i32, c_i32], c_i32),
     "gs_get_render_variants": ([P(c_i32), P(c_i32), P(c_i32), P(c_i32)], c_i32),
+    "gs_decode_keyframes": ([c_p, c_p, c_i64, c_f, c_p, c_p, c_p], c_i32),
     "gs_loss_l1": ([c_p, c_p, c_p, c_p, c_p, c_i64, c_f, c_f, c_i32, c_f, c_p, c_p, c_p, c_p], c_i32),
     "gs_ssim_workspace_size": ([c_i64], c_sz),
     "gs_loss_ssim": ([c_p, c_p, P(GsView), c_i32, c_f, c_p, c_p, c_p, c_sz, c_p], c_i32),

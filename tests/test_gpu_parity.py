@@ -183,6 +183,25 @@ def test_overwrite_grads_equals_accumulating_into_zeros(name, scene, cams):
         np.testing.assert_array_equal(out["overwrite"][k], out["add"][k], err_msg=k)
 
 
+@pytest.mark.parametrize("n", [1, 5, 1_000_003])
+def test_keyframe_decoding_matches_oracle(n):
+    """Sensor-format keyframes decode bit for bit as the oracle's FP32
+    definition, over a ragged pixel count (the last n mod 4 pixels take the
+    scalar path)."""
+    rng = np.random.default_rng(n)
+    rgb8 = rng.integers(0, 256, (n, 3), dtype=np.uint8)
+    d16 = rng.integers(0, 65536, n, dtype=np.uint32).astype(np.uint16)
+    d16[: min(n, 2)] = (0, 65535)[: min(n, 2)]
+    ref_rgb, ref_depth = oracle.decode_keyframes(rgb8, d16, 1 / 5000)
+    rgb = torch.empty(n, 3, device="cuda")
+    depth = torch.empty(n, device="cuda")
+    gs.gs_decode_keyframes(torch.from_numpy(rgb8).cuda(), torch.from_numpy(d16.view(np.int16)).cuda(), 1 / 5000, rgb,
+                           depth)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(rgb.cpu().numpy().view(np.uint32), ref_rgb.view(np.uint32))
+    np.testing.assert_array_equal(depth.cpu().numpy().view(np.uint32), ref_depth.view(np.uint32))
+
+
 def test_batched_views_equal_plain_views():
     """Rendering several views in one launch gives the same images as one view per launch."""
     name, scene, cams = CASES[1]

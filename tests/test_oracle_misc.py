@@ -140,3 +140,24 @@ def test_se3_exp_matches_matrix_exponential(scale):
         E2 = rng.standard_normal((3, 4))
         full = Tm @ np.vstack([E2, [0, 0, 0, 1]])
         np.testing.assert_allclose(oracle.se3_exp_apply(xi, E2), full[:3], atol=1e-13, rtol=1e-12)
+
+
+def test_keyframe_decoding_is_correctly_rounded():
+    """Every colour byte maps to the FP32 number nearest c/255 (checked in
+    exact rational arithmetic against both FP32 neighbours), and depths to the
+    FP32 product, with the closed values 0 -> 0 and 255 -> 1."""
+    from fractions import Fraction
+    c = np.arange(256, dtype=np.uint8)
+    rgb, depth = oracle.decode_keyframes(np.stack([c, c, c], 1), np.array([0, 5000, 65535], np.uint16), 1 / 5000)
+    assert rgb.dtype == np.float32 and depth.dtype == np.float32
+    assert rgb[0, 0] == 0.0 and rgb[255, 2] == 1.0
+    for k in range(256):
+        x = rgb[k, 0]
+        exact = Fraction(k, 255)
+        err = abs(Fraction(float(x)) - exact)
+        for nb in (np.nextafter(x, np.float32(-1)), np.nextafter(x, np.float32(2))):
+            assert err <= abs(Fraction(float(nb)) - exact), k
+    s = np.float32(1 / 5000)
+    assert depth[0] == 0.0
+    assert depth[1] == np.float32(np.float32(5000) * s) and abs(float(depth[1]) - 1.0) < 1e-6
+    assert depth[2] == np.float32(np.float32(65535) * s)
