@@ -16,6 +16,8 @@ Paper passages followed (arXiv 2405.19614):
   * Sec. 3.3 border mask M_b(p) (= accumulated opacity) and filter gates G(p).
   * Sec. 3.3 joint loss L = w1 L_rpj + w2 L_c + w3 L_d; Sec. 3.2 Eq. lba (L_rpj).
   * Sec. 3.4 mapping loss L_m (L1 parts), gradient-based optimisation.
+  * Sec. 4 RGB-D keyframes (TUM RGB-D: 8-bit colour, 16-bit depth) decoded to
+    the FP32 loss targets (decode_keyframes).
 
 Parity pins for every function are in tests/test_oracle_*.py; none is unpinned.
 """
