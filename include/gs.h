@@ -196,13 +196,14 @@ gs_status_t gs_render_stats(const gs_projected_t *proj, int64_t n, const gs_bins
                             const gs_view_t *views, int32_t n_views, uint32_t *n_eval, uint32_t *n_blend,
                             uint32_t *work_counter, void *stream);
 
-/* Kernel variants of the compositing (a5, a7): pixels per thread and the
- * number of splat records staged per shared-memory batch, as indices into
- * fwd: (1,256) (2,128) (2,256) (4,64) (4,128) (8,64) and
- * bwd: (1,256) (2,128) (4,64) (4,128) (8,64).  All variants compute the same
- * result; the autotuner times them on the workload and sets the fastest.  The
- * setting is process-wide and read when a kernel is launched.
- * GS_ERR_INVALID_ARG for an index out of range. */
+/* Kernel variants of the compositing (a5, a7): (pixels per thread, band
+ * width BW), a warp's band of a 16x16 tile being BW x (pixels per thread *
+ * 32 / BW) pixels, as indices 0..5 into (1,8) (2,8) (2,16) (4,8) (4,16)
+ * (8,16) for both the forward and the backward (defaults: forward 1,
+ * backward 3).  All variants compute the same result; the autotuner times
+ * them on the workload and sets the fastest.  The setting is process-wide and
+ * read when a kernel is launched.  GS_ERR_INVALID_ARG for an index out of
+ * range. */
 gs_status_t gs_set_render_variants(int32_t fwd, int32_t bwd);
 
 /* Current variants and the number of each (any pointer may be NULL). */
