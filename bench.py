@@ -303,7 +303,8 @@ def stage_work(w):
         # per entry up to the last blend 14 ops to recompute alpha; per blended
         # entry ~46 ops of reverse mode (T recovery, 10 partial derivatives)
         "render_bwd": ("alu", 14 * C + 46 * B),
-        "project_bwd": ("hbm", param_b * N + 96 * Vv + 2 * param_b * N),
+        # parameters read, 2D gradients read and cleared, parameter gradients written (not accumulated)
+        "project_bwd": ("hbm", param_b * N + 96 * Vv + param_b * N),
         "adam": ("hbm", 28 * (param_b // 4) * N),
     }
 
