@@ -86,6 +86,10 @@ class MappingStep:
         self.keypoints = keypoints  # dict(points [n,3], obs [n,2], view_ids [n]) on the device
         self.w_rpj = float(w_rpj)
         self.optimise_params = True
+        # the keypoint re-projection term needs only the poses and keypoints:
+        # it runs on a second stream, beside the render (it is a small,
+        # latency-bound launch)
+        self.side = torch.cuda.Stream(device=dev) if dev.type == "cuda" else None
 
     def run(self, timers=None, stream=None):
         """Enqueue one iteration.  timers: optional dict stage -> list to which
@@ -105,12 +109,24 @@ class MappingStep:
             timers.setdefault(tok[0], []).append((tok[1], e))
 
         r = self.rast
+        main = stream if stream is not None else torch.cuda.current_stream()
         tok = mark("zero")
         # grad_buf needs no clearing: the projection backward writes every entry
         self.loss.zero_()
         self.d_twist.zero_()
         close(tok)
         from . import gs_bin_sort, gs_project, gs_render_fwd, gs_render_bwd_splats, gs_project_bwd
+        side = self.keypoints is not None and self.side is not None
+        if side:
+            # after the accumulators are cleared; its atomic adds to the loss and
+            # the twist gradients mix with the render's in any order
+            self.side.wait_stream(main)
+            with torch.cuda.stream(self.side):
+                tok = mark("reproj")
+                kp = self.keypoints
+                gs_reproj_loss_grad(kp["points"], kp["obs"], kp.get("view_ids"), r.views, self.viewmats, self.w_rpj,
+                                    self.loss, self.d_twist, r.near_z, self.side)
+                close(tok)
         tok = mark("project")
         gs_project(self.params, r.views, self.viewmats, r.proj, r.near_z, r.blur, stream)
         close(tok)
@@ -138,7 +154,7 @@ class MappingStep:
         gs_project_bwd(self.params, r.views, self.viewmats, r.proj, r.grad2d, self.grads, self.d_twist, r.near_z,
                        r.blur, stream, overwrite_grads=True)
         close(tok)
-        if self.keypoints is not None:
+        if self.keypoints is not None and not side:
             tok = mark("reproj")
             kp = self.keypoints
             gs_reproj_loss_grad(kp["points"], kp["obs"], kp.get("view_ids"), r.views, self.viewmats, self.w_rpj,
@@ -148,6 +164,8 @@ class MappingStep:
             tok = mark("adam")
             gs_adam_step(self.flat.buf, self.grad_buf, self.m, self.v, self.groups, self.step_count, stream=stream)
             close(tok)
+        if side:
+            main.wait_stream(self.side)  # the step ends when both streams are done
 
     def reorder_spatially(self, stream=None):
         """Stores the Gaussians (parameters and Adam state) in the Morton order
