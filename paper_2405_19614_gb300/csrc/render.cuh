@@ -111,10 +111,11 @@ __device__ __forceinline__ bool splat_misses_box(const float4 &p, const float4 &
 constexpr int kRenderThreads = 128;
 
 // Blocks per SM asked of the register allocator, per pixels per thread:
-// 64 registers a thread up to two pixels, 80 for four (128 for the backward,
-// whose packed gradient state spills at 80), 128 for eight.
+// 64 registers a thread up to two pixels, 80 for four (102 for the backward,
+// whose packed gradient state spills at 80; five blocks of four warps measured
+// 1.5 % faster than four), 128 for eight.
 #ifndef GS_BWD_BLOCKS_PPT4
-#define GS_BWD_BLOCKS_PPT4 4
+#define GS_BWD_BLOCKS_PPT4 5
 #endif
 template <int PPT>
 struct RenderOccupancy {
