@@ -212,8 +212,7 @@ def plain_steps(c, step, cap, device):
 
 def run_plain(c, step, rs):
     import paper_2405_19614_gb300 as gs
-    step.loss.zero_()
-    step.d_twist.zero_()
+    step.acc.zero_()  # the loss and the twist gradients
     base = 0
     for v, r in enumerate(rs):
         vm = step.viewmats[v:v + 1]

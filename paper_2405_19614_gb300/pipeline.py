@@ -77,8 +77,10 @@ class MappingStep:
         P = self.rast.n_pix
         self.d_rgb = torch.zeros(P, 3, device=dev)
         self.d_depth = torch.zeros(P, device=dev)
-        self.loss = torch.zeros(1, device=dev)
-        self.d_twist = torch.zeros(self.rast.V, 6, device=dev)
+        # the loss and the twist gradients share one buffer, cleared by one fill a step
+        self.acc = torch.zeros(4 + 6 * self.rast.V, device=dev)
+        self.loss = self.acc[0:1]
+        self.d_twist = self.acc[4:].view(self.rast.V, 6)
         self.w_c, self.w_d, self.use_gate, self.gamma = float(w_c), float(w_d), bool(use_gate), float(gamma)
         self.zeta = float(zeta)
         self.ssim_ws = (torch.empty(gs_ssim_workspace_size(P), dtype=torch.uint8, device=dev)
@@ -112,8 +114,7 @@ class MappingStep:
         main = stream if stream is not None else torch.cuda.current_stream()
         tok = mark("zero")
         # grad_buf needs no clearing: the projection backward writes every entry
-        self.loss.zero_()
-        self.d_twist.zero_()
+        self.acc.zero_()  # the loss and the twist gradients
         close(tok)
         from . import gs_bin_sort, gs_project, gs_render_fwd, gs_render_bwd_splats, gs_project_bwd
         side = self.keypoints is not None and self.side is not None
