@@ -534,7 +534,9 @@ def main_ours(args):
         torch.cuda.synchronize()
         return
 
-    # timed region: eager launches with per-stage events on the launching stream
+    # timed region 1: eager launches with per-stage events on the launching
+    # stream (the stage times); timed region 2 below replays the same step as
+    # a CUDA graph, the way a fixed mapping loop runs (the headline value)
     barrier(world)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
@@ -548,8 +550,7 @@ def main_ours(args):
     t1.record()
     torch.cuda.synchronize()
     barrier(world)
-    clk = clocks.stop()
-    ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, world)
+    eager_ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, world)
     stage_ms = {k: sum(a.elapsed_time(b) for a, b in v) / len(v) for k, v in timers.items()}
 
     # the same step captured once as a CUDA graph and replayed
@@ -566,6 +567,7 @@ def main_ours(args):
             step.run()
         for _ in range(args.warmup):
             g.replay()
+        barrier(world)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -574,10 +576,13 @@ def main_ours(args):
             g.replay()
         e1.record()
         torch.cuda.synchronize()
+        barrier(world)
         graph_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
-    except Exception as exc:  # graph capture is reported, not required
+    except Exception as exc:  # without a graph the eager time is the headline
         graph_ms = None
         print(f"graph capture failed: {exc}", file=sys.stderr)
+    clk = clocks.stop()  # sampled over both timed regions
+    ms = graph_ms if graph_ms is not None else eager_ms
 
     # end to end through the public API: host keyframes in, loss out, every
     # step.  The keyframes travel in their sensor format (8-bit colour, 16-bit
@@ -707,9 +712,10 @@ def main_ours(args):
                    "l2": "inputs larger than L2 (params 236 MB + pair arrays), no flush",
                    "gaussian_order": "Morton order of the means (map maintenance at setup)"},
         "iters_per_s": 1e3 / ms,
-        "graph": None if graph_ms is None else {"ms_per_step": graph_ms, "value": world * px_per_step / graph_ms / 1e3},
+        "timing": "CUDA graph replay of the step" if graph_ms is not None else "eager launches",
+        "eager": {"ms_per_step": eager_ms, "value": world * px_per_step / eager_ms / 1e3},
         "plain": plain,
-        "batched_vs_plain": None if plain is None else plain["ms_per_step"] / ms,
+        "batched_vs_plain": None if plain is None else plain["ms_per_step"] / eager_ms,
         "e2e": {"value": world * px_per_step / e2e_ms / 1e3, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 4},
         "gpu_launches": step.kernels_per_step() * args.steps,
