@@ -599,15 +599,39 @@ def main_ours(args):
     for _ in range(2):
         step.run()
     torch.cuda.synchronize()
+    # the step in two captured parts: part 1 (up to the losses) is the only one
+    # that reads the keyframe targets, so the next keyframes are decoded into
+    # the target buffers while part 2 (the backward) runs
+    parts = [lambda: step.run(part=1), lambda: step.run(part=2)]
+    try:
+        graphs = []
+        for k in (1, 2):
+            gk = torch.cuda.CUDAGraph()
+            s_cap = torch.cuda.Stream()
+            s_cap.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s_cap):
+                step.run(part=k)
+            torch.cuda.current_stream().wait_stream(s_cap)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(gk):
+                step.run(part=k)
+            graphs.append(gk)
+        parts = [graphs[0].replay, graphs[1].replay]
+        for _ in range(2):
+            parts[0]()
+            parts[1]()
+    except Exception as exc:  # eager parts still measure the same path
+        print(f"graph capture of the step's parts failed: {exc}", file=sys.stderr)
+    torch.cuda.synchronize()
     barrier(world)
-    # keyframes are double-buffered: the copy of step i + 1's keyframes (on a
-    # copy stream) overlaps step i; every step's copy is inside the timed region
+    # raw keyframes are double-buffered on a copy stream: step i + 1's upload
+    # overlaps step i, its decode into the targets overlaps step i's part 2;
+    # every step's copy and decode is inside the timed region
     compute = torch.cuda.current_stream()
     copier = torch.cuda.Stream()
-    bufs = [(step.target_rgb, step.target_depth), (torch.empty_like(step.target_rgb), torch.empty_like(step.target_depth))]
     raw = [(torch.empty_like(h_rgb, device=device), torch.empty_like(h_depth, device=device)) for _ in range(2)]
-    ready = [torch.cuda.Event(), torch.cuda.Event()]
-    free = [torch.cuda.Event(), torch.cuda.Event()]
+    decoded = torch.cuda.Event()
+    targets_read = torch.cuda.Event()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
 
@@ -615,28 +639,32 @@ def main_ours(args):
         with torch.cuda.stream(copier):
             raw[k][0].copy_(h_rgb, non_blocking=True)
             raw[k][1].copy_(h_depth, non_blocking=True)
-            gs_api.gs_decode_keyframes(raw[k][0], raw[k][1], DEPTH_UNIT, bufs[k][0], bufs[k][1], stream=copier)
-            ready[k].record(copier)
 
-    for k in range(2):
-        free[k].record(compute)
+    def decode(k):
+        gs_api.gs_decode_keyframes(raw[k][0], raw[k][1], DEPTH_UNIT, step.target_rgb, step.target_depth,
+                                   stream=copier)
+        decoded.record(copier)
+
     e0.record(compute)
     copier.wait_event(e0)
     upload(0)
+    decode(0)
+    if args.steps > 1:
+        upload(1)
     for i in range(args.steps):
-        cur = i % 2
-        if i + 1 < args.steps:
-            copier.wait_event(free[1 - cur])  # the step that last read that buffer is done
-            upload(1 - cur)
-        compute.wait_event(ready[cur])
-        step.target_rgb, step.target_depth = bufs[cur]
+        compute.wait_event(decoded)  # this step's targets
         step.viewmats.copy_(h_vm, non_blocking=True)
-        step.run()
-        free[cur].record(compute)
+        parts[0]()
+        targets_read.record(compute)
+        if i + 1 < args.steps:
+            copier.wait_event(targets_read)
+            decode((i + 1) % 2)
+            if i + 2 < args.steps:
+                upload(i % 2)  # its decode (this step's) is done: the copy stream is in order
+        parts[1]()
         h_loss.copy_(step.loss, non_blocking=True)
     e1.record(compute)
     torch.cuda.synchronize()
-    step.target_rgb, step.target_depth = bufs[0]
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     h2d = h_rgb.numel() * h_rgb.element_size() + h_depth.numel() * h_depth.element_size() + h_vm.numel() * 4
 

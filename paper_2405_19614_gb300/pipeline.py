@@ -93,9 +93,16 @@ class MappingStep:
         # latency-bound launch)
         self.side = torch.cuda.Stream(device=dev) if dev.type == "cuda" else None
 
-    def run(self, timers=None, stream=None):
+    def run(self, timers=None, stream=None, part=0):
         """Enqueue one iteration.  timers: optional dict stage -> list to which
-        (start, end) CUDA events are appended."""
+        (start, end) CUDA events are appended.  part 1 enqueues the step up to
+        the losses (the only launches that read the keyframe targets), part 2
+        the rest; 0 both."""
+        if part == 0:
+            self.run(timers, stream, 1)
+            self.run(timers, stream, 2)
+            return
+
         def mark(name):
             if timers is None:
                 return None
@@ -112,12 +119,15 @@ class MappingStep:
 
         r = self.rast
         main = stream if stream is not None else torch.cuda.current_stream()
+        from . import gs_bin_sort, gs_project, gs_render_fwd
+        side = self.keypoints is not None and self.side is not None
+        if part == 2:
+            self._run_backward(mark, close, stream, side)
+            return
         tok = mark("zero")
         # grad_buf needs no clearing: the projection backward writes every entry
         self.acc.zero_()  # the loss and the twist gradients
         close(tok)
-        from . import gs_bin_sort, gs_project, gs_render_fwd, gs_render_bwd_splats, gs_project_bwd
-        side = self.keypoints is not None and self.side is not None
         if side:
             # after the accumulators are cleared; its atomic adds to the loss and
             # the twist gradients mix with the render's in any order
@@ -147,6 +157,14 @@ class MappingStep:
             gs_loss_ssim(r.img["rgb"], self.target_rgb, r.views, self.zeta, self.loss, self.d_rgb, self.ssim_ws,
                          stream)
             close(tok)
+        if side:
+            main.wait_stream(self.side)  # the re-projection has overlapped the render
+
+    def _run_backward(self, mark, close, stream, side):
+        """Part 2 of run(): the backward, the re-projection term (when it has no
+        second stream) and the optimiser step."""
+        from . import gs_project_bwd, gs_render_bwd_splats
+        r = self.rast
         tok = mark("render_bwd")
         gs_render_bwd_splats(r.proj, r.n, r.bins, r.views, r.img, self.d_rgb, self.d_depth, None, r.grad2d,
                              r.work_counter, stream)
@@ -165,8 +183,6 @@ class MappingStep:
             tok = mark("adam")
             gs_adam_step(self.flat.buf, self.grad_buf, self.m, self.v, self.groups, self.step_count, stream=stream)
             close(tok)
-        if side:
-            main.wait_stream(self.side)  # the step ends when both streams are done
 
     def reorder_spatially(self, stream=None):
         """Stores the Gaussians (parameters and Adam state) in the Morton order
