@@ -8,8 +8,11 @@ re-projection term -> Adam on all Gaussian parameters.  Default workload:
 1M Gaussians (SH degree 3) on synthetic room surfaces, 8 keyframes of
 1200x680, rendered and backpropagated in one batched launch per stage.
 
-Prints one JSON line (metric fwd+bwd Mpix/s).  --impl reference times the CPU
-oracle instead, on a bounded crop of the same workload.
+Prints one JSON line (metric fwd+bwd Mpix/s): the headline times the step
+replayed as a CUDA graph, `eager` the same step launched from Python with
+per-stage events, `e2e` the step with sensor-format keyframes uploaded and
+decoded every iteration.  --impl reference times the CPU oracle instead, on
+bounded strips of the same workload over every host core.
 """
 from __future__ import annotations
 
