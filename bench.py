@@ -313,7 +313,7 @@ def stage_work(w):
 
 
 # --------------------------------------------------------------------------
-# CPU oracle baseline (a bounded crop of the same workload)
+# CPU oracle baselines (bounded strips of the same workload)
 # --------------------------------------------------------------------------
 
 def crop_cams(cams, v, y0, rows):
