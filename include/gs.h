@@ -189,6 +189,17 @@ gs_status_t gs_render_fwd(const gs_projected_t *proj, int64_t n, const gs_bins_t
                           const gs_view_t *views, int32_t n_views, gs_image_t *img,
                           uint32_t *work_counter, void *stream);
 
+/* a5 + a6 fused: gs_render_fwd that also evaluates gs_loss_l1 on each pixel as
+ * it finishes (same arguments and results as gs_loss_l1 over all pixels of the
+ * views: adds L to *loss, WRITES d_rgb [P,3] and d_depth [P]), so the image is
+ * not read back by a separate loss launch.  d_rgb and d_depth equal
+ * gs_loss_l1's bit for bit; *loss differs only in summation order.
+ * Errors as gs_render_fwd, and GS_ERR_INVALID_ARG for null loss arguments. */
+gs_status_t gs_render_fwd_l1(const gs_projected_t *proj, int64_t n, const gs_bins_t *bins, const gs_view_t *views,
+                             int32_t n_views, gs_image_t *img, uint32_t *work_counter, const float *target_rgb,
+                             const float *target_depth, float w_c, float w_d, int32_t use_gate, float gamma,
+                             float *loss, float *d_rgb, float *d_depth, void *stream);
+
 /* Work counts of a5 for measurement: per pixel, the list entries evaluated
  * (n_eval [P]) and blended (n_blend [P]) by the forward compositing under the
  * same skip and stop rules.  Writes no image. */

@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import (GS_MAX_ADAM_GROUPS, GS_MAX_VIEWS, GS_TILE, GsAdamGroup, GsBins, GsError, GsImage, GsOptions,
                    GsParamGrads, GsParams, GsProjected, GsView, check)
 
-__all__ = ["gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd", "gs_render_stats", "gs_set_render_variants",
+__all__ = ["gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd", "gs_render_fwd_l1", "gs_render_stats", "gs_set_render_variants",
            "gs_get_render_variants", "gs_loss_l1", "gs_loss_ssim", "gs_render_bwd", "gs_render_bwd_splats",
            "gs_project_bwd", "gs_decode_keyframes", "gs_reproj_loss_grad", "gs_adam_step", "gs_pose_update", "gs_densify",
            "gs_prune_select", "gs_compact_rows", "gs_spatial_order_workspace_size", "gs_spatial_order",
@@ -121,6 +121,15 @@ def gs_bin_sort_noalloc(proj, n, views, bins, stream=None):
 def gs_render_fwd(proj, n, bins, views, img, work_counter, stream=None):
     check(lib().gs_render_fwd(ctypes.byref(_proj(proj)), n, ctypes.byref(_bins(bins)), views, len(views),
                               ctypes.byref(_img(img)), _ptr(work_counter), _stream(stream)), "gs_render_fwd")
+
+
+def gs_render_fwd_l1(proj, n, bins, views, img, work_counter, target_rgb, target_depth, w_c, w_d, use_gate, gamma,
+                     loss, d_rgb, d_depth, stream=None):
+    """gs_render_fwd with gs_loss_l1 evaluated on each pixel as it finishes."""
+    check(lib().gs_render_fwd_l1(ctypes.byref(_proj(proj)), n, ctypes.byref(_bins(bins)), views, len(views),
+                                 ctypes.byref(_img(img)), _ptr(work_counter), _ptr(target_rgb), _ptr(target_depth),
+                                 w_c, w_d, int(use_gate), gamma, _ptr(loss), _ptr(d_rgb), _ptr(d_depth),
+                                 _stream(stream)), "gs_render_fwd_l1")
 
 
 def gs_render_stats(proj, n, bins, views, n_eval, n_blend, work_counter, stream=None):

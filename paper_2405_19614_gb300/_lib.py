@@ -69,6 +69,8 @@ SIGNATURES = {
     "gs_bin_sort": ([P(GsProjected), c_i64, P(GsView), c_i32, P(GsBins), c_p, c_sz, c_p], c_i32),
     "gs_bin_sort_noalloc": ([P(GsProjected), c_i64, P(GsView), c_i32, P(GsBins), c_p], c_i32),
     "gs_render_fwd": ([P(GsProjected), c_i64, P(GsBins), P(GsView), c_i32, P(GsImage), c_p, c_p], c_i32),
+    "gs_render_fwd_l1": ([P(GsProjected), c_i64, P(GsBins), P(GsView), c_i32, P(GsImage), c_p, c_p, c_p, c_f, c_f,
+                          c_i32, c_f, c_p, c_p, c_p, c_p], c_i32),
     "gs_render_stats": ([P(GsProjected), c_i64, P(GsBins), P(GsView), c_i32, c_p, c_p, c_p, c_p], c_i32),
     "gs_set_render_variants": ([c_i32, c_i32], c_i32),
     "gs_get_render_variants": ([P(c_i32), P(c_i32), P(c_i32), P(c_i32)], c_i32),

@@ -27,7 +27,14 @@ struct RenderFwdArgs {
     uint32_t *n_contrib;
     uint32_t *n_eval, *n_blend;  // STATS variant only
     uint32_t *work_counter;
+    // LOSS variant only: the L1 terms of a6 evaluated as each pixel finishes
+    const float *trgb, *tdepth;
+    float kc, kd, gamma;
+    int32_t use_gate;
+    float *loss, *d_rgb, *d_depth;
 };
+
+__device__ __forceinline__ float sgn(float x) { return (float)((x > 0.0f) - (x < 0.0f)); }
 
 // The three float4 of list entry idx of a tile (zeros past the end).
 __device__ __forceinline__ void load_entry(const RenderFwdArgs &a, int64_t rbase, uint32_t idx, uint32_t e,
@@ -46,10 +53,12 @@ __device__ __forceinline__ void load_entry(const RenderFwdArgs &a, int64_t rbase
 // STATS = true counts, per pixel, the list entries evaluated and blended (the
 // algorithmic work of the compositing, without culling) instead of writing the
 // image.
-template <int PPT, int BW, bool STATS>
+template <int PPT, int BW, bool STATS, bool LOSS>
 __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) render_fwd_kernel(RenderFwdArgs a,
                                                                                              ViewTable vt)
 {
+    __shared__ float s_loss[kRenderThreads / 32];
+    float lacc = 0.0f;  // LOSS: this thread's share of the loss
     constexpr int WARPS = kRenderThreads / 32;
     constexpr int RS = 32 / BW;                  // rows between a thread's pixels
     constexpr int BH = PPT * RS;                 // band height (width BW)
@@ -175,15 +184,45 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
                 a.alpha[pix] = 1.0f - t;
                 a.final_T[pix] = t;
                 a.n_contrib[pix] = last[k];
+                if (LOSS) {
+                    // the a6 terms of this pixel, in the operations of gs_loss_l1
+                    const float C[3] = {hi ? C0[i].y : C0[i].x, hi ? C1[i].y : C1[i].x, hi ? C2[i].y : C2[i].x};
+                    const float Dp = hi ? D[i].y : D[i].x, Dt = a.tdepth[pix];
+                    bool gate = true;
+                    if (a.use_gate) gate = (Dt > 0.0f) && (Dp > 0.0f) && (1.0f - t > a.gamma);
+                    const float g = gate ? 1.0f : 0.0f;
+                    float l = 0.0f;
+                    #pragma unroll
+                    for (int ch = 0; ch < 3; ch++) {
+                        const float r = C[ch] - a.trgb[3 * pix + ch];
+                        l += a.kc * fabsf(r);
+                        a.d_rgb[3 * pix + ch] = g * a.kc * sgn(r);
+                    }
+                    const float r = Dp - Dt;
+                    l += a.kd * fabsf(r);
+                    a.d_depth[pix] = g * a.kd * sgn(r);
+                    lacc += g * l;
+                }
             }
+        }
+    }
+    if (LOSS) {  // one atomic per block (every warp has left the item loop)
+        lacc = warp_sum(lacc);
+        if (lane == 0) s_loss[warp] = lacc;
+        __syncthreads();
+        if (tid == 0) {
+            float sum = 0.0f;
+            #pragma unroll
+            for (int w = 0; w < kRenderThreads / 32; w++) sum += s_loss[w];
+            atomicAdd(a.loss, sum);
         }
     }
 }
 
-template <int PPT, int BW, bool STATS>
+template <int PPT, int BW, bool STATS, bool LOSS = false>
 static gs_status_t launch_fwd(const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
 {
-    auto kern = render_fwd_kernel<PPT, BW, STATS>;
+    auto kern = render_fwd_kernel<PPT, BW, STATS, LOSS>;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, 0);
     const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
@@ -194,16 +233,16 @@ static gs_status_t launch_fwd(const RenderFwdArgs &a, const ViewTable &vt, cudaS
     return launch_status();
 }
 
-template <bool STATS>
+template <bool STATS, bool LOSS = false>
 static gs_status_t dispatch_fwd(const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
 {
     switch (render_variant_fwd()) {
-    case 0: return launch_fwd<1, 8, STATS>(a, vt, s);
-    case 1: return launch_fwd<2, 8, STATS>(a, vt, s);
-    case 2: return launch_fwd<2, 16, STATS>(a, vt, s);
-    case 3: return launch_fwd<4, 8, STATS>(a, vt, s);
-    case 4: return launch_fwd<4, 16, STATS>(a, vt, s);
-    default: return launch_fwd<8, 16, STATS>(a, vt, s);
+    case 0: return launch_fwd<1, 8, STATS, LOSS>(a, vt, s);
+    case 1: return launch_fwd<2, 8, STATS, LOSS>(a, vt, s);
+    case 2: return launch_fwd<2, 16, STATS, LOSS>(a, vt, s);
+    case 3: return launch_fwd<4, 8, STATS, LOSS>(a, vt, s);
+    case 4: return launch_fwd<4, 16, STATS, LOSS>(a, vt, s);
+    default: return launch_fwd<8, 16, STATS, LOSS>(a, vt, s);
     }
 }
 
@@ -236,6 +275,45 @@ extern "C" gs_status_t gs_render_fwd(const gs_projected_t *proj, int64_t n, cons
     a.n_contrib = img->n_contrib;
     a.work_counter = work_counter;
     return dispatch_fwd<false>(a, vt, s);
+}
+
+extern "C" gs_status_t gs_render_fwd_l1(const gs_projected_t *proj, int64_t n, const gs_bins_t *bins,
+                                        const gs_view_t *views, int32_t n_views, gs_image_t *img,
+                                        uint32_t *work_counter, const float *target_rgb, const float *target_depth,
+                                        float w_c, float w_d, int32_t use_gate, float gamma, float *loss,
+                                        float *d_rgb, float *d_depth, void *stream)
+{
+    if (!proj || !bins || !img || !work_counter || n < 0) return GS_ERR_INVALID_ARG;
+    ViewTable vt;
+    gs_status_t st = make_view_table(views, n_views, &vt);
+    if (st != GS_OK) return st;
+    if (!img->rgb || !img->depth || !img->alpha || !img->final_T || !img->n_contrib || !bins->ranges ||
+        !bins->vals || (n > 0 && !proj->rec) || !target_rgb || !target_depth || !loss || !d_rgb || !d_depth)
+        return GS_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    if (cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
+    RenderFwdArgs a = {};
+    a.rec = reinterpret_cast<const float4 *>(proj->rec);
+    a.n = n;
+    a.vals = bins->vals;
+    a.ranges = bins->ranges;
+    a.rgb = img->rgb;
+    a.depth = img->depth;
+    a.alpha = img->alpha;
+    a.final_T = img->final_T;
+    a.n_contrib = img->n_contrib;
+    a.work_counter = work_counter;
+    // the weights of gs_loss_l1, over all pixels of the views
+    a.kc = (float)((double)w_c / (3.0 * (double)vt.n_pix_total));
+    a.kd = (float)((double)w_d / (double)vt.n_pix_total);
+    a.trgb = target_rgb;
+    a.tdepth = target_depth;
+    a.use_gate = use_gate;
+    a.gamma = gamma;
+    a.loss = loss;
+    a.d_rgb = d_rgb;
+    a.d_depth = d_depth;
+    return dispatch_fwd<false, true>(a, vt, s);
 }
 
 extern "C" gs_status_t gs_render_stats(const gs_projected_t *proj, int64_t n, const gs_bins_t *bins,

@@ -119,7 +119,7 @@ class MappingStep:
 
         r = self.rast
         main = stream if stream is not None else torch.cuda.current_stream()
-        from . import gs_bin_sort, gs_project, gs_render_fwd
+        from . import gs_bin_sort, gs_project, gs_render_fwd_l1
         side = self.keypoints is not None and self.side is not None
         if part == 2:
             self._run_backward(mark, close, stream, side)
@@ -144,13 +144,12 @@ class MappingStep:
         tok = mark("bin_sort")
         gs_bin_sort(r.proj, r.n, r.views, r.bins, r.workspace, stream)
         close(tok)
+        # a5 + a6: the compositing evaluates the L1 terms as each pixel finishes
         tok = mark("render_fwd")
-        gs_render_fwd(r.proj, r.n, r.bins, r.views, r.img, r.work_counter, stream)
-        close(tok)
-        tok = mark("loss")
         k1 = 1.0 - self.zeta
-        gs_loss_l1(r.img["rgb"], r.img["depth"], r.img["alpha"], self.target_rgb, self.target_depth, k1 * self.w_c,
-                   k1 * self.w_d, self.use_gate, self.gamma, self.loss, self.d_rgb, self.d_depth, stream)
+        gs_render_fwd_l1(r.proj, r.n, r.bins, r.views, r.img, r.work_counter, self.target_rgb, self.target_depth,
+                         k1 * self.w_c, k1 * self.w_d, self.use_gate, self.gamma, self.loss, self.d_rgb, self.d_depth,
+                         stream)
         close(tok)
         if self.zeta > 0:
             tok = mark("ssim")
@@ -211,8 +210,8 @@ class MappingStep:
         # passes (8 bits each) and the ranges
         tile_passes = max(1, (max(self.rast.n_tiles - 1, 0).bit_length() + 7) // 8)
         k_bin = 3 + 4 + 3 + tile_passes + 1
-        # project, bin, fwd, loss, bwd, pbwd colour + geometry
-        k = 1 + k_bin + 1 + 1 + 1 + 2
+        # project, bin, fwd (with the L1 loss), bwd, pbwd colour + geometry
+        k = 1 + k_bin + 1 + 1 + 2
         k += 2 if self.zeta > 0 else 0
         k += 1 if self.keypoints is not None else 0
         k += 1 if self.optimise_params else 0

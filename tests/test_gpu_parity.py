@@ -202,6 +202,31 @@ def test_keyframe_decoding_matches_oracle(n):
     np.testing.assert_array_equal(depth.cpu().numpy().view(np.uint32), ref_depth.view(np.uint32))
 
 
+@pytest.mark.parametrize("gate", [False, True])
+@pytest.mark.parametrize("name,scene,cams", CASES, ids=[c[0] for c in CASES])
+def test_fused_forward_l1_equals_separate_calls(name, scene, cams, gate):
+    """gs_render_fwd_l1 gives the images of gs_render_fwd and the gradients of
+    gs_loss_l1 bit for bit, and its loss up to summation order."""
+    rast, p, vm = _run(scene, cams)
+    P = rast.n_pix
+    rng = np.random.default_rng(12)
+    t_rgb = t(rng.uniform(0, 1, (P, 3)))
+    t_depth = t(rng.uniform(0, 4, P) * (rng.uniform(0, 1, P) > 0.1))  # some pixels without a sensor reading
+    img_ref = {k: v.clone() for k, v in rast.img.items()}
+    loss_a, loss_b = torch.zeros(1, device="cuda"), torch.zeros(1, device="cuda")
+    dr_a, dd_a = torch.empty(P, 3, device="cuda"), torch.empty(P, device="cuda")
+    dr_b, dd_b = torch.full((P, 3), 7.0, device="cuda"), torch.full((P,), 7.0, device="cuda")
+    gs.gs_loss_l1(rast.img["rgb"], rast.img["depth"], rast.img["alpha"], t_rgb, t_depth, 0.7, 0.3, gate, 0.5, loss_a,
+                  dr_a, dd_a)
+    gs.gs_render_fwd_l1(rast.proj, rast.n, rast.bins, rast.views, rast.img, rast.work_counter, t_rgb, t_depth, 0.7, 0.3,
+                        gate, 0.5, loss_b, dr_b, dd_b)
+    torch.cuda.synchronize()
+    for k, v in img_ref.items():
+        assert torch.equal(rast.img[k], v), k
+    assert torch.equal(dr_a, dr_b) and torch.equal(dd_a, dd_b)
+    assert abs(float(loss_a) - float(loss_b)) <= 1e-5 * abs(float(loss_a))
+
+
 def test_batched_views_equal_plain_views():
     """Rendering several views in one launch gives the same images as one view per launch."""
     name, scene, cams = CASES[1]
