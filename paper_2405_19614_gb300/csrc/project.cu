@@ -241,21 +241,26 @@ __global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable v
     q[2] = q4.z;
     q[3] = q4.w;
     const float opacity = 1.0f / (1.0f + __expf(-__ldg(a.opacity_logit + i)));
+    // the SH coefficients are read only for the views the Gaussian is drawn
+    // in (they come from L1 after the first): 48 registers fewer a thread than
+    // holding them across the view loop, and no read for a Gaussian no view draws
     float sh[K * 3];
     const float *shp = a.sh + (int64_t)K * 3 * i;
-    if constexpr ((K * 3) % 4 == 0) {
-        #pragma unroll
-        for (int k = 0; k < K * 3 / 4; k++) {
-            float4 t = __ldg(reinterpret_cast<const float4 *>(shp) + k);
-            sh[4 * k] = t.x;
-            sh[4 * k + 1] = t.y;
-            sh[4 * k + 2] = t.z;
-            sh[4 * k + 3] = t.w;
+    auto load_sh = [&]() {
+        if constexpr ((K * 3) % 4 == 0) {
+            #pragma unroll
+            for (int k = 0; k < K * 3 / 4; k++) {
+                float4 t = __ldg(reinterpret_cast<const float4 *>(shp) + k);
+                sh[4 * k] = t.x;
+                sh[4 * k + 1] = t.y;
+                sh[4 * k + 2] = t.z;
+                sh[4 * k + 3] = t.w;
+            }
+        } else {
+            #pragma unroll
+            for (int k = 0; k < K * 3; k++) sh[k] = __ldg(shp + k);
         }
-    } else {
-        #pragma unroll
-        for (int k = 0; k < K * 3; k++) sh[k] = __ldg(shp + k);
-    }
+    };
 
     #pragma unroll 1
     for (int v = 0; v < vt.n_views; v++) {
@@ -272,6 +277,7 @@ __global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable v
         dx *= rn;
         dy *= rn;
         dz *= rn;
+        load_sh();
         float Y[K];
         sh_basis<DEG>(dx, dy, dz, Y);
         float col[3];
