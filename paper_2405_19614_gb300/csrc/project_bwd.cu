@@ -199,26 +199,27 @@ __global__ void __launch_bounds__(128) project_bwd_color_kernel(ProjectBwdArgs a
                 }
             }
         }
-        if (DEG == 0) continue;  // the colour does not depend on the view direction
-        // sum the channels' direction gradients over the quad
-        #pragma unroll
-        for (int k = 0; k < 3; k++) {
-            gdir[k] += __shfl_xor_sync(kFullMask, gdir[k], 1);
-            gdir[k] += __shfl_xor_sync(kFullMask, gdir[k], 2);
+        if constexpr (DEG > 0) {  // (at degree 0 the colour does not depend on the view direction)
+            // sum the channels' direction gradients over the quad
+            #pragma unroll
+            for (int k = 0; k < 3; k++) {
+                gdir[k] += __shfl_xor_sync(kFullMask, gdir[k], 1);
+                gdir[k] += __shfl_xor_sync(kFullMask, gdir[k], 2);
+            }
+            float tw[3] = {0.0f, 0.0f, 0.0f};
+            if (vis && ch == 0) {
+                const float dd = gdir[0] * dx + gdir[1] * dy + gdir[2] * dz;
+                const float gvx = (gdir[0] - dx * dd) * rn, gvy = (gdir[1] - dy * dd) * rn, gvz = (gdir[2] - dz * dd) * rn;
+                gm[0] += gvx;
+                gm[1] += gvy;
+                gm[2] += gvz;
+                const float *E = s_E[v];
+                tw[0] = E[0] * gvx + E[1] * gvy + E[2] * gvz;
+                tw[1] = E[4] * gvx + E[5] * gvy + E[6] * gvz;
+                tw[2] = E[8] * gvx + E[9] * gvy + E[10] * gvz;
+            }
+            if (put_twist) twist_put<3>(twt, v, tw, lane, vt.n_views, s_tw);
         }
-        float tw[3] = {0.0f, 0.0f, 0.0f};
-        if (vis && ch == 0) {
-            const float dd = gdir[0] * dx + gdir[1] * dy + gdir[2] * dz;
-            const float gvx = (gdir[0] - dx * dd) * rn, gvy = (gdir[1] - dy * dd) * rn, gvz = (gdir[2] - dz * dd) * rn;
-            gm[0] += gvx;
-            gm[1] += gvy;
-            gm[2] += gvz;
-            const float *E = s_E[v];
-            tw[0] = E[0] * gvx + E[1] * gvy + E[2] * gvz;
-            tw[1] = E[4] * gvx + E[5] * gvy + E[6] * gvz;
-            tw[2] = E[8] * gvx + E[9] * gvy + E[10] * gvz;
-        }
-        if (put_twist) twist_put<3>(twt, v, tw, lane, vt.n_views, s_tw);
     }
     if (active && a.g_means) {
         if (ch < 3) {
