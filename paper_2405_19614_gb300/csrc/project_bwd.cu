@@ -12,15 +12,17 @@
 // Twist xi = (rho, phi) with pose Exp(xi) E at xi = 0: p -> p + rho + phi x p,
 // Sc -> Exp(phi) Sc Exp(phi)^T, c -> c - W^T rho.
 //
-// Two kernels, each looping over all views so that gradients summed over views
-// reach HBM once.  The colour kernel runs four lanes per Gaussian, one per
-// colour channel (the fourth idle), so each lane holds only its channel's SH
-// coefficients and gradients; it propagates the view-direction gradient to the
-// mean and to the twist.  The geometry kernel, one thread per Gaussian, then
-// does the mean, covariance, opacity and pose paths and clears the 2D gradient
-// entries it consumed.  Keeping the SH state out of the geometry kernel keeps
-// both at a register count that lets many warps hide latency.
+// Two kernels, one thread per Gaussian, each looping over all views so that
+// gradients summed over views reach HBM once.  The colour kernel keeps the
+// Gaussian's SH coefficients and their gradients in registers (the basis and
+// its direction gradient are evaluated once per view for all three channels)
+// and propagates the view-direction gradient to the mean and to the twist.
+// The geometry kernel then does the mean, covariance, opacity and pose paths
+// and clears the 2D gradient entries it consumed.  Keeping the SH state out of
+// the geometry kernel keeps it at a register count that lets many warps hide
+// latency.
 #include "common.cuh"
+#include "async_copy.cuh"
 #include "sh.cuh"
 
 namespace gs {
@@ -120,113 +122,259 @@ __device__ __forceinline__ uint64_t visible_views(const int32_t *radii, int64_t 
     return mask;
 }
 
-// Colour path: lanes 4g .. 4g+3 of the grid handle Gaussian g, lane 4g+c its
-// colour channel c (c = 3 idle).
+// Colour path: one thread per Gaussian, holding its 3K SH coefficients and
+// their gradients in registers for the whole walk over the views.  A block's
+// coefficients travel through shared memory both ways, so that every global
+// access is a contiguous run over the block's rows: row r of the tile is
+// Gaussian i0 + r, its 3K floats (coefficient-major, channel-minor) at pitch
+// ShTile::pitch.  With 3K a multiple of 4 (degrees 1 and 3) the copies and the
+// row reads are 16-byte, and the pitch is four times an odd number, so the
+// eight rows a quarter warp reads fall on distinct bank groups; otherwise they
+// are 4-byte with an odd pitch.
 template <int DEG>
-__global__ void __launch_bounds__(128) project_bwd_color_kernel(ProjectBwdArgs a, ViewTable vt)
+struct ShTile {
+    static constexpr int K = ShCount<DEG>::value;
+    static constexpr int row = 3 * K;
+    static constexpr bool vec = row % 4 == 0;
+    static constexpr int pitch = vec ? ((row / 4) % 2 ? row : row + 4) : (row % 2 ? row : row + 1);
+};
+
+// tile <- rows [0, rows) of the block's coefficients at src, as asynchronous
+// copies (vec4: src is 16-byte aligned); complete after cp_async_wait_all
+template <int DEG>
+__device__ __forceinline__ void sh_tile_load_async(const float *src, int rows, bool vec4, float *tile)
 {
-    constexpr int K = ShCount<DEG>::value;
+    using T = ShTile<DEG>;
+    const int total = rows * T::row;
+    if (T::vec && vec4) {
+        for (int u = threadIdx.x; u < total / 4; u += blockDim.x) {
+            const int f = 4 * u, r = f / T::row;
+            cp_async16(tile + r * T::pitch + (f - r * T::row), src + f);
+        }
+    } else {
+        for (int f = threadIdx.x; f < total; f += blockDim.x) {
+            const int r = f / T::row;
+            cp_async4(tile + r * T::pitch + (f - r * T::row), src + f, true);
+        }
+    }
+}
+
+// dst = tile (overwrite) or dst += tile, rows [0, rows)
+template <int DEG>
+__device__ __forceinline__ void sh_tile_store(float *dst, int rows, bool vec4, const float *tile, bool overwrite)
+{
+    using T = ShTile<DEG>;
+    const int total = rows * T::row;
+    if (T::vec && vec4) {
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        for (int u = threadIdx.x; u < total / 4; u += blockDim.x) {
+            const int f = 4 * u, r = f / T::row;
+            float4 g = *reinterpret_cast<const float4 *>(tile + r * T::pitch + (f - r * T::row));
+            if (!overwrite) {
+                const float4 o = d4[u];
+                g = make_float4(o.x + g.x, o.y + g.y, o.z + g.z, o.w + g.w);
+            }
+            d4[u] = g;
+        }
+    } else {
+        for (int f = threadIdx.x; f < total; f += blockDim.x) {
+            const int r = f / T::row;
+            put_grad(dst + f, tile[r * T::pitch + (f - r * T::row)], overwrite);
+        }
+    }
+}
+
+// this thread's row of the tile <-> registers
+template <int DEG>
+__device__ __forceinline__ void sh_row_read(const float *row, float (&x)[3 * ShCount<DEG>::value])
+{
+    using T = ShTile<DEG>;
+    if constexpr (T::vec) {
+        #pragma unroll
+        for (int q = 0; q < T::row / 4; q++) {
+            const float4 w = reinterpret_cast<const float4 *>(row)[q];
+            x[4 * q] = w.x;
+            x[4 * q + 1] = w.y;
+            x[4 * q + 2] = w.z;
+            x[4 * q + 3] = w.w;
+        }
+    } else {
+        #pragma unroll
+        for (int f = 0; f < T::row; f++) x[f] = row[f];
+    }
+}
+
+template <int DEG>
+__device__ __forceinline__ void sh_row_write(float *row, const float (&x)[3 * ShCount<DEG>::value])
+{
+    using T = ShTile<DEG>;
+    if constexpr (T::vec) {
+        #pragma unroll
+        for (int q = 0; q < T::row / 4; q++)
+            reinterpret_cast<float4 *>(row)[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+    } else {
+        #pragma unroll
+        for (int f = 0; f < T::row; f++) row[f] = x[f];
+    }
+}
+
+constexpr int kColorThreads = 32 * kPbwdWarps;
+
+template <int DEG>
+__global__ void __launch_bounds__(kColorThreads, 3) project_bwd_color_kernel(ProjectBwdArgs a, ViewTable vt)
+{
+    using T = ShTile<DEG>;
+    constexpr int K = T::K;
     __shared__ float s_E[GS_MAX_VIEWS][12];
     __shared__ float s_c[GS_MAX_VIEWS][3];
     __shared__ float s_tw[GS_MAX_VIEWS][6];
     __shared__ __align__(16) float s_twt[kPbwdWarps][kTwGroup * 3][kTwPitch];
-    load_views(a.viewmats, vt.n_views, s_E, s_c, s_tw);
+    __shared__ __align__(16) float s_sh[kColorThreads * T::pitch];
 
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t i = t >> 2;
-    const int ch = (int)(t & 3);
-    const int lane = threadIdx.x & 31;
-    const bool active = i < a.n;
-    const bool want_twist = a.d_twist != nullptr;
-    float sh[K], gsh[K];
+    const int64_t i0 = (int64_t)blockIdx.x * kColorThreads;
+    const int rows = a.n - i0 < kColorThreads ? (int)(a.n - i0) : kColorThreads;
+    const int64_t i = i0 + threadIdx.x;
+    const bool active = threadIdx.x < rows;
+    const bool vec4 = (reinterpret_cast<uintptr_t>(a.sh) & 15) == 0 &&
+                      (!a.g_sh || (reinterpret_cast<uintptr_t>(a.g_sh) & 15) == 0);
+    // Prologue: every global load that depends on no other is put in flight
+    // at once (the tile and the view matrices as asynchronous copies, then the
+    // radii and the mean), so that a block waits on one load latency here
+    // instead of a chain of them.  (Issuing the first group's colour gradients
+    // here as well spills at three blocks per SM and measured slower.)
+    for (int k = threadIdx.x; k < vt.n_views * 12; k += kColorThreads)
+        cp_async4(&s_E[k / 12][k % 12], a.viewmats + k, true);
+    sh_tile_load_async<DEG>(a.sh + (int64_t)T::row * i0, rows, vec4, s_sh);
+    for (int k = threadIdx.x; k < vt.n_views * 6; k += kColorThreads) s_tw[k / 6][k % 6] = 0.0f;
+    const uint64_t vis_mask = visible_views(a.radii, a.n, i, active, vt.n_views);
     float m[3] = {0.0f, 0.0f, 0.0f};
-    #pragma unroll
-    for (int k = 0; k < K; k++) {
-        sh[k] = (active && ch < 3) ? a.sh[((int64_t)K * i + k) * 3 + ch] : 0.0f;
-        gsh[k] = 0.0f;
-    }
     if (active) {
         #pragma unroll
         for (int k = 0; k < 3; k++) m[k] = a.means[3 * i + k];
     }
-    float gm[3] = {0.0f, 0.0f, 0.0f};
-    const uint64_t vis_mask = visible_views(a.radii, a.n, i, active, vt.n_views);
+    // The colour gradients (entries 6..8 of the 2D records) of a group of views
+    // are fetched together, by independent loads, and parked in this thread's
+    // own row of the tile (free once the coefficients are in registers), so
+    // that the walk over the group's views waits on one load latency instead
+    // of one per view.
+    constexpr int kSlot = T::vec ? 4 : 3;
+    constexpr int kGroup = T::pitch / kSlot < 8 ? T::pitch / kSlot : 8;
     const float *g2 = reinterpret_cast<const float *>(a.grad2d);
-    // this lane's colour gradient for the first visible view, then one view ahead
-    float gcol_next = 0.0f;
-    if (vis_mask && ch < 3) gcol_next = g2[12 * ((int64_t)(__ffsll((long long)vis_mask) - 1) * a.n + i) + 6 + ch];
+    float gq[kGroup][3];
+    auto fetch_group = [&](int v0) {
+        #pragma unroll
+        for (int j = 0; j < kGroup; j++) {
+            const int v = v0 + j;
+            const bool on = v < vt.n_views && ((vis_mask >> v) & 1ull);
+            const int64_t o = 12 * ((int64_t)v * a.n + i) + 6;
+            #pragma unroll
+            for (int c = 0; c < 3; c++) gq[j][c] = on ? g2[o + c] : 0.0f;
+        }
+    };
+    cp_async_wait_all();
+    __syncthreads();
+    for (int v = threadIdx.x; v < vt.n_views; v += kColorThreads) {
+        const float *E = s_E[v];
+        #pragma unroll
+        for (int k = 0; k < 3; k++) s_c[v][k] = -(E[k] * E[3] + E[4 + k] * E[7] + E[8 + k] * E[11]);
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const bool want_twist = a.d_twist != nullptr;
+    float sh[3 * K], gsh[3 * K];
+    if (active) {
+        sh_row_read<DEG>(s_sh + threadIdx.x * T::pitch, sh);
+    } else {
+        #pragma unroll
+        for (int f = 0; f < 3 * K; f++) sh[f] = 0.0f;
+    }
+    #pragma unroll
+    for (int f = 0; f < 3 * K; f++) gsh[f] = 0.0f;
+    float gm[3] = {0.0f, 0.0f, 0.0f};
+    float *slots = s_sh + threadIdx.x * T::pitch;
 
     float(*twt)[kTwPitch] = s_twt[threadIdx.x >> 5];
     const bool put_twist = want_twist && DEG > 0;  // the colour depends on the view direction
     #pragma unroll 1
-    for (int v = 0; v < vt.n_views; v++) {
-        const bool vis = (vis_mask >> v) & 1ull;
-        if (!__any_sync(kFullMask, vis)) {
-            if (put_twist) {
-                const float zero[3] = {0.0f, 0.0f, 0.0f};
-                twist_put<3>(twt, v, zero, lane, vt.n_views, s_tw);
-            }
-            continue;
-        }
-        float gcol = 0.0f;
-        if (vis) {
-            gcol = gcol_next;
-            const uint64_t rest = vis_mask & ~((2ull << v) - 1ull);
-            if (rest && ch < 3) gcol_next = g2[12 * ((int64_t)(__ffsll((long long)rest) - 1) * a.n + i) + 6 + ch];
-        }
-        float gdir[3] = {0.0f, 0.0f, 0.0f};
-        float dx = 0.0f, dy = 0.0f, dz = 0.0f, rn = 0.0f;
-        if (vis) {
-            const float vx = m[0] - s_c[v][0], vy = m[1] - s_c[v][1], vz = m[2] - s_c[v][2];
-            rn = rsqrtf(vx * vx + vy * vy + vz * vz);
-            dx = vx * rn;
-            dy = vy * rn;
-            dz = vz * rn;
-            if (ch < 3) {
-                float Y[K];
-                sh_basis<DEG>(dx, dy, dz, Y);
-                float acc = 0.5f;
+    for (int v0 = 0; v0 < vt.n_views; v0 += kGroup) {
+        fetch_group(v0);
+        #pragma unroll
+        for (int j = 0; j < kGroup; j++) {
+            if constexpr (T::vec) {
+                reinterpret_cast<float4 *>(slots)[j] = make_float4(gq[j][0], gq[j][1], gq[j][2], 0.0f);
+            } else {
                 #pragma unroll
-                for (int k = 0; k < K; k++) acc += sh[k] * Y[k];
-                if (acc >= 0.0f && gcol != 0.0f) {
-                    float wk[K];
-                    #pragma unroll
-                    for (int k = 0; k < K; k++) {
-                        gsh[k] += Y[k] * gcol;
-                        wk[k] = sh[k] * gcol;
-                    }
-                    if (DEG > 0) sh_basis_grad<DEG>(dx, dy, dz, wk, gdir);
-                }
+                for (int c = 0; c < 3; c++) slots[3 * j + c] = gq[j][c];
             }
         }
-        if constexpr (DEG > 0) {  // (at degree 0 the colour does not depend on the view direction)
-            // sum the channels' direction gradients over the quad
-            #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                gdir[k] += __shfl_xor_sync(kFullMask, gdir[k], 1);
-                gdir[k] += __shfl_xor_sync(kFullMask, gdir[k], 2);
-            }
+        #pragma unroll 1
+        for (int j = 0; j < kGroup && v0 + j < vt.n_views; j++) {
+            const int v = v0 + j;
+            const bool vis = (vis_mask >> v) & 1ull;
             float tw[3] = {0.0f, 0.0f, 0.0f};
-            if (vis && ch == 0) {
-                const float dd = gdir[0] * dx + gdir[1] * dy + gdir[2] * dz;
-                const float gvx = (gdir[0] - dx * dd) * rn, gvy = (gdir[1] - dy * dd) * rn, gvz = (gdir[2] - dz * dd) * rn;
-                gm[0] += gvx;
-                gm[1] += gvy;
-                gm[2] += gvz;
-                const float *E = s_E[v];
-                tw[0] = E[0] * gvx + E[1] * gvy + E[2] * gvz;
-                tw[1] = E[4] * gvx + E[5] * gvy + E[6] * gvz;
-                tw[2] = E[8] * gvx + E[9] * gvy + E[10] * gvz;
+            if (!__any_sync(kFullMask, vis)) {
+                if (put_twist) twist_put<3>(twt, v, tw, lane, vt.n_views, s_tw);
+                continue;
+            }
+            if (vis) {
+                float gc[3];
+                if constexpr (T::vec) {
+                    const float4 q = reinterpret_cast<const float4 *>(slots)[j];
+                    gc[0] = q.x;
+                    gc[1] = q.y;
+                    gc[2] = q.z;
+                } else {
+                    #pragma unroll
+                    for (int c = 0; c < 3; c++) gc[c] = slots[3 * j + c];
+                }
+                if (gc[0] != 0.0f || gc[1] != 0.0f || gc[2] != 0.0f) {
+                    const float vx = m[0] - s_c[v][0], vy = m[1] - s_c[v][1], vz = m[2] - s_c[v][2];
+                    const float rn = rsqrtf(vx * vx + vy * vy + vz * vz);
+                    const float dx = vx * rn, dy = vy * rn, dz = vz * rn;
+                    float Y[K];
+                    sh_basis<DEG>(dx, dy, dz, Y);
+                    float col[3] = {0.5f, 0.5f, 0.5f};
+                    #pragma unroll
+                    for (int k = 0; k < K; k++)
+                        #pragma unroll
+                        for (int c = 0; c < 3; c++) col[c] += sh[3 * k + c] * Y[k];
+                    // colour = max(0, SH + 1/2): no gradient where it is clamped
+                    #pragma unroll
+                    for (int c = 0; c < 3; c++)
+                        if (!(col[c] >= 0.0f)) gc[c] = 0.0f;
+                    #pragma unroll
+                    for (int k = 0; k < K; k++)
+                        #pragma unroll
+                        for (int c = 0; c < 3; c++) gsh[3 * k + c] += Y[k] * gc[c];
+                    if constexpr (DEG > 0) {
+                        float wk[K];
+                        #pragma unroll
+                        for (int k = 0; k < K; k++) wk[k] = sh[3 * k] * gc[0] + sh[3 * k + 1] * gc[1] + sh[3 * k + 2] * gc[2];
+                        float gdir[3];
+                        sh_basis_grad<DEG>(dx, dy, dz, wk, gdir);
+                        const float dd = gdir[0] * dx + gdir[1] * dy + gdir[2] * dz;
+                        const float gvx = (gdir[0] - dx * dd) * rn, gvy = (gdir[1] - dy * dd) * rn,
+                                    gvz = (gdir[2] - dz * dd) * rn;
+                        gm[0] += gvx;
+                        gm[1] += gvy;
+                        gm[2] += gvz;
+                        const float *E = s_E[v];
+                        tw[0] = E[0] * gvx + E[1] * gvy + E[2] * gvz;
+                        tw[1] = E[4] * gvx + E[5] * gvy + E[6] * gvz;
+                        tw[2] = E[8] * gvx + E[9] * gvy + E[10] * gvz;
+                    }
+                }
             }
             if (put_twist) twist_put<3>(twt, v, tw, lane, vt.n_views, s_tw);
         }
     }
-    if (active && a.g_means) {
-        if (ch < 3) {
-            #pragma unroll
-            for (int k = 0; k < K; k++) put_grad(a.g_sh + ((int64_t)K * i + k) * 3 + ch, gsh[k], a.overwrite);
-        }
-        if (ch == 0 && DEG > 0) {
+    if (a.g_sh) {
+        // (each thread has used only its own row since the tile was loaded)
+        if (active) sh_row_write<DEG>(s_sh + threadIdx.x * T::pitch, gsh);
+        __syncthreads();
+        sh_tile_store<DEG>(a.g_sh + (int64_t)T::row * i0, rows, vec4, s_sh, a.overwrite);
+        if (active && DEG > 0) {
             #pragma unroll
             for (int k = 0; k < 3; k++) put_grad(a.g_means + 3 * i + k, gm[k], a.overwrite);
         }
@@ -505,12 +653,12 @@ extern "C" gs_status_t gs_project_bwd(const gs_params_t *params, const gs_view_t
     const int threads = 128;
     cudaStream_t s = as_stream(stream);
     // colour first: the geometry kernel clears the 2D gradients after use
-    const unsigned cblocks = (unsigned)((4 * params->n + threads - 1) / threads);
+    const unsigned cblocks = (unsigned)((params->n + kColorThreads - 1) / kColorThreads);
     switch (params->sh_degree) {
-    case 0: project_bwd_color_kernel<0><<<cblocks, threads, 0, s>>>(a, vt); break;
-    case 1: project_bwd_color_kernel<1><<<cblocks, threads, 0, s>>>(a, vt); break;
-    case 2: project_bwd_color_kernel<2><<<cblocks, threads, 0, s>>>(a, vt); break;
-    default: project_bwd_color_kernel<3><<<cblocks, threads, 0, s>>>(a, vt); break;
+    case 0: project_bwd_color_kernel<0><<<cblocks, kColorThreads, 0, s>>>(a, vt); break;
+    case 1: project_bwd_color_kernel<1><<<cblocks, kColorThreads, 0, s>>>(a, vt); break;
+    case 2: project_bwd_color_kernel<2><<<cblocks, kColorThreads, 0, s>>>(a, vt); break;
+    default: project_bwd_color_kernel<3><<<cblocks, kColorThreads, 0, s>>>(a, vt); break;
     }
     const unsigned gblocks = (unsigned)((params->n + threads - 1) / threads);
     project_bwd_geom_kernel<<<gblocks, threads, 0, s>>>(a, vt);

@@ -29,6 +29,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "async_copy.cuh"
 
 namespace gs {
 
@@ -53,25 +54,6 @@ constexpr size_t kSsimStatsSmem =
     sizeof(float) * (2 * kSsimRows * kSsimInPitchXY + 4 * kSsimRows * kSsimHPitch);
 constexpr size_t kSsimGradSmem =
     sizeof(float) * (2 * 3 * kSsimRows * kSsimInPitch + 3 * kSsimRows * kSsimHPitch + kSsimTH * kSsimOutPitch);
-
-// 4-byte asynchronous copy global -> shared (Ampere-style cp.async); a
-// source size of 0 writes a zero instead (the zero padding of the window).
-__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid)
-{
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-
-// Waits until at most N of this thread's committed copy groups are pending.
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 struct SsimTiles {
     int32_t n_views;

@@ -158,6 +158,53 @@ def test_splat_gradients_parity():
         assert e <= GRAD_TOL, nm
 
 
+@pytest.mark.parametrize("deg", [1, 2])
+def test_backward_parity_sh_degrees_1_and_2(deg):
+    """Degrees 1 (3K = 12 floats a row, 16-byte copies) and 2 (27 floats,
+    4-byte copies) of the colour backward, with a ragged last block (n = 1001)."""
+    sc = scenes.cube_scene(1001, seed=80 + deg, sh_degree=deg, log_scale=(-3.2, 0.5))
+    out, gref = _backward_case(sc, CASES[1][2])
+    for k in (*PARAM_KEYS, "twist"):
+        e = rel_l2(out[k], gref[k])
+        print(f"sh{deg}: grad {k:14s} rel-L2 err = {e:.3e}")
+        assert e <= GRAD_TOL, k
+
+
+def test_colour_backward_unaligned_sh_equals_aligned():
+    """The SH rows travel 16 bytes at a time when the coefficient and gradient
+    pointers are 16-byte aligned, 4 bytes at a time otherwise: both give the
+    same gradients bit for bit."""
+    _, scene, cams = CASES[1]
+    rast, p, vm = _run(scene, cams)
+    rng = np.random.default_rng(10)
+    P = rast.n_pix
+    gs.gs_render_bwd_splats(rast.proj, rast.n, rast.bins, rast.views, rast.img, t(rng.normal(0, 1, (P, 3))),
+                            t(rng.normal(0, 1, P)), None, rast.grad2d, rast.work_counter)
+    g2d = rast.grad2d.clone()
+
+    def shifted(x):  # the same values, 4 bytes past a 16-byte boundary
+        buf = torch.zeros(x.numel() + 1, device=x.device)
+        y = buf[1:].view(x.shape)
+        y.copy_(x)
+        assert y.data_ptr() % 16 == 4
+        return y
+
+    out = {}
+    for mode in ("aligned", "unaligned"):
+        rast.grad2d.copy_(g2d)
+        q = dict(p)
+        g = zero_grads(p)
+        if mode == "unaligned":
+            q["sh"] = shifted(p["sh"])
+            g["sh"] = shifted(g["sh"])
+        gs.gs_project_bwd(q, rast.views, vm, rast.proj, rast.grad2d, g, None)
+        torch.cuda.synchronize()
+        out[mode] = {k: g[k].cpu().numpy() for k in PARAM_KEYS}
+    for k in PARAM_KEYS:
+        assert np.abs(out["aligned"][k]).max() > 0, k
+        np.testing.assert_array_equal(out["unaligned"][k], out["aligned"][k], err_msg=k)
+
+
 @pytest.mark.parametrize("name,scene,cams", CASES, ids=[c[0] for c in CASES])
 def test_overwrite_grads_equals_accumulating_into_zeros(name, scene, cams):
     """With overwrite_grads the projection backward writes every Gaussian's
