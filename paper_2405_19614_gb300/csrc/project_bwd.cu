@@ -43,22 +43,6 @@ struct ProjectBwdArgs {
 // dst = v (overwrite) or dst += v
 __device__ __forceinline__ void put_grad(float *dst, float v, bool overwrite) { *dst = overwrite ? v : *dst + v; }
 
-__device__ __forceinline__ void load_views(const float *viewmats, int n_views, float (*s_E)[12], float (*s_c)[3],
-                                           float (*s_tw)[6])
-{
-    for (int k = threadIdx.x; k < n_views * 12; k += blockDim.x) s_E[k / 12][k % 12] = viewmats[k];
-    for (int k = threadIdx.x; k < n_views * 6; k += blockDim.x) s_tw[k / 6][k % 6] = 0.0f;
-    __syncthreads();
-    if (s_c) {
-        for (int v = threadIdx.x; v < n_views; v += blockDim.x) {
-            const float *E = s_E[v];
-            #pragma unroll
-            for (int i = 0; i < 3; i++) s_c[v][i] = -(E[i] * E[3] + E[4 + i] * E[7] + E[8 + i] * E[11]);
-        }
-        __syncthreads();
-    }
-}
-
 __device__ __forceinline__ void flush_twist(float *d_twist, int n_views, float (*s_tw)[6])
 {
     __syncthreads();
@@ -388,7 +372,12 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a,
     __shared__ float s_E[GS_MAX_VIEWS][12];
     __shared__ float s_tw[GS_MAX_VIEWS][6];
     __shared__ __align__(16) float s_twt[kPbwdWarps][kTwGroup * 6][kTwPitch];
-    load_views(a.viewmats, vt.n_views, s_E, nullptr, s_tw);
+    // prologue as in the colour kernel: the view matrices as asynchronous
+    // copies, then the parameters, the radii and the first visible view's 2D
+    // gradients, all in flight before the block waits
+    for (int k = threadIdx.x; k < vt.n_views * 12; k += blockDim.x)
+        cp_async4(&s_E[k / 12][k % 12], a.viewmats + k, true);
+    for (int k = threadIdx.x; k < vt.n_views * 6; k += blockDim.x) s_tw[k / 6][k % 6] = 0.0f;
 
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < a.n;
@@ -409,6 +398,17 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a,
         q[3] = q4.w;
         ol = a.opacity_logit[i];
     }
+    const uint64_t vis_mask = visible_views(a.radii, a.n, i, active, vt.n_views);
+    // 2D gradients of the first visible view, then always one visible view ahead
+    float4 N0 = make_float4(0.f, 0.f, 0.f, 0.f), N1 = N0, N2 = N0;
+    if (vis_mask) {
+        const int64_t o = (int64_t)(__ffsll((long long)vis_mask) - 1) * a.n + i;
+        N0 = a.grad2d[3 * o];
+        N1 = a.grad2d[3 * o + 1];
+        N2 = a.grad2d[3 * o + 2];
+    }
+    cp_async_wait_all();
+    __syncthreads();
     const float qn2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     const float qinv = rsqrtf(fmaxf(qn2, 1e-30f));
     const float w = q[0] * qinv, qa = q[1] * qinv, qb = q[2] * qinv, qc = q[3] * qinv;
@@ -435,15 +435,6 @@ __global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a,
     const float opac = 1.0f / (1.0f + expf(-ol));
 
     float gm[3] = {0, 0, 0}, Gw[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gol = 0.0f;
-    const uint64_t vis_mask = visible_views(a.radii, a.n, i, active, vt.n_views);
-    // 2D gradients of the first visible view, then always one visible view ahead
-    float4 N0 = make_float4(0.f, 0.f, 0.f, 0.f), N1 = N0, N2 = N0;
-    if (vis_mask) {
-        const int64_t o = (int64_t)(__ffsll((long long)vis_mask) - 1) * a.n + i;
-        N0 = a.grad2d[3 * o];
-        N1 = a.grad2d[3 * o + 1];
-        N2 = a.grad2d[3 * o + 2];
-    }
     float(*twt)[kTwPitch] = s_twt[threadIdx.x >> 5];
     #pragma unroll 1
     for (int v = 0; v < vt.n_views; v++) {
