@@ -194,8 +194,15 @@ __global__ void __launch_bounds__(kEmitThreads) pair_count_kernel(const uint2 *_
                                                                   const uint32_t *n_vis_p, uint64_t *block_sums)
 {
     __shared__ uint64_t tmp[kEmitThreads / 32];
+    // the grid covers every record slot; chunks past the drawn records
+    // (about four in five on a multi-view batch) only report an empty sum
+    const uint32_t n_vis = *n_vis_p;
+    if ((int64_t)blockIdx.x * kPairChunk >= (int64_t)n_vis) {
+        if (threadIdx.x == 0) block_sums[blockIdx.x] = 0;
+        return;
+    }
     uint32_t r[kPairItems], c[kPairItems];
-    chunk_counts(recs, tt, *n_vis_p, r, c);
+    chunk_counts(recs, tt, n_vis, r, c);
     uint64_t s = 0;
     #pragma unroll
     for (int k = 0; k < kPairItems; k++) s += c[k];
@@ -221,9 +228,11 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
     __shared__ uint32_t h[kMaxTilePasses][kRadix];
     constexpr int kRun = 8;  // consecutive pairs a thread emits per round
     __shared__ uint32_t s_tk[kEmitThreads * kRun], s_tv[kEmitThreads * kRun];
+    const uint32_t n_vis = *n_vis_p;
+    if ((int64_t)blockIdx.x * kPairChunk >= (int64_t)n_vis) return;  // no drawn record: nothing to emit
     clear_hist(h, tile_passes);
     uint32_t r[kPairItems], c[kPairItems];
-    chunk_counts(recs, tt, *n_vis_p, r, c);
+    chunk_counts(recs, tt, n_vis, r, c);
     uint64_t sum = 0;
     #pragma unroll
     for (int k = 0; k < kPairItems; k++) sum += c[k];
