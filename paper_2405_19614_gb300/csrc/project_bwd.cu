@@ -204,6 +204,8 @@ __device__ __forceinline__ void sh_row_write(float *row, const float (&x)[3 * Sh
 
 constexpr int kColorThreads = 32 * kPbwdWarps;
 
+// Three blocks per SM: at most 168 registers a thread, of which the SH
+// coefficients and their gradients take 96 at degree 3.
 template <int DEG>
 __global__ void __launch_bounds__(kColorThreads, 3) project_bwd_color_kernel(ProjectBwdArgs a, ViewTable vt)
 {
