@@ -276,7 +276,11 @@ gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t n, const gs
  * set, grads are written (=) instead of accumulated.  grads = NULL selects the
  * pose-only mode of tracking (Sec. 3.3: the pose is refined, the map is not):
  * only d_twist is written.  Entries of grad2d it reads are set back to zero,
- * so a buffer that starts zeroed is zero again when the call completes. */
+ * so a buffer that starts zeroed is zero again when the call completes.
+ * grad2d and params->quats must be 16-byte aligned (GS_ERR_INVALID_ARG
+ * otherwise); params->sh and grads->sh need only 4-byte alignment (when both
+ * are 16-byte aligned the SH rows are copied 16 bytes at a time; the results
+ * are the same bit for bit). */
 gs_status_t gs_project_bwd(const gs_params_t *params, const gs_view_t *views, const float *viewmats,
                            int32_t n_views, const gs_options_t *opt, const gs_projected_t *proj,
                            float *grad2d, gs_param_grads_t *grads, float *d_twist, void *stream);
