@@ -124,6 +124,50 @@ const char *gs_version(void);
 /* Text for a status code. */
 const char *gs_status_string(gs_status_t s);
 
+/* Host read of an asynchronous error word (the status of gs_bins_t, or of
+ * any call that takes one): copies *status_dev (device uint32) to
+ * *status_host after the work already enqueued on stream, and waits for it.
+ * This is the one call of the library that synchronises.  Bit
+ * 1 << GS_ERR_CAPACITY: a pair capacity was exceeded; 1 << GS_ERR_TIMEOUT: a
+ * bounded wait expired.  GS_ERR_INVALID_ARG for null pointers, GS_ERR_CUDA if
+ * the copy fails. */
+gs_status_t gs_get_device_status(const uint32_t *status_dev, uint32_t *status_host, void *stream);
+
+/* Workspace bytes of one operation in one place (each also has its own size
+ * call): GS_OP_BIN_SORT (n_views * n records, pair_capacity),
+ * GS_OP_GRAD2D (the 2D gradient buffer of n Gaussians in n_views views),
+ * GS_OP_SSIM (n_pixels), GS_OP_SELECT (n items: densification and pruning),
+ * GS_OP_SPATIAL_ORDER (n Gaussians), GS_OP_CHECK_LOOKBACK.  0 for an unknown
+ * op or negative sizes. */
+enum {
+    GS_OP_BIN_SORT = 0,
+    GS_OP_GRAD2D = 1,
+    GS_OP_SSIM = 2,
+    GS_OP_SELECT = 3,
+    GS_OP_SPATIAL_ORDER = 4,
+    GS_OP_CHECK_LOOKBACK = 5
+};
+size_t gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t pair_capacity, int64_t n_pixels);
+
+/* Check of the asynchronous timeout path of the radix passes (the paper has
+ * no counterpart; the bounded waits of the onesweep look-back are this
+ * library's design).  Enqueues one onesweep counting pass over 8,192
+ * pseudo-random uint32 keys (key i = i * 2654435761 mod 2^32, value i) in
+ * two 4,096-key tiles, sorted stably by their low byte.  With
+ * withhold_first_tile = 0 the pass runs normally: the sorted keys and values
+ * are left at byte offsets 0 and 32,768 of the workspace and *status is not
+ * touched.  With withhold_first_tile != 0 the pass starts its tile counter at
+ * 1, so tile 0 is never published: tile 1's look-back gives up after
+ * spin_limit waits of about 32 ns, ORs 1 << GS_ERR_TIMEOUT into *status
+ * (device uint32) and the kernel returns; its outputs are then meaningless
+ * but every write stays inside the workspace.  spin_limit 0 takes the
+ * library's default (2^22).  workspace: device, 256-byte aligned,
+ * >= gs_check_lookback_timeout_workspace_size() bytes.  GS_ERR_INVALID_ARG
+ * for a null or short workspace or a null status. */
+size_t gs_check_lookback_timeout_workspace_size(void);
+gs_status_t gs_check_lookback_timeout(uint32_t spin_limit, int32_t withhold_first_tile, uint32_t *status,
+                                      void *workspace, size_t workspace_bytes, void *stream);
+
 /* Total tiles and pixels over the views (host helper). */
 gs_status_t gs_layout(const gs_view_t *views /* host */, int32_t n_views, int64_t *n_tiles_total,
                       int64_t *n_pixels_total);
@@ -166,11 +210,12 @@ gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const gs_view_t *
  * CUDA graph capture, fixed-rate tracking loops that cannot take the device
  * synchronisation an allocation may cause, or host frameworks that own all
  * device memory and pass a plugin only its inputs and outputs).  Same inputs,
- * outputs and results as gs_bin_sort, but the scratch workspace is an 80 MiB
- * static device array inside the library, held on every GPU that loads it
- * until the process exits.  Limits: n_views * n <= 4,194,304 records and
- * bins->capacity <= 1,048,576 pairs; larger calls return GS_ERR_CAPACITY and
- * enqueue nothing.  The first call on a device looks up
+ * outputs and results as gs_bin_sort, but the scratch workspace is a
+ * static device array inside the library (about 65 MiB: exactly gs_bin_sort's
+ * workspace at both limits), held on every GPU that loads it until the
+ * process exits.  Limits: n_views * n <= 2,097,152 records and
+ * bins->capacity <= 2,097,152 pairs; every call within them fits, larger
+ * calls return GS_ERR_CAPACITY and enqueue nothing.  The first call on a device looks up
  * the array's address (cudaGetSymbolAddress) and should come before any
  * stream capture.  All
  * calls share the array and it keeps the last call's contents (what must

@@ -19,7 +19,7 @@ from . import _lib
 from ._lib import (GS_MAX_ADAM_GROUPS, GS_MAX_VIEWS, GS_TILE, GsAdamGroup, GsBins, GsError, GsImage, GsOptions,
                    GsParamGrads, GsParams, GsProjected, GsView, check)
 
-__all__ = ["gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd", "gs_render_fwd_l1", "gs_render_stats", "gs_set_render_variants",
+__all__ = ["gs_get_device_status", "gs_workspace_size", "gs_check_lookback_timeout", "gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd", "gs_render_fwd_l1", "gs_render_stats", "gs_set_render_variants",
            "gs_get_render_variants", "gs_loss_l1", "gs_loss_ssim", "gs_render_bwd", "gs_render_bwd_splats",
            "gs_project_bwd", "gs_decode_keyframes", "gs_reproj_loss_grad", "gs_adam_step", "gs_pose_update", "gs_densify",
            "gs_prune_select", "gs_compact_rows", "gs_spatial_order_workspace_size", "gs_spatial_order",
@@ -78,6 +78,25 @@ def _gref(grads):
 # one wrapper per C entry point
 # --------------------------------------------------------------------------
 
+def gs_get_device_status(status, stream=None):
+    """Host value of a device uint32 error word after the stream's work (synchronises)."""
+    out = ctypes.c_uint32()
+    check(lib().gs_get_device_status(_ptr(status), ctypes.byref(out), _stream(stream)), "gs_get_device_status")
+    return int(out.value)
+
+
+def gs_workspace_size(op, n=0, n_views=0, pair_capacity=0, n_pixels=0):
+    return int(lib().gs_workspace_size(int(op), int(n), int(n_views), int(pair_capacity), int(n_pixels)))
+
+
+def gs_check_lookback_timeout(spin_limit, withhold_first_tile, status, workspace, stream=None):
+    """One two-tile onesweep pass; with withhold_first_tile its look-back wait
+    must expire and set the timeout bit of status (device uint32)."""
+    check(lib().gs_check_lookback_timeout(int(spin_limit), int(bool(withhold_first_tile)), _ptr(status),
+                                          _ptr(workspace), workspace.numel(), _stream(stream)),
+          "gs_check_lookback_timeout")
+
+
 def gs_project(params, views, viewmats, proj, near_z=0.2, blur=0.3, stream=None):
     opt = GsOptions(near_z, blur)
     pj = _proj(proj)
@@ -111,9 +130,9 @@ def gs_bin_sort(proj, n, views, bins, workspace, stream=None):
 def gs_bin_sort_noalloc(proj, n, views, bins, stream=None):
     """gs_bin_sort without a caller workspace: for callers that cannot
     allocate device memory (mid graph capture, fixed-rate loops, hosts that own
-    all device memory).  Uses a fixed 80 MiB scratch array inside the library;
-    at most 4,194,304 records and a pair capacity of 1,048,576.  Calls must not
-    overlap on the GPU."""
+    all device memory).  Uses a fixed scratch array inside the library (about
+    65 MiB); at most 2,097,152 records (views x Gaussians) and a pair capacity
+    of at most 2,097,152.  Calls must not overlap on the GPU."""
     check(lib().gs_bin_sort_noalloc(ctypes.byref(_proj(proj)), n, views, len(views), ctypes.byref(_bins(bins)),
                                     _stream(stream)), "gs_bin_sort_noalloc")
 
@@ -286,8 +305,9 @@ def _layout(size):
 class Rasterizer:
     """Device buffers and launches for n Gaussians rendered into a fixed set of
     views (sizes and intrinsics fixed; poses are device tensors and may change).
-    One forward/backward pair in flight at a time: outputs live in the
-    rasterizer's buffers until the next forward."""
+    ``forward`` leaves its outputs in the rasterizer's buffers until the next
+    forward; ``generation`` counts the forwards run, so a caller holding an
+    older result can tell that the buffers no longer hold it."""
 
     def __init__(self, n, sh_degree, intr, size, pair_capacity=None, device="cuda", near_z=0.2, blur=0.3):
         self.n, self.sh_degree = int(n), int(sh_degree)
@@ -318,12 +338,14 @@ class Rasterizer:
                         n_contrib=torch.empty(P, dtype=i32, device=d))
         self.grad2d = torch.zeros(R * 12, dtype=f32, device=d)
         self.work_counter = torch.zeros(1, dtype=i32, device=d)
+        self.generation = 0
 
     def forward(self, params, viewmats, stream=None):
         """Project, bin and composite; results in self.img (device, async)."""
         gs_project(params, self.views, viewmats, self.proj, self.near_z, self.blur, stream)
         gs_bin_sort(self.proj, self.n, self.views, self.bins, self.workspace, stream)
         gs_render_fwd(self.proj, self.n, self.bins, self.views, self.img, self.work_counter, stream)
+        self.generation += 1
         return self.img
 
     def backward(self, params, viewmats, d_rgb, d_depth, d_alpha, grads, d_twist=None, stream=None,
@@ -344,35 +366,52 @@ class Rasterizer:
 
 
 class _RasterizeFn(torch.autograd.Function):
+    """Forward and backward of the compositing behind autograd.
+
+    The outputs are copies, so a later forward on the same rasterizer cannot
+    change tensors autograd still holds.  The backward needs this call's
+    projected records, tile lists, final transmittance and last indices; if
+    another forward has run on the rasterizer since (two renders in one joint
+    loss), it runs this call's forward again first.  The forward is
+    deterministic (fixed-order arithmetic, stable sorts), so the recomputed
+    state is the one this call's outputs came from, bit for bit."""
+
     @staticmethod
     def forward(ctx, rast, sh_degree, viewmats, twist, means, log_scales, quats, opacity_logit, sh):
         params = dict(means=means, log_scales=log_scales, quats=quats, opacity_logit=opacity_logit, sh=sh,
                       sh_degree=sh_degree)
         img = rast.forward(params, viewmats)
         ctx.rast = rast
+        ctx.generation = rast.generation
         ctx.sh_degree = sh_degree
         ctx.save_for_backward(viewmats, means, log_scales, quats, opacity_logit, sh)
         ctx.want_twist = twist is not None and twist.requires_grad
-        return img["rgb"], img["depth"], img["alpha"]
+        return img["rgb"].clone(), img["depth"].clone(), img["alpha"].clone()
 
     @staticmethod
     def backward(ctx, g_rgb, g_depth, g_alpha):
         viewmats, means, log_scales, quats, opacity_logit, sh = ctx.saved_tensors
         params = dict(means=means, log_scales=log_scales, quats=quats, opacity_logit=opacity_logit, sh=sh,
                       sh_degree=ctx.sh_degree)
+        rast = ctx.rast
+        if rast.generation != ctx.generation:
+            rast.forward(params, viewmats)
+            ctx.generation = rast.generation
         grads = dict(means=torch.empty_like(means), log_scales=torch.empty_like(log_scales),
                      quats=torch.empty_like(quats), opacity_logit=torch.empty_like(opacity_logit),
                      sh=torch.empty_like(sh))
         d_twist = torch.zeros(viewmats.shape[0], 6, device=means.device) if ctx.want_twist else None
         c = lambda t: None if t is None else t.contiguous()
-        ctx.rast.backward(params, viewmats, c(g_rgb), c(g_depth), c(g_alpha), grads, d_twist, overwrite_grads=True)
+        rast.backward(params, viewmats, c(g_rgb), c(g_depth), c(g_alpha), grads, d_twist, overwrite_grads=True)
         return (None, None, None, d_twist, grads["means"], grads["log_scales"], grads["quats"],
                 grads["opacity_logit"], grads["sh"])
 
 
 def rasterize(rast, params, viewmats, twist=None):
-    """Differentiable render: returns (rgb [P,3], depth [P], alpha [P]).
-    twist: optional [V,6] leaf standing for the left perturbation Exp(xi) E of
-    each pose at xi = 0 (its value is not read); its .grad receives dL/dxi."""
+    """Differentiable render: returns (rgb [P,3], depth [P], alpha [P]), new
+    tensors owned by the caller.  Several calls on one rasterizer may share a
+    graph before one backward.  twist: optional [V,6] leaf standing for the
+    left perturbation Exp(xi) E of each pose at xi = 0 (its value is not read);
+    its .grad receives dL/dxi."""
     return _RasterizeFn.apply(rast, int(params["sh_degree"]), viewmats, twist, params["means"],
                               params["log_scales"], params["quats"], params["opacity_logit"], params["sh"])

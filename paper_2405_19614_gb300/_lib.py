@@ -19,6 +19,7 @@ GS_MAX_ADAM_GROUPS = 8
 STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_CAPACITY", 4: "GS_ERR_TIMEOUT",
           5: "GS_ERR_UNSUPPORTED"}
 ERR_CAPACITY, ERR_TIMEOUT = 3, 4
+GS_OP_BIN_SORT, GS_OP_GRAD2D, GS_OP_SSIM, GS_OP_SELECT, GS_OP_SPATIAL_ORDER, GS_OP_CHECK_LOOKBACK = range(6)
 
 
 class GsView(ctypes.Structure):
@@ -96,6 +97,10 @@ SIGNATURES = {
     "gs_spatial_order_workspace_size": ([c_i64], c_sz),
     "gs_spatial_order": ([c_p, c_i64, c_p, c_p, c_sz, c_p, c_p], c_i32),
     "gs_select_views": ([c_p, c_p, c_i32, c_f, c_i32, c_p], c_i32),
+    "gs_get_device_status": ([c_p, c_p, c_p], c_i32),
+    "gs_workspace_size": ([c_i32, c_i64, c_i32, c_i64, c_i64], c_sz),
+    "gs_check_lookback_timeout_workspace_size": ([], c_sz),
+    "gs_check_lookback_timeout": ([ctypes.c_uint32, c_i32, c_p, c_p, c_sz, c_p], c_i32),
 }
 
 _lib = None

@@ -19,18 +19,11 @@
 // pass needs a histogram kernel.  Emission is load-balanced: a block scans its
 // records' tile counts in shared memory and consecutive threads take
 // consecutive pairs, finding their record by binary search.
+#include "binning.cuh"
 #include "common.cuh"
 #include "sort.cuh"
 
 namespace gs {
-
-constexpr int kEmitThreads = 256;
-constexpr int kEmitItems = 8;
-constexpr int kEmitChunk = kEmitThreads * kEmitItems;  // records per block, compaction
-constexpr int kPairItems = 2;
-constexpr int kPairChunk = kEmitThreads * kPairItems;  // sorted records per block, pair emission
-constexpr int kDepthPasses = 4;
-constexpr int kMaxTilePasses = 4;
 
 __device__ __forceinline__ uint64_t block_exclusive_scan_u64(uint64_t x, uint64_t *tmp /* [8] */, uint64_t *total)
 {
@@ -359,37 +352,24 @@ struct BinWorkspace {
     size_t lb_bytes, small_bytes, bytes;
 };
 
-constexpr int kSmallWords = 1 + kDepthPasses + kMaxTilePasses + (kDepthPasses + kMaxTilePasses) * kRadix;
-
 static BinWorkspace carve(void *base, int64_t n_records, int64_t cap)
 {
-    BinWorkspace w;
-    const int64_t nb = (n_records + kPairChunk - 1) / kPairChunk + 1;  // the larger of the two block counts
+    const BinOffsets o = bin_offsets(n_records, cap);
     unsigned char *p = static_cast<unsigned char *>(base);
-    size_t off = 0;
-    w.block_sums = reinterpret_cast<uint64_t *>(p + off);
-    off += align256(sizeof(uint64_t) * (size_t)nb);
-    w.small = reinterpret_cast<uint32_t *>(p + off);
-    w.small_bytes = sizeof(uint32_t) * kSmallWords;
-    off += align256(w.small_bytes);
+    BinWorkspace w;
+    w.block_sums = reinterpret_cast<uint64_t *>(p + o.block_sums);
+    w.small = reinterpret_cast<uint32_t *>(p + o.small);
+    w.small_bytes = o.small_bytes;
     for (int i = 0; i < 2; i++) {
-        w.rz[i] = reinterpret_cast<uint32_t *>(p + off);
-        off += align256(sizeof(uint32_t) * (size_t)n_records);
-        w.rid[i] = reinterpret_cast<uint32_t *>(p + off);
-        off += align256(sizeof(uint32_t) * (size_t)n_records);
+        w.rz[i] = reinterpret_cast<uint32_t *>(p + o.rz[i]);
+        w.rid[i] = reinterpret_cast<uint32_t *>(p + o.rid[i]);
+        w.lb[i] = reinterpret_cast<uint32_t *>(p + o.lb[i]);
     }
-    w.recs = reinterpret_cast<uint2 *>(p + off);
-    off += align256(sizeof(uint2) * (size_t)n_records);
-    w.lb_bytes = onesweep_lookback_bytes(n_records > cap ? n_records : cap);
-    for (int i = 0; i < 2; i++) {
-        w.lb[i] = reinterpret_cast<uint32_t *>(p + off);
-        off += w.lb_bytes;
-    }
-    w.pk = reinterpret_cast<uint32_t *>(p + off);
-    off += align256(sizeof(uint32_t) * (size_t)cap);
-    w.pv = reinterpret_cast<uint32_t *>(p + off);
-    off += align256(sizeof(uint32_t) * (size_t)cap);
-    w.bytes = off;
+    w.recs = reinterpret_cast<uint2 *>(p + o.recs);
+    w.lb_bytes = o.lb_bytes;
+    w.pk = reinterpret_cast<uint32_t *>(p + o.pk);
+    w.pv = reinterpret_cast<uint32_t *>(p + o.pv);
+    w.bytes = o.bytes;
     return w;
 }
 
@@ -401,7 +381,7 @@ extern "C" size_t gs_bin_sort_workspace_size(int64_t n_records, int64_t pair_cap
 {
     (void)n_tiles_total;
     if (n_records < 0 || pair_capacity < 1) return 0;
-    return carve(nullptr, n_records > 0 ? n_records : 1, pair_capacity).bytes;
+    return bin_offsets(n_records > 0 ? n_records : 1, pair_capacity).bytes;
 }
 
 extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const gs_view_t *views, int32_t n_views,

@@ -13,8 +13,11 @@
 // process exits.
 //
 // Limits: at most kNoAllocMaxRecords (view, Gaussian) records (n_views * n)
-// and a pair capacity of at most kNoAllocMaxPairs; larger calls are rejected
-// with GS_ERR_CAPACITY before anything is enqueued.
+// and a pair capacity of at most kNoAllocMaxPairs (2,097,152 each); larger
+// calls are rejected with GS_ERR_CAPACITY before anything is enqueued.  The
+// array is exactly the workspace gs_bin_sort needs at both limits (about
+// 65 MiB), computed at compile time from the same layout, so every call
+// within the limits fits.
 //
 // Sharing: every call uses the same array and it keeps the previous call's
 // contents.  Everything the sort needs at zero is cleared inside the call, so
@@ -28,13 +31,18 @@
 // stream capture begins, so the capture only records kernel launches.
 #include <mutex>
 
+#include "binning.cuh"
 #include "common.cuh"
 
 namespace gs {
 
-constexpr int64_t kNoAllocMaxRecords = int64_t(1) << 22;  // 4,194,304 records
-constexpr int64_t kNoAllocMaxPairs = int64_t(1) << 20;    // 1,048,576 pairs
-constexpr size_t kNoAllocScratchBytes = size_t(80) << 20; // 80 MiB >= workspace at the limits (~75 MiB)
+constexpr int64_t kNoAllocMaxRecords = int64_t(1) << 21;  // 2,097,152 records
+constexpr int64_t kNoAllocMaxPairs = int64_t(1) << 21;    // 2,097,152 pairs
+// the workspace layout is monotone in both sizes, so its size at the limits
+// bounds every call within them
+constexpr size_t kNoAllocScratchBytes = bin_offsets(kNoAllocMaxRecords, kNoAllocMaxPairs).bytes;
+static_assert(kNoAllocScratchBytes <= (size_t(66) << 20), "the fixed scratch array stays about 65 MiB");
+static_assert(kNoAllocScratchBytes % 256 == 0, "whole 256-byte regions");
 
 static __device__ __align__(256) unsigned char g_bin_scratch[kNoAllocScratchBytes];
 

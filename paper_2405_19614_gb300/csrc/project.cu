@@ -366,7 +366,30 @@ extern "C" gs_status_t gs_layout(const gs_view_t *views, int32_t n_views, int64_
     return GS_OK;
 }
 
-extern "C" const char *gs_version(void) { return "gs-sm103a 0.1"; }
+extern "C" const char *gs_version(void) { return "gs-sm103a 0.2"; }
+
+extern "C" gs_status_t gs_get_device_status(const uint32_t *status_dev, uint32_t *status_host, void *stream)
+{
+    if (!status_dev || !status_host) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    if (cudaMemcpyAsync(status_host, status_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return GS_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+extern "C" size_t gs_workspace_size(int32_t op, int64_t n, int32_t n_views, int64_t pair_capacity, int64_t n_pixels)
+{
+    if (n < 0 || n_views < 0 || pair_capacity < 0 || n_pixels < 0) return 0;
+    switch (op) {
+    case GS_OP_BIN_SORT: return gs_bin_sort_workspace_size(n * n_views, pair_capacity, 0);
+    case GS_OP_GRAD2D: return gs_grad2d_size(n, n_views);
+    case GS_OP_SSIM: return gs_ssim_workspace_size(n_pixels);
+    case GS_OP_SELECT: return gs_select_workspace_size(n);
+    case GS_OP_SPATIAL_ORDER: return gs_spatial_order_workspace_size(n);
+    case GS_OP_CHECK_LOOKBACK: return gs_check_lookback_timeout_workspace_size();
+    default: return 0;
+    }
+}
 
 extern "C" const char *gs_status_string(gs_status_t s)
 {

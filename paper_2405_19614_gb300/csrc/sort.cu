@@ -16,7 +16,7 @@ constexpr int kSortItems = kSortTileKeys / kSortThreads;  // 16
 constexpr uint32_t kLbAgg = 1u << 30;   // tile aggregate published
 constexpr uint32_t kLbInc = 2u << 30;   // inclusive prefix published
 constexpr uint32_t kLbMask = (1u << 30) - 1;
-constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kSpinLimit = 1u << 22;  // spins (32 ns sleeps) before a look-back wait gives up
 #ifndef GS_SORT_LOOKBACK
 #define GS_SORT_LOOKBACK 4
 #endif
@@ -90,7 +90,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) onesweep_kernel(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *n_p, uint32_t cap, const uint32_t *__restrict__ hist,
-    uint32_t *lb, uint32_t *lb_next, uint32_t *block_counter, int shift, SortExpand ex, uint32_t *status)
+    uint32_t *lb, uint32_t *lb_next, uint32_t *block_counter, int shift, SortExpand ex, uint32_t *status,
+    uint32_t spin_limit)
 {
     __shared__ SortSmem S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) onesweep_ker
                 j -= used;
                 if (j < 0) done = true;
                 if (!done && used < kLookback) {  // entry j not published yet
-                    if (++spins > kSpinLimit) {
+                    if (++spins > spin_limit) {
                         raise_status(status, GS_ERR_TIMEOUT);
                         break;
                     }
@@ -240,16 +241,11 @@ __global__ void __launch_bounds__(kSortThreads, GS_SORT_MIN_BLOCKS) onesweep_ker
     }
 }
 
-size_t onesweep_lookback_bytes(int64_t cap)
-{
-    const int64_t tiles = (cap + kSortTileKeys - 1) / kSortTileKeys + 1;
-    return align256(sizeof(uint32_t) * (size_t)tiles * kRadix);
-}
-
 template <int MODE>
 static void launch_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                         const uint32_t *n_dev, int64_t cap, const uint32_t *hist, uint32_t *lb, uint32_t *lb_next,
-                        uint32_t *block_counter, int shift, const SortExpand &ex, uint32_t *status, cudaStream_t s)
+                        uint32_t *block_counter, int shift, const SortExpand &ex, uint32_t *status, cudaStream_t s,
+                        uint32_t spin_limit = kSpinLimit)
 {
     static int per_sm = 0;  // resident blocks per SM (the same on every GB300)
     if (!per_sm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel<MODE>, kSortThreads, 0);
@@ -257,7 +253,7 @@ static void launch_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout
     const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
     const unsigned grid = (unsigned)(tiles < slots ? tiles : slots);
     onesweep_kernel<MODE><<<grid, kSortThreads, 0, s>>>(kin, vin, kout, vout, n_dev, (uint32_t)cap, hist, lb,
-                                                         lb_next, block_counter, shift, ex, status);
+                                                         lb_next, block_counter, shift, ex, status, spin_limit);
 }
 
 gs_status_t onesweep_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
@@ -286,4 +282,57 @@ gs_status_t onesweep_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *ko
     return launch_status();
 }
 
+// Check of the asynchronous timeout path: two 4096-key tiles of pseudo-random
+// keys sorted by their low byte.  The fill kernel writes the keys, values,
+// digit histogram and key count, and starts the tile counter at 1 when tile 0
+// is to be withheld, so that no block ever publishes tile 0.
+constexpr int kCheckKeys = 2 * kSortTileKeys;
+struct CheckLayout {
+    static constexpr size_t kout = 0, vout = 4 * kCheckKeys, kin = 8 * kCheckKeys, vin = 12 * kCheckKeys,
+                            hist = 16 * kCheckKeys, counter = hist + 4 * kRadix, n = counter + 4,
+                            lb = align256(n + 4), bytes = lb + onesweep_lookback_bytes(kCheckKeys);
+};
+
+__global__ void check_fill_kernel(unsigned char *ws, int withhold_first_tile)
+{
+    uint32_t *kin = reinterpret_cast<uint32_t *>(ws + CheckLayout::kin);
+    uint32_t *vin = reinterpret_cast<uint32_t *>(ws + CheckLayout::vin);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(ws + CheckLayout::hist);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kCheckKeys) return;
+    const uint32_t k = (uint32_t)i * 2654435761u;  // multiplicative hash of the index
+    kin[i] = k;
+    vin[i] = (uint32_t)i;
+    atomicAdd(&hist[k & 0xffu], 1u);
+    if (i == 0) {
+        *reinterpret_cast<uint32_t *>(ws + CheckLayout::counter) = withhold_first_tile ? 1u : 0u;
+        *reinterpret_cast<uint32_t *>(ws + CheckLayout::n) = (uint32_t)kCheckKeys;
+    }
+}
+
 }  // namespace gs
+
+using namespace gs;
+
+extern "C" size_t gs_check_lookback_timeout_workspace_size(void) { return CheckLayout::bytes; }
+
+extern "C" gs_status_t gs_check_lookback_timeout(uint32_t spin_limit, int32_t withhold_first_tile, uint32_t *status,
+                                                 void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!status || !workspace || workspace_bytes < CheckLayout::bytes ||
+        (reinterpret_cast<uintptr_t>(workspace) & 255))
+        return GS_ERR_INVALID_ARG;
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    cudaStream_t s = as_stream(stream);
+    // histogram, counters and look-back flags start at zero
+    if (cudaMemsetAsync(ws + CheckLayout::hist, 0, CheckLayout::bytes - CheckLayout::hist, s) != cudaSuccess)
+        return GS_ERR_CUDA;
+    check_fill_kernel<<<kCheckKeys / 256, 256, 0, s>>>(ws, withhold_first_tile != 0);
+    const SortExpand none = {};
+    auto u32 = [&](size_t off) { return reinterpret_cast<uint32_t *>(ws + off); };
+    launch_pass<kSortPlain>(u32(CheckLayout::kin), u32(CheckLayout::vin), u32(CheckLayout::kout),
+                            u32(CheckLayout::vout), u32(CheckLayout::n), kCheckKeys, u32(CheckLayout::hist),
+                            u32(CheckLayout::lb), nullptr, u32(CheckLayout::counter), 0, none, status, s,
+                            spin_limit ? spin_limit : kSpinLimit);
+    return launch_status();
+}

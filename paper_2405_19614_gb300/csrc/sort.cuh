@@ -8,10 +8,14 @@ namespace gs {
 constexpr int kSortTileKeys = 4096;  // keys ranked per block of a pass
 constexpr int kRadix = 256;
 
-inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-// Bytes of one look-back region for passes over up to cap keys.
-size_t onesweep_lookback_bytes(int64_t cap);
+// Bytes of one look-back region for passes over up to cap keys: one 256-digit
+// row of flags per block of kSortTileKeys keys, plus one.
+constexpr size_t onesweep_lookback_bytes(int64_t cap)
+{
+    return align256(sizeof(uint32_t) * (size_t)((cap + kSortTileKeys - 1) / kSortTileKeys + 1) * kRadix);
+}
 
 // Output modes of a pass: separate key and value arrays; (key, value) pairs
 // interleaved in kout as uint2; or expanded through SortExpand.

@@ -13,31 +13,9 @@ import pytest
 
 import oracle
 import scenes
+from helpers import grad_cams as _cams, grad_scene as _tiny_scene
 
 H_REL = 1e-6
-
-
-def _tiny_scene(deg, seed, edge=False):
-    sc = scenes.cube_scene(40, seed=seed, sh_degree=deg, centre=(0.1, -0.05, 3.0), half=0.8,
-                           log_scale=(-2.8, 0.3))
-    if edge:
-        # near-opaque Gaussians (alpha clamp at 0.99 active near their centres) and
-        # large ones beyond 1.3x the half field of view (tangent clamp active)
-        sc["opacity_logit"][:6] = 6.0
-        sc["means"][6:10] = [[3.0, 0.2, 3.0], [-3.1, -0.3, 3.0], [0.3, 2.4, 3.0], [-0.2, -2.5, 3.1]]
-        sc["log_scales"][6:10] = -0.9
-    # keep colours inside (0, 1) so that no channel sits near the clamp at 0
-    rng = np.random.default_rng(seed + 7)
-    sc["sh"][:, 0, :] = (rng.uniform(0.3, 0.7, (40, 3)) - 0.5) / scenes.SH_C0
-    sc["sh"][:, 1:, :] *= 0.5
-    return {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in sc.items()}
-
-
-def _cams(oblique):
-    if oblique:
-        vm = scenes.look_at((0.25, -0.2, -0.3), (0.05, 0.1, 3.0))
-        return scenes.pinhole(64, 48, 60.0, viewmats=vm[None])
-    return scenes.pinhole(64, 48, 60.0)
 
 
 def _functional(img, w):

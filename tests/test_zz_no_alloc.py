@@ -5,7 +5,9 @@ fixed-rate tracking loop that cannot take an allocation's synchronisation).
 gs_bin_sort_noalloc must produce exactly what gs_bin_sort produces with a
 caller-owned workspace (keys, values and ranges are integers: bit-exact), on two
 calls in a row with different inputs (its static scratch keeps the previous
-call's contents), and must refuse sizes beyond its fixed limits."""
+call's contents), must accept a call exactly at both of its limits
+(2,097,152 records and 2,097,152 pairs of capacity) and must refuse a call one
+past either."""
 import numpy as np
 import pytest
 import torch
@@ -28,9 +30,13 @@ def _bins_like(rast):
     return {k: torch.zeros_like(v) for k, v in b.items()}
 
 
-def _compare(scene, cams):
+MAX_RECORDS = 1 << 21
+MAX_PAIRS = 1 << 21
+
+
+def _compare(scene, cams, capacity=1 << 18):
     rast = gs.Rasterizer(scene["means"].shape[0], scene["sh_degree"], cams["intr"], cams["size"],
-                         pair_capacity=1 << 18)
+                         pair_capacity=capacity)
     p = params_on_device(scene)
     vm = viewmats_on_device(cams)
     gs.gs_project(p, rast.views, vm, rast.proj)
@@ -55,11 +61,19 @@ def test_noalloc_matches_workspace_path_twice_in_a_row():
     _compare(sc, cams)
 
 
+def test_noalloc_exactly_at_both_limits():
+    # every (view, Gaussian) record counts toward the limit, drawn or not:
+    # all but 20,000 Gaussians sit behind the camera, so the pairs stay few
+    sc = scenes.cube_scene(MAX_RECORDS, seed=77, sh_degree=0, log_scale=(-3.5, 0.3))
+    sc["means"][20000:, 2] = -5.0
+    _compare(sc, scenes.pinhole(320, 240, 300.0), capacity=MAX_PAIRS)
+
+
 def test_noalloc_rejects_sizes_beyond_its_limits():
     c = scenes.config(1)
     cams = c["cams"]
     views = gs.make_views(cams["intr"], cams["size"])
-    big = 5_000_000  # records beyond the 4,194,304 limit; nothing is enqueued
+    big = MAX_RECORDS + 1  # one record past the limit; nothing is enqueued
     proj = dict(rec=torch.zeros(16, device="cuda"), rect=torch.zeros(4, 2, dtype=torch.int32, device="cuda"),
                 radii=torch.zeros(4, dtype=torch.int32, device="cuda"),
                 tiles_touched=torch.zeros(4, dtype=torch.int32, device="cuda"))
@@ -70,6 +84,6 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
                 status=torch.zeros(1, dtype=torch.int32, device="cuda"))
     with pytest.raises(gs.GsError, match="CAPACITY"):
         gs.gs_bin_sort_noalloc(proj, big, views, bins)
-    bins["keys"] = torch.zeros((1 << 20) + 1, dtype=torch.int64, device="cuda")
+    bins["keys"] = torch.zeros(MAX_PAIRS + 1, dtype=torch.int64, device="cuda")
     with pytest.raises(gs.GsError, match="CAPACITY"):
         gs.gs_bin_sort_noalloc(proj, 4, views, bins)
