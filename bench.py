@@ -258,34 +258,41 @@ def work_counts(step):
 TRAFFIC_SOURCES = {"render_bwd": ("render_bwd.cu", "render.cuh", "common.cuh")}
 
 
-def kernel_traffic(stage, workload, rast):
-    """DRAM bytes per launch of a stage's kernel from the committed ncu
-    summary (profiles/traffic_<workload>.md), or None when there is none for
-    this kernel, variant and workload, or when the kernel's sources have
-    changed since the counters were taken."""
+def traffic_sources_sha256(stage, root=None):
+    """SHA-256 of the sources of a stage's kernel (None for a stage without a capture)."""
     import hashlib
-    import re
-
-    import paper_2405_19614_gb300 as gs
     files = TRAFFIC_SOURCES.get(stage)
     if files is None:
         return None
-    try:
-        text = open(os.path.join(ROOT, "profiles", f"traffic_{workload}.md")).read()
-    except OSError:
-        return None
-    m = re.search(rf"traffic {stage} variant=(\d+) workload={re.escape(workload)} bytes_per_launch=(\d+) "
-                  r"sources_sha256=([0-9a-f]+)", text)
-    if m is None:
-        return None
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, "paper_2405_19614_gb300", "csrc", f), "rb") as fh:
+        with open(os.path.join(root or ROOT, "paper_2405_19614_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    _, bwd_variant, _, _ = gs.gs_get_render_variants()
-    if h.hexdigest() != m.group(3) or int(m.group(1)) != bwd_variant:
+    return h.hexdigest()
+
+
+def kernel_traffic(stage, workload, rast):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu
+    counters (profiles/traffic.json: one record per stage with the workload,
+    kernel variant, bytes per launch and the SHA-256 of the kernel's sources
+    when they were taken), or None when there is none for this kernel,
+    variant and workload, or when the kernel's sources have changed since."""
+    import json
+
+    import paper_2405_19614_gb300 as gs
+    if stage not in TRAFFIC_SOURCES:
         return None
-    return int(m.group(2))
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh).get(stage)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("workload") != workload:
+        return None
+    _, bwd_variant, _, _ = gs.gs_get_render_variants()
+    if traffic_sources_sha256(stage) != rec.get("sources_sha256") or int(rec.get("variant", -1)) != bwd_variant:
+        return None
+    return int(rec["bytes_per_launch"])
 
 
 def stage_work(w):

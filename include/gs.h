@@ -77,12 +77,19 @@ typedef struct {
 } gs_options_t;
 
 /* Output of gs_project, one entry per (view, Gaussian) at [v * n + i]:
- *   rec [., 12] floats: (u, v, z, opacity), (conicA, conicB, conicC, du),
+ *   rec [., 12] floats: (u, v, z, log2 o), (A', B', C', du),
  *                       (red, green, blue, dv); u, v, z are the FP32 values of
  *                       the binning contract and du, dv the remainders
  *                       u* - u, v* - v of the 2D mean computed in double-FP32
  *                       arithmetic, so the compositing sees the mean to
- *                       ~1e-7 px; 16-byte aligned;
+ *                       ~1e-7 px; log2 o is the opacity's base-2 logarithm
+ *                       and (A', B', C') = -log2(e) (A/2, B, C/2) the conic
+ *                       (A, B, C) = (c, -b, a) / det of the 2D covariance
+ *                       (a, b, c) in base 2, so that log2(o exp(power)) =
+ *                       log2 o + A' dx^2 + B' dx dy + C' dy^2.  u, v, du, dv,
+ *                       log2 o and A', B', C' follow one fixed sequence of
+ *                       correctly rounded FP32 operations (the compositing's
+ *                       alpha decisions are taken on them); 16-byte aligned;
  *   rect [., 2] uint32: x0 | y0 << 16 and x1 | y1 << 16, the inclusive tile
  *                       rectangle;
  *   radii [.]   int32 support radius in pixels, 0 = not drawn in that view;

@@ -37,6 +37,13 @@ ALPHA_MIN = 1.0 / 255.0
 ALPHA_MAX = 0.99
 T_MIN = 1e-4
 FLAG_ALPHA_MIN, FLAG_T_MIN, FLAG_ALPHA_MAX = 1, 2, 4
+# the FP32 cuts of the decisions on l2 = log2(raw alpha): log2(1/255) and
+# log2(0.99), each rounded to the nearest float32
+L2_ALPHA_MIN = float(np.float32(-7.994353436858858))
+L2_ALPHA_MAX = float(np.float32(-0.014499569695115089))
+# relative error bound the transmittance band assumes for the kernel's 2^x
+# (two units in the last place; measured over every FP32 input in [-8, 0): 2^-22.73)
+EX2_REL = 2.0 ** -22
 
 
 def build(force: bool = False) -> str:
@@ -71,12 +78,16 @@ def _L():
         i32, i64, f32, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
         _lib.orc_geom_expf.argtypes = [f32]
         _lib.orc_geom_expf.restype = f32
+        _lib.orc_geom_log2f.argtypes = [f32]
+        _lib.orc_geom_log2f.restype = f32
+        _lib.orc_blend_records.argtypes = [i32, P, i64, P, P, P, P, f32, f32, i32, i32, P]
+        _lib.orc_blend_l2_many.argtypes = [i64, P, P, P, P]
         _lib.orc_project_geom.argtypes = [i32, P, i64, P, P, P, f32, f32, i32, i32, P, P, P, P]
         _lib.orc_bin.argtypes = [i32, P, i64, i32, i32, P, P, P, i64, P, P, P]
         _lib.orc_sh_eval.argtypes = [P, i64, i32, P]
         _lib.orc_project64.argtypes = [i32, P, i64, P, P, P, P, P, i32, f64, P, P]
-        _lib.orc_render.argtypes = [i32, P, i64, P, i32, i32, P, P, P, P, Margins, P, P, P, P, P, P]
-        _lib.orc_render_bwd.argtypes = [i32, P, i64, P, i32, i32, P, P, P, P, P, P, P, P]
+        _lib.orc_render.argtypes = [i32, P, i64, P, P, i32, i32, P, P, P, P, Margins, P, P, P, P, P, P, P]
+        _lib.orc_render_bwd.argtypes = [i32, P, i64, P, P, i32, i32, P, P, P, P, P, P, P, P]
         _lib.orc_project_bwd.argtypes = [i32, P, i64, P, P, P, P, P, i32, f64, P, P, P, P, P, P, P, P]
         _lib.orc_loss_l1.argtypes = [i64, P, P, P, P, P, f64, f64, i32, f64, P, P]
         _lib.orc_loss_l1.restype = f64
@@ -139,6 +150,35 @@ def geom_expf(x: float) -> float:
     return float(np.float32(_L().orc_geom_expf(float(np.float32(x)))))
 
 
+def geom_log2f(x: float) -> float:
+    return float(np.float32(_L().orc_geom_log2f(float(np.float32(x)))))
+
+
+DREC_COLS = ("u", "v", "du", "dv", "log2o", "A2", "B2", "C2")
+
+
+def blend_records(params, cams, near_z=0.2, blur=0.3, tile=(16, 16)):
+    """FP32 decision records [V*n, 8] (u, v, du, dv, log2 o, A', B', C') of
+    every drawn (view, Gaussian), zeros elsewhere."""
+    L = _L()
+    means, ls, q, ol = (_c(params[k], np.float64) for k in ("means", "log_scales", "quats", "opacity_logit"))
+    n = means.shape[0]
+    views = make_views(cams)
+    out = np.zeros((len(views) * n, 8), np.float32)
+    L.orc_blend_records(len(views), views, n, _p(means), _p(ls), _p(q), _p(ol), float(near_z), float(blur),
+                        tile[0], tile[1], _p(out))
+    return out
+
+
+def blend_l2(drec_rows, px, py):
+    """FP32 l2 = log2(raw alpha) of decision records [m, 8] at pixels (px, py)."""
+    d = _c(drec_rows, np.float32).reshape(-1, 8)
+    px, py = _c(px, np.int32).ravel(), _c(py, np.int32).ravel()
+    out = np.zeros(d.shape[0], np.float32)
+    _L().orc_blend_l2_many(d.shape[0], _p(d), _p(px), _p(py), _p(out))
+    return out
+
+
 def project_geom(params, cams, near_z=0.2, blur=0.3, tile=(16, 16)):
     """FP32 geometry (binning contract) for every (view, Gaussian)."""
     L = _L()
@@ -194,27 +234,35 @@ def project64(params, cams, geom, blur=0.3):
     return out
 
 
-def render(cams, proj, bins, n, tile=(16, 16), margin_alpha=2e-5, margin_T=2e-5):
-    """FP64 compositing of RGB, depth and alpha (border mask) for all views."""
+def render(cams, proj, drec, bins, n, tile=(16, 16), margin_alpha=0.0, margin_T=0.0):
+    """FP64 compositing of RGB, depth and alpha (border mask) for all views,
+    with the alpha decisions taken on the FP32 decision records drec.
+    flags marks pixels whose stop decision lies within the transmittance band
+    (FLAG_T_MIN); slack [P, 4] = (w, w * max colour, w * depth) of the entry at
+    that decision, w its blend weight, and the relative band of the final T.  margin_alpha > 0 additionally flags
+    FP64 alphas within that relative margin of a cut, and margin_T widens the
+    band (test knobs for finite differences)."""
     L = _L()
     views = make_views(cams)
     P = bins["n_pix"]
     out = dict(rgb=np.zeros((P, 3)), depth=np.zeros(P), alpha=np.zeros(P), final_T=np.zeros(P),
-               n_contrib=np.zeros(P, np.int32), flags=np.zeros(P, np.int32))
-    L.orc_render(len(views), views, n, _p(proj), tile[0], tile[1], _p(bins["tile_base"]),
-                 _p(bins["pix_base"]), _p(_c(bins["vals"], np.uint32)), _p(bins["ranges"]),
-                 Margins(margin_alpha, margin_T), _p(out["rgb"]), _p(out["depth"]),
-                 _p(out["alpha"]), _p(out["final_T"]), _p(out["n_contrib"]), _p(out["flags"]))
+               n_contrib=np.zeros(P, np.int32), flags=np.zeros(P, np.int32), slack=np.zeros((P, 4)))
+    L.orc_render(len(views), views, n, _p(proj), _p(_c(drec, np.float32)), tile[0], tile[1],
+                 _p(bins["tile_base"]), _p(bins["pix_base"]), _p(_c(bins["vals"], np.uint32)),
+                 _p(bins["ranges"]), Margins(margin_alpha, margin_T), _p(out["rgb"]), _p(out["depth"]),
+                 _p(out["alpha"]), _p(out["final_T"]), _p(out["n_contrib"]), _p(out["flags"]),
+                 _p(out["slack"]))
     return out
 
 
-def render_bwd(cams, proj, bins, n, dC, dD, dA, tile=(16, 16)):
+def render_bwd(cams, proj, drec, bins, n, dC, dD, dA, tile=(16, 16)):
     """Per-(view, Gaussian) 2D gradients [V*n, 10] (u, v, conicA, conicB, conicC,
     opacity, r, g, b, z) for upstream image gradients."""
     L = _L()
     views = make_views(cams)
     g2d = np.zeros((len(views) * n, 10), np.float64)
-    L.orc_render_bwd(len(views), views, n, _p(proj), tile[0], tile[1], _p(bins["tile_base"]),
+    L.orc_render_bwd(len(views), views, n, _p(proj), _p(_c(drec, np.float32)), tile[0], tile[1],
+                     _p(bins["tile_base"]),
                      _p(bins["pix_base"]), _p(_c(bins["vals"], np.uint32)), _p(bins["ranges"]),
                      _p(_c(dC, np.float64)), _p(_c(dD, np.float64)), _p(_c(dA, np.float64)),
                      _p(g2d))
@@ -296,15 +344,16 @@ def forward(params, cams, near_z=0.2, blur=0.3, tile=(16, 16), **margins):
     geom = project_geom(params, cams, near_z, blur, tile)
     bins = bin_tiles(cams, geom, tile)
     proj = project64(params, cams, geom, blur)
-    img = render(cams, proj, bins, geom["n"], tile, **margins)
-    return dict(geom=geom, bins=bins, proj=proj, img=img)
+    drec = blend_records(params, cams, near_z, blur, tile)
+    img = render(cams, proj, drec, bins, geom["n"], tile, **margins)
+    return dict(geom=geom, bins=bins, proj=proj, drec=drec, img=img)
 
 
 def backward(params, cams, fwd, dC, dD, dA=None, blur=0.3, tile=(16, 16)):
     n = fwd["geom"]["n"]
     if dA is None:
         dA = np.zeros_like(np.asarray(dD, np.float64))
-    g2d = render_bwd(cams, fwd["proj"], fwd["bins"], n, dC, dD, dA, tile)
+    g2d = render_bwd(cams, fwd["proj"], fwd["drec"], fwd["bins"], n, dC, dD, dA, tile)
     grads = project_bwd(params, cams, fwd["geom"], g2d, blur)
     grads["g2d"] = g2d
     return grads

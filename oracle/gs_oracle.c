@@ -24,9 +24,10 @@
  *   - Adam (the gradient-based optimiser; Sec. 3.4 leaves it unnamed).
  *   - The SE(3) exponential used for the pose twist.
  *
- * Precision: FP64 everywhere except the geometry that decides tile membership
- * and order, which follows the FP32 operation order written out in
- * orc_geom_one() (round to nearest, no contraction; build with
+ * Precision: FP64 everywhere except what decides tile membership and order
+ * (the FP32 operation order written out in orc_geom_one()) and the alpha skip
+ * and clamp decisions (the FP32 operation order of orc_blend_records() and
+ * orc_blend_l2()): round to nearest, no contraction (build with
  * -ffp-contract=off).  Single threaded on purpose.
  */
 #include <math.h>
@@ -79,6 +80,8 @@ typedef struct {
     int32_t radius;
     int32_t x0, y0, x1, y1; /* inclusive tile rectangle */
     float u, v, z;
+    float ca, cb, cc, det; /* 2D covariance (with the blur) and its determinant */
+    int footprint;         /* u, v, z, ca, cb, cc, det are set (touching a tile or not) */
 } orc_geom_t;
 
 /* Geometry of one Gaussian in one view, FP32.  Returns 1 if the Gaussian
@@ -89,6 +92,7 @@ static int orc_geom_one(const double md[3], const double lsd[3], const double qd
                         int th, orc_geom_t *g)
 {
     float m[3], ls[3], q[4], E[12];
+    g->footprint = 0;
     for (int i = 0; i < 3; i++) {
         m[i] = (float)md[i];
         ls[i] = (float)lsd[i];
@@ -166,6 +170,14 @@ static int orc_geom_one(const double md[3], const double lsd[3], const double qd
     float u = (Vfx * x) / z + Vcx;
     float v = (Vfy * y) / z + Vcy;
     if (!(fabsf(u) < 0x1p24f && fabsf(v) < 0x1p24f && rad < 0x1p24f)) return 0;
+    g->u = u;
+    g->v = v;
+    g->z = z;
+    g->ca = ca;
+    g->cb = cb;
+    g->cc = cc;
+    g->det = det;
+    g->footprint = 1;
 
     int ntx = (V->width + tw - 1) / tw, nty = (V->height + th - 1) / th;
     float fx0 = floorf((u - rad) / (float)tw), fx1 = floorf((u + rad) / (float)tw);
@@ -181,9 +193,6 @@ static int orc_geom_one(const double md[3], const double lsd[3], const double qd
     g->y0 = (int32_t)fy0;
     g->x1 = (int32_t)fx1;
     g->y1 = (int32_t)fy1;
-    g->u = u;
-    g->v = v;
-    g->z = z;
     return 1;
 }
 
@@ -220,6 +229,155 @@ void orc_project_geom(int32_t n_views, const orc_view_t *views, int64_t n,
                 tiles_touched[o] = 0;
             }
         }
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP32 alpha decisions                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* The compositing's two alpha decisions (skip an entry when alpha < 1/255,
+ * clamp alpha at 0.99) are taken, on both sides, on one FP32 value: the
+ * base-2 logarithm of the raw alpha o exp(-1/2 d^T conic d) of Eq. gauss,
+ *   l2 = log2 o + A' dx^2 + dy (B' dx + C' dy),
+ *   (A', B', C') = -log2(e) (A/2, B, C/2),  d = 2D mean - pixel centre,
+ * evaluated by the fixed sequence of correctly rounded FP32 operations below
+ * from a per-(view, Gaussian) record that is itself such a sequence on the
+ * FP32 geometry: the decisions are then reproducible bit for bit, and the
+ * FP64 image takes them from here, as it takes tile membership from the FP32
+ * geometry.  The values blended stay FP64. */
+
+/* log2 of y >= 1: y = m 2^e with m in (sqrt(1/2), sqrt(2)], log2 m =
+ * (2/ln 2) atanh(s) with s = (m - 1)/(m + 1), by the odd series
+ * s (C1 + s^2 (C3 + s^2 (C5 + s^2 (C7 + s^2 C9)))), C_k = 2/(k ln 2), in Horner
+ * form with fused multiply-adds (|s| <= 0.172: the next term is below 1e-9
+ * relative). */
+float orc_geom_log2f(float y)
+{
+    union { float f; uint32_t u; } b;
+    b.f = y;
+    int e = (int)((b.u >> 23) & 0xffu) - 127;
+    b.u = (b.u & 0x7fffffu) | 0x3f800000u;
+    float m = b.f;
+    if (m > 0x1.6a09e6p+0f) { /* sqrt(2) rounded to FP32 */
+        m = m * 0.5f;
+        e += 1;
+    }
+    float s = (m - 1.0f) / (m + 1.0f);
+    float s2 = s * s;
+    float p = 0x1.484b14p-2f;       /* 2/(9 ln 2) */
+    p = fmaf(p, s2, 0x1.a61762p-2f); /* 2/(7 ln 2) */
+    p = fmaf(p, s2, 0x1.2776c6p-1f); /* 2/(5 ln 2) */
+    p = fmaf(p, s2, 0x1.ec709ep-1f); /* 2/(3 ln 2) */
+    p = fmaf(p, s2, 0x1.715476p+1f); /* 2/ln 2 */
+    return (float)e + s * p;
+}
+
+/* Error-free transformations: a + b = s + e and a b = p + e exactly. */
+static void orc_two_sum(float a, float b, float *s, float *e)
+{
+    float ss = a + b;
+    float bb = ss - a;
+    *e = (a - (ss - bb)) + (b - bb);
+    *s = ss;
+}
+
+static void orc_two_prod(float a, float b, float *p, float *e)
+{
+    float pp = a * b;
+    *e = fmaf(a, b, -pp);
+    *p = pp;
+}
+
+/* r0 m0 + r1 m1 + r2 m2 + t as hi + lo; hi equals the geometry's coordinate. */
+static void orc_dot3_plus(const float *r, const float *m, float t, float *hi, float *lo)
+{
+    float s, l, p, e, es;
+    orc_two_prod(r[0], m[0], &s, &l);
+    orc_two_prod(r[1], m[1], &p, &e);
+    orc_two_sum(s, p, &s, &es);
+    l = l + (e + es);
+    orc_two_prod(r[2], m[2], &p, &e);
+    orc_two_sum(s, p, &s, &es);
+    l = l + (e + es);
+    orc_two_sum(s, t, &s, &es);
+    l = l + es;
+    *hi = s;
+    *lo = l;
+}
+
+/* (f x / z + c) - ref for x = xh + xl, z = zh + zl, in double-FP32. */
+static float orc_pixel_remainder(float f, float xh, float xl, float zh, float zl, float c, float ref)
+{
+    float q = xh / zh;
+    float r = fmaf(-q, zh, xh) + (xl - q * zl);
+    float ql = r / zh;
+    float m, me, s, se;
+    orc_two_prod(f, q, &m, &me);
+    float ml = me + f * ql;
+    orc_two_sum(m, c, &s, &se);
+    return (s - ref) + (se + ml);
+}
+
+#define ORC_NEG_HALF_LOG2E (-0x1.715476p-1f) /* -log2(e)/2 rounded to FP32 */
+#define ORC_LOG2E_F (0x1.715476p+0f)         /* log2(e) rounded to FP32 */
+#define ORC_L2_ALPHA_MIN (-0x1.ffa37cp+2f)   /* log2(1/255) rounded to FP32 */
+#define ORC_L2_ALPHA_MAX (-0x1.db1f34p-7f)   /* log2(0.99) rounded to FP32 */
+
+/* Decision records [n_views * n, 8] of every (view, Gaussian) with a 2D
+ * footprint (in front of the near plane, positive definite covariance; drawn
+ * or not): (u, v, du, dv, log2 o, A', B', C'), zeros elsewhere.  u, v are the
+ * geometry's; du, dv the remainders of the 2D mean in double-FP32 (camera
+ * point by compensated dot products, then f x / z + c); log2 o =
+ * -log2(1 + exp(-logit)) with the geometry's exp and the log2 above;
+ * A' = (-log2(e)/2 c) / det, B' = (log2(e) b) / det, C' = (-log2(e)/2 a) / det
+ * for the 2D covariance (a, b, c) and its determinant. */
+void orc_blend_records(int32_t n_views, const orc_view_t *views, int64_t n, const double *means,
+                       const double *log_scales, const double *quats, const double *opacity_logit,
+                       float near_z, float blur, int32_t tw, int32_t th, float *drec)
+{
+    for (int32_t v = 0; v < n_views; v++) {
+        const orc_view_t *V = &views[v];
+        float E[12];
+        for (int k = 0; k < 12; k++) E[k] = (float)V->viewmat[k];
+        for (int64_t i = 0; i < n; i++) {
+            float *r = drec + 8 * ((int64_t)v * n + i);
+            for (int k = 0; k < 8; k++) r[k] = 0.0f;
+            orc_geom_t g;
+            orc_geom_one(means + 3 * i, log_scales + 3 * i, quats + 4 * i, V, near_z, blur, tw, th, &g);
+            if (!g.footprint) continue;
+            float m[3] = {(float)means[3 * i], (float)means[3 * i + 1], (float)means[3 * i + 2]};
+            float xh, xl, yh, yl, zh, zl;
+            orc_dot3_plus(E + 0, m, E[3], &xh, &xl);
+            orc_dot3_plus(E + 4, m, E[7], &yh, &yl);
+            orc_dot3_plus(E + 8, m, E[11], &zh, &zl);
+            r[0] = g.u;
+            r[1] = g.v;
+            r[2] = orc_pixel_remainder((float)V->fx, xh, xl, zh, zl, (float)V->cx, g.u);
+            r[3] = orc_pixel_remainder((float)V->fy, yh, yl, zh, zl, (float)V->cy, g.v);
+            float l = (float)opacity_logit[i];
+            r[4] = -orc_geom_log2f(1.0f + orc_geom_expf(-l));
+            r[5] = (ORC_NEG_HALF_LOG2E * g.cc) / g.det;
+            r[6] = (ORC_LOG2E_F * g.cb) / g.det;
+            r[7] = (ORC_NEG_HALF_LOG2E * g.ca) / g.det;
+        }
+    }
+}
+
+/* l2 of a decision record at pixel (px, py), sampled at its centre. */
+static float orc_blend_l2(const float *r, int px, int py)
+{
+    float sx = (float)px + 0.5f, sy = (float)py + 0.5f;
+    float dx = (r[0] - sx) + r[2];
+    float base = fmaf(r[5] * dx, dx, r[4]);
+    float bdx = r[6] * dx;
+    float dy = (r[1] - sy) + r[3];
+    return fmaf(dy, fmaf(r[7], dy, bdx), base);
+}
+
+/* l2 for m (record, pixel) pairs, for the tests of this arithmetic. */
+void orc_blend_l2_many(int64_t m, const float *drec, const int32_t *px, const int32_t *py, float *out)
+{
+    for (int64_t k = 0; k < m; k++) out[k] = orc_blend_l2(drec + 8 * k, px[k], py[k]);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -498,8 +656,8 @@ void orc_project64(int32_t n_views, const orc_view_t *views, int64_t n,
 #define ORC_FLAG_ALPHA_MAX 4
 
 typedef struct {
-    double margin_alpha; /* relative band around 1/255 and 0.99 */
-    double margin_T;     /* relative band around 1e-4 */
+    double margin_alpha; /* test knob: also flag FP64 alphas within this relative margin of 1/255 or 0.99 */
+    double margin_T;     /* extra relative band around 1e-4 added to the computed one */
 } orc_margins_t;
 
 static void orc_view_tiles(const orc_view_t *V, int tw, int th, int *ntx, int *nty)
@@ -508,33 +666,16 @@ static void orc_view_tiles(const orc_view_t *V, int tw, int th, int *ntx, int *n
     *nty = (V->height + th - 1) / th;
 }
 
-/* One unit in the last place of x in FP32. */
-static double orc_ulp32(double x)
-{
-    int e;
-    if (x == 0.0) return ldexp(1.0, -149);
-    frexp(x, &e);
-    return ldexp(1.0, e - 24);
-}
-
-/* Bound on how far an FP32 evaluation of the exponent may be from this FP64
- * one: the offset d = mean - pixel is rounded to FP32 (one ulp of dx, dy, plus
- * 1e-6 px for a mean carried in double-FP32, moves the exponent by
- * |dpower/dx| and |dpower/dy| times that), and the quadratic form is evaluated
- * from an FP32 conic whose relative error grows with the eccentricity
- * kappa = lambda_max / lambda_min of the 2D covariance (the determinant
- * cancels), bounded by 1e-6 (4 + kappa) times the magnitude of its terms. */
-static double orc_power_uncertainty(const double *r, double dx, double dy)
-{
-    double A = r[3], B = r[4], C = r[5];
-    double gu = fabs(A * dx + B * dy), gv = fabs(B * dx + C * dy);
-    double mag = 0.5 * (A * dx * dx + C * dy * dy) + fabs(B * dx * dy);
-    double ca = r[10], cb = r[11], cc = r[12];
-    double mid = 0.5 * (ca + cc), rad = sqrt(0.25 * (ca - cc) * (ca - cc) + cb * cb);
-    double lmin = mid - rad > 1e-30 ? mid - rad : 1e-30;
-    double kappa = (mid + rad) / lmin;
-    return gu * (orc_ulp32(dx) + 1e-6) + gv * (orc_ulp32(dy) + 1e-6) + 1e-6 * (4.0 + kappa) * mag + 1e-6;
-}
+/* Bound on the relative error of the kernel's approximate 2^x (the GPU's
+ * ex2.approx.ftz.f32): two units in the last place of FP32, 2^-22.  Measured
+ * over every FP32 input in [-8, 0): at most 2^-22.73. */
+#define ORC_EX2_REL 0x1p-22
+/* The kernel rounds T (1 - alpha) to FP32 (relative error at most 2^-24) and
+ * 1 - alpha, which is exact for alpha >= 1/2 and otherwise lies in (1/2, 1],
+ * so that its rounding error is at most 2^-25 absolute. */
+static double orc_t_round(double a) { return 0x1p-24 + (a < 0.5 ? 0x1p-25 / (1.0 - a) : 0.0); }
+/* The kernel compares with 1e-4 rounded to FP32 (2.6e-9 relative below). */
+#define ORC_T_CUT_REL 3e-9
 
 /* Composites every pixel of every view front to back over its tile's list:
  *   alpha_i = min(0.99, o_i exp(-1/2 d^T conic d)), skipped if < 1/255;
@@ -543,15 +684,28 @@ static double orc_power_uncertainty(const double *r, double dx, double dy)
  * Pixel (px, py) is sampled at (px + 0.5, py + 0.5).  Images are stored per
  * view at pix_base[v] + py * width + px.  n_contrib = number of list entries
  * consumed up to and including the last blended one.
- * A pixel is flagged when a decision's FP64 quantity lies within the margin
- * plus the FP32 uncertainty (orc_power_uncertainty, accumulated along the ray
- * for the transmittance) of its threshold. */
+ * The skip and clamp decisions are taken on the FP32 l2 of the decision
+ * records drec (orc_blend_records); the alphas blended are the FP64 values.
+ * The stop decision compares the FP64 T (1 - alpha) with 1e-4; a kernel that
+ * computes T in FP32 from alphas min(0.99, 2^l2) (approximate exponential,
+ * relative error below ORC_EX2_REL) may decide it the other way only when the
+ * FP64 product lies within the relative deviation its alphas can accumulate:
+ * per blended entry, alpha / (1 - alpha) times the known |l2 ln 2 - ln alpha|
+ * of that evaluation (|ln(0.99f / 0.99)| where the clamp is in force) plus
+ * ORC_EX2_REL, and the roundings of 1 - alpha and of the product
+ * (orc_t_round).  Such pixels are flagged (ORC_FLAG_T_MIN) and slack [P, 4]
+ * receives the blend weight alpha T of the entry at that decision, times its
+ * largest colour channel and times its depth (a result that stops one entry
+ * earlier or later differs by exactly that entry's contribution), and, for
+ * every pixel, the accumulated relative band of its final T. */
 void orc_render(int32_t n_views, const orc_view_t *views, int64_t n,
-                const double *proj, int32_t tw, int32_t th, const int32_t *tile_base,
+                const double *proj, const float *drec, int32_t tw, int32_t th, const int32_t *tile_base,
                 const int64_t *pix_base, const uint32_t *vals, const uint32_t *ranges,
                 orc_margins_t mg, double *rgb, double *depth, double *alpha,
-                double *final_T, int32_t *n_contrib, int32_t *flags)
+                double *final_T, int32_t *n_contrib, int32_t *flags, double *slack)
 {
+    const double ln2 = 0.69314718055994530942;
+    const double dev_clamp = fabs(log((double)0.99f / ORC_ALPHA_MAX));
     for (int32_t v = 0; v < n_views; v++) {
         const orc_view_t *V = &views[v];
         int ntx, nty;
@@ -564,20 +718,34 @@ void orc_render(int32_t n_views, const orc_view_t *views, int64_t n,
                 double T = 1.0, C[3] = {0, 0, 0}, D = 0.0, lnT_unc = 0.0;
                 int32_t last = 0, fl = 0;
                 double sx = px + 0.5, sy = py + 0.5;
+                slack[4 * pix] = slack[4 * pix + 1] = slack[4 * pix + 2] = 0.0;
                 for (uint32_t k = b; k < e; k++) {
-                    const double *r = proj + 16 * ((int64_t)v * n + vals[k]);
+                    int64_t o = (int64_t)v * n + vals[k];
+                    const double *r = proj + 16 * o;
+                    float l2 = orc_blend_l2(drec + 8 * o, px, py);
                     double dx = r[0] - sx, dy = r[1] - sy;
                     double power = -0.5 * (r[3] * dx * dx + r[5] * dy * dy) - r[4] * dx * dy;
                     double araw = r[6] * exp(power);
-                    double unc = orc_power_uncertainty(r, dx, dy);
-                    if (fabs(log(araw / ORC_ALPHA_MAX)) <= mg.margin_alpha + unc) fl |= ORC_FLAG_ALPHA_MAX;
-                    double a = araw < ORC_ALPHA_MAX ? araw : ORC_ALPHA_MAX;
-                    if (fabs(log(a / ORC_ALPHA_MIN)) <= mg.margin_alpha + unc) fl |= ORC_FLAG_ALPHA_MIN;
-                    if (a < ORC_ALPHA_MIN) continue;
+                    if (mg.margin_alpha > 0.0) {
+                        if (fabs(log(araw / ORC_ALPHA_MAX)) <= mg.margin_alpha) fl |= ORC_FLAG_ALPHA_MAX;
+                        double a0 = araw < ORC_ALPHA_MAX ? araw : ORC_ALPHA_MAX;
+                        if (fabs(log(a0 / ORC_ALPHA_MIN)) <= mg.margin_alpha) fl |= ORC_FLAG_ALPHA_MIN;
+                    }
+                    if (l2 < ORC_L2_ALPHA_MIN) continue;
+                    int clamp = l2 >= ORC_L2_ALPHA_MAX;
+                    double a = clamp ? ORC_ALPHA_MAX : araw;
+                    double dev = (clamp ? dev_clamp : fabs((double)l2 * ln2 - log(araw))) + ORC_EX2_REL;
+                    double step_unc = a / (1.0 - a) * dev + orc_t_round(a);
                     double tT = T * (1.0 - a);
-                    /* FP32 error of the factor (1 - alpha) and of the product's rounding */
-                    double step_unc = a / (1.0 - a) * unc + 2.0e-7;
-                    if (fabs(log(tT / ORC_T_MIN)) <= mg.margin_T + lnT_unc + step_unc) fl |= ORC_FLAG_T_MIN;
+                    if (fabs(log(tT / ORC_T_MIN)) <= mg.margin_T + lnT_unc + step_unc + ORC_T_CUT_REL) {
+                        fl |= ORC_FLAG_T_MIN;
+                        double w = a * T, cm = r[7];
+                        if (r[8] > cm) cm = r[8];
+                        if (r[9] > cm) cm = r[9];
+                        slack[4 * pix] = w;
+                        slack[4 * pix + 1] = w * cm;
+                        slack[4 * pix + 2] = w * r[2];
+                    }
                     if (tT < ORC_T_MIN) break;
                     for (int ch = 0; ch < 3; ch++) C[ch] += r[7 + ch] * a * T;
                     D += r[2] * a * T;
@@ -591,6 +759,7 @@ void orc_render(int32_t n_views, const orc_view_t *views, int64_t n,
                 final_T[pix] = T;
                 n_contrib[pix] = last;
                 flags[pix] = fl;
+                slack[4 * pix + 3] = lnT_unc;
             }
     }
 }
@@ -607,9 +776,10 @@ void orc_render(int32_t n_views, const orc_view_t *views, int64_t n,
  * so with s = sum over later blended entries k of (c_k.gC + z_k gD) alpha_k T_k:
  *   dL/dalpha_i = T_i (c_i.gC + z_i gD) - s / (1 - alpha_i)
  *                 + gA T_final / (1 - alpha_i).
- * The clamp alpha = min(0.99, o g) passes no gradient where it is active. */
+ * The skip and clamp decisions are orc_render's (on the FP32 l2 of drec); the
+ * clamp alpha = min(0.99, o g) passes no gradient where it is active. */
 void orc_render_bwd(int32_t n_views, const orc_view_t *views, int64_t n,
-                    const double *proj, int32_t tw, int32_t th, const int32_t *tile_base,
+                    const double *proj, const float *drec, int32_t tw, int32_t th, const int32_t *tile_base,
                     const int64_t *pix_base, const uint32_t *vals, const uint32_t *ranges,
                     const double *dC, const double *dD, const double *dA, double *g2d)
 {
@@ -641,14 +811,16 @@ void orc_render_bwd(int32_t n_views, const orc_view_t *views, int64_t n,
                 int64_t nb = 0;
                 double T = 1.0;
                 for (uint32_t k = b; k < e; k++) {
-                    const double *r = proj + 16 * ((int64_t)v * n + vals[k]);
+                    int64_t o = (int64_t)v * n + vals[k];
+                    const double *r = proj + 16 * o;
+                    float l2 = orc_blend_l2(drec + 8 * o, px, py);
+                    if (l2 < ORC_L2_ALPHA_MIN) continue;
                     double dx = r[0] - sx, dy = r[1] - sy;
                     double power = -0.5 * (r[3] * dx * dx + r[5] * dy * dy) - r[4] * dx * dy;
                     double g = exp(power);
                     double araw = r[6] * g;
-                    int c = !(araw < ORC_ALPHA_MAX);
+                    int c = l2 >= ORC_L2_ALPHA_MAX;
                     double a = c ? ORC_ALPHA_MAX : araw;
-                    if (a < ORC_ALPHA_MIN) continue;
                     double tT = T * (1.0 - a);
                     if (tT < ORC_T_MIN) break;
                     ids[nb] = vals[k];

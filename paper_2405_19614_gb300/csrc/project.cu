@@ -6,8 +6,11 @@
 // parameters are read from HBM once per launch however many views there are.
 // The radius, tile rectangle and depth follow a fixed sequence of correctly
 // rounded FP32 operations (explicit __f*_rn intrinsics, never contracted) so
-// that the tile keys are reproducible bit for bit; everything else (conic,
-// opacity, colour) is ordinary FP32.
+// that the tile keys are reproducible bit for bit.  So does every quantity the
+// compositing takes a decision on: the record carries log2(o) and the conic
+// scaled to base 2, and the 2D mean's double-FP32 remainder, so that
+// log2(alpha) at a pixel (render.cuh) and with it the alpha skip and clamp
+// decisions are reproducible bit for bit too.  Colour is ordinary FP32.
 #include "common.cuh"
 #include "sh.cuh"
 
@@ -43,9 +46,40 @@ __device__ __forceinline__ float geom_expf(float x)
     return MUL(p, __int_as_float((ki + 127) << 23));
 }
 
+// log2 for the decision record, y >= 1: y = m 2^e with m in (sqrt(1/2),
+// sqrt(2)], then log2 m = (2 / ln 2) atanh(s), s = (m - 1) / (m + 1), by the
+// odd series s (C1 + s^2 (C3 + s^2 (C5 + s^2 (C7 + s^2 C9)))), C_k = 2 / (k ln 2)
+// (|s| <= 0.172, so the next term is below 1e-9 relative), Horner with fused
+// multiply-adds.  Each step is one correctly rounded operation.
+__device__ __forceinline__ float geom_log2f(float y)
+{
+    const uint32_t bits = __float_as_uint(y);
+    int e = (int)((bits >> 23) & 0xffu) - 127;
+    float m = __uint_as_float((bits & 0x7fffffu) | 0x3f800000u);
+    if (m > 0x1.6a09e6p+0f) {
+        m = MUL(m, 0.5f);
+        e += 1;
+    }
+    const float s = DIV(SUB(m, 1.0f), ADD(m, 1.0f));
+    const float s2 = MUL(s, s);
+    float p = 0x1.484b14p-2f;
+    p = __fmaf_rn(p, s2, 0x1.a61762p-2f);
+    p = __fmaf_rn(p, s2, 0x1.2776c6p-1f);
+    p = __fmaf_rn(p, s2, 0x1.ec709ep-1f);
+    p = __fmaf_rn(p, s2, 0x1.715476p+1f);
+    return ADD((float)e, MUL(s, p));
+}
+
+// log2 of the opacity sigmoid(l) = 1 / (1 + e^-l): -log2(1 + e^-l).
+__device__ __forceinline__ float geom_log2_opacity(float l)
+{
+    return -geom_log2f(ADD(1.0f, geom_expf(-l)));
+}
+
 struct Geom {
     float u, v, z;
     float ca, cb, cc;   // 2D covariance including the blur
+    float det;
     int32_t radius;
     int32_t x0, y0, x1, y1;
 };
@@ -141,6 +175,7 @@ __device__ __forceinline__ bool geometry(const float m[3], const float ls[3], co
     g.ca = ca;
     g.cb = cb;
     g.cc = cc;
+    g.det = det;
     g.radius = (int32_t)rad;
     g.x0 = (int32_t)fx0;
     g.y0 = (int32_t)fy0;
@@ -149,38 +184,34 @@ __device__ __forceinline__ bool geometry(const float m[3], const float ls[3], co
     return true;
 }
 
-#undef MUL
-#undef ADD
-#undef SUB
-#undef DIV
-
 // Error-free transformations for double-FP32 arithmetic (hi + lo).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    s = ADD(a, b);
+    const float bb = SUB(s, a);
+    e = ADD(SUB(a, SUB(s, bb)), SUB(b, bb));
 }
 
 __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
 {
-    p = __fmul_rn(a, b);
+    p = MUL(a, b);
     e = __fmaf_rn(a, b, -p);
 }
 
-// r0 m0 + r1 m1 + r2 m2 + t as hi + lo (compensated dot product).
+// r0 m0 + r1 m1 + r2 m2 + t as hi + lo (compensated dot product); hi is the
+// geometry's camera coordinate, bit for bit.
 __device__ __forceinline__ void dot3_plus(const float *r, const float *m, float t, float &hi, float &lo)
 {
     float p, e, s, es;
     two_prod(r[0], m[0], s, lo);
     two_prod(r[1], m[1], p, e);
     two_sum(s, p, s, es);
-    lo += e + es;
+    lo = ADD(lo, ADD(e, es));
     two_prod(r[2], m[2], p, e);
     two_sum(s, p, s, es);
-    lo += e + es;
+    lo = ADD(lo, ADD(e, es));
     two_sum(s, t, s, es);
-    lo += es;
+    lo = ADD(lo, es);
     hi = s;
 }
 
@@ -188,17 +219,28 @@ __device__ __forceinline__ void dot3_plus(const float *r, const float *m, float 
 // as hi + lo pairs, in double-FP32 arithmetic.
 __device__ __forceinline__ float pixel_remainder(float f, float xh, float xl, float zh, float zl, float c, float ref)
 {
-    const float q = __fdiv_rn(xh, zh);
+    const float q = DIV(xh, zh);
     // x - q z, exactly for the hi parts, then the lo parts
-    const float r = __fmaf_rn(-q, zh, xh) + (xl - q * zl);
-    const float ql = r / zh;
+    const float r = ADD(__fmaf_rn(-q, zh, xh), SUB(xl, MUL(q, zl)));
+    const float ql = DIV(r, zh);
     float m, me;
     two_prod(f, q, m, me);
-    const float ml = me + f * ql;
+    const float ml = ADD(me, MUL(f, ql));
     float s, se;
     two_sum(m, c, s, se);
-    return (s - ref) + (se + ml);
+    return ADD(SUB(s, ref), ADD(se, ml));
 }
+
+// Base-2 conic of a 2D covariance (a, b, c) with determinant det:
+// (A', B', C') = (-log2(e)/2 c, log2(e) b, -log2(e)/2 a) / det, so that
+// log2(o exp(-1/2 d^T conic d)) = log2(o) + A' dx^2 + B' dx dy + C' dy^2.
+constexpr float kNegHalfLog2e = -0x1.715476p-1f;
+constexpr float kLog2eF = 0x1.715476p+0f;
+
+#undef MUL
+#undef ADD
+#undef SUB
+#undef DIV
 
 struct ProjectArgs {
     const float *means, *log_scales, *quats, *opacity_logit, *sh;
@@ -240,7 +282,7 @@ __global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable v
     q[1] = q4.y;
     q[2] = q4.z;
     q[3] = q4.w;
-    const float opacity = 1.0f / (1.0f + __expf(-__ldg(a.opacity_logit + i)));
+    const float log2o = geom_log2_opacity(__ldg(a.opacity_logit + i));
     // the SH coefficients are read only for the views the Gaussian is drawn
     // in (they come from L1 after the first): 48 registers fewer a thread than
     // holding them across the view loop, and no read for a Gaussian no view draws
@@ -271,7 +313,6 @@ __global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable v
             a.tiles_touched[o] = 0;
             continue;
         }
-        const float inv = 1.0f / (g.ca * g.cc - g.cb * g.cb);
         float dx = m[0] - s_c[v][0], dy = m[1] - s_c[v][1], dz = m[2] - s_c[v][2];
         const float rn = rsqrtf(dx * dx + dy * dy + dz * dz);
         dx *= rn;
@@ -299,8 +340,10 @@ __global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable v
         const float dv = pixel_remainder(V.fy, yh, yl, zh, zl, V.cy, g.v);
         const uint32_t r0 = (uint32_t)g.x0 | ((uint32_t)g.y0 << 16);
         const uint32_t r1 = (uint32_t)g.x1 | ((uint32_t)g.y1 << 16);
-        a.rec[3 * o + 0] = make_float4(g.u, g.v, g.z, opacity);
-        a.rec[3 * o + 1] = make_float4(g.cc * inv, -g.cb * inv, g.ca * inv, du);
+        a.rec[3 * o + 0] = make_float4(g.u, g.v, g.z, log2o);
+        a.rec[3 * o + 1] = make_float4(__fdiv_rn(__fmul_rn(kNegHalfLog2e, g.cc), g.det),
+                                       __fdiv_rn(__fmul_rn(kLog2eF, g.cb), g.det),
+                                       __fdiv_rn(__fmul_rn(kNegHalfLog2e, g.ca), g.det), du);
         a.rec[3 * o + 2] = make_float4(col[0], col[1], col[2], dv);
         a.rect[o] = make_uint2(r0, r1);
         a.radii[o] = g.radius;

@@ -21,25 +21,26 @@ __device__ __forceinline__ float ex2_approx(float x)
 // with power = -1/2 (A dx^2 + C dy^2) - B dx dy and d = mean - pixel centre,
 //   log2(o exp(power)) = log2(o) + A' dx^2 + dy (B' dx + C' dy),
 //   A' = -log2(e)/2 A, B' = -log2(e) B, C' = -log2(e)/2 C,
-// so an entry costs two packed FMAs per pixel pair up to the blend test, which
-// compares this logarithm with log2(1/255); the exponential is taken only
-// where the entry is blended.  The forward and backward kernels go through the
-// same helpers with the same explicitly rounded operations, so both take the
-// same skip decisions and the same alphas bit for bit.
-constexpr float kLog2e = 1.442695041f;
+// and the projection writes the record in that form (log2 o and A', B', C'
+// by a fixed sequence of correctly rounded operations).  An entry costs two
+// packed FMAs per pixel pair up to the blend test.  Both alpha decisions are
+// taken on this logarithm l2, before any exponential: the entry is skipped
+// when l2 < log2(1/255), and the clamp at 0.99 (which passes no gradient) is
+// in force when l2 >= log2(0.99).  l2 itself is one fixed sequence of
+// correctly rounded FP32 operations on the record, so the decisions are
+// reproducible bit for bit (the CPU oracle takes them on the same FP32
+// value).  The value blended is min(0.99, 2^l2), branch free; next to the cut
+// it may differ from 0.99 by the exponential's last bits either way, which is
+// a continuous difference, not a decision.  The forward and backward kernels
+// go through the same helpers, so both take the same decisions and the same
+// alphas.
 constexpr float kLn2 = 0.6931471806f;
-constexpr float kLog2AlphaMin = -7.994353294f;  // FP32 value nearest log2(1/255), within 1e-7 relative of it
+constexpr float kLog2AlphaMin = -0x1.ffa37cp+2f;  // FP32 value nearest log2(1/255)
+constexpr float kLog2AlphaMax = -0x1.db1f34p-7f;  // FP32 value nearest log2(0.99)
 
-// Turns a record, as staged in shared memory for the per-pixel walk, into the
-// base-2 form: p.w = log2(o), c.xyz = (A', B', C').  The mean remainders (c.w,
-// col.w), depth and colour are unchanged.
-__device__ __forceinline__ void stage_log2(float4 &p, float4 &c)
-{
-    p.w = __log2f(p.w);
-    c.x = __fmul_rn(c.x, -0.5f * kLog2e);
-    c.y = __fmul_rn(c.y, -kLog2e);
-    c.z = __fmul_rn(c.z, -0.5f * kLog2e);
-}
+// alpha of a blended entry from its l2: min(0.99, 2^l2), the exponential by
+// the approximate instruction.
+__device__ __forceinline__ float alpha_of_l2(float l2) { return fminf(kAlphaMax, ex2_approx(l2)); }
 
 // The part of log2(raw alpha) that a thread's pixels share (they lie in one
 // column sx): dx, log2(o) + A' dx^2 and B' dx.  The mean is u + du: u - sx is
@@ -82,14 +83,15 @@ __device__ __forceinline__ float edge_min(float P, float B, float Q, float s, fl
 }
 
 // Conservative test that a splat cannot reach alpha >= 1/255 anywhere in a box
-// of pixel centres [x0, x1] x [y0, y1].  With d = pixel - mean, alpha at a
-// pixel is min(0.99, o exp(-q(d)/2)), q(d) = A dx^2 + 2 B dx dy + C dy^2 (the
-// conic is positive definite).  q is convex with minimum 0 at the mean, so over
-// a box not containing the mean its minimum lies on one of the four edges, where
-// it is a one-dimensional quadratic; the box minimum bounds q at every pixel
-// centre inside.  The entry is dropped when o exp(-q_min/2) is below 1/255 by a
-// factor e^-(0.001 + 2e-6 M), M the magnitude of the terms of q: more than the
-// FP32 rounding of this bound and of the per-pixel evaluation together, so a
+// of pixel centres [x0, x1] x [y0, y1].  With d = pixel - mean, log2 of the
+// raw alpha at a pixel is log2(o) - q(d), q(d) = P dx^2 + 2 B dx dy + Q dy^2
+// with (P, B, Q) = -(A', B'/2, C') from the record (positive definite).  q is
+// convex with minimum 0 at the mean, so over a box not containing the mean its
+// minimum lies on one of the four edges, where it is a one-dimensional
+// quadratic; the box minimum bounds q at every pixel centre inside.  The entry
+// is dropped when log2(o) - q_min is below log2(1/255) by more than
+// 1.5e-3 + 4e-6 M, M the magnitude of the terms of q: more than the FP32
+// rounding of this bound and of the per-pixel evaluation together, so a
 // dropped entry is one the per-pixel test would have skipped: results are
 // unchanged, only work is saved.  (A bound through the smallest eigenvalue of
 // the conic is weaker and, for elongated splats, cancels badly in FP32.)
@@ -99,12 +101,11 @@ __device__ __forceinline__ bool splat_misses_box(const float4 &p, const float4 &
     const float ex0 = x0 - p.x, ex1 = x1 - p.x, ey0 = y0 - p.y, ey1 = y1 - p.y;
     float q = 0.0f, mag = 0.0f;
     if (!(ex0 <= 0.0f && ex1 >= 0.0f && ey0 <= 0.0f && ey1 >= 0.0f)) {
-        const float A = c.x, B = c.y, C = c.z;
-        q = fminf(fminf(edge_min(A, B, C, ex0, ey0, ey1, &mag), edge_min(A, B, C, ex1, ey0, ey1, &mag)),
-                  fminf(edge_min(C, B, A, ey0, ex0, ex1, &mag), edge_min(C, B, A, ey1, ex0, ex1, &mag)));
+        const float P = -c.x, B = -0.5f * c.y, Q = -c.z;
+        q = fminf(fminf(edge_min(P, B, Q, ex0, ey0, ey1, &mag), edge_min(P, B, Q, ex1, ey0, ey1, &mag)),
+                  fminf(edge_min(Q, B, P, ey0, ex0, ex1, &mag), edge_min(Q, B, P, ey1, ex0, ex1, &mag)));
     }
-    // alpha bound < (1/255) e^-margin  <=>  -q/2 < -ln(255 o) - margin
-    return -0.5f * q < -__logf(255.0f * p.w) - (1e-3f + 2e-6f * mag);
+    return p.w - q < kLog2AlphaMin - (1.5e-3f + 4e-6f * mag);
 }
 
 // Threads per block of the compositing kernels (each warp works alone).

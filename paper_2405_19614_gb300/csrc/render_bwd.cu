@@ -9,8 +9,9 @@
 //   dL/dalpha_i = T_i (c_i.gC + z_i gD) - s / (1 - alpha_i) + gA T_final / (1 - alpha_i),
 // and through alpha_i = min(0.99, o_i g_i), g_i = exp(power_i), to the
 // opacity, the 2D mean and the conic (no gradient where the clamp is active).
-// With t = dL/dalpha o g (0 where the clamp is active; o g is the raw alpha
-// the walk computes) and d = mean - pixel,
+// With t = dL/dalpha o g (0 where the clamp is active, a decision taken on
+// log2(o g) as in the forward; o g is the raw alpha the walk computes) and
+// d = mean - pixel,
 // power = -1/2 (A dx^2 + 2 B dx dy + C dy^2), so over a thread's pixels (one
 // column: dx is common) the mean and conic gradients need only
 // G = sum t, S1 = sum t dy, S2 = sum t dy^2:
@@ -184,11 +185,9 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
             const uint32_t nlo = lo > 32u ? lo - 32u : 0u;
             if (lo > 0) load_bwd_entry(a, rbase, b + nlo + lane, nlo + lane < lo, n0, n1, n2, ng);
             uint32_t todo = __ballot_sync(kFullMask, have && !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
-            float4 q0 = r0, q1 = r1;
-            stage_log2(q0, q1);
             __syncwarp();  // the previous chunk's records have been read
-            s_rec[warp][0][lane] = q0;
-            s_rec[warp][1][lane] = q1;
+            s_rec[warp][0][lane] = r0;
+            s_rec[warp][1][lane] = r1;
             s_rec[warp][2][lane] = r2;
             s_gid[warp][lane] = g_self;
             __syncwarp();
@@ -226,6 +225,8 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
                         // raw alpha 0, so its w, t and sums are exactly zero
                         const float2 araw = f2(hx[i] ? ex2_approx(l2[i].x) : 0.0f, hy[i] ? ex2_approx(l2[i].y) : 0.0f);
                         const float2 al = f2(fminf(kAlphaMax, araw.x), fminf(kAlphaMax, araw.y));
+                        // where the clamp is in force (decided on l2) no gradient passes
+                        const bool cx = l2[i].x >= kLog2AlphaMax, cy = l2[i].y >= kLog2AlphaMax;
                         const float2 om = __ffma2_rn(al, f2(-1.0f), f2(1.0f));
                         // 1 - alpha >= 0.01: the fast reciprocal is within 2 ulp
                         const float2 inv = f2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
                         // T of a pixel that does not blend stays exact
                         T[i] = f2(hx[i] ? Tb.x : T[i].x, hy[i] ? Tb.y : T[i].y);
                         const float2 tg = __fmul2_rn(dalpha, araw);
-                        const float2 t = f2(araw.x < kAlphaMax ? tg.x : 0.0f, araw.y < kAlphaMax ? tg.y : 0.0f);
+                        const float2 t = f2(cx ? 0.0f : tg.x, cy ? 0.0f : tg.y);
                         const float2 u = __fmul2_rn(t, dy[i]);
                         G2 = __fadd2_rn(G2, t);
                         S12 = __fadd2_rn(S12, u);

@@ -10,7 +10,7 @@
 // entries, one per lane, loading the next chunk's records while it works on
 // the current one, drops (in parallel) the entries that provably cannot reach
 // alpha = 1/255 in its band (splat_misses_box), stages the rest in its own
-// shared-memory slot (in the base-2 form of render.cuh) and walks them; it stops once all its pixels have run out
+// shared-memory slot (records are in the base-2 form of render.cuh) and walks them; it stops once all its pixels have run out
 // of transmittance.  Warps never wait for one another.  PPT is chosen per
 // workload by the autotuner, with the band width BW.
 #include "common.cuh"
@@ -116,11 +116,9 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
             const bool keep = have && (STATS || !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
             uint32_t todo = __ballot_sync(kFullMask, keep);
             if (alive == 0) todo = 0;
-            float4 q0 = r0, q1 = r1;
-            stage_log2(q0, q1);
             __syncwarp();  // the previous chunk's records have been read
-            s_rec[warp][0][lane] = q0;
-            s_rec[warp][1][lane] = q1;
+            s_rec[warp][0][lane] = r0;
+            s_rec[warp][1][lane] = r1;
             s_rec[warp][2][lane] = r2;
             __syncwarp();
             while (todo) {
@@ -137,7 +135,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
                     float2 dy;
                     const float2 l2 = splat_log2a2(
                         kc, p, c, col, f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f), &dy);
-                    const float2 al = f2(fminf(kAlphaMax, ex2_approx(l2.x)), fminf(kAlphaMax, ex2_approx(l2.y)));
+                    const float2 al = f2(alpha_of_l2(l2.x), alpha_of_l2(l2.y));
                     const float2 tT = __fmul2_rn(T[i], __fadd2_rn(f2(1.0f), f2(-al.x, -al.y)));  // T (1 - alpha)
                     const float2 aT = __fmul2_rn(al, T[i]);
                     bool blend[2];

@@ -1,5 +1,5 @@
 """Host-side pieces of bench.py that decide what the JSON line reports: the
-DRAM-traffic figure is taken from the committed ncu summary only while the
+DRAM-traffic figure is taken from the committed ncu counters only while the
 profiled kernel's sources, variant and workload are the ones captured; the
 per-stage work model is complete and positive; the oracle pool's plan keeps a
 sample near its time budget."""
@@ -20,17 +20,23 @@ def _built():
 
 
 def test_traffic_is_reported_for_the_profiled_sources_only(tmp_path, monkeypatch):
-    assert bench.kernel_traffic("render_bwd", WORKLOAD, None) > 0  # the committed capture matches
-    assert bench.kernel_traffic("render_bwd", "another-workload", None) is None
-    assert bench.kernel_traffic("ssim", WORKLOAD, None) is None  # no capture for that stage
-    # a copy of the tree whose backward source differs by one byte reports nothing
+    import json
+    import paper_2405_19614_gb300 as gs
     root = tmp_path / "repo"
-    shutil.copytree(os.path.join(bench.ROOT, "profiles"), root / "profiles")
     shutil.copytree(os.path.join(bench.ROOT, "paper_2405_19614_gb300", "csrc"),
                     root / "paper_2405_19614_gb300" / "csrc")
+    (root / "profiles").mkdir()
+    _, variant, _, _ = gs.gs_get_render_variants()
+    rec = dict(workload=WORKLOAD, variant=variant, bytes_per_launch=123456,
+               sources_sha256=bench.traffic_sources_sha256("render_bwd", str(root)))
+    (root / "profiles" / "traffic.json").write_text(json.dumps({"render_bwd": rec}))
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.kernel_traffic("render_bwd", WORKLOAD, None) == 123456  # record matches the sources
+    assert bench.kernel_traffic("render_bwd", "another-workload", None) is None
+    assert bench.kernel_traffic("ssim", WORKLOAD, None) is None  # no capture for that stage
+    # the backward source differs by one byte: nothing is reported
     src = root / "paper_2405_19614_gb300" / "csrc" / "render_bwd.cu"
     src.write_text(src.read_text() + "\n")
-    monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.kernel_traffic("render_bwd", WORKLOAD, None) is None
 
 

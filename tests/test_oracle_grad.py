@@ -45,7 +45,8 @@ def _setup(deg, seed, oblique, edge=False):
 
 def _eval(scene, cams, fwd, w):
     proj = oracle.project64(scene, cams, fwd["geom"])
-    return _functional(oracle.render(cams, proj, fwd["bins"], fwd["geom"]["n"]), w)
+    drec = oracle.blend_records(scene, cams)
+    return _functional(oracle.render(cams, proj, drec, fwd["bins"], fwd["geom"]["n"]), w)
 
 
 @pytest.mark.parametrize("deg,seed,oblique,edge", [(0, 11, False, False), (3, 12, True, False),
