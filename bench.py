@@ -34,6 +34,7 @@ import numpy as np  # noqa: E402
 import scenes  # noqa: E402
 
 METRIC = "fwd+bwd Mpix/s and mapping iters/s, batched vs plain on one GB300, at oracle tol"
+SUSTAIN_S = 3.0  # seconds of the sustained replay
 
 
 def parse():
@@ -51,6 +52,8 @@ def parse():
                     "(0 = every host core, as memory allows)")
     ap.add_argument("--profile-steps", type=int, default=0, help="run N untimed steps and exit (for ncu)")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default kernel variants")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (configs key)")
+    ap.add_argument("--configs", default="1,2,3,5", help="other workloads measured after the headline")
     return ap.parse_args()
 
 
@@ -237,6 +240,17 @@ def run_plain(c, step, rs):
     gs.gs_reproj_loss_grad(kp["points"], kp["obs"], kp["view_ids"], step.rast.views, step.viewmats, step.w_rpj,
                            step.loss, step.d_twist)
     gs.gs_adam_step(step.flat.buf, step.grad_buf, step.m, step.v, step.groups, step.step_count)
+
+
+def snapshot(step):
+    """Copies of what a step changes (parameters, Adam moments and step
+    counter), so every timed region starts from the same map."""
+    return [t.clone() for t in (step.flat.buf, step.m, step.v, step.step_count)]
+
+
+def restore(step, snap):
+    for t, s_ in zip((step.flat.buf, step.m, step.v, step.step_count), snap):
+        t.copy_(s_)
 
 
 def work_counts(step):
@@ -479,6 +493,279 @@ def oracle_workers(want):
 
 
 # --------------------------------------------------------------------------
+# the other workloads (the `configs` key of the JSON line)
+# --------------------------------------------------------------------------
+
+def device_peaks(device):
+    """HBM GB/s and FP32 TFLOP/s denominators: the measured copy bandwidth of
+    MEASURED_PEAKS.json and 128 FP32 lanes x 2 flops per SM cycle at its
+    maximum SM clock."""
+    import torch
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(device).multi_processor_count
+    return hbm_peak, n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+
+
+def stage_roofline(stage, stage_ms, works, hbm_peak, alu_peak):
+    kind, amount = works[stage]
+    sec = stage_ms[stage] / 1e3
+    if kind == "hbm":
+        return {"bound": "hbm", "achieved": amount / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": amount / sec / 1e9 / hbm_peak, "algorithmic_bytes": amount}
+    return {"bound": "alu", "achieved": amount / sec / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": amount / sec / 1e12 / alu_peak, "algorithmic_flops": amount}
+
+
+def graph_time_ms(fn, steps, warmup, reset=None):
+    """Average ms of fn replayed as one captured CUDA graph (events on the
+    current stream), or None when the capture fails; reset() runs before the
+    timed replays."""
+    import torch
+    try:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            fn()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            fn()
+        for _ in range(warmup):
+            g.replay()
+        if reset is not None:
+            reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+    except Exception as exc:
+        print(f"graph capture failed: {exc}", file=sys.stderr)
+        return None
+
+
+def oracle_view_sample(c, v, rows=None):
+    """One oracle fwd+bwd (FP64, one thread, in this process) of view v of a
+    workload, or of its first `rows` rows (a multiple of 16); Mpix/s."""
+    cams = c["cams"]
+    W, H = (int(x) for x in cams["size"][v])
+    rows = H if rows is None else min(rows, H)
+    cc = crop_cams(cams, v, 0, rows)
+    scene = {k: (x.astype(np.float64) if isinstance(x, np.ndarray) else x) for k, x in c["scene"].items()}
+    rng = np.random.default_rng(7)
+    P = W * rows
+    t0 = time.perf_counter()
+    oracle_step(scene, cc, rng.uniform(0, 1, (P, 3)), rng.uniform(0, 4, P), c.get("w_c", 1.0), c.get("w_d", 0.5),
+                c.get("zeta", 0.0))
+    sec = time.perf_counter() - t0
+    return {"value": P / sec / 1e6, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle fwd+bwd of view {v} rows 0-{rows} ({W}x{rows} px, all {scene['means'].shape[0]} "
+                      f"Gaussians projected) in one thread, {sec:.1f} s"}
+
+
+def measure_mapping_config(idx, args, device, with_plain):
+    """A mapping workload measured like the headline: autotuned variants, the
+    step replayed as a CUDA graph, per-stage events in an eager pass, the
+    dominant stage against its roofline; optionally one view per launch."""
+    import torch
+
+    from paper_2405_19614_gb300.autotune import tune
+    c, step, cap = build_workload(idx, 1.0, device)
+    P = step.rast.n_pix
+    step.run()
+    torch.cuda.synchronize()
+    tuned = tune(step.rast, step.params, step.viewmats, step.d_rgb, step.d_depth, use_cache=False)
+    steps = max(args.steps, 20 if P > 100_000 else 200)
+    for _ in range(max(3, args.warmup)):
+        step.run()
+    torch.cuda.synchronize()
+    if step.rast.status() != 0:
+        raise SystemExit(f"{c['name']}: device status {step.rast.status()}")
+    snap = snapshot(step)
+    timers = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step.run(timers)
+    e1.record()
+    torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1) / steps
+    stage_ms = {k: sum(a.elapsed_time(b) for a, b in v) / len(v) for k, v in timers.items()}
+    restore(step, snap)
+    ms = graph_time_ms(step.run, steps, max(3, args.warmup), lambda: restore(step, snap)) or eager_ms
+    restore(step, snap)
+    step.run()
+    torch.cuda.synchronize()
+    w = work_counts(step)
+    works = stage_work(w)
+    hbm_peak, alu_peak = device_peaks(device)
+    dom = max(stage_ms, key=lambda k: stage_ms[k] if k in works else -1)
+    floor = sum(works[k][1] / (hbm_peak * 1e9 if works[k][0] == "hbm" else alu_peak * 1e12) * 1e3
+                for k in stage_ms if k in works)
+    out = {"workload": c["name"], "gaussians": w["N"], "views": w["V"], "pixels_per_step": P, "pairs": w["K"],
+           "value": P / ms / 1e3, "unit": "Mpix/s", "ms_per_step": ms, "iters_per_s": 1e3 / ms,
+           "timing": "CUDA graph replay of the step", "steps": steps,
+           "eager": {"ms_per_step": eager_ms, "value": P / eager_ms / 1e3},
+           "stages": {k: round(v, 4) for k, v in stage_ms.items()},
+           "roofline": dict(stage_roofline(dom, stage_ms, works, hbm_peak, alu_peak), kernel=dom),
+           "roofline_step": {"floor_ms": floor, "ms": ms, "frac": floor / ms},
+           "tuned": None if tuned is None else {"fwd": tuned["fwd"], "bwd": tuned["bwd"]}}
+    if with_plain and step.rast.V > 1:
+        rs = plain_steps(c, step, cap, device)
+        for _ in range(2):
+            run_plain(c, step, rs)
+        restore(step, snap)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            run_plain(c, step, rs)
+        e1.record()
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1) / steps
+        out["plain"] = {"value": P / plain_ms / 1e3, "ms_per_step": plain_ms}
+        out["batched_vs_plain"] = plain_ms / eager_ms
+        del rs
+    if not args.no_cpu:
+        # a bounded sample: one whole view, or 16-row strips of large scenes
+        out["cpu_baseline"] = oracle_view_sample(c, 0, None if w["N"] <= 300_000 else 64)
+    del step
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_tracking_config(args, device):
+    """The TUM-shaped tracking workload: 100 pose-only iterations of the joint
+    loss (rendering L1 with the gate plus the keypoint re-projection term) from a
+    perturbed pose, set up with the library's own calls, the loop replayed as
+    100 graph launches of one iteration."""
+    import torch
+
+    import paper_2405_19614_gb300 as gs
+    from paper_2405_19614_gb300.pipeline import TrackingStep
+    c = scenes.config(3)
+    scene, cams = c["scene"], c["cams"]
+    n = scene["means"].shape[0]
+    W, H = (int(x) for x in cams["size"][0])
+    p = {k: torch.as_tensor(scene[k], device=device) for k in ("means", "log_scales", "quats", "opacity_logit", "sh")}
+    p["sh_degree"] = scene["sh_degree"]
+    E_true = torch.as_tensor(cams["viewmats"].reshape(1, 12), device=device)
+
+    def moved(xi, E):  # Exp(xi) E by the library's pose update
+        vm = E.clone()
+        gs.gs_pose_update(vm, torch.as_tensor(np.asarray(xi, np.float32).reshape(1, 6), device=device).clone())
+        return vm
+
+    # target: mean of the sub-renders along the motion, plus pixel noise (setup)
+    r = gs.Rasterizer(n, scene["sh_degree"], cams["intr"], cams["size"], device=device)
+    acc_rgb = torch.zeros(W * H, 3, device=device)
+    acc_d = torch.zeros(W * H, device=device)
+    for s_ in np.linspace(-0.5, 0.5, c["n_sub"]):
+        r.forward(p, moved(s_ * c["motion"], E_true))
+        acc_rgb += r.img["rgb"]
+        acc_d += r.img["depth"]
+    acc_rgb /= c["n_sub"]
+    acc_d /= c["n_sub"]
+    gen = torch.Generator(device=device).manual_seed(c["noise_seed"])
+    t_rgb = (acc_rgb + 0.02 * torch.randn(acc_rgb.shape, device=device, generator=gen)).contiguous()
+    t_depth = acc_d.contiguous()
+    px, py = scenes.keypoint_pixels(c["keypoint_seed"], W, H, c["n_keypoints"])
+    pts, ok = scenes.backproject(cams["viewmats"][0], cams["intr"][0], px, py, acc_d.cpu().numpy(), W)
+    rng = np.random.default_rng(c["noise_seed"])
+    obs = np.stack([px + 0.5, py + 0.5], 1)[ok] + rng.normal(0, 1.0, (int(ok.sum()), 2))
+    kp = dict(points=torch.as_tensor(pts[ok].astype(np.float32), device=device),
+              obs=torch.as_tensor(obs.astype(np.float32), device=device))
+    E0 = moved(c["init_offset"], E_true)
+    step = TrackingStep(p, cams["intr"], cams["size"], E0.cpu().numpy(), t_rgb, t_depth, keypoints=kp,
+                        w_rpj=c["w_rpj"], w_c=c["w_c"], w_d=c["w_d"], gamma=c["gamma"], device=device)
+    del r
+
+    def reset():
+        step.viewmats.copy_(E0)
+        for b in (step.twist, step.m, step.v, step.step_count):
+            b.zero_()
+
+    iters = c["iters"]
+    for _ in range(3):
+        step.run()
+    torch.cuda.synchronize()
+    # eager: the loop as a tracker launches it
+    reset()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        step.run()
+    e1.record()
+    torch.cuda.synchronize()
+    eager_ms = e0.elapsed_time(e1)
+    # graph: one iteration captured, replayed iters times from the same start
+    graph_ms = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            step.run()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            step.run()
+        reset()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(iters):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        graph_ms = e0.elapsed_time(e1)
+    except Exception as exc:
+        print(f"tracking graph capture failed: {exc}", file=sys.stderr)
+    ms = graph_ms if graph_ms is not None else eager_ms
+    E = step.viewmats.view(3, 4).cpu().numpy().astype(np.float64)
+    Et = cams["viewmats"][0].astype(np.float64)
+    ctr = lambda M: -M[:, :3].T @ M[:, 3]
+    err_cm = 100 * float(np.linalg.norm(ctr(E) - ctr(Et)))
+    err0_cm = 100 * float(np.linalg.norm(ctr(E0.view(3, 4).cpu().numpy().astype(np.float64)) - ctr(Et)))
+    out = {"workload": c["name"], "gaussians": n, "views": 1, "pixels_per_step": W * H, "iterations": iters,
+           "value": W * H * iters / ms / 1e3, "unit": "Mpix/s", "ms_per_loop": ms, "ms_per_iter": ms / iters,
+           "iters_per_s": 1e3 * iters / ms,
+           "timing": ("CUDA graph of one iteration replayed" if graph_ms is not None else "eager launches"),
+           "eager": {"ms_per_loop": eager_ms, "iters_per_s": 1e3 * iters / eager_ms},
+           "pose_centre_error_cm": {"start": err0_cm, "after": err_cm},
+           "status": step.rast.status()}
+    if not args.no_cpu:
+        cpu = oracle_view_sample(c, 0)
+        cpu["iters_per_s"] = cpu["value"] * 1e6 / (W * H)
+        out["cpu_baseline"] = cpu
+    del step
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_configs(args, device):
+    res = {}
+    for tok in args.configs.split(","):
+        tok = tok.strip()
+        if not tok:
+            continue
+        idx = int(tok)
+        t0 = time.perf_counter()
+        res[str(idx)] = (measure_tracking_config(args, device) if idx == 3 else
+                         measure_mapping_config(idx, args, device, with_plain=(idx == 5)))
+        res[str(idx)]["wall_s"] = round(time.perf_counter() - t0, 1)
+    return res
+
+
+# --------------------------------------------------------------------------
 # arms
 # --------------------------------------------------------------------------
 
@@ -544,6 +831,8 @@ def main_ours(args):
         torch.cuda.synchronize()
         return
 
+    # every timed region starts from this map (a step moves the parameters)
+    snap = snapshot(step)
     # timed region 1: eager launches with per-stage events on the launching
     # stream (the stage times); timed region 2 below replays the same step as
     # a CUDA graph, the way a fixed mapping loop runs (the headline value)
@@ -577,6 +866,7 @@ def main_ours(args):
             step.run()
         for _ in range(args.warmup):
             g.replay()
+        restore(step, snap)
         barrier(world)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -590,8 +880,32 @@ def main_ours(args):
         graph_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     except Exception as exc:  # without a graph the eager time is the headline
         graph_ms = None
+        g = None
         print(f"graph capture failed: {exc}", file=sys.stderr)
     clk = clocks.stop()  # sampled over both timed regions
+    # the same graph replayed for about SUSTAIN_S seconds, with its own clock
+    # samples: the step's rate once power and clocks have settled
+    # (in chunks of --steps steps, each from the same map as the headline; the
+    # restores between chunks are outside the timed events)
+    sustained = None
+    if g is not None:
+        n_chunks = max(1, int(SUSTAIN_S * 1e3 / max(graph_ms * args.steps, 1e-3)))
+        clocks2 = ClockSampler(local)
+        clocks2.start()
+        barrier(world)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_chunks)]
+        for a, b in ev:
+            restore(step, snap)
+            a.record()
+            for _ in range(args.steps):
+                g.replay()
+            b.record()
+        torch.cuda.synchronize()
+        sus_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / (n_chunks * args.steps), world)
+        sustained = {"steps": n_chunks * args.steps, "chunks": n_chunks, "seconds": sus_ms * n_chunks * args.steps / 1e3,
+                     "ms_per_step": sus_ms, "value": world * px_per_step / sus_ms / 1e3, "clocks": clocks2.stop()}
+    restore(step, snap)
     ms = graph_ms if graph_ms is not None else eager_ms
 
     # end to end through the public API: host keyframes in, loss out, every
@@ -632,6 +946,7 @@ def main_ours(args):
             parts[1]()
     except Exception as exc:  # eager parts still measure the same path
         print(f"graph capture of the step's parts failed: {exc}", file=sys.stderr)
+    restore(step, snap)
     torch.cuda.synchronize()
     barrier(world)
     # raw keyframes are double-buffered on a copy stream: step i + 1's upload
@@ -684,6 +999,7 @@ def main_ours(args):
         rs = plain_steps(c, step, cap, device)
         for _ in range(2):
             run_plain(c, step, rs)
+        restore(step, snap)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -696,6 +1012,10 @@ def main_ours(args):
         plain = {"value": world * px_per_step / plain_ms / 1e3, "ms_per_step": plain_ms}
         del rs
 
+    # the work of the map the timed regions started from
+    restore(step, snap)
+    step.run()
+    torch.cuda.synchronize()
     w = work_counts(step)
     works = stage_work(w)
     dom = max(stage_ms, key=lambda k: stage_ms[k] if k in works else -1)
@@ -740,6 +1060,13 @@ def main_ours(args):
             with OraclePool(args.workload, args.scale, c["cams"], n_all) as pool:
                 cpu_all = line(pool.sample(args.cpu_seconds), n_all)
 
+    launches = step.kernels_per_step() * args.steps
+    configs = None
+    if not args.no_configs and world == 1 and not args.profile_steps:
+        del step
+        torch.cuda.empty_cache()
+        configs = measure_configs(args, device)
+
     value = world * px_per_step / ms / 1e3
     out = {
         "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
@@ -751,12 +1078,13 @@ def main_ours(args):
                    "gaussian_order": "Morton order of the means (map maintenance at setup)"},
         "iters_per_s": 1e3 / ms,
         "timing": "CUDA graph replay of the step" if graph_ms is not None else "eager launches",
+        "sustained": sustained,
         "eager": {"ms_per_step": eager_ms, "value": world * px_per_step / eager_ms / 1e3},
         "plain": plain,
         "batched_vs_plain": None if plain is None else plain["ms_per_step"] / eager_ms,
         "e2e": {"value": world * px_per_step / e2e_ms / 1e3, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 4},
-        "gpu_launches": step.kernels_per_step() * args.steps,
+        "gpu_launches": launches,
         "tuned": tuned,
         "stages": stages,
         "work": w,
@@ -766,6 +1094,7 @@ def main_ours(args):
         "clocks": clk,
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,
+        "configs": configs,
     }
     if rank == 0:
         print(json.dumps(out))
