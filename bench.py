@@ -211,7 +211,7 @@ def plain_steps(c, step, cap, device):
     rs = []
     for v in range(len(cams["size"])):
         r = gs.Rasterizer(step.flat.n, step.flat.sh_degree, cams["intr"][v:v + 1], cams["size"][v:v + 1],
-                          max(1 << 20, cap // len(cams["size"]) * 2), device)
+                          max(1 << 20, cap // len(cams["size"]) * 2), device, tile=step.rast.tile)
         rs.append(r)
     return rs
 
@@ -579,12 +579,12 @@ def measure_mapping_config(idx, args, device, with_plain):
     dominant stage against its roofline; optionally one view per launch."""
     import torch
 
-    from paper_2405_19614_gb300.autotune import tune
+    from paper_2405_19614_gb300.autotune import tune_tiles
     c, step, cap = build_workload(idx, 1.0, device)
     P = step.rast.n_pix
     step.run()
     torch.cuda.synchronize()
-    tuned = tune(step.rast, step.params, step.viewmats, step.d_rgb, step.d_depth, use_cache=False)
+    step.rast, tuned = tune_tiles(step.rast, step.params, step.viewmats, step.d_rgb, step.d_depth)
     steps = max(args.steps, 20 if P > 100_000 else 200)
     for _ in range(max(3, args.warmup)):
         step.run()
@@ -613,13 +613,14 @@ def measure_mapping_config(idx, args, device, with_plain):
     floor = sum(works[k][1] / (hbm_peak * 1e9 if works[k][0] == "hbm" else alu_peak * 1e12) * 1e3
                 for k in stage_ms if k in works)
     out = {"workload": c["name"], "gaussians": w["N"], "views": w["V"], "pixels_per_step": P, "pairs": w["K"],
+           "tile": list(step.rast.tile),
            "value": P / ms / 1e3, "unit": "Mpix/s", "ms_per_step": ms, "iters_per_s": 1e3 / ms,
            "timing": "CUDA graph replay of the step", "steps": steps,
            "eager": {"ms_per_step": eager_ms, "value": P / eager_ms / 1e3},
            "stages": {k: round(v, 4) for k, v in stage_ms.items()},
            "roofline": dict(stage_roofline(dom, stage_ms, works, hbm_peak, alu_peak), kernel=dom),
            "roofline_step": {"floor_ms": floor, "ms": ms, "frac": floor / ms},
-           "tuned": None if tuned is None else {"fwd": tuned["fwd"], "bwd": tuned["bwd"]}}
+           "tuned": tuned}
     if with_plain and step.rast.V > 1:
         rs = plain_steps(c, step, cap, device)
         for _ in range(2):
@@ -814,12 +815,12 @@ def main_ours(args):
 
     # warm-up (also sets kernel attributes before any capture), then pick the
     # compositing variants on this workload (setup, not timed)
-    from paper_2405_19614_gb300.autotune import tune
+    from paper_2405_19614_gb300.autotune import tune_tiles
     step.run()
     torch.cuda.synchronize()
     tuned = None
     if not args.no_tune and not args.profile_steps:
-        tuned = tune(step.rast, step.params, step.viewmats, step.d_rgb, step.d_depth, use_cache=False)
+        step.rast, tuned = tune_tiles(step.rast, step.params, step.viewmats, step.d_rgb, step.d_depth)
     for _ in range(max(1, args.warmup)):
         step.run()
     torch.cuda.synchronize()
@@ -1061,6 +1062,7 @@ def main_ours(args):
                 cpu_all = line(pool.sample(args.cpu_seconds), n_all)
 
     launches = step.kernels_per_step() * args.steps
+    step_tile = step.rast.tile
     configs = None
     if not args.no_configs and world == 1 and not args.profile_steps:
         del step
@@ -1075,7 +1077,8 @@ def main_ours(args):
         "config": {"workload": c["name"], "gaussians": w["N"], "views": w["V"], "pixels_per_step": px_per_step,
                    "pairs": w["K"], "visible": w["V_vis"], "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (params 236 MB + pair arrays), no flush",
-                   "gaussian_order": "Morton order of the means (map maintenance at setup)"},
+                   "gaussian_order": "Morton order of the means (map maintenance at setup)",
+                   "tile": list(step_tile)},
         "iters_per_s": 1e3 / ms,
         "timing": "CUDA graph replay of the step" if graph_ms is not None else "eager launches",
         "sustained": sustained,

@@ -19,7 +19,8 @@
  *    Per-view arrays are concatenated: projected records and radii at
  *    [v * n + i]; pixels at pix_base[v] + y * width + x with pix_base the
  *    running sum of width*height; tiles at tile_base[v] + ty * tiles_x + tx with
- *    tile_base the running sum of tiles_x * tiles_y.
+ *    tile_base the running sum of tiles_x * tiles_y, tiles_x = ceil(width /
+ *    tile_w) and tiles_y = ceil(height / tile_h) for the view's tile shape.
  *  - Pixel (x, y) is sampled at (x + 0.5, y + 0.5); u = fx * X/Z + cx.
  *  - Poses are world -> camera row-major 3x4 [R | t] (device, FP32) so that an
  *    on-device pose update needs no host round trip; the twist is
@@ -36,7 +37,7 @@ extern "C" {
 #endif
 
 #define GS_MAX_VIEWS 64
-#define GS_TILE 16 /* tiles are 16 x 16 pixels */
+#define GS_TILE 16 /* default tile width and height in pixels */
 
 typedef enum {
     GS_OK = 0,
@@ -48,9 +49,16 @@ typedef enum {
 } gs_status_t;
 
 /* Host-side camera intrinsics and image size (Sec. 3.4 "Projection": K). */
+/* A view: pinhole intrinsics, image size and the tile shape that bins and
+ * composites it (Sec. 3.4 "Differentiable Rasterization" sorts Gaussians per
+ * screen tile; the shape is this library's choice, picked by its autotuner).
+ * tile_w, tile_h: 8, 16, 32 or 64 pixels with tile_w * tile_h <= 2048, or 0
+ * for GS_TILE.  Every call that takes the views of one configuration must
+ * get the same tile shapes (they define the tile ids and ranges). */
 typedef struct {
     float fx, fy, cx, cy;
     int32_t width, height;
+    int32_t tile_w, tile_h;
 } gs_view_t;
 
 /* Gaussian parameters, structure of arrays (Sec. 3.4 "Gaussian

@@ -23,7 +23,7 @@ __all__ = ["gs_get_device_status", "gs_workspace_size", "gs_check_lookback_timeo
            "gs_get_render_variants", "gs_loss_l1", "gs_loss_ssim", "gs_render_bwd", "gs_render_bwd_splats",
            "gs_project_bwd", "gs_decode_keyframes", "gs_reproj_loss_grad", "gs_adam_step", "gs_pose_update", "gs_densify",
            "gs_prune_select", "gs_compact_rows", "gs_spatial_order_workspace_size", "gs_spatial_order",
-           "gs_select_views", "Rasterizer", "rasterize",
+           "gs_select_views", "Rasterizer", "rasterize", "make_views", "variant_fits",
            "GsError", "lib"]
 
 
@@ -46,16 +46,28 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def make_views(intr, size):
-    """ctypes array of gs_view_t from intr [V,4] (fx, fy, cx, cy) and size [V,2]."""
+def make_views(intr, size, tile=None):
+    """ctypes array of gs_view_t from intr [V,4] (fx, fy, cx, cy), size [V,2]
+    and the tile shape (tile_w, tile_h) of every view (None: the default)."""
     intr = [[float(x) for x in row] for row in (intr.tolist() if hasattr(intr, "tolist") else intr)]
     size = [[int(x) for x in row] for row in (size.tolist() if hasattr(size, "tolist") else size)]
+    tw, th = (0, 0) if tile is None else (int(tile[0]), int(tile[1]))
     V = len(intr)
     arr = (GsView * V)()
     for v in range(V):
         arr[v].fx, arr[v].fy, arr[v].cx, arr[v].cy = intr[v]
         arr[v].width, arr[v].height = size[v]
+        arr[v].tile_w, arr[v].tile_h = tw, th
     return arr
+
+
+def variant_fits(variant, tile):
+    """Whether a compositing variant's band divides the tile (else the library
+    uses the (2, 8) band with the variant's chunk size)."""
+    base = variant % _lib.N_BAND_VARIANTS
+    bw = _lib.VARIANT_BW[base]
+    bh = _lib.VARIANT_PPT[base] * (32 // bw)
+    return tile[0] % bw == 0 and tile[1] % bh == 0
 
 
 def _params(p):
@@ -294,9 +306,9 @@ def gs_select_views(matches, totals, alpha=0.75, beta=20):
 # buffer owner for one configuration
 # --------------------------------------------------------------------------
 
-def _layout(size):
-    ntx = [(int(w) + GS_TILE - 1) // GS_TILE for w, _ in size]
-    nty = [(int(h) + GS_TILE - 1) // GS_TILE for _, h in size]
+def _layout(size, tile=(GS_TILE, GS_TILE)):
+    ntx = [(int(w) + tile[0] - 1) // tile[0] for w, _ in size]
+    nty = [(int(h) + tile[1] - 1) // tile[1] for _, h in size]
     n_tiles = sum(a * b for a, b in zip(ntx, nty))
     n_pix = sum(int(w) * int(h) for w, h in size)
     return n_tiles, n_pix
@@ -309,18 +321,26 @@ class Rasterizer:
     forward; ``generation`` counts the forwards run, so a caller holding an
     older result can tell that the buffers no longer hold it."""
 
-    def __init__(self, n, sh_degree, intr, size, pair_capacity=None, device="cuda", near_z=0.2, blur=0.3):
+    def __init__(self, n, sh_degree, intr, size, pair_capacity=None, device="cuda", near_z=0.2, blur=0.3,
+                 tile=(GS_TILE, GS_TILE)):
         self.n, self.sh_degree = int(n), int(sh_degree)
         self.size = [(int(w), int(h)) for w, h in (size.tolist() if hasattr(size, "tolist") else size)]
-        self.views = make_views(intr, self.size)
+        self.intr = [[float(x) for x in row] for row in (intr.tolist() if hasattr(intr, "tolist") else intr)]
+        self.tile = (int(tile[0]), int(tile[1]))
+        if self.tile[0] not in _lib.TILE_SIDES or self.tile[1] not in _lib.TILE_SIDES or \
+                self.tile[0] * self.tile[1] > 2048:
+            raise GsError(f"tile sides must be 8, 16, 32 or 64 with at most 2048 pixels, not {self.tile}")
+        self.views = make_views(self.intr, self.size, self.tile)
         self.V = len(self.size)
         if not 1 <= self.V <= GS_MAX_VIEWS:
             raise GsError(f"between 1 and {GS_MAX_VIEWS} views")
         self.near_z, self.blur = float(near_z), float(blur)
-        self.n_tiles, self.n_pix = _layout(self.size)
+        self.device = device
+        self.n_tiles, self.n_pix = _layout(self.size, self.tile)
         if pair_capacity is None:
             pair_capacity = max(1 << 16, 8 * self.n * self.V)
         self.capacity = int(min(pair_capacity, (1 << 30) - 1))
+        self.pair_capacity = pair_capacity
         d = torch.device(device)
         R = self.V * self.n
         i32, f32 = torch.int32, torch.float32

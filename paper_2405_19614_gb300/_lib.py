@@ -14,7 +14,11 @@ LIB_PATH = os.path.join(_PKG, "libgs.so")
 c_f, c_i32, c_i64, c_p, c_sz = ctypes.c_float, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t
 
 GS_MAX_VIEWS = 64
-GS_TILE = 16
+GS_TILE = 16  # default tile side
+TILE_SIDES = (8, 16, 32, 64)
+N_BAND_VARIANTS = 6
+VARIANT_PPT = (1, 2, 2, 4, 4, 8)
+VARIANT_BW = (8, 8, 16, 8, 16, 16)
 GS_MAX_ADAM_GROUPS = 8
 STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CUDA", 3: "GS_ERR_CAPACITY", 4: "GS_ERR_TIMEOUT",
           5: "GS_ERR_UNSUPPORTED"}
@@ -23,7 +27,8 @@ GS_OP_BIN_SORT, GS_OP_GRAD2D, GS_OP_SSIM, GS_OP_SELECT, GS_OP_SPATIAL_ORDER, GS_
 
 
 class GsView(ctypes.Structure):
-    _fields_ = [("fx", c_f), ("fy", c_f), ("cx", c_f), ("cy", c_f), ("width", c_i32), ("height", c_i32)]
+    _fields_ = [("fx", c_f), ("fy", c_f), ("cx", c_f), ("cy", c_f), ("width", c_i32), ("height", c_i32),
+                ("tile_w", c_i32), ("tile_h", c_i32)]
 
 
 class GsParams(ctypes.Structure):

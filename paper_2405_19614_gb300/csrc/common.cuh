@@ -8,16 +8,18 @@
 
 namespace gs {
 
-constexpr int kTile = GS_TILE;              // 16 x 16 pixel tiles
-constexpr int kTilePix = kTile * kTile;     // 256 pixels = 256 threads per render block
+constexpr int kTile = GS_TILE;              // default tile width and height
 constexpr uint32_t kFullMask = 0xffffffffu;
 
 // Per-view constants passed by value to kernels.
 struct ViewInfo {
     float fx, fy, cx, cy;
     int32_t width, height, tiles_x, tiles_y;
-    int32_t tile_base, pad;
+    int32_t tile_base;
+    int16_t tile_w, tile_h;  // tile shape in pixels
     int64_t pix_base;
+    int32_t item_base;  // first compositing work item of the view (set by the launcher)
+    int32_t pad;
 };
 
 struct ViewTable {
@@ -27,7 +29,10 @@ struct ViewTable {
     ViewInfo v[GS_MAX_VIEWS];
 };
 
-static_assert(sizeof(ViewTable) <= 3200, "view table must fit in kernel parameters");
+static_assert(sizeof(ViewTable) <= 3700, "view table must fit in kernel parameters with the other arguments");
+
+// A tile side: 8, 16, 32 or 64 pixels (0 means the default).
+inline bool valid_tile_side(int32_t t) { return t == 8 || t == 16 || t == 32 || t == 64; }
 
 inline gs_status_t make_view_table(const gs_view_t *views, int32_t n_views, ViewTable *vt)
 {
@@ -38,6 +43,8 @@ inline gs_status_t make_view_table(const gs_view_t *views, int32_t n_views, View
         const gs_view_t &s = views[i];
         if (s.width <= 0 || s.height <= 0 || s.width > (1 << 20) || s.height > (1 << 20)) return GS_ERR_INVALID_ARG;
         if (!(s.fx > 0.0f) || !(s.fy > 0.0f)) return GS_ERR_INVALID_ARG;
+        const int32_t tw = s.tile_w ? s.tile_w : kTile, th = s.tile_h ? s.tile_h : kTile;
+        if (!valid_tile_side(tw) || !valid_tile_side(th) || tw * th > 2048) return GS_ERR_INVALID_ARG;
         ViewInfo &d = vt->v[i];
         d.fx = s.fx;
         d.fy = s.fy;
@@ -45,14 +52,17 @@ inline gs_status_t make_view_table(const gs_view_t *views, int32_t n_views, View
         d.cy = s.cy;
         d.width = s.width;
         d.height = s.height;
-        d.tiles_x = (s.width + kTile - 1) / kTile;
-        d.tiles_y = (s.height + kTile - 1) / kTile;
+        d.tile_w = (int16_t)tw;
+        d.tile_h = (int16_t)th;
+        d.tiles_x = (s.width + tw - 1) / tw;
+        d.tiles_y = (s.height + th - 1) / th;
         d.tile_base = (int32_t)tiles;
+        d.item_base = 0;
         d.pad = 0;
         d.pix_base = pix;
         tiles += (int64_t)d.tiles_x * d.tiles_y;
         pix += (int64_t)s.width * s.height;
-        if (tiles >= (int64_t(1) << 31)) return GS_ERR_INVALID_ARG;
+        if (tiles >= (int64_t(1) << 31) || pix >= (int64_t(1) << 35)) return GS_ERR_INVALID_ARG;
     }
     vt->n_tiles_total = (int32_t)tiles;
     vt->n_pix_total = pix;
@@ -66,6 +76,16 @@ __device__ __forceinline__ int view_of_tile(const ViewTable &vt, int tile)
     #pragma unroll 1
     for (int k = 1; k < vt.n_views; k++)
         if (tile >= vt.v[k].tile_base) v = k;
+    return v;
+}
+
+// View that owns a compositing work item.
+__device__ __forceinline__ int view_of_item(const ViewTable &vt, int item)
+{
+    int v = 0;
+    #pragma unroll 1
+    for (int k = 1; k < vt.n_views; k++)
+        if (item >= vt.v[k].item_base) v = k;
     return v;
 }
 

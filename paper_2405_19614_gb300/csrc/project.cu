@@ -160,9 +160,10 @@ __device__ __forceinline__ bool geometry(const float m[3], const float ls[3], co
     float v = ADD(DIV(MUL(V.fy, y), z), V.cy);
     if (!(fabsf(u) < 0x1p24f && fabsf(v) < 0x1p24f && rad < 0x1p24f)) return false;
 
-    const float tw = (float)kTile;
+    // tile sides are powers of two, so these quotients are exact
+    const float tw = (float)V.tile_w, th = (float)V.tile_h;
     float fx0 = floorf(DIV(SUB(u, rad), tw)), fx1 = floorf(DIV(ADD(u, rad), tw));
-    float fy0 = floorf(DIV(SUB(v, rad), tw)), fy1 = floorf(DIV(ADD(v, rad), tw));
+    float fy0 = floorf(DIV(SUB(v, rad), th)), fy1 = floorf(DIV(ADD(v, rad), th));
     fx0 = fmaxf(fx0, 0.0f);
     fy0 = fmaxf(fy0, 0.0f);
     fx1 = fminf(fx1, (float)(V.tiles_x - 1));

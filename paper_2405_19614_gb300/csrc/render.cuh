@@ -124,13 +124,42 @@ struct RenderOccupancy {
     static constexpr int bwd = PPT <= 2 ? 8 : PPT == 4 ? GS_BWD_BLOCKS_PPT4 : 4;
 };
 
-// Kernel variants the autotuner picks from, as (pixels per thread, band
-// width): (1, 8) (2, 8) (2, 16) (4, 8) (4, 16) (8, 16).  A warp's band is
-// BW x PPT * 32 / BW pixels; a thread's pixels share a column, 32 / BW rows
+// Kernel variants the autotuner picks from: a band shape as (pixels per
+// thread, band width) (1, 8) (2, 8) (2, 16) (4, 8) (4, 16) (8, 16), each with a
+// staged chunk of 32 (variants 0-5) or 64 list entries (6-11).  A warp's band
+// is BW x PPT * 32 / BW pixels; a thread's pixels share a column, 32 / BW rows
 // apart.
-constexpr int kFwdVariants = 6;
-constexpr int kBwdVariants = 6;
+constexpr int kBandVariants = 6;
+constexpr int kFwdVariants = 2 * kBandVariants;
+constexpr int kBwdVariants = 2 * kBandVariants;
+constexpr int kVariantPPT[kBandVariants] = {1, 2, 2, 4, 4, 8};
+constexpr int kVariantBW[kBandVariants] = {8, 8, 16, 8, 16, 16};
 int render_variant_fwd();
 int render_variant_bwd();
+
+// The variant a launch uses: var when its band divides the tile of every view,
+// else the (2, 8) band (8 x 8 pixels, which divides every allowed tile) with
+// var's chunk size.
+inline int fitting_variant(const ViewTable &vt, int var)
+{
+    const int base = var % kBandVariants, ch = var / kBandVariants;
+    const int bw = kVariantBW[base], bh = kVariantPPT[base] * (32 / bw);
+    for (int k = 0; k < vt.n_views; k++)
+        if (vt.v[k].tile_w % bw || vt.v[k].tile_h % bh) return 1 + ch * kBandVariants;
+    return var;
+}
+
+// Sets each view's first work item for bands of bw x bh pixels (work items
+// are the bands of every tile, view by view) and returns the total.
+inline uint32_t render_items(ViewTable *vt, int bw, int bh)
+{
+    int64_t items = 0;
+    for (int k = 0; k < vt->n_views; k++) {
+        ViewInfo &V = vt->v[k];
+        V.item_base = (int32_t)items;
+        items += (int64_t)V.tiles_x * V.tiles_y * (V.tile_w / bw) * (V.tile_h / bh);
+    }
+    return (uint32_t)items;
+}
 
 }  // namespace gs

@@ -47,6 +47,7 @@ struct RenderBwdArgs {
     const float *d_rgb, *d_depth, *d_alpha;
     float *grad2d;
     uint32_t *work_counter;
+    uint32_t n_items;  // (view, tile, band) work items, set by the launcher
 };
 
 constexpr int kAcc = 10;
@@ -77,33 +78,35 @@ __device__ __forceinline__ void load_bwd_entry(const RenderBwdArgs &a, int64_t r
     }
 }
 
-template <int PPT, int BW>
+template <int PPT, int BW, int CH>
 __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
     render_bwd_kernel(RenderBwdArgs a, ViewTable vt)
 {
     constexpr int WARPS = kRenderThreads / 32;
-    constexpr int RS = 32 / BW;                  // rows between a thread's pixels
-    constexpr int BH = PPT * RS;                 // band height (width BW)
-    constexpr int BANDS_X = kTile / BW;
-    constexpr int BANDS = BANDS_X * (kTile / BH);  // bands per tile
-    __shared__ float4 s_rec[WARPS][3][32];
-    __shared__ uint32_t s_gid[WARPS][32];
+    constexpr int RS = 32 / BW;   // rows between a thread's pixels
+    constexpr int BH = PPT * RS;  // band height (width BW)
+    constexpr int NC = CH / 32;   // entries a lane stages per chunk
+    __shared__ float4 s_rec[WARPS][3][CH];
+    __shared__ uint32_t s_gid[WARPS][CH];
     __shared__ __align__(16) float s_red[WARPS][kRedRows][kRedPitch];
     __shared__ uint32_t s_bgid[WARPS][kBatch];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t n_items = (uint32_t)vt.n_tiles_total * BANDS;
     const int red_entry = lane / kAcc, red_value = lane % kAcc;  // the row this lane adds up
     for (;;) {
         uint32_t wi = 0;
         if (lane == 0) wi = atomicAdd(a.work_counter, 1u);
         wi = __shfl_sync(kFullMask, wi, 0);
-        if (wi >= n_items) break;
-        const int item = (int)(wi / BANDS), band = (int)(wi % BANDS);
-        const int bxo = (band % BANDS_X) * BW, byo = (band / BANDS_X) * BH;  // band origin in the tile
-        const int v = view_of_tile(vt, item);
+        if (wi >= a.n_items) break;
+        // work item -> view, tile of the view, band of the tile
+        const int v = view_of_item(vt, (int)wi);
         const ViewInfo &V = vt.v[v];
-        const int lt = item - V.tile_base;
-        const int tx0 = (lt % V.tiles_x) * kTile, ty0 = (lt / V.tiles_x) * kTile;
+        // tile sides and band sides are powers of two: the band index splits by shifts
+        const int sx_shift = __ffs(V.tile_w) - __ffs(BW), sb_shift = sx_shift + __ffs(V.tile_h) - __ffs(BH);
+        const int local = (int)wi - V.item_base;
+        const int lt = local >> sb_shift, band = local & ((1 << sb_shift) - 1);
+        const int item = V.tile_base + lt;  // global tile id
+        const int bxo = (band & ((1 << sx_shift) - 1)) * BW, byo = (band >> sx_shift) * BH;  // band origin in the tile
+        const int tx0 = (lt % V.tiles_x) * V.tile_w, ty0 = (lt / V.tiles_x) * V.tile_h;
         const int px = tx0 + bxo + lane % BW;
         const int py0 = ty0 + byo + lane / BW;  // this thread's rows: py0 + RS k
         const float sx = (float)px + 0.5f;
@@ -172,37 +175,50 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
         }
         const uint32_t warp_last = __reduce_max_sync(kFullMask, my_last);
 
-        // chunks [lo, hi) of the list, from the warp's last blend down to 0
+        // chunks [lo, hi) of the list, from the warp's last blend down to 0,
+        // CH entries a chunk; within a chunk the entries are taken from the
+        // highest index down
         uint32_t hi = warp_last;
-        uint32_t lo = hi > 32u ? hi - 32u : 0u;
-        float4 n0, n1, n2;
-        uint32_t ng;
-        load_bwd_entry(a, rbase, b + lo + lane, lo + lane < hi, n0, n1, n2, ng);
+        uint32_t lo = hi > (uint32_t)CH ? hi - CH : 0u;
+        float4 n0[NC], n1[NC], n2[NC];
+        uint32_t ng[NC];
+        #pragma unroll
+        for (int c = 0; c < NC; c++)
+            load_bwd_entry(a, rbase, b + lo + 32 * c + lane, lo + 32 * c + lane < hi, n0[c], n1[c], n2[c], ng[c]);
         while (hi > 0) {
-            const float4 r0 = n0, r1 = n1, r2 = n2;
-            const uint32_t g_self = ng;
-            const bool have = lo + lane < hi;
-            const uint32_t nlo = lo > 32u ? lo - 32u : 0u;
-            if (lo > 0) load_bwd_entry(a, rbase, b + nlo + lane, nlo + lane < lo, n0, n1, n2, ng);
-            uint32_t todo = __ballot_sync(kFullMask, have && !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
+            const uint32_t nlo = lo > (uint32_t)CH ? lo - CH : 0u;
+            uint32_t todo[NC];
             __syncwarp();  // the previous chunk's records have been read
-            s_rec[warp][0][lane] = r0;
-            s_rec[warp][1][lane] = r1;
-            s_rec[warp][2][lane] = r2;
-            s_gid[warp][lane] = g_self;
+            #pragma unroll
+            for (int c = 0; c < NC; c++) {
+                const float4 r0 = n0[c], r1 = n1[c], r2 = n2[c];
+                const uint32_t g_self = ng[c];
+                const bool have = lo + 32 * c + lane < hi;
+                if (lo > 0)
+                    load_bwd_entry(a, rbase, b + nlo + 32 * c + lane, nlo + 32 * c + lane < lo, n0[c], n1[c], n2[c],
+                                   ng[c]);
+                todo[c] = __ballot_sync(kFullMask, have && !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
+                s_rec[warp][0][32 * c + lane] = r0;
+                s_rec[warp][1][32 * c + lane] = r1;
+                s_rec[warp][2][32 * c + lane] = r2;
+                s_gid[warp][32 * c + lane] = g_self;
+            }
             __syncwarp();
-            while (todo) {
-                const int bit = 31 - __clz(todo);
-                todo &= ~(1u << bit);
-                const uint32_t pos = lo + (uint32_t)bit;
+            #pragma unroll
+            for (int cc = NC - 1; cc >= 0; cc--)
+            while (todo[cc]) {
+                const int bit = 31 - __clz(todo[cc]);
+                todo[cc] &= ~(1u << bit);
+                const int slot = 32 * cc + bit;
+                const uint32_t pos = lo + (uint32_t)slot;
                 // per pixel pair: colour (3) and depth gradients, and the sums
                 // G, S1, S2 (of t = dL/dalpha o g), accumulated two pixels at a time
                 float2 gc[4] = {f2(0.f), f2(0.f), f2(0.f), f2(0.f)};
                 float2 G2 = f2(0.f), S12 = f2(0.f), S22 = f2(0.f);
                 bool contrib = false;
-                const float4 p = s_rec[warp][0][bit];
-                const float4 c = s_rec[warp][1][bit];
-                const float4 col = s_rec[warp][2][bit];
+                const float4 p = s_rec[warp][0][slot];
+                const float4 c = s_rec[warp][1][slot];
+                const float4 col = s_rec[warp][2][slot];
                 const SplatColumn kc = splat_column(p, c, sx);
                 if (pos < my_last) {
                     // the blend tests of all the thread's pixels first, then the
@@ -269,7 +285,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
                     gr[9] = gc[3].x + gc[3].y;
                     #pragma unroll
                     for (int k = 0; k < kAcc; k++) s_red[warp][nb * kAcc + k][lane] = gr[k];
-                    if (lane == 0) s_bgid[warp][nb] = s_gid[warp][bit];
+                    if (lane == 0) s_bgid[warp][nb] = s_gid[warp][slot];
                     if (++nb == kBatch) flush();
                 }
             }
@@ -280,18 +296,32 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
     }
 }
 
-template <int PPT, int BW>
-static gs_status_t launch_bwd(const RenderBwdArgs &a, const ViewTable &vt, cudaStream_t s)
+template <int PPT, int BW, int CH>
+static gs_status_t launch_bwd(RenderBwdArgs a, ViewTable vt, cudaStream_t s)
 {
-    auto kern = render_bwd_kernel<PPT, BW>;
+    // work items: the bands of every tile of every view (tile shapes are per view)
+    a.n_items = render_items(&vt, BW, PPT * (32 / BW));
+    auto kern = render_bwd_kernel<PPT, BW, CH>;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, 0);
     const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-    const int64_t warps_needed = (int64_t)vt.n_tiles_total * (kTile / BW) * (kTile / (PPT * (32 / BW)));
-    const int64_t blocks_needed = (warps_needed + kRenderThreads / 32 - 1) / (kRenderThreads / 32);
+    const int64_t blocks_needed = ((int64_t)a.n_items + kRenderThreads / 32 - 1) / (kRenderThreads / 32);
     const int grid = (int)(slots < blocks_needed ? slots : blocks_needed);
     kern<<<grid > 0 ? grid : 1, kRenderThreads, 0, s>>>(a, vt);
     return launch_status();
+}
+
+template <int CH>
+static gs_status_t dispatch_bwd_ch(int base, const RenderBwdArgs &a, const ViewTable &vt, cudaStream_t s)
+{
+    switch (base) {
+    case 0: return launch_bwd<1, 8, CH>(a, vt, s);
+    case 1: return launch_bwd<2, 8, CH>(a, vt, s);
+    case 2: return launch_bwd<2, 16, CH>(a, vt, s);
+    case 3: return launch_bwd<4, 8, CH>(a, vt, s);
+    case 4: return launch_bwd<4, 16, CH>(a, vt, s);
+    default: return launch_bwd<8, 16, CH>(a, vt, s);
+    }
 }
 
 }  // namespace gs
@@ -318,7 +348,7 @@ extern "C" gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t 
     if (reinterpret_cast<uintptr_t>(grad2d) & 15) return GS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     if (cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
-    RenderBwdArgs a;
+    RenderBwdArgs a = {};
     a.rec = reinterpret_cast<const float4 *>(proj->rec);
     a.n = n;
     a.vals = bins->vals;
@@ -330,12 +360,6 @@ extern "C" gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t 
     a.d_alpha = d_alpha;
     a.grad2d = grad2d;
     a.work_counter = work_counter;
-    switch (render_variant_bwd()) {
-    case 0: return launch_bwd<1, 8>(a, vt, s);
-    case 1: return launch_bwd<2, 8>(a, vt, s);
-    case 2: return launch_bwd<2, 16>(a, vt, s);
-    case 3: return launch_bwd<4, 8>(a, vt, s);
-    case 4: return launch_bwd<4, 16>(a, vt, s);
-    default: return launch_bwd<8, 16>(a, vt, s);
-    }
+    const int var = fitting_variant(vt, render_variant_bwd());
+    return var < kBandVariants ? dispatch_bwd_ch<32>(var, a, vt, s) : dispatch_bwd_ch<64>(var - kBandVariants, a, vt, s);
 }

@@ -27,6 +27,7 @@ struct RenderFwdArgs {
     uint32_t *n_contrib;
     uint32_t *n_eval, *n_blend;  // STATS variant only
     uint32_t *work_counter;
+    uint32_t n_items;  // (view, tile, band) work items, set by the launcher
     // LOSS variant only: the L1 terms of a6 evaluated as each pixel finishes
     const float *trgb, *tdepth;
     float kc, kd, gamma;
@@ -52,32 +53,35 @@ __device__ __forceinline__ void load_entry(const RenderFwdArgs &a, int64_t rbase
 
 // STATS = true counts, per pixel, the list entries evaluated and blended (the
 // algorithmic work of the compositing, without culling) instead of writing the
-// image.
-template <int PPT, int BW, bool STATS, bool LOSS>
+// image.  CH list entries (32 or 64: one or two a lane) are loaded, culled and
+// staged together; the next CH are loaded while they are walked.
+template <int PPT, int BW, int CH, bool STATS, bool LOSS>
 __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) render_fwd_kernel(RenderFwdArgs a,
                                                                                              ViewTable vt)
 {
     __shared__ float s_loss[kRenderThreads / 32];
     float lacc = 0.0f;  // LOSS: this thread's share of the loss
     constexpr int WARPS = kRenderThreads / 32;
-    constexpr int RS = 32 / BW;                  // rows between a thread's pixels
-    constexpr int BH = PPT * RS;                 // band height (width BW)
-    constexpr int BANDS_X = kTile / BW;
-    constexpr int BANDS = BANDS_X * (kTile / BH);  // bands per tile
-    __shared__ float4 s_rec[WARPS][3][32];  // (u, v, z, log2 o), (base-2 conic, du), (rgb, dv) of a chunk
+    constexpr int RS = 32 / BW;   // rows between a thread's pixels
+    constexpr int BH = PPT * RS;  // band height (width BW)
+    constexpr int NC = CH / 32;   // entries a lane stages per chunk
+    __shared__ float4 s_rec[WARPS][3][CH];  // (u, v, z, log2 o), (base-2 conic, du), (rgb, dv) of a chunk
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t n_items = (uint32_t)vt.n_tiles_total * BANDS;
     for (;;) {
         uint32_t wi = 0;
         if (lane == 0) wi = atomicAdd(a.work_counter, 1u);
         wi = __shfl_sync(kFullMask, wi, 0);
-        if (wi >= n_items) break;
-        const int item = (int)(wi / BANDS), band = (int)(wi % BANDS);
-        const int bxo = (band % BANDS_X) * BW, byo = (band / BANDS_X) * BH;  // band origin in the tile
-        const int v = view_of_tile(vt, item);
+        if (wi >= a.n_items) break;
+        // work item -> view, tile of the view, band of the tile
+        const int v = view_of_item(vt, (int)wi);
         const ViewInfo &V = vt.v[v];
-        const int lt = item - V.tile_base;
-        const int tx0 = (lt % V.tiles_x) * kTile, ty0 = (lt / V.tiles_x) * kTile;
+        // tile sides and band sides are powers of two: the band index splits by shifts
+        const int sx_shift = __ffs(V.tile_w) - __ffs(BW), sb_shift = sx_shift + __ffs(V.tile_h) - __ffs(BH);
+        const int local = (int)wi - V.item_base;
+        const int lt = local >> sb_shift, band = local & ((1 << sb_shift) - 1);
+        const int item = V.tile_base + lt;  // global tile id
+        const int bxo = (band & ((1 << sx_shift) - 1)) * BW, byo = (band >> sx_shift) * BH;  // band origin in the tile
+        const int tx0 = (lt % V.tiles_x) * V.tile_w, ty0 = (lt / V.tiles_x) * V.tile_h;
         const int px = tx0 + bxo + lane % BW;
         const int py0 = ty0 + byo + lane / BW;  // this thread's rows: py0 + RS k
         const float sx = (float)px + 0.5f;
@@ -106,61 +110,75 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
             live[k] = k < PPT && px < V.width && (py0 + RS * k) < V.height;
             alive += live[k];
         }
-        float4 n0, n1, n2;  // this lane's entry of the next chunk
-        load_entry(a, rbase, b + lane, e, n0, n1, n2);
-        for (uint32_t m = b; m < e; m += 32) {
+        float4 n0[NC], n1[NC], n2[NC];  // this lane's entries of the next chunk
+        #pragma unroll
+        for (int c = 0; c < NC; c++) load_entry(a, rbase, b + 32 * c + lane, e, n0[c], n1[c], n2[c]);
+        for (uint32_t m = b; m < e; m += CH) {
             if (!__any_sync(kFullMask, alive > 0)) break;
-            const float4 r0 = n0, r1 = n1, r2 = n2;
-            const bool have = m + lane < e;
-            if (m + 32 < e) load_entry(a, rbase, m + 32 + lane, e, n0, n1, n2);
-            const bool keep = have && (STATS || !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
-            uint32_t todo = __ballot_sync(kFullMask, keep);
-            if (alive == 0) todo = 0;
+            uint32_t todo[NC];
             __syncwarp();  // the previous chunk's records have been read
-            s_rec[warp][0][lane] = r0;
-            s_rec[warp][1][lane] = r1;
-            s_rec[warp][2][lane] = r2;
+            #pragma unroll
+            for (int c = 0; c < NC; c++) {
+                const float4 r0 = n0[c], r1 = n1[c], r2 = n2[c];
+                const bool have = m + 32 * c + lane < e;
+                if (m + CH < e) load_entry(a, rbase, m + CH + 32 * c + lane, e, n0[c], n1[c], n2[c]);
+                const bool keep = have && (STATS || !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
+                todo[c] = __ballot_sync(kFullMask, keep);
+                if (alive == 0) todo[c] = 0;
+                s_rec[warp][0][32 * c + lane] = r0;
+                s_rec[warp][1][32 * c + lane] = r1;
+                s_rec[warp][2][32 * c + lane] = r2;
+            }
             __syncwarp();
-            while (todo) {
-                const int j = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const float4 p = s_rec[warp][0][j];
-                const float4 c = s_rec[warp][1][j];
-                const float4 col = s_rec[warp][2][j];
-                const SplatColumn kc = splat_column(p, c, sx);
-                // two pixels per packed evaluation and update; branch-free per
-                // pixel (a skipped pixel adds exactly zero), so the chains interleave
-                #pragma unroll
-                for (int i = 0; i < NP; i++) {
-                    float2 dy;
-                    const float2 l2 = splat_log2a2(
-                        kc, p, c, col, f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f), &dy);
-                    const float2 al = f2(alpha_of_l2(l2.x), alpha_of_l2(l2.y));
-                    const float2 tT = __fmul2_rn(T[i], __fadd2_rn(f2(1.0f), f2(-al.x, -al.y)));  // T (1 - alpha)
-                    const float2 aT = __fmul2_rn(al, T[i]);
-                    bool blend[2];
+            #pragma unroll
+            for (int c = 0; c < NC; c++) {
+                while (todo[c]) {
+                    const int j = __ffs(todo[c]) - 1;
+                    todo[c] &= todo[c] - 1;
+                    const int slot = 32 * c + j;
+                    const float4 p = s_rec[warp][0][slot];
+                    const float4 cc = s_rec[warp][1][slot];
+                    const float4 col = s_rec[warp][2][slot];
+                    const SplatColumn kc = splat_column(p, cc, sx);
+                    // two pixels per packed evaluation and update; branch-free per
+                    // pixel (a skipped pixel adds exactly zero), so the chains interleave
                     #pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const int k = 2 * i + h;
-                        const bool hit = live[k] && (h ? l2.y : l2.x) >= kLog2AlphaMin;
-                        const bool stop = hit && (h ? tT.y : tT.x) < kTMin;  // stops before this entry
-                        blend[h] = hit && !stop;
-                        if (STATS) {
-                            n_eval[k] += live[k];
-                            n_blend[k] += blend[h];
+                    for (int i = 0; i < NP; i++) {
+                        float2 dy;
+                        const float2 l2 = splat_log2a2(
+                            kc, p, cc, col,
+                            f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f), &dy);
+                        const float2 al = f2(alpha_of_l2(l2.x), alpha_of_l2(l2.y));
+                        const float2 tT = __fmul2_rn(T[i], __fadd2_rn(f2(1.0f), f2(-al.x, -al.y)));  // T (1 - alpha)
+                        const float2 aT = __fmul2_rn(al, T[i]);
+                        bool blend[2];
+                        #pragma unroll
+                        for (int h = 0; h < 2; h++) {
+                            const int k = 2 * i + h;
+                            const bool hit = live[k] && (h ? l2.y : l2.x) >= kLog2AlphaMin;
+                            const bool stop = hit && (h ? tT.y : tT.x) < kTMin;  // stops before this entry
+                            blend[h] = hit && !stop;
+                            if (STATS) {
+                                n_eval[k] += live[k];
+                                n_blend[k] += blend[h];
+                            }
+                            last[k] = blend[h] ? m - b + (uint32_t)slot + 1u : last[k];
+                            live[k] = live[k] && !stop;
+                            alive -= stop;
                         }
-                        last[k] = blend[h] ? m - b + (uint32_t)j + 1u : last[k];
-                        live[k] = live[k] && !stop;
-                        alive -= stop;
+                        const float2 w = f2(blend[0] ? aT.x : 0.0f, blend[1] ? aT.y : 0.0f);
+                        C0[i] = __ffma2_rn(f2(col.x), w, C0[i]);
+                        C1[i] = __ffma2_rn(f2(col.y), w, C1[i]);
+                        C2[i] = __ffma2_rn(f2(col.z), w, C2[i]);
+                        D[i] = __ffma2_rn(f2(p.z), w, D[i]);
+                        T[i] = f2(blend[0] ? tT.x : T[i].x, blend[1] ? tT.y : T[i].y);
                     }
-                    const float2 w = f2(blend[0] ? aT.x : 0.0f, blend[1] ? aT.y : 0.0f);
-                    C0[i] = __ffma2_rn(f2(col.x), w, C0[i]);
-                    C1[i] = __ffma2_rn(f2(col.y), w, C1[i]);
-                    C2[i] = __ffma2_rn(f2(col.z), w, C2[i]);
-                    D[i] = __ffma2_rn(f2(p.z), w, D[i]);
-                    T[i] = f2(blend[0] ? tT.x : T[i].x, blend[1] ? tT.y : T[i].y);
+                    if (alive == 0) {
+                        #pragma unroll
+                        for (int c2 = 0; c2 < NC; c2++) todo[c2] = 0;
+                        break;
+                    }
                 }
-                if (alive == 0) break;
             }
         }
         #pragma unroll
@@ -217,31 +235,40 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
     }
 }
 
-template <int PPT, int BW, bool STATS, bool LOSS = false>
-static gs_status_t launch_fwd(const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
+template <int PPT, int BW, int CH, bool STATS, bool LOSS = false>
+static gs_status_t launch_fwd(RenderFwdArgs a, ViewTable vt, cudaStream_t s)
 {
-    auto kern = render_fwd_kernel<PPT, BW, STATS, LOSS>;
+    // work items: the bands of every tile of every view (tile shapes are per view)
+    a.n_items = render_items(&vt, BW, PPT * (32 / BW));
+    auto kern = render_fwd_kernel<PPT, BW, CH, STATS, LOSS>;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, 0);
     const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
-    const int64_t warps_needed = (int64_t)vt.n_tiles_total * (kTile / BW) * (kTile / (PPT * (32 / BW)));
-    const int64_t blocks_needed = (warps_needed + kRenderThreads / 32 - 1) / (kRenderThreads / 32);
+    const int64_t blocks_needed = ((int64_t)a.n_items + kRenderThreads / 32 - 1) / (kRenderThreads / 32);
     const int grid = (int)(slots < blocks_needed ? slots : blocks_needed);
     kern<<<grid > 0 ? grid : 1, kRenderThreads, 0, s>>>(a, vt);
     return launch_status();
 }
 
+template <int CH, bool STATS, bool LOSS>
+static gs_status_t dispatch_fwd_ch(int base, const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
+{
+    switch (base) {
+    case 0: return launch_fwd<1, 8, CH, STATS, LOSS>(a, vt, s);
+    case 1: return launch_fwd<2, 8, CH, STATS, LOSS>(a, vt, s);
+    case 2: return launch_fwd<2, 16, CH, STATS, LOSS>(a, vt, s);
+    case 3: return launch_fwd<4, 8, CH, STATS, LOSS>(a, vt, s);
+    case 4: return launch_fwd<4, 16, CH, STATS, LOSS>(a, vt, s);
+    default: return launch_fwd<8, 16, CH, STATS, LOSS>(a, vt, s);
+    }
+}
+
 template <bool STATS, bool LOSS = false>
 static gs_status_t dispatch_fwd(const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
 {
-    switch (render_variant_fwd()) {
-    case 0: return launch_fwd<1, 8, STATS, LOSS>(a, vt, s);
-    case 1: return launch_fwd<2, 8, STATS, LOSS>(a, vt, s);
-    case 2: return launch_fwd<2, 16, STATS, LOSS>(a, vt, s);
-    case 3: return launch_fwd<4, 8, STATS, LOSS>(a, vt, s);
-    case 4: return launch_fwd<4, 16, STATS, LOSS>(a, vt, s);
-    default: return launch_fwd<8, 16, STATS, LOSS>(a, vt, s);
-    }
+    const int var = fitting_variant(vt, render_variant_fwd());
+    return var < kBandVariants ? dispatch_fwd_ch<32, STATS, LOSS>(var, a, vt, s)
+                               : dispatch_fwd_ch<64, STATS, LOSS>(var - kBandVariants, a, vt, s);
 }
 
 }  // namespace gs
@@ -333,7 +360,7 @@ extern "C" gs_status_t gs_render_stats(const gs_projected_t *proj, int64_t n, co
     a.n_eval = n_eval;
     a.n_blend = n_blend;
     a.work_counter = work_counter;
-    return launch_fwd<1, 16, true>(a, vt, s);
+    return launch_fwd<1, 16, 32, true>(a, vt, s);
 }
 
 // Compositing kernel variants in use (see kFwdVariants), set by the

@@ -59,7 +59,7 @@ class MappingStep:
 
     def __init__(self, scene, intr, size, viewmats, target_rgb, target_depth, w_c=1.0, w_d=0.5,
                  use_gate=False, gamma=0.99, keypoints=None, w_rpj=1.5, lrs=None, pair_capacity=None,
-                 zeta=0.0, device="cuda"):
+                 zeta=0.0, device="cuda", tile=(16, 16)):
         dev = torch.device(device)
         self.flat = FlatParams(scene, dev)
         self.params = self.flat.views()
@@ -70,7 +70,7 @@ class MappingStep:
         self.step_count = torch.zeros(2, dtype=torch.int32, device=dev)
         lrs = dict(DEFAULT_LR, **(lrs or {}))
         self.groups = [(self.flat.offsets[k], self.flat.widths[k], lrs[k]) for k in PARAM_ORDER]
-        self.rast = Rasterizer(self.flat.n, self.flat.sh_degree, intr, size, pair_capacity, dev)
+        self.rast = Rasterizer(self.flat.n, self.flat.sh_degree, intr, size, pair_capacity, dev, tile=tile)
         self.viewmats = torch.as_tensor(np.asarray(viewmats, np.float32).reshape(-1, 12), device=dev).contiguous()
         self.target_rgb = target_rgb
         self.target_depth = target_depth
@@ -225,11 +225,12 @@ class TrackingStep:
     phi with lr_phi) and folds them into the poses, E <- Exp(xi) E, on device."""
 
     def __init__(self, params, intr, size, viewmats, target_rgb, target_depth, keypoints=None, w_rpj=1.5,
-                 w_c=0.5, w_d=1.0, gamma=0.99, lr_rho=5e-4, lr_phi=3e-4, pair_capacity=None, device="cuda"):
+                 w_c=0.5, w_d=1.0, gamma=0.99, lr_rho=5e-4, lr_phi=3e-4, pair_capacity=None, device="cuda",
+                 tile=(16, 16)):
         dev = torch.device(device)
         self.params = params
         n = int(params["means"].shape[0])
-        self.rast = Rasterizer(n, params["sh_degree"], intr, size, pair_capacity, dev)
+        self.rast = Rasterizer(n, params["sh_degree"], intr, size, pair_capacity, dev, tile=tile)
         V = self.rast.V
         if V > GS_MAX_TRACK_VIEWS:
             raise ValueError(f"at most {GS_MAX_TRACK_VIEWS} views per tracking step")

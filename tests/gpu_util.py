@@ -58,7 +58,7 @@ def check_image(img, ref, name, log=True):
     return rec
 
 
-def check_single_blend_alpha(img, fwd, cams, name):
+def check_single_blend_alpha(img, fwd, cams, name, tile=(16, 16)):
     """Where a pixel blends only the first entry of its list, its depth is
     z * alpha with alpha the kernel's 2^l2 (T = 1): relative to 2^l2 on the
     oracle's FP32 l2 it must stay within the approximate exponential's bound
@@ -74,8 +74,8 @@ def check_single_blend_alpha(img, fwd, cams, name):
     v = np.searchsorted(bins["pix_base"], sel, side="right") - 1
     local = sel - bins["pix_base"][v]
     py, px = local // width[v], local % width[v]
-    tile = bins["tile_base"][v] + (py // 16) * bins["ntx"][v] + px // 16
-    o = v * n + bins["vals"][bins["ranges"][tile, 0]].astype(np.int64)
+    tile_id = bins["tile_base"][v] + (py // tile[1]) * bins["ntx"][v] + px // tile[0]
+    o = v * n + bins["vals"][bins["ranges"][tile_id, 0]].astype(np.int64)
     l2 = blend_l2(drec[o], px, py)
     a_ref = np.where(l2 >= L2_ALPHA_MAX, float(np.float32(0.99)), 2.0 ** l2.astype(np.float64))
     z = geom["uvz"][o, 2].astype(np.float64)
@@ -106,9 +106,9 @@ def viewmats_on_device(cams):
     return t(np.asarray(cams["viewmats"], np.float32).reshape(-1, 12))
 
 
-def make_rast(scene, cams, capacity=None):
+def make_rast(scene, cams, capacity=None, tile=(16, 16)):
     return gs.Rasterizer(scene["means"].shape[0], scene["sh_degree"], cams["intr"], cams["size"],
-                         pair_capacity=capacity)
+                         pair_capacity=capacity, tile=tile)
 
 
 def zero_grads(p):

@@ -48,6 +48,18 @@ def test_layout_and_sizes(lib):
     assert lib.gs_bin_sort_workspace_size(1000, 1 << 20, 12) >= 8 * (1 << 20) + 16 * 1000
 
 
+def test_tile_shapes_in_the_layout(lib):
+    nt, npix = ctypes.c_int64(), ctypes.c_int64()
+    for (tw, th) in [(8, 8), (16, 8), (32, 16), (64, 32), (16, 16)]:
+        views = gs.make_views([[600, 600, 600, 340]], [[1200, 680]], (tw, th))
+        assert lib.gs_layout(views, 1, ctypes.byref(nt), ctypes.byref(npix)) == 0
+        assert nt.value == -(-1200 // tw) * -(-680 // th)
+    for bad in [(12, 16), (16, 4), (64, 64), (128, 8)]:
+        views = gs.make_views([[600, 600, 600, 340]], [[1200, 680]], bad)
+        assert lib.gs_layout(views, 1, ctypes.byref(nt), ctypes.byref(npix)) == 1, bad
+    assert gs.variant_fits(3, (16, 16)) and not gs.variant_fits(3, (16, 8))  # (4, 8): 8 x 16 bands
+
+
 def test_argument_errors_are_synchronous(lib):
     views = gs.make_views([[60, 60, 32, 24]], [[64, 48]])
     bad = gs.make_views([[60, 60, 32, 24]], [[0, 48]])

@@ -445,3 +445,70 @@ def test_ssim_term_parity():
     e = rel_l2(d_rgb.cpu().numpy() - base, g)
     print(f"SSIM gradient rel-L2 err = {e:.3e}, loss {float(loss) - 0.25:.6f} vs {L:.6f}")
     assert e <= GRAD_TOL
+
+
+TILES = [(8, 8), (16, 8), (32, 16), (16, 32), (32, 32), (64, 32)]
+
+
+@pytest.mark.parametrize("tile", TILES, ids=[f"{a}x{b}" for a, b in TILES])
+def test_tile_shapes_match_oracle(tile):
+    """Every tile shape the autotuner may pick, against the oracle run with the
+    same tiles: rectangles, keys, lists and ranges bit for bit; the images of
+    every compositing variant whose band fits the tile (32- and 64-entry
+    chunks) identical to each other and within the image bar; the gradients of
+    every fitting backward variant within the gradient bar."""
+    name, scene, cams = CASES[1]
+    fwd0, bwd0, n_fwd, n_bwd = gs.gs_get_render_variants()
+    try:
+        rast = make_rast(scene, cams, tile=tile)
+        p = params_on_device(scene)
+        vm = viewmats_on_device(cams)
+        rast.forward(p, vm)
+        torch.cuda.synchronize()
+        assert rast.status() == 0
+        geom = oracle.project_geom(scene, cams, tile=tile)
+        _, radii, _, rect = gpu_geom(rast)
+        vis = geom["radius"] > 0
+        np.testing.assert_array_equal(rect[vis], geom["rect"][vis])
+        bins = oracle.bin_tiles(cams, geom, tile)
+        keys, vals, ranges = gpu_bins(rast)
+        assert rast.n_pairs() == bins["n_pairs"]
+        np.testing.assert_array_equal(keys, bins["keys"])
+        np.testing.assert_array_equal(vals, bins["vals"])
+        np.testing.assert_array_equal(ranges, bins["ranges"])
+        ref = oracle.forward(scene, cams, tile=tile)
+        first = None
+        fitting = [v for v in range(n_fwd) if gs.variant_fits(v, tile)]
+        assert len(fitting) >= 4
+        for fv in fitting:
+            gs.gs_set_render_variants(fv, bwd0)
+            gs.gs_render_fwd(rast.proj, rast.n, rast.bins, rast.views, rast.img, rast.work_counter)
+            img = {k: v.cpu().numpy() for k, v in rast.img.items()}
+            if first is None:
+                first = img
+                check_image(img, ref["img"], f"{name} tile {tile[0]}x{tile[1]}")
+                check_single_blend_alpha(img, ref, cams, f"{name} tile {tile[0]}x{tile[1]}", tile)
+            for k in img:
+                np.testing.assert_array_equal(img[k], first[k], err_msg=f"fwd variant {fv} {k}")
+        keep = ref["img"]["flags"] == 0
+        rng = np.random.default_rng(21)
+        P = rast.n_pix
+        dC, dD, dA = rng.normal(0, 1, (P, 3)), rng.normal(0, 1, P), rng.normal(0, 1e-2, P)
+        dC[~keep], dD[~keep], dA[~keep] = 0, 0, 0
+        g2d = oracle.render_bwd(cams, ref["proj"], ref["drec"], ref["bins"], ref["geom"]["n"], dC, dD, dA, tile)
+        worst = 0.0
+        for bv in range(n_bwd):
+            if not gs.variant_fits(bv, tile):
+                continue
+            gs.gs_set_render_variants(fwd0, bv)
+            rast.grad2d.zero_()
+            gs.gs_render_bwd_splats(rast.proj, rast.n, rast.bins, rast.views, rast.img, t(dC), t(dD), t(dA),
+                                    rast.grad2d, rast.work_counter)
+            torch.cuda.synchronize()
+            G = rast.grad2d.view(-1, 12).cpu().numpy()[:, :10]
+            e = rel_l2(G, g2d)
+            worst = max(worst, e)
+            assert e <= GRAD_TOL, (bv, e)
+        parity_log(dict(kind="grad", name=f"{name} tile {tile[0]}x{tile[1]} all bwd variants", g2d=worst))
+    finally:
+        gs.gs_set_render_variants(fwd0, bwd0)
