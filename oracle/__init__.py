@@ -83,7 +83,8 @@ def _L():
         _lib.orc_blend_records.argtypes = [i32, P, i64, P, P, P, P, f32, f32, i32, i32, P]
         _lib.orc_blend_l2_many.argtypes = [i64, P, P, P, P]
         _lib.orc_project_geom.argtypes = [i32, P, i64, P, P, P, f32, f32, i32, i32, P, P, P, P]
-        _lib.orc_bin.argtypes = [i32, P, i64, i32, i32, P, P, P, i64, P, P, P]
+        _lib.orc_bin.argtypes = [i32, P, i64, i32, i32, P, P, P, P, i64, P, P, P]
+        _lib.orc_tile_cull.argtypes = [i32, P, i64, P, P, i32, i32, P, P]
         _lib.orc_sh_eval.argtypes = [P, i64, i32, P]
         _lib.orc_project64.argtypes = [i32, P, i64, P, P, P, P, P, i32, f64, P, P]
         _lib.orc_render.argtypes = [i32, P, i64, P, P, i32, i32, P, P, P, P, Margins, P, P, P, P, P, P, P]
@@ -179,8 +180,11 @@ def blend_l2(drec_rows, px, py):
     return out
 
 
-def project_geom(params, cams, near_z=0.2, blur=0.3, tile=(16, 16)):
-    """FP32 geometry (binning contract) for every (view, Gaussian)."""
+def project_geom(params, cams, near_z=0.2, blur=0.3, tile=(16, 16), tile_cull=True):
+    """FP32 geometry (binning contract) for every (view, Gaussian): radius,
+    tile rectangle, (u, v, z), the decision records (drec), and the tiles
+    each drawn Gaussian keeps (tile_mask, tiles_touched; every tile of the
+    rectangle without tile_cull)."""
     L = _L()
     means, ls, q = (_c(params[k], np.float64) for k in ("means", "log_scales", "quats"))
     n = means.shape[0]
@@ -192,7 +196,12 @@ def project_geom(params, cams, near_z=0.2, blur=0.3, tile=(16, 16)):
     tt = np.zeros(V * n, np.uint32)
     L.orc_project_geom(V, views, n, _p(means), _p(ls), _p(q), float(near_z), float(blur),
                        tile[0], tile[1], _p(radius), _p(rect), _p(uvz), _p(tt))
-    return dict(radius=radius, rect=rect, uvz=uvz, tiles_touched=tt, n=n, n_views=V)
+    drec = blend_records(params, cams, near_z, blur, tile)
+    mask = np.zeros(V * n, np.uint64)
+    if tile_cull:
+        L.orc_tile_cull(V, views, n, _p(drec), _p(rect), tile[0], tile[1], _p(mask), _p(tt))
+    return dict(radius=radius, rect=rect, uvz=uvz, tiles_touched=tt, n=n, n_views=V, drec=drec,
+                tile_mask=mask if tile_cull else None)
 
 
 def bin_tiles(cams, geom, tile=(16, 16)):
@@ -204,8 +213,10 @@ def bin_tiles(cams, geom, tile=(16, 16)):
     keys = np.zeros(max(K, 1), np.uint64)
     vals = np.zeros(max(K, 1), np.uint32)
     ranges = np.zeros((lay["n_tiles"], 2), np.uint32)
-    L.orc_bin(len(views), views, geom["n"], tile[0], tile[1], _p(geom["rect"]), _p(geom["uvz"]),
-              _p(lay["tile_base"]), lay["n_tiles"], _p(keys), _p(vals), _p(ranges))
+    mask = geom.get("tile_mask")
+    L.orc_bin(len(views), views, geom["n"], tile[0], tile[1], _p(geom["rect"]),
+              None if mask is None else _p(mask), _p(geom["uvz"]), _p(lay["tile_base"]), lay["n_tiles"], _p(keys),
+              _p(vals), _p(ranges))
     return dict(keys=keys[:K], vals=vals[:K], ranges=ranges, n_pairs=K, **lay)
 
 
@@ -340,11 +351,11 @@ def se3_exp_apply(xi, E):
 # whole pipeline conveniences
 # --------------------------------------------------------------------------
 
-def forward(params, cams, near_z=0.2, blur=0.3, tile=(16, 16), **margins):
-    geom = project_geom(params, cams, near_z, blur, tile)
+def forward(params, cams, near_z=0.2, blur=0.3, tile=(16, 16), tile_cull=True, **margins):
+    geom = project_geom(params, cams, near_z, blur, tile, tile_cull)
     bins = bin_tiles(cams, geom, tile)
     proj = project64(params, cams, geom, blur)
-    drec = blend_records(params, cams, near_z, blur, tile)
+    drec = geom["drec"]
     img = render(cams, proj, drec, bins, geom["n"], tile, **margins)
     return dict(geom=geom, bins=bins, proj=proj, drec=drec, img=img)
 

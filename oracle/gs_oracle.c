@@ -363,6 +363,81 @@ void orc_blend_records(int32_t n_views, const orc_view_t *views, int64_t n, cons
     }
 }
 
+/* Minimum over t in [t0, t1] of P s^2 + 2 B s t + Q t^2 at the clamped
+ * near-minimiser t = (-B s) (1/Q), FP32; *mag = the largest sum of the
+ * magnitudes of the terms. */
+static float orc_edge_min(float P, float B, float Q, float invQ, float s, float t0, float t1, float *mag)
+{
+    float t = fminf(fmaxf((-B * s) * invQ, t0), t1);
+    float a = (P * s) * s;
+    float b = ((2.0f * B) * s) * t;
+    float c = (Q * t) * t;
+    float m = (a + fabsf(b)) + c;
+    if (m > *mag) *mag = m;
+    return (a + b) + c;
+}
+
+/* Keep-mask of the w x h <= 64 tiles of a rectangle from (x0, y0) for a
+ * decision record r: bit j * w + i is set unless the splat's log2 of the raw
+ * alpha stays below log2(1/255) by more than 1.5e-3 + 4e-6 M over the pixel
+ * centres of tile (x0 + i, y0 + j) (M the magnitude of the quadratic form's
+ * terms at the box minimum).  With d = pixel - mean, log2 raw alpha =
+ * log2 o - q(d), q = P dx^2 + 2 B dx dy + Q dy^2, (P, B, Q) = -(A', B'/2, C');
+ * q is convex with minimum 0 at the mean, so over a box not containing the
+ * mean its minimum is on an edge.  FP32, in this operation order. */
+uint64_t orc_tile_mask(const float *r, int x0, int y0, int w, int h, int tw, int th)
+{
+    float u = r[0], v = r[1], du = r[2], dv = r[3], l2o = r[4];
+    float P = -r[5], Q = -r[7], B = -0.5f * r[6];
+    float invP = 1.0f / P, invQ = 1.0f / Q;
+    uint64_t mask = 0;
+    for (int j = 0; j < h; j++) {
+        float cy0 = (float)((y0 + j) * th) + 0.5f, cy1 = cy0 + (float)(th - 1);
+        float ey0 = (cy0 - v) - dv, ey1 = (cy1 - v) - dv;
+        for (int i = 0; i < w; i++) {
+            float cx0 = (float)((x0 + i) * tw) + 0.5f, cx1 = cx0 + (float)(tw - 1);
+            float ex0 = (cx0 - u) - du, ex1 = (cx1 - u) - du;
+            float q = 0.0f, mag = 0.0f;
+            if (!(ex0 <= 0.0f && ex1 >= 0.0f && ey0 <= 0.0f && ey1 >= 0.0f)) {
+                float q0 = orc_edge_min(P, B, Q, invQ, ex0, ey0, ey1, &mag);
+                float q1 = orc_edge_min(P, B, Q, invQ, ex1, ey0, ey1, &mag);
+                float q2 = orc_edge_min(Q, B, P, invP, ey0, ex0, ex1, &mag);
+                float q3 = orc_edge_min(Q, B, P, invP, ey1, ex0, ex1, &mag);
+                q = fminf(fminf(q0, q1), fminf(q2, q3));
+            }
+            if (l2o - q >= ORC_L2_ALPHA_MIN - (1.5e-3f + 4e-6f * mag)) mask |= (uint64_t)1 << (j * w + i);
+        }
+    }
+    return mask;
+}
+
+/* Tiles each drawn (view, Gaussian) keeps: for rectangles of up to 64 tiles
+ * the set bits of orc_tile_mask, else every tile (mask 0); tiles_touched [.]
+ * receives the number kept.  rect, drec as orc_project_geom and
+ * orc_blend_records give them. */
+void orc_tile_cull(int32_t n_views, const orc_view_t *views, int64_t n, const float *drec, const int32_t *rect,
+                   int32_t tw, int32_t th, uint64_t *mask, uint32_t *tiles_touched)
+{
+    (void)views;
+    for (int64_t o = 0; o < (int64_t)n_views * n; o++) {
+        int32_t x0 = rect[4 * o], y0 = rect[4 * o + 1], x1 = rect[4 * o + 2], y1 = rect[4 * o + 3];
+        mask[o] = 0;
+        if (x1 < x0 || y1 < y0) {
+            tiles_touched[o] = 0;
+            continue;
+        }
+        int w = x1 - x0 + 1, h = y1 - y0 + 1;
+        if (w * h <= 64) {
+            mask[o] = orc_tile_mask(drec + 8 * o, x0, y0, w, h, tw, th);
+            uint32_t c = 0;
+            for (uint64_t m = mask[o]; m; m &= m - 1) c++;
+            tiles_touched[o] = c;
+        } else {
+            tiles_touched[o] = (uint32_t)(w * h);
+        }
+    }
+}
+
 /* l2 of a decision record at pixel (px, py), sampled at its centre. */
 static float orc_blend_l2(const float *r, int px, int py)
 {
@@ -407,11 +482,13 @@ int64_t orc_count_pairs(int64_t total, const uint32_t *tiles_touched)
 
 /* Builds every (Gaussian, tile) pair with key (global tile id << 32) | bits(z)
  * and value = Gaussian index, then orders them by (key, Gaussian index): tiles
- * ascending, and within a tile front to back with ties broken by index.
+ * ascending, and within a tile front to back with ties broken by index.  The
+ * tiles of a rectangle of up to 64 tiles are those its mask keeps (every tile
+ * when mask is NULL).
  * ranges[2t], ranges[2t+1] = [start, end) of global tile t.
  * tile_base[v] = global id of view v's first tile. */
 void orc_bin(int32_t n_views, const orc_view_t *views, int64_t n, int32_t tw,
-             int32_t th, const int32_t *rect, const float *uvz,
+             int32_t th, const int32_t *rect, const uint64_t *mask, const float *uvz,
              const int32_t *tile_base, int64_t n_tiles_total, uint64_t *keys,
              uint32_t *vals, uint32_t *ranges)
 {
@@ -431,8 +508,11 @@ void orc_bin(int32_t n_views, const orc_view_t *views, int64_t n, int32_t tw,
             if (x1 < x0 || y1 < y0) continue;
             union { float f; uint32_t u; } zb;
             zb.f = uvz[3 * o + 2];
+            int rw = x1 - x0 + 1, rh = y1 - y0 + 1;
+            int masked = mask != NULL && rw * rh <= 64;
             for (int32_t ty = y0; ty <= y1; ty++)
                 for (int32_t tx = x0; tx <= x1; tx++) {
+                    if (masked && !((mask[o] >> ((ty - y0) * rw + (tx - x0))) & 1)) continue;
                     uint64_t tile = (uint64_t)(tile_base[v] + ty * ntx + tx);
                     pairs[w].key = (tile << 32) | (uint64_t)zb.u;
                     pairs[w].val = (uint32_t)i;

@@ -117,7 +117,8 @@ def gs_project(params, views, viewmats, proj, near_z=0.2, blur=0.3, stream=None)
 
 
 def _proj(proj):
-    return GsProjected(_ptr(proj["rec"]), _ptr(proj["rect"]), _ptr(proj["radii"]), _ptr(proj["tiles_touched"]))
+    return GsProjected(_ptr(proj["rec"]), _ptr(proj["rect"]), _ptr(proj["radii"]), _ptr(proj["tiles_touched"]),
+                       _ptr(proj["tile_mask"]))
 
 
 def _bins(bins):
@@ -345,7 +346,8 @@ class Rasterizer:
         R = self.V * self.n
         i32, f32 = torch.int32, torch.float32
         self.proj = dict(rec=torch.empty(R * 12, dtype=f32, device=d), rect=torch.empty(R, 2, dtype=i32, device=d),
-                         radii=torch.empty(R, dtype=i32, device=d), tiles_touched=torch.empty(R, dtype=i32, device=d))
+                         radii=torch.empty(R, dtype=i32, device=d), tiles_touched=torch.empty(R, dtype=i32, device=d),
+                         tile_mask=torch.empty(R, dtype=torch.int64, device=d))
         self.bins = dict(keys=torch.empty(self.capacity, dtype=torch.int64, device=d),
                          vals=torch.empty(self.capacity, dtype=i32, device=d),
                          ranges=torch.zeros(self.n_tiles, 2, dtype=i32, device=d),

@@ -204,10 +204,19 @@ __global__ void __launch_bounds__(kEmitThreads) pair_count_kernel(const uint2 *_
     if (threadIdx.x == 0) block_sums[blockIdx.x] = all;
 }
 
+// Index of the (k + 1)-th set bit of m (m has more than k set bits).
+__device__ __forceinline__ int nth_set_bit(unsigned long long m, uint32_t k)
+{
+    for (uint32_t i = 0; i < k; i++) m &= m - 1ull;
+    return __ffsll((long long)m) - 1;
+}
+
 // 2b. Emission of (tile id, depth rank) pairs in depth order, and the
-// histograms of the tile-id digits.
+// histograms of the tile-id digits.  A record's pairs are the tiles its mask
+// keeps (rectangles of up to 64 tiles) or every tile of its rectangle.
 __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__restrict__ recs,
                                                                  const uint2 *__restrict__ rect,
+                                                                 const unsigned long long *__restrict__ tmask,
                                                                  const uint32_t *__restrict__ tt,
                                                                  const uint32_t *n_vis_p, uint32_t n, ViewTable vt,
                                                                  const uint64_t *__restrict__ block_off, int64_t cap,
@@ -217,6 +226,7 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
     __shared__ uint64_t tmp[kEmitThreads / 32];
     __shared__ uint32_t s_excl[kPairChunk + 1];
     __shared__ uint32_t s_r0[kPairChunk], s_r1[kPairChunk];
+    __shared__ unsigned long long s_m[kPairChunk];
     __shared__ uint16_t s_v[kPairChunk];
     __shared__ uint32_t h[kMaxTilePasses][kRadix];
     constexpr int kRun = 8;  // consecutive pairs a thread emits per round
@@ -240,6 +250,7 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
             const uint2 rr = rect[r[k]];
             s_r0[q] = rr.x;
             s_r1[q] = rr.y;
+            s_m[q] = tmask[r[k]];
             s_v[q] = (uint16_t)(r[k] / n);
         }
     }
@@ -267,16 +278,32 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
                 const int mid = (lo + hi) >> 1;
                 if (s_excl[mid] <= qs) lo = mid; else hi = mid;
             }
-            uint32_t x0, x1, tx, row, tiles_x;
-            auto enter = [&](int rec, uint32_t k) {  // record rec, its k-th tile
+            uint32_t x0, x1, w, tx, row, row0, tiles_x;
+            unsigned long long rem;  // kept tiles after the current one (masked records)
+            bool masked;
+            auto place = [&](uint32_t idx) {  // the idx-th tile of the rectangle, row-major
+                const uint32_t ky = idx / w;
+                tx = x0 + (idx - ky * w);
+                row = row0 + ky * tiles_x;
+            };
+            auto enter = [&](int rec, uint32_t k) {  // record rec, its k-th pair
                 const uint32_t r0 = s_r0[rec], r1 = s_r1[rec];
                 x0 = r0 & 0xffff;
                 x1 = r1 & 0xffff;
-                const uint32_t w = x1 - x0 + 1, ky = k / w;
+                w = x1 - x0 + 1;
+                const uint32_t h = (r1 >> 16) - (r0 >> 16) + 1;
                 const ViewInfo &V = vt.v[s_v[rec]];
                 tiles_x = (uint32_t)V.tiles_x;
-                tx = x0 + (k - ky * w);
-                row = (uint32_t)V.tile_base + ((r0 >> 16) + ky) * tiles_x;
+                row0 = (uint32_t)V.tile_base + (r0 >> 16) * tiles_x;
+                masked = w * h <= 64;
+                uint32_t idx = k;
+                rem = 0ull;
+                if (masked) {
+                    const unsigned long long m = s_m[rec];
+                    idx = (uint32_t)nth_set_bit(m, k);
+                    rem = idx < 63 ? m & ~((2ull << idx) - 1ull) : 0ull;
+                }
+                place(idx);
             };
             enter(lo, qs - s_excl[lo]);
             #pragma unroll
@@ -294,7 +321,12 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
                 valid[j] = true;
                 s_tk[threadIdx.x * kRun + j] = tile[j];
                 s_tv[threadIdx.x * kRun + j] = j0 + (uint32_t)lo;
-                if (++tx > x1) {
+                if (masked) {
+                    if (rem) {
+                        place((uint32_t)(__ffsll((long long)rem) - 1));
+                        rem &= rem - 1ull;
+                    }
+                } else if (++tx > x1) {
                     tx = x0;
                     row += tiles_x;
                 }
@@ -408,7 +440,7 @@ extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const 
         if (cudaMemsetAsync(bins->n_pairs, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
         return GS_OK;
     }
-    if (!proj->rec || !proj->rect || !proj->tiles_touched) return GS_ERR_INVALID_ARG;
+    if (!proj->rec || !proj->rect || !proj->tiles_touched || !proj->tile_mask) return GS_ERR_INVALID_ARG;
 
     uint32_t *n_vis = w.small;
     uint32_t *counters = w.small + 1;  // one per pass
@@ -442,6 +474,7 @@ extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const 
     pair_count_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, proj->tiles_touched, n_vis, w.block_sums);
     scan_sums_kernel<<<1, 1024, 0, s>>>(w.block_sums, np, cap, bins->n_pairs, bins->status);
     pair_emit_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, reinterpret_cast<const uint2 *>(proj->rect),
+                                                  reinterpret_cast<const unsigned long long *>(proj->tile_mask),
                                                  proj->tiles_touched, n_vis, (uint32_t)n, vt, w.block_sums, cap,
                                                  buf_k[e], buf_v[e], hist_tile, tile_passes);
     st = launch_status();

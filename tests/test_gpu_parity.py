@@ -65,6 +65,10 @@ def test_projection_and_binning_bit_exact(name, scene, cams):
     np.testing.assert_array_equal(tt, geom["tiles_touched"])
     np.testing.assert_array_equal(rect[vis], geom["rect"][vis])
     np.testing.assert_array_equal(rec[vis][:, 0:3].view(np.uint32), geom["uvz"][vis].view(np.uint32))
+    # the tiles each splat keeps (exact tile test), bit for bit
+    mask = rast.proj["tile_mask"].cpu().numpy().view(np.uint64)
+    np.testing.assert_array_equal(mask[vis], geom["tile_mask"][vis])
+    assert (tt[vis] < (rect[vis, 2] - rect[vis, 0] + 1) * (rect[vis, 3] - rect[vis, 1] + 1)).any()
     bins = oracle.bin_tiles(cams, geom)
     keys, vals, ranges = gpu_bins(rast)
     assert rast.n_pairs() == bins["n_pairs"]

@@ -169,7 +169,7 @@ def test_culling_rules():
 def test_binning_is_front_to_back_per_tile():
     c = scenes.config(1)
     cams = c["cams"]
-    geom = oracle.project_geom(c["scene"], cams)
+    geom = oracle.project_geom(c["scene"], cams, tile_cull=False)
     bins = oracle.bin_tiles(cams, geom)
     keys, vals, ranges = bins["keys"], bins["vals"], bins["ranges"]
     assert bins["n_pairs"] == int(geom["tiles_touched"].sum())
@@ -192,3 +192,34 @@ def test_binning_is_front_to_back_per_tile():
         order = np.lexsort((ids, z[ids]))
         np.testing.assert_array_equal(order, np.arange(len(ids)))
     assert ranges[-1, 1] == len(keys)
+
+
+def test_tile_cull_drops_only_tiles_no_pixel_blends():
+    """The exact tile test (rectangles of up to 64 tiles) removes a pair only
+    where the splat's FP32 log2 alpha is below log2(1/255) at every pixel of
+    the tile (checked by brute force over the tile's pixels); the lists keep
+    every other pair in the same order, so the FP64 images are bit-identical
+    with and without the test; and it removes a good share of the pairs."""
+    for tile in [(16, 16), (32, 16), (8, 8)]:
+        sc = scenes.cube_scene(1500, seed=44, sh_degree=0, log_scale=(-3.0, 0.6), opacity=(-1.0, 1.5))
+        cams = scenes.pinhole(96, 80, 70.0)
+        W, H = 96, 80
+        full = oracle.forward(sc, cams, tile=tile, tile_cull=False)
+        cut = oracle.forward(sc, cams, tile=tile)
+        for k in ("rgb", "depth", "alpha", "final_T"):
+            np.testing.assert_array_equal(cut["img"][k], full["img"][k])
+        pairs = lambda f: set(zip((f["bins"]["keys"] >> np.uint64(32)).astype(int).tolist(),
+                                  f["bins"]["vals"].astype(int).tolist()))
+        kept, every = pairs(cut), pairs(full)
+        assert kept <= every
+        dropped = every - kept
+        assert len(dropped) > 0.1 * len(every), (len(dropped), len(every))
+        ntx = (W + tile[0] - 1) // tile[0]
+        drec = cut["drec"]
+        for t, i in dropped:
+            ty, tx = divmod(t, ntx)
+            xs = np.arange(tx * tile[0], min((tx + 1) * tile[0], W))
+            ys = np.arange(ty * tile[1], min((ty + 1) * tile[1], H))
+            PX, PY = np.meshgrid(xs, ys)
+            l2 = oracle.blend_l2(np.repeat(drec[i][None], PX.size, 0), PX.ravel(), PY.ravel())
+            assert np.all(l2 < oracle.L2_ALPHA_MIN), (tile, t, i, float(l2.max()))
