@@ -182,9 +182,9 @@ def blend_l2(drec_rows, px, py):
 
 def project_geom(params, cams, near_z=0.2, blur=0.3, tile=(16, 16), tile_cull=True):
     """FP32 geometry (binning contract) for every (view, Gaussian): radius,
-    tile rectangle, (u, v, z), the decision records (drec), and the tiles
-    each drawn Gaussian keeps (tile_mask, tiles_touched; every tile of the
-    rectangle without tile_cull)."""
+    tile rectangle and its tile count (tiles_touched), (u, v, z), the decision
+    records (drec), and the tiles each drawn Gaussian keeps (tile_mask, and
+    their number in kept; every tile of the rectangle without tile_cull)."""
     L = _L()
     means, ls, q = (_c(params[k], np.float64) for k in ("means", "log_scales", "quats"))
     n = means.shape[0]
@@ -198,10 +198,11 @@ def project_geom(params, cams, near_z=0.2, blur=0.3, tile=(16, 16), tile_cull=Tr
                        tile[0], tile[1], _p(radius), _p(rect), _p(uvz), _p(tt))
     drec = blend_records(params, cams, near_z, blur, tile)
     mask = np.zeros(V * n, np.uint64)
+    kept = tt.copy()
     if tile_cull:
-        L.orc_tile_cull(V, views, n, _p(drec), _p(rect), tile[0], tile[1], _p(mask), _p(tt))
+        L.orc_tile_cull(V, views, n, _p(drec), _p(rect), tile[0], tile[1], _p(mask), _p(kept))
     return dict(radius=radius, rect=rect, uvz=uvz, tiles_touched=tt, n=n, n_views=V, drec=drec,
-                tile_mask=mask if tile_cull else None)
+                tile_mask=mask if tile_cull else None, kept=kept)
 
 
 def bin_tiles(cams, geom, tile=(16, 16)):
@@ -209,7 +210,7 @@ def bin_tiles(cams, geom, tile=(16, 16)):
     L = _L()
     lay = layout(cams, tile)
     views = make_views(cams)
-    K = int(geom["tiles_touched"].astype(np.int64).sum())
+    K = int(geom["kept"].astype(np.int64).sum())
     keys = np.zeros(max(K, 1), np.uint64)
     vals = np.zeros(max(K, 1), np.uint32)
     ranges = np.zeros((lay["n_tiles"], 2), np.uint32)

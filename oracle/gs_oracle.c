@@ -412,18 +412,18 @@ uint64_t orc_tile_mask(const float *r, int x0, int y0, int w, int h, int tw, int
 }
 
 /* Tiles each drawn (view, Gaussian) keeps: for rectangles of up to 64 tiles
- * the set bits of orc_tile_mask, else every tile (mask 0); tiles_touched [.]
- * receives the number kept.  rect, drec as orc_project_geom and
- * orc_blend_records give them. */
+ * the set bits of orc_tile_mask, else every tile (mask 0); kept [.] receives
+ * the number kept.  rect, drec as orc_project_geom and orc_blend_records give
+ * them. */
 void orc_tile_cull(int32_t n_views, const orc_view_t *views, int64_t n, const float *drec, const int32_t *rect,
-                   int32_t tw, int32_t th, uint64_t *mask, uint32_t *tiles_touched)
+                   int32_t tw, int32_t th, uint64_t *mask, uint32_t *kept)
 {
     (void)views;
     for (int64_t o = 0; o < (int64_t)n_views * n; o++) {
         int32_t x0 = rect[4 * o], y0 = rect[4 * o + 1], x1 = rect[4 * o + 2], y1 = rect[4 * o + 3];
         mask[o] = 0;
         if (x1 < x0 || y1 < y0) {
-            tiles_touched[o] = 0;
+            kept[o] = 0;
             continue;
         }
         int w = x1 - x0 + 1, h = y1 - y0 + 1;
@@ -431,9 +431,9 @@ void orc_tile_cull(int32_t n_views, const orc_view_t *views, int64_t n, const fl
             mask[o] = orc_tile_mask(drec + 8 * o, x0, y0, w, h, tw, th);
             uint32_t c = 0;
             for (uint64_t m = mask[o]; m; m &= m - 1) c++;
-            tiles_touched[o] = c;
+            kept[o] = c;
         } else {
-            tiles_touched[o] = (uint32_t)(w * h);
+            kept[o] = (uint32_t)(w * h);
         }
     }
 }

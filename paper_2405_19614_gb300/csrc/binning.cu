@@ -166,10 +166,76 @@ __global__ void __launch_bounds__(kEmitThreads) vis_compact_kernel(const float *
     flush_hist(h, kDepthPasses, hist);
 }
 
-// Record ids and tile counts of the depth-sorted records j < n_vis of a
+#define MUL __fmul_rn
+#define ADD __fadd_rn
+#define SUB __fsub_rn
+#define DIV __fdiv_rn
+
+// Minimum over t in [t0, t1] of P s^2 + 2 B s t + Q t^2 for a fixed s, at the
+// clamped near-minimiser t = (-B s) (1/Q) (within a few ulp of the minimiser,
+// which moves the value by far less than the tile test's margin), in correctly
+// rounded operations; *mag receives the largest sum of the magnitudes of the
+// terms.
+__device__ __forceinline__ float edge_min_rn(float P, float B, float Q, float invQ, float s, float t0, float t1,
+                                             float *mag)
+{
+    const float t = fminf(fmaxf(MUL(MUL(-B, s), invQ), t0), t1);
+    const float a = MUL(MUL(P, s), s);
+    const float b = MUL(MUL(MUL(2.0f, B), s), t);
+    const float c = MUL(MUL(Q, t), t);
+    *mag = fmaxf(*mag, ADD(ADD(a, fabsf(b)), c));
+    return ADD(ADD(a, b), c);
+}
+
+// Tiles of a rectangle of at most 64 tiles (w x h, row-major bits from tile
+// (x0, y0)) that a splat can reach with alpha >= 1/255.  With d = pixel -
+// mean (mean u + du, v + dv) and q(d) = P dx^2 + 2 B dx dy + Q dy^2,
+// (P, B, Q) = -(A', B'/2, C') of the record, log2 of the raw alpha is
+// log2 o - q(d).  q is convex with minimum 0 at the mean, so over a tile's box
+// of pixel centres that does not contain the mean its minimum lies on an edge;
+// the tile is dropped when log2 o - q_min is below log2(1/255) by more than
+// 1.5e-3 + 4e-6 M (M the magnitude of the terms): more than the rounding of
+// this bound and of the per-pixel evaluation, so a dropped tile is one where
+// every pixel would skip the splat.  One fixed sequence of correctly rounded
+// operations, so the tile lists are reproducible bit for bit.
+__device__ __forceinline__ unsigned long long tile_keep_mask(float u, float v, float du, float dv, float log2o,
+                                                             float A2, float B2, float C2, int x0, int y0, int w,
+                                                             int h, int tw, int th)
+{
+    constexpr float kCut = -0x1.ffa37cp+2f;  // log2(1/255) rounded to FP32
+    const float P = -A2, Q = -C2, B = MUL(-0.5f, B2);
+    const float invP = DIV(1.0f, P), invQ = DIV(1.0f, Q);
+    unsigned long long mask = 0ull;
+    #pragma unroll 1
+    for (int j = 0; j < h; j++) {
+        const float cy0 = (float)((y0 + j) * th) + 0.5f, cy1 = ADD(cy0, (float)(th - 1));
+        const float ey0 = SUB(SUB(cy0, v), dv), ey1 = SUB(SUB(cy1, v), dv);
+        #pragma unroll 1
+        for (int i = 0; i < w; i++) {
+            const float cx0 = (float)((x0 + i) * tw) + 0.5f, cx1 = ADD(cx0, (float)(tw - 1));
+            const float ex0 = SUB(SUB(cx0, u), du), ex1 = SUB(SUB(cx1, u), du);
+            float q = 0.0f, mag = 0.0f;
+            if (!(ex0 <= 0.0f && ex1 >= 0.0f && ey0 <= 0.0f && ey1 >= 0.0f)) {
+                q = fminf(fminf(edge_min_rn(P, B, Q, invQ, ex0, ey0, ey1, &mag),
+                                edge_min_rn(P, B, Q, invQ, ex1, ey0, ey1, &mag)),
+                          fminf(edge_min_rn(Q, B, P, invP, ey0, ex0, ex1, &mag),
+                                edge_min_rn(Q, B, P, invP, ey1, ex0, ex1, &mag)));
+            }
+            if (SUB(log2o, q) >= SUB(kCut, ADD(1.5e-3f, MUL(4e-6f, mag)))) mask |= 1ull << (j * w + i);
+        }
+    }
+    return mask;
+}
+
+#undef MUL
+#undef ADD
+#undef SUB
+#undef DIV
+
+// Record ids and kept tile counts of the depth-sorted records j < n_vis of a
 // block's chunk (thread t holds j = first + 2 t, first + 2 t + 1); recs holds
-// (depth bits, record id) pairs.
-__device__ __forceinline__ void chunk_counts(const uint2 *__restrict__ recs, const uint32_t *__restrict__ tt,
+// (depth bits, record id) pairs, cnt the counts pair_count wrote.
+__device__ __forceinline__ void chunk_counts(const uint2 *__restrict__ recs, const uint32_t *__restrict__ cnt,
                                              uint32_t n_vis, uint32_t (&r)[kPairItems], uint32_t (&c)[kPairItems])
 {
     const int64_t first = (int64_t)blockIdx.x * kPairChunk + (int64_t)threadIdx.x * kPairItems;
@@ -177,14 +243,19 @@ __device__ __forceinline__ void chunk_counts(const uint2 *__restrict__ recs, con
     for (int k = 0; k < kPairItems; k++) {
         const int64_t j = first + k;
         r[k] = j < n_vis ? recs[j].y : 0u;
-        c[k] = j < n_vis ? tt[r[k]] : 0u;
+        c[k] = j < n_vis ? cnt[j] : 0u;
     }
 }
 
-// 2a. Pairs of each block of kPairChunk depth-sorted records.
+// 2a. The tiles each depth-sorted record keeps (keep-mask and count, for
+// rectangles of up to 64 tiles; every tile of a larger one) and the pairs of
+// each block of kPairChunk records.
 __global__ void __launch_bounds__(kEmitThreads) pair_count_kernel(const uint2 *__restrict__ recs,
-                                                                  const uint32_t *__restrict__ tt,
-                                                                  const uint32_t *n_vis_p, uint64_t *block_sums)
+                                                                  const uint2 *__restrict__ rect,
+                                                                  const float4 *__restrict__ rec, uint32_t n,
+                                                                  ViewTable vt, const uint32_t *n_vis_p,
+                                                                  uint32_t *cnt, unsigned long long *msk,
+                                                                  uint64_t *block_sums)
 {
     __shared__ uint64_t tmp[kEmitThreads / 32];
     // the grid covers every record slot; chunks past the drawn records
@@ -194,11 +265,29 @@ __global__ void __launch_bounds__(kEmitThreads) pair_count_kernel(const uint2 *_
         if (threadIdx.x == 0) block_sums[blockIdx.x] = 0;
         return;
     }
-    uint32_t r[kPairItems], c[kPairItems];
-    chunk_counts(recs, tt, n_vis, r, c);
+    const int64_t first = (int64_t)blockIdx.x * kPairChunk + (int64_t)threadIdx.x * kPairItems;
     uint64_t s = 0;
     #pragma unroll
-    for (int k = 0; k < kPairItems; k++) s += c[k];
+    for (int k = 0; k < kPairItems; k++) {
+        const int64_t j = first + k;
+        if (j >= n_vis) continue;
+        const uint32_t rid = recs[j].y;
+        const uint2 rr = rect[rid];
+        const int x0 = (int)(rr.x & 0xffff), y0 = (int)(rr.x >> 16);
+        const int w = (int)(rr.y & 0xffff) - x0 + 1, h = (int)(rr.y >> 16) - y0 + 1;
+        uint32_t c = (uint32_t)(w * h);
+        unsigned long long m = 0ull;
+        if (w * h <= 64) {
+            const float4 p = rec[3 * (int64_t)rid], q = rec[3 * (int64_t)rid + 1];
+            const float dv = rec[3 * (int64_t)rid + 2].w;
+            const ViewInfo &V = vt.v[rid / n];
+            m = tile_keep_mask(p.x, p.y, q.w, dv, p.w, q.x, q.y, q.z, x0, y0, w, h, V.tile_w, V.tile_h);
+            c = (uint32_t)__popcll(m);
+        }
+        cnt[j] = c;
+        msk[j] = m;
+        s += c;
+    }
     uint64_t all;
     block_exclusive_scan_u64(s, tmp, &all);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = all;
@@ -216,8 +305,8 @@ __device__ __forceinline__ int nth_set_bit(unsigned long long m, uint32_t k)
 // keeps (rectangles of up to 64 tiles) or every tile of its rectangle.
 __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__restrict__ recs,
                                                                  const uint2 *__restrict__ rect,
-                                                                 const unsigned long long *__restrict__ tmask,
-                                                                 const uint32_t *__restrict__ tt,
+                                                                 const unsigned long long *__restrict__ msk,
+                                                                 const uint32_t *__restrict__ cnt,
                                                                  const uint32_t *n_vis_p, uint32_t n, ViewTable vt,
                                                                  const uint64_t *__restrict__ block_off, int64_t cap,
                                                                  uint32_t *tk, uint32_t *tv, uint32_t *hist,
@@ -235,7 +324,7 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
     if ((int64_t)blockIdx.x * kPairChunk >= (int64_t)n_vis) return;  // no drawn record: nothing to emit
     clear_hist(h, tile_passes);
     uint32_t r[kPairItems], c[kPairItems];
-    chunk_counts(recs, tt, n_vis, r, c);
+    chunk_counts(recs, cnt, n_vis, r, c);
     uint64_t sum = 0;
     #pragma unroll
     for (int k = 0; k < kPairItems; k++) sum += c[k];
@@ -250,7 +339,7 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
             const uint2 rr = rect[r[k]];
             s_r0[q] = rr.x;
             s_r1[q] = rr.y;
-            s_m[q] = tmask[r[k]];
+            s_m[q] = msk[(int64_t)blockIdx.x * kPairChunk + q];
             s_v[q] = (uint16_t)(r[k] / n);
         }
     }
@@ -381,6 +470,8 @@ struct BinWorkspace {
     uint2 *recs;  // depth-sorted (depth bits, record id)
     uint32_t *lb[2];
     uint32_t *pk, *pv;  // pair buffer
+    uint32_t *cnt;            // kept tiles of each depth-sorted record
+    unsigned long long *msk;  // their keep-masks
     size_t lb_bytes, small_bytes, bytes;
 };
 
@@ -401,6 +492,8 @@ static BinWorkspace carve(void *base, int64_t n_records, int64_t cap)
     w.lb_bytes = o.lb_bytes;
     w.pk = reinterpret_cast<uint32_t *>(p + o.pk);
     w.pv = reinterpret_cast<uint32_t *>(p + o.pv);
+    w.cnt = reinterpret_cast<uint32_t *>(p + o.cnt);
+    w.msk = reinterpret_cast<unsigned long long *>(p + o.msk);
     w.bytes = o.bytes;
     return w;
 }
@@ -440,7 +533,7 @@ extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const 
         if (cudaMemsetAsync(bins->n_pairs, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
         return GS_OK;
     }
-    if (!proj->rec || !proj->rect || !proj->tiles_touched || !proj->tile_mask) return GS_ERR_INVALID_ARG;
+    if (!proj->rec || !proj->rect || !proj->tiles_touched) return GS_ERR_INVALID_ARG;
 
     uint32_t *n_vis = w.small;
     uint32_t *counters = w.small + 1;  // one per pass
@@ -471,11 +564,12 @@ extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const 
     uint32_t *buf_v[2] = {w.pv, reinterpret_cast<uint32_t *>(bins->keys) + cap};
     const int e = (tile_passes & 1) ? 0 : 1;
     const unsigned np = (unsigned)((total + kPairChunk - 1) / kPairChunk);
-    pair_count_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, proj->tiles_touched, n_vis, w.block_sums);
+    pair_count_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, reinterpret_cast<const uint2 *>(proj->rect),
+                                                  reinterpret_cast<const float4 *>(proj->rec), (uint32_t)n, vt, n_vis,
+                                                  w.cnt, w.msk, w.block_sums);
     scan_sums_kernel<<<1, 1024, 0, s>>>(w.block_sums, np, cap, bins->n_pairs, bins->status);
-    pair_emit_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, reinterpret_cast<const uint2 *>(proj->rect),
-                                                  reinterpret_cast<const unsigned long long *>(proj->tile_mask),
-                                                 proj->tiles_touched, n_vis, (uint32_t)n, vt, w.block_sums, cap,
+    pair_emit_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, reinterpret_cast<const uint2 *>(proj->rect), w.msk,
+                                                 w.cnt, n_vis, (uint32_t)n, vt, w.block_sums, cap,
                                                  buf_k[e], buf_v[e], hist_tile, tile_passes);
     st = launch_status();
     if (st != GS_OK) return st;

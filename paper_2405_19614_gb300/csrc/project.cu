@@ -237,60 +237,6 @@ __device__ __forceinline__ float pixel_remainder(float f, float xh, float xl, fl
 // log2(o exp(-1/2 d^T conic d)) = log2(o) + A' dx^2 + B' dx dy + C' dy^2.
 constexpr float kNegHalfLog2e = -0x1.715476p-1f;
 constexpr float kLog2eF = 0x1.715476p+0f;
-constexpr float kLog2AlphaMinF = -0x1.ffa37cp+2f;  // log2(1/255) rounded to FP32
-
-// Minimum over t in [t0, t1] of P s^2 + 2 B s t + Q t^2 for a fixed s, at the
-// clamped minimiser t = (-B s) (1/Q) (within a few ulp of it, which moves the
-// value by far less than the tile test's margin), in correctly rounded
-// operations; *mag receives the largest sum of the magnitudes of the terms.
-__device__ __forceinline__ float edge_min_rn(float P, float B, float Q, float invQ, float s, float t0, float t1,
-                                             float *mag)
-{
-    const float t = fminf(fmaxf(MUL(MUL(-B, s), invQ), t0), t1);
-    const float a = MUL(MUL(P, s), s);
-    const float b = MUL(MUL(MUL(2.0f, B), s), t);
-    const float c = MUL(MUL(Q, t), t);
-    *mag = fmaxf(*mag, ADD(ADD(a, fabsf(b)), c));
-    return ADD(ADD(a, b), c);
-}
-
-// Tiles of a rectangle of at most 64 tiles (w x h, row-major bits) that the
-// splat can reach with alpha >= 1/255: with d = pixel - mean (mean u + du,
-// v + dv) and q(d) = P dx^2 + 2 B dx dy + Q dy^2, (P, B, Q) = -(A', B'/2, C'),
-// log2 of the raw alpha is log2 o - q(d).  q is convex with minimum 0 at the
-// mean, so over a tile's box of pixel centres that does not contain the mean
-// its minimum lies on an edge; the tile is dropped when log2 o - q_min is below
-// log2(1/255) by more than 1.5e-3 + 4e-6 M (M the magnitude of the terms): more
-// than the rounding of this bound and of the per-pixel evaluation, so a dropped
-// tile is one where every pixel would skip the splat.  One fixed sequence of
-// correctly rounded operations, so the tile lists are reproducible bit for bit.
-__device__ __forceinline__ uint64_t tile_keep_mask(float u, float v, float du, float dv, float log2o, float A2,
-                                                   float B2, float C2, int x0, int y0, int w, int h, int tw, int th)
-{
-    const float P = -A2, Q = -C2, B = MUL(-0.5f, B2);
-    const float invP = DIV(1.0f, P), invQ = DIV(1.0f, Q);
-    const float cut = kLog2AlphaMinF;
-    uint64_t mask = 0;
-    #pragma unroll 1
-    for (int j = 0; j < h; j++) {
-        const float cy0 = (float)((y0 + j) * th) + 0.5f, cy1 = ADD(cy0, (float)(th - 1));
-        const float ey0 = SUB(SUB(cy0, v), dv), ey1 = SUB(SUB(cy1, v), dv);
-        #pragma unroll 1
-        for (int i = 0; i < w; i++) {
-            const float cx0 = (float)((x0 + i) * tw) + 0.5f, cx1 = ADD(cx0, (float)(tw - 1));
-            const float ex0 = SUB(SUB(cx0, u), du), ex1 = SUB(SUB(cx1, u), du);
-            float q = 0.0f, mag = 0.0f;
-            if (!(ex0 <= 0.0f && ex1 >= 0.0f && ey0 <= 0.0f && ey1 >= 0.0f)) {
-                q = fminf(fminf(edge_min_rn(P, B, Q, invQ, ex0, ey0, ey1, &mag),
-                                edge_min_rn(P, B, Q, invQ, ex1, ey0, ey1, &mag)),
-                          fminf(edge_min_rn(Q, B, P, invP, ey0, ex0, ex1, &mag),
-                                edge_min_rn(Q, B, P, invP, ey1, ex0, ex1, &mag)));
-            }
-            if (SUB(log2o, q) >= SUB(cut, ADD(1.5e-3f, MUL(4e-6f, mag)))) mask |= 1ull << (j * w + i);
-        }
-    }
-    return mask;
-}
 
 #undef MUL
 #undef ADD
@@ -306,7 +252,6 @@ struct ProjectArgs {
     uint2 *rect;
     int32_t *radii;
     uint32_t *tiles_touched;
-    unsigned long long *tile_mask;
 };
 
 template <int DEG>
@@ -367,7 +312,6 @@ __global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable v
         if (!geometry(m, ls, q, s_E[v], vt.v[v], a.near_z, a.blur, g)) {
             a.radii[o] = 0;
             a.tiles_touched[o] = 0;
-            a.tile_mask[o] = 0ull;
             continue;
         }
         float dx = m[0] - s_c[v][0], dy = m[1] - s_c[v][1], dz = m[2] - s_c[v][2];
@@ -397,26 +341,14 @@ __global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable v
         const float dv = pixel_remainder(V.fy, yh, yl, zh, zl, V.cy, g.v);
         const uint32_t r0 = (uint32_t)g.x0 | ((uint32_t)g.y0 << 16);
         const uint32_t r1 = (uint32_t)g.x1 | ((uint32_t)g.y1 << 16);
-        const float A2 = __fdiv_rn(__fmul_rn(kNegHalfLog2e, g.cc), g.det);
-        const float B2 = __fdiv_rn(__fmul_rn(kLog2eF, g.cb), g.det);
-        const float C2 = __fdiv_rn(__fmul_rn(kNegHalfLog2e, g.ca), g.det);
         a.rec[3 * o + 0] = make_float4(g.u, g.v, g.z, log2o);
-        a.rec[3 * o + 1] = make_float4(A2, B2, C2, du);
+        a.rec[3 * o + 1] = make_float4(__fdiv_rn(__fmul_rn(kNegHalfLog2e, g.cc), g.det),
+                                       __fdiv_rn(__fmul_rn(kLog2eF, g.cb), g.det),
+                                       __fdiv_rn(__fmul_rn(kNegHalfLog2e, g.ca), g.det), du);
         a.rec[3 * o + 2] = make_float4(col[0], col[1], col[2], dv);
         a.rect[o] = make_uint2(r0, r1);
         a.radii[o] = g.radius;
-        // tiles the splat reaches: the kept bits of a rectangle of up to 64
-        // tiles, else the whole rectangle
-        const int w = g.x1 - g.x0 + 1, h = g.y1 - g.y0 + 1;
-        uint32_t touched = (uint32_t)(w * h);
-        unsigned long long mask = 0ull;
-        if (w * h <= 64) {
-            mask = tile_keep_mask(g.u, g.v, du, dv, log2o, A2, B2, C2, g.x0, g.y0, w, h, vt.v[v].tile_w,
-                                  vt.v[v].tile_h);
-            touched = (uint32_t)__popcll(mask);
-        }
-        a.tile_mask[o] = mask;
-        a.tiles_touched[o] = touched;
+        a.tiles_touched[o] = (uint32_t)((g.x1 - g.x0 + 1) * (g.y1 - g.y0 + 1));
     }
 }
 
@@ -434,10 +366,9 @@ extern "C" gs_status_t gs_project(const gs_params_t *params, const gs_view_t *vi
     if (st != GS_OK) return st;
     if (params->n == 0) return GS_OK;
     if (!params->means || !params->log_scales || !params->quats || !params->opacity_logit || !params->sh ||
-        !out->rec || !out->rect || !out->radii || !out->tiles_touched || !out->tile_mask)
+        !out->rec || !out->rect || !out->radii || !out->tiles_touched)
         return GS_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(out->rect) & 7) || (reinterpret_cast<uintptr_t>(out->tile_mask) & 7))
-        return GS_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(out->rect) & 7) return GS_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(out->rec) & 15) || (reinterpret_cast<uintptr_t>(params->quats) & 15))
         return GS_ERR_INVALID_ARG;
     if ((params->sh_degree == 1 || params->sh_degree == 3) && (reinterpret_cast<uintptr_t>(params->sh) & 15))
@@ -456,7 +387,6 @@ extern "C" gs_status_t gs_project(const gs_params_t *params, const gs_view_t *vi
     a.rect = reinterpret_cast<uint2 *>(out->rect);
     a.radii = out->radii;
     a.tiles_touched = out->tiles_touched;
-    a.tile_mask = reinterpret_cast<unsigned long long *>(out->tile_mask);
     const int threads = 128;
     const unsigned blocks = (unsigned)((params->n + threads - 1) / threads);
     cudaStream_t s = as_stream(stream);

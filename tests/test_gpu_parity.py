@@ -65,10 +65,8 @@ def test_projection_and_binning_bit_exact(name, scene, cams):
     np.testing.assert_array_equal(tt, geom["tiles_touched"])
     np.testing.assert_array_equal(rect[vis], geom["rect"][vis])
     np.testing.assert_array_equal(rec[vis][:, 0:3].view(np.uint32), geom["uvz"][vis].view(np.uint32))
-    # the tiles each splat keeps (exact tile test), bit for bit
-    mask = rast.proj["tile_mask"].cpu().numpy().view(np.uint64)
-    np.testing.assert_array_equal(mask[vis], geom["tile_mask"][vis])
-    assert (tt[vis] < (rect[vis, 2] - rect[vis, 0] + 1) * (rect[vis, 3] - rect[vis, 1] + 1)).any()
+    # the exact tile test kept fewer pairs than the rectangles hold
+    assert rast.n_pairs() < int(tt.astype(np.int64).sum())
     bins = oracle.bin_tiles(cams, geom)
     keys, vals, ranges = gpu_bins(rast)
     assert rast.n_pairs() == bins["n_pairs"]
@@ -397,7 +395,7 @@ def test_capacity_overflow_is_reported_not_fatal():
     rast, p, vm = _run(c["scene"], c["cams"], capacity=500)
     geom = oracle.project_geom(c["scene"], c["cams"])
     assert rast.status() & (1 << 3)
-    assert rast.n_pairs() == int(geom["tiles_touched"].sum()) > 500
+    assert rast.n_pairs() == int(geom["kept"].sum()) > 500
     # the pipeline still completes with in-bounds output
     assert torch.isfinite(rast.img["rgb"]).all()
 
