@@ -363,49 +363,58 @@ void orc_blend_records(int32_t n_views, const orc_view_t *views, int64_t n, cons
     }
 }
 
-/* Minimum over t in [t0, t1] of P s^2 + 2 B s t + Q t^2 at the clamped
- * near-minimiser t = (-B s) (1/Q), FP32; *mag = the largest sum of the
- * magnitudes of the terms. */
-static float orc_edge_min(float P, float B, float Q, float invQ, float s, float t0, float t1, float *mag)
-{
-    float t = fminf(fmaxf((-B * s) * invQ, t0), t1);
-    float a = (P * s) * s;
-    float b = ((2.0f * B) * s) * t;
-    float c = (Q * t) * t;
-    float m = (a + fabsf(b)) + c;
-    if (m > *mag) *mag = m;
-    return (a + b) + c;
-}
-
 /* Keep-mask of the w x h <= 64 tiles of a rectangle from (x0, y0) for a
- * decision record r: bit j * w + i is set unless the splat's log2 of the raw
- * alpha stays below log2(1/255) by more than 1.5e-3 + 4e-6 M over the pixel
- * centres of tile (x0 + i, y0 + j) (M the magnitude of the quadratic form's
- * terms at the box minimum).  With d = pixel - mean, log2 raw alpha =
- * log2 o - q(d), q = P dx^2 + 2 B dx dy + Q dy^2, (P, B, Q) = -(A', B'/2, C');
- * q is convex with minimum 0 at the mean, so over a box not containing the
- * mean its minimum is on an edge.  FP32, in this operation order. */
+ * decision record r: bit j * w + i is set when the splat may reach alpha >=
+ * 1/255 at a pixel of tile (x0 + i, y0 + j).  With d = pixel - mean and
+ * q = P dx^2 + 2 B dx dy + Q dy^2, (P, B, Q) = -(A', B'/2, C'), log2 of the raw
+ * alpha is log2 o - q, so such pixels lie in the ellipse q <= K, K = log2 o -
+ * log2(1/255) + margin, margin = 1.5e-3 + 3.2e-5 (sqrt(PQ) + |B|)^2 / D,
+ * D = PQ - B^2 (twice the FP32 error bound of the per-pixel evaluation inside
+ * the ellipse).  Per tile row (pixel centres y in [a, b]) the ellipse's points
+ * form an x-interval, whose ends are the ellipse's extreme points x = +-X,
+ * X = sqrt(K Q / D), at y = -+B X / Q when those lie in [a, b], else the
+ * crossings of the band's edge y = c: x = (-B c +- sqrt(P K - D c^2)) / P.  A
+ * tile is kept when its pixel centres' x-range meets the interval widened by
+ * 2e-3 + 2e-5 X.  FP32, in this operation order. */
 uint64_t orc_tile_mask(const float *r, int x0, int y0, int w, int h, int tw, int th)
 {
     float u = r[0], v = r[1], du = r[2], dv = r[3], l2o = r[4];
     float P = -r[5], Q = -r[7], B = -0.5f * r[6];
-    float invP = 1.0f / P, invQ = 1.0f / Q;
+    float D = P * Q - B * B;
+    if (!(D > 0.0f)) return ~(uint64_t)0 >> (64 - w * h);
+    float rr = sqrtf(P * Q) + fabsf(B);
+    float K = (l2o - ORC_L2_ALPHA_MIN) + (1.5e-3f + (3.2e-5f * (rr * rr)) / D);
+    if (!(K > 0.0f)) return 0;
+    float X = sqrtf((K * Q) / D);
+    float yR = (-B * X) / Q, yL = -yR;
+    float delta = 2e-3f + 2e-5f * X;
+    float PK = P * K;
     uint64_t mask = 0;
     for (int j = 0; j < h; j++) {
         float cy0 = (float)((y0 + j) * th) + 0.5f, cy1 = cy0 + (float)(th - 1);
-        float ey0 = (cy0 - v) - dv, ey1 = (cy1 - v) - dv;
+        float a = (cy0 - v) - dv, b = (cy1 - v) - dv;
+        float xr, xl;
+        if (yR >= a && yR <= b) {
+            xr = X;
+        } else {
+            float c = yR > b ? b : a;
+            float disc = PK - (D * c) * c;
+            if (!(disc >= 0.0f)) continue;
+            xr = ((-B * c) + sqrtf(disc)) / P;
+        }
+        if (yL >= a && yL <= b) {
+            xl = -X;
+        } else {
+            float c = yL > b ? b : a;
+            float disc = PK - (D * c) * c;
+            if (!(disc >= 0.0f)) continue;
+            xl = ((-B * c) - sqrtf(disc)) / P;
+        }
+        float lo = xl - delta, hi = xr + delta;
         for (int i = 0; i < w; i++) {
             float cx0 = (float)((x0 + i) * tw) + 0.5f, cx1 = cx0 + (float)(tw - 1);
-            float ex0 = (cx0 - u) - du, ex1 = (cx1 - u) - du;
-            float q = 0.0f, mag = 0.0f;
-            if (!(ex0 <= 0.0f && ex1 >= 0.0f && ey0 <= 0.0f && ey1 >= 0.0f)) {
-                float q0 = orc_edge_min(P, B, Q, invQ, ex0, ey0, ey1, &mag);
-                float q1 = orc_edge_min(P, B, Q, invQ, ex1, ey0, ey1, &mag);
-                float q2 = orc_edge_min(Q, B, P, invP, ey0, ex0, ex1, &mag);
-                float q3 = orc_edge_min(Q, B, P, invP, ey1, ex0, ex1, &mag);
-                q = fminf(fminf(q0, q1), fminf(q2, q3));
-            }
-            if (l2o - q >= ORC_L2_ALPHA_MIN - (1.5e-3f + 4e-6f * mag)) mask |= (uint64_t)1 << (j * w + i);
+            float e0 = (cx0 - u) - du, e1 = (cx1 - u) - du;
+            if (lo <= e1 && e0 <= hi) mask |= (uint64_t)1 << (j * w + i);
         }
     }
     return mask;

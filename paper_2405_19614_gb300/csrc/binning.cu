@@ -171,57 +171,67 @@ __global__ void __launch_bounds__(kEmitThreads) vis_compact_kernel(const float *
 #define SUB __fsub_rn
 #define DIV __fdiv_rn
 
-// Minimum over t in [t0, t1] of P s^2 + 2 B s t + Q t^2 for a fixed s, at the
-// clamped near-minimiser t = (-B s) (1/Q) (within a few ulp of the minimiser,
-// which moves the value by far less than the tile test's margin), in correctly
-// rounded operations; *mag receives the largest sum of the magnitudes of the
-// terms.
-__device__ __forceinline__ float edge_min_rn(float P, float B, float Q, float invQ, float s, float t0, float t1,
-                                             float *mag)
-{
-    const float t = fminf(fmaxf(MUL(MUL(-B, s), invQ), t0), t1);
-    const float a = MUL(MUL(P, s), s);
-    const float b = MUL(MUL(MUL(2.0f, B), s), t);
-    const float c = MUL(MUL(Q, t), t);
-    *mag = fmaxf(*mag, ADD(ADD(a, fabsf(b)), c));
-    return ADD(ADD(a, b), c);
-}
-
 // Tiles of a rectangle of at most 64 tiles (w x h, row-major bits from tile
 // (x0, y0)) that a splat can reach with alpha >= 1/255.  With d = pixel -
 // mean (mean u + du, v + dv) and q(d) = P dx^2 + 2 B dx dy + Q dy^2,
 // (P, B, Q) = -(A', B'/2, C') of the record, log2 of the raw alpha is
-// log2 o - q(d).  q is convex with minimum 0 at the mean, so over a tile's box
-// of pixel centres that does not contain the mean its minimum lies on an edge;
-// the tile is dropped when log2 o - q_min is below log2(1/255) by more than
-// 1.5e-3 + 4e-6 M (M the magnitude of the terms): more than the rounding of
-// this bound and of the per-pixel evaluation, so a dropped tile is one where
-// every pixel would skip the splat.  One fixed sequence of correctly rounded
-// operations, so the tile lists are reproducible bit for bit.
+// log2 o - q(d), so the pixels that can blend lie in the ellipse q <= K,
+// K = log2 o - log2(1/255) + margin.  The margin, 1.5e-3 + 3.2e-5
+// (sqrt(PQ) + |B|)^2 / (PQ - B^2), is twice the bound on the FP32 evaluation
+// error of the per-pixel test inside that ellipse (whose terms are at most
+// K (sqrt(PQ) + |B|)^2 / (PQ - B^2) in magnitude).  For each tile row, a
+// horizontal band of pixel centres y in [a, b], the ellipse's points in the
+// band form an x-interval: an end is the ellipse's own extreme point x = +-X,
+// X = sqrt(K Q / (PQ - B^2)) at y = -+B X / Q, when that lies in the band, else
+// where the band's edge y = c crosses the ellipse, x = (-B c +- sqrt(PK -
+// (PQ - B^2) c^2)) / P.  A tile is kept when its pixel centres' x-range meets
+// the interval widened by 2e-3 + 2e-5 X (more than the rounding of the ends).
+// So a dropped tile is one where every pixel would skip the splat.  One fixed
+// sequence of correctly rounded operations, so the tile lists are
+// reproducible bit for bit.
 __device__ __forceinline__ unsigned long long tile_keep_mask(float u, float v, float du, float dv, float log2o,
                                                              float A2, float B2, float C2, int x0, int y0, int w,
                                                              int h, int tw, int th)
 {
     constexpr float kCut = -0x1.ffa37cp+2f;  // log2(1/255) rounded to FP32
     const float P = -A2, Q = -C2, B = MUL(-0.5f, B2);
-    const float invP = DIV(1.0f, P), invQ = DIV(1.0f, Q);
+    const float D = SUB(MUL(P, Q), MUL(B, B));
+    if (!(D > 0.0f)) return ~0ull >> (64 - w * h);  // degenerate: keep every tile
+    const float r = ADD(__fsqrt_rn(MUL(P, Q)), fabsf(B));
+    const float K = ADD(SUB(log2o, kCut), ADD(1.5e-3f, DIV(MUL(3.2e-5f, MUL(r, r)), D)));
+    if (!(K > 0.0f)) return 0ull;  // no pixel reaches the cut
+    const float X = __fsqrt_rn(DIV(MUL(K, Q), D));
+    const float yR = DIV(MUL(-B, X), Q), yL = -yR;  // heights of the rightmost and leftmost points
+    const float delta = ADD(2e-3f, MUL(2e-5f, X));
+    const float PK = MUL(P, K);
     unsigned long long mask = 0ull;
     #pragma unroll 1
     for (int j = 0; j < h; j++) {
         const float cy0 = (float)((y0 + j) * th) + 0.5f, cy1 = ADD(cy0, (float)(th - 1));
-        const float ey0 = SUB(SUB(cy0, v), dv), ey1 = SUB(SUB(cy1, v), dv);
+        const float a = SUB(SUB(cy0, v), dv), b = SUB(SUB(cy1, v), dv);
+        float xr, xl;
+        if (yR >= a && yR <= b) {
+            xr = X;
+        } else {
+            const float c = yR > b ? b : a;
+            const float disc = SUB(PK, MUL(MUL(D, c), c));
+            if (!(disc >= 0.0f)) continue;  // the band misses the ellipse
+            xr = DIV(ADD(MUL(-B, c), __fsqrt_rn(disc)), P);
+        }
+        if (yL >= a && yL <= b) {
+            xl = -X;
+        } else {
+            const float c = yL > b ? b : a;
+            const float disc = SUB(PK, MUL(MUL(D, c), c));
+            if (!(disc >= 0.0f)) continue;
+            xl = DIV(SUB(MUL(-B, c), __fsqrt_rn(disc)), P);
+        }
+        const float lo = SUB(xl, delta), hi = ADD(xr, delta);
         #pragma unroll 1
         for (int i = 0; i < w; i++) {
             const float cx0 = (float)((x0 + i) * tw) + 0.5f, cx1 = ADD(cx0, (float)(tw - 1));
-            const float ex0 = SUB(SUB(cx0, u), du), ex1 = SUB(SUB(cx1, u), du);
-            float q = 0.0f, mag = 0.0f;
-            if (!(ex0 <= 0.0f && ex1 >= 0.0f && ey0 <= 0.0f && ey1 >= 0.0f)) {
-                q = fminf(fminf(edge_min_rn(P, B, Q, invQ, ex0, ey0, ey1, &mag),
-                                edge_min_rn(P, B, Q, invQ, ex1, ey0, ey1, &mag)),
-                          fminf(edge_min_rn(Q, B, P, invP, ey0, ex0, ex1, &mag),
-                                edge_min_rn(Q, B, P, invP, ey1, ex0, ex1, &mag)));
-            }
-            if (SUB(log2o, q) >= SUB(kCut, ADD(1.5e-3f, MUL(4e-6f, mag)))) mask |= 1ull << (j * w + i);
+            const float e0 = SUB(SUB(cx0, u), du), e1 = SUB(SUB(cx1, u), du);
+            if (lo <= e1 && e0 <= hi) mask |= 1ull << (j * w + i);
         }
     }
     return mask;
