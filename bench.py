@@ -314,7 +314,8 @@ def stage_work(w):
     N, V, P, K, Vv, E, B, C, S = (w[k] for k in ("N", "V", "P", "K", "V_vis", "E", "B", "C", "sh_floats"))
     param_b = 4 * (3 + 3 + 4 + 1 + S)
     return {
-        "project": ("hbm", param_b * N + 8 * V * N + 48 * Vv),
+        # parameters read; radius and tile count of every record, the drawn records and their tile masks
+        "project": ("hbm", param_b * N + 8 * V * N + 56 * Vv),
         # tile counts and rectangles read, depth of the drawn records, sorted keys and values and
         # the tile ranges written (the per-tile buckets in between are not counted)
         "bin_sort": ("hbm", 4 * V * N + 12 * Vv + 12 * K + 8 * w["T"]),

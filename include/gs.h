@@ -101,12 +101,21 @@ typedef struct {
  *   rect [., 2] uint32: x0 | y0 << 16 and x1 | y1 << 16, the inclusive tile
  *                       rectangle;
  *   radii [.]   int32 support radius in pixels, 0 = not drawn in that view;
- *   tiles_touched [.] uint32 number of tiles of the rectangle. */
+ *   tile_mask [.] uint64, written for drawn records whose rectangle has
+ *                       w x h <= 64 tiles: bit (j * w + i) set when the splat
+ *                       can reach alpha >= 1/255 in tile (x0 + i, y0 + j) (a
+ *                       conservative FP32 test of the record's quadratic form
+ *                       over the tile's pixel centres, per tile row: a
+ *                       cleared tile is one where every pixel would skip the
+ *                       splat); 8-byte aligned;
+ *   tiles_touched [.] uint32 number of tiles kept (the set bits of tile_mask,
+ *                       or every tile of a larger rectangle); 0 = no pair. */
 typedef struct {
     float *rec;
     uint32_t *rect;
     int32_t *radii;
     uint32_t *tiles_touched;
+    uint64_t *tile_mask;
 } gs_projected_t;
 
 /* Output of gs_bin_sort:
@@ -226,7 +235,7 @@ gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const gs_view_t *
  * synchronisation an allocation may cause, or host frameworks that own all
  * device memory and pass a plugin only its inputs and outputs).  Same inputs,
  * outputs and results as gs_bin_sort, but the scratch workspace is a
- * static device array inside the library (about 89 MiB: exactly gs_bin_sort's
+ * static device array inside the library (about 65 MiB: exactly gs_bin_sort's
  * workspace at both limits), held on every GPU that loads it until the
  * process exits.  Limits: n_views * n <= 2,097,152 records and
  * bins->capacity <= 2,097,152 pairs; every call within them fits, larger

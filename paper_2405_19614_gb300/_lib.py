@@ -45,7 +45,7 @@ class GsOptions(ctypes.Structure):
 
 
 class GsProjected(ctypes.Structure):
-    _fields_ = [("rec", c_p), ("rect", c_p), ("radii", c_p), ("tiles_touched", c_p)]
+    _fields_ = [("rec", c_p), ("rect", c_p), ("radii", c_p), ("tiles_touched", c_p), ("tile_mask", c_p)]
 
 
 class GsBins(ctypes.Structure):

@@ -166,86 +166,10 @@ __global__ void __launch_bounds__(kEmitThreads) vis_compact_kernel(const float *
     flush_hist(h, kDepthPasses, hist);
 }
 
-#define MUL __fmul_rn
-#define ADD __fadd_rn
-#define SUB __fsub_rn
-#define DIV __fdiv_rn
-
-// Tiles of a rectangle of at most 64 tiles (w x h, row-major bits from tile
-// (x0, y0)) that a splat can reach with alpha >= 1/255.  With d = pixel -
-// mean (mean u + du, v + dv) and q(d) = P dx^2 + 2 B dx dy + Q dy^2,
-// (P, B, Q) = -(A', B'/2, C') of the record, log2 of the raw alpha is
-// log2 o - q(d), so the pixels that can blend lie in the ellipse q <= K,
-// K = log2 o - log2(1/255) + margin.  The margin, 1.5e-3 + 3.2e-5
-// (sqrt(PQ) + |B|)^2 / (PQ - B^2), is twice the bound on the FP32 evaluation
-// error of the per-pixel test inside that ellipse (whose terms are at most
-// K (sqrt(PQ) + |B|)^2 / (PQ - B^2) in magnitude).  For each tile row, a
-// horizontal band of pixel centres y in [a, b], the ellipse's points in the
-// band form an x-interval: an end is the ellipse's own extreme point x = +-X,
-// X = sqrt(K Q / (PQ - B^2)) at y = -+B X / Q, when that lies in the band, else
-// where the band's edge y = c crosses the ellipse, x = (-B c +- sqrt(PK -
-// (PQ - B^2) c^2)) / P.  A tile is kept when its pixel centres' x-range meets
-// the interval widened by 2e-3 + 2e-5 X (more than the rounding of the ends).
-// So a dropped tile is one where every pixel would skip the splat.  One fixed
-// sequence of correctly rounded operations, so the tile lists are
-// reproducible bit for bit.
-__device__ __forceinline__ unsigned long long tile_keep_mask(float u, float v, float du, float dv, float log2o,
-                                                             float A2, float B2, float C2, int x0, int y0, int w,
-                                                             int h, int tw, int th)
-{
-    constexpr float kCut = -0x1.ffa37cp+2f;  // log2(1/255) rounded to FP32
-    const float P = -A2, Q = -C2, B = MUL(-0.5f, B2);
-    const float D = SUB(MUL(P, Q), MUL(B, B));
-    if (!(D > 0.0f)) return ~0ull >> (64 - w * h);  // degenerate: keep every tile
-    const float r = ADD(__fsqrt_rn(MUL(P, Q)), fabsf(B));
-    const float K = ADD(SUB(log2o, kCut), ADD(1.5e-3f, DIV(MUL(3.2e-5f, MUL(r, r)), D)));
-    if (!(K > 0.0f)) return 0ull;  // no pixel reaches the cut
-    const float X = __fsqrt_rn(DIV(MUL(K, Q), D));
-    const float yR = DIV(MUL(-B, X), Q), yL = -yR;  // heights of the rightmost and leftmost points
-    const float delta = ADD(2e-3f, MUL(2e-5f, X));
-    const float PK = MUL(P, K);
-    unsigned long long mask = 0ull;
-    #pragma unroll 1
-    for (int j = 0; j < h; j++) {
-        const float cy0 = (float)((y0 + j) * th) + 0.5f, cy1 = ADD(cy0, (float)(th - 1));
-        const float a = SUB(SUB(cy0, v), dv), b = SUB(SUB(cy1, v), dv);
-        float xr, xl;
-        if (yR >= a && yR <= b) {
-            xr = X;
-        } else {
-            const float c = yR > b ? b : a;
-            const float disc = SUB(PK, MUL(MUL(D, c), c));
-            if (!(disc >= 0.0f)) continue;  // the band misses the ellipse
-            xr = DIV(ADD(MUL(-B, c), __fsqrt_rn(disc)), P);
-        }
-        if (yL >= a && yL <= b) {
-            xl = -X;
-        } else {
-            const float c = yL > b ? b : a;
-            const float disc = SUB(PK, MUL(MUL(D, c), c));
-            if (!(disc >= 0.0f)) continue;
-            xl = DIV(SUB(MUL(-B, c), __fsqrt_rn(disc)), P);
-        }
-        const float lo = SUB(xl, delta), hi = ADD(xr, delta);
-        #pragma unroll 1
-        for (int i = 0; i < w; i++) {
-            const float cx0 = (float)((x0 + i) * tw) + 0.5f, cx1 = ADD(cx0, (float)(tw - 1));
-            const float e0 = SUB(SUB(cx0, u), du), e1 = SUB(SUB(cx1, u), du);
-            if (lo <= e1 && e0 <= hi) mask |= 1ull << (j * w + i);
-        }
-    }
-    return mask;
-}
-
-#undef MUL
-#undef ADD
-#undef SUB
-#undef DIV
-
-// Record ids and kept tile counts of the depth-sorted records j < n_vis of a
+// Record ids and tile counts of the depth-sorted records j < n_vis of a
 // block's chunk (thread t holds j = first + 2 t, first + 2 t + 1); recs holds
-// (depth bits, record id) pairs, cnt the counts pair_count wrote.
-__device__ __forceinline__ void chunk_counts(const uint2 *__restrict__ recs, const uint32_t *__restrict__ cnt,
+// (depth bits, record id) pairs.
+__device__ __forceinline__ void chunk_counts(const uint2 *__restrict__ recs, const uint32_t *__restrict__ tt,
                                              uint32_t n_vis, uint32_t (&r)[kPairItems], uint32_t (&c)[kPairItems])
 {
     const int64_t first = (int64_t)blockIdx.x * kPairChunk + (int64_t)threadIdx.x * kPairItems;
@@ -253,19 +177,14 @@ __device__ __forceinline__ void chunk_counts(const uint2 *__restrict__ recs, con
     for (int k = 0; k < kPairItems; k++) {
         const int64_t j = first + k;
         r[k] = j < n_vis ? recs[j].y : 0u;
-        c[k] = j < n_vis ? cnt[j] : 0u;
+        c[k] = j < n_vis ? tt[r[k]] : 0u;
     }
 }
 
-// 2a. The tiles each depth-sorted record keeps (keep-mask and count, for
-// rectangles of up to 64 tiles; every tile of a larger one) and the pairs of
-// each block of kPairChunk records.
+// 2a. Pairs of each block of kPairChunk depth-sorted records.
 __global__ void __launch_bounds__(kEmitThreads) pair_count_kernel(const uint2 *__restrict__ recs,
-                                                                  const uint2 *__restrict__ rect,
-                                                                  const float4 *__restrict__ rec, uint32_t n,
-                                                                  ViewTable vt, const uint32_t *n_vis_p,
-                                                                  uint32_t *cnt, unsigned long long *msk,
-                                                                  uint64_t *block_sums)
+                                                                  const uint32_t *__restrict__ tt,
+                                                                  const uint32_t *n_vis_p, uint64_t *block_sums)
 {
     __shared__ uint64_t tmp[kEmitThreads / 32];
     // the grid covers every record slot; chunks past the drawn records
@@ -275,29 +194,11 @@ __global__ void __launch_bounds__(kEmitThreads) pair_count_kernel(const uint2 *_
         if (threadIdx.x == 0) block_sums[blockIdx.x] = 0;
         return;
     }
-    const int64_t first = (int64_t)blockIdx.x * kPairChunk + (int64_t)threadIdx.x * kPairItems;
+    uint32_t r[kPairItems], c[kPairItems];
+    chunk_counts(recs, tt, n_vis, r, c);
     uint64_t s = 0;
     #pragma unroll
-    for (int k = 0; k < kPairItems; k++) {
-        const int64_t j = first + k;
-        if (j >= n_vis) continue;
-        const uint32_t rid = recs[j].y;
-        const uint2 rr = rect[rid];
-        const int x0 = (int)(rr.x & 0xffff), y0 = (int)(rr.x >> 16);
-        const int w = (int)(rr.y & 0xffff) - x0 + 1, h = (int)(rr.y >> 16) - y0 + 1;
-        uint32_t c = (uint32_t)(w * h);
-        unsigned long long m = 0ull;
-        if (w * h <= 64) {
-            const float4 p = rec[3 * (int64_t)rid], q = rec[3 * (int64_t)rid + 1];
-            const float dv = rec[3 * (int64_t)rid + 2].w;
-            const ViewInfo &V = vt.v[rid / n];
-            m = tile_keep_mask(p.x, p.y, q.w, dv, p.w, q.x, q.y, q.z, x0, y0, w, h, V.tile_w, V.tile_h);
-            c = (uint32_t)__popcll(m);
-        }
-        cnt[j] = c;
-        msk[j] = m;
-        s += c;
-    }
+    for (int k = 0; k < kPairItems; k++) s += c[k];
     uint64_t all;
     block_exclusive_scan_u64(s, tmp, &all);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = all;
@@ -315,8 +216,8 @@ __device__ __forceinline__ int nth_set_bit(unsigned long long m, uint32_t k)
 // keeps (rectangles of up to 64 tiles) or every tile of its rectangle.
 __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__restrict__ recs,
                                                                  const uint2 *__restrict__ rect,
-                                                                 const unsigned long long *__restrict__ msk,
-                                                                 const uint32_t *__restrict__ cnt,
+                                                                 const unsigned long long *__restrict__ tmask,
+                                                                 const uint32_t *__restrict__ tt,
                                                                  const uint32_t *n_vis_p, uint32_t n, ViewTable vt,
                                                                  const uint64_t *__restrict__ block_off, int64_t cap,
                                                                  uint32_t *tk, uint32_t *tv, uint32_t *hist,
@@ -334,7 +235,7 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
     if ((int64_t)blockIdx.x * kPairChunk >= (int64_t)n_vis) return;  // no drawn record: nothing to emit
     clear_hist(h, tile_passes);
     uint32_t r[kPairItems], c[kPairItems];
-    chunk_counts(recs, cnt, n_vis, r, c);
+    chunk_counts(recs, tt, n_vis, r, c);
     uint64_t sum = 0;
     #pragma unroll
     for (int k = 0; k < kPairItems; k++) sum += c[k];
@@ -349,7 +250,7 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
             const uint2 rr = rect[r[k]];
             s_r0[q] = rr.x;
             s_r1[q] = rr.y;
-            s_m[q] = msk[(int64_t)blockIdx.x * kPairChunk + q];
+            s_m[q] = tmask[r[k]];
             s_v[q] = (uint16_t)(r[k] / n);
         }
     }
@@ -480,8 +381,6 @@ struct BinWorkspace {
     uint2 *recs;  // depth-sorted (depth bits, record id)
     uint32_t *lb[2];
     uint32_t *pk, *pv;  // pair buffer
-    uint32_t *cnt;            // kept tiles of each depth-sorted record
-    unsigned long long *msk;  // their keep-masks
     size_t lb_bytes, small_bytes, bytes;
 };
 
@@ -502,8 +401,6 @@ static BinWorkspace carve(void *base, int64_t n_records, int64_t cap)
     w.lb_bytes = o.lb_bytes;
     w.pk = reinterpret_cast<uint32_t *>(p + o.pk);
     w.pv = reinterpret_cast<uint32_t *>(p + o.pv);
-    w.cnt = reinterpret_cast<uint32_t *>(p + o.cnt);
-    w.msk = reinterpret_cast<unsigned long long *>(p + o.msk);
     w.bytes = o.bytes;
     return w;
 }
@@ -543,7 +440,7 @@ extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const 
         if (cudaMemsetAsync(bins->n_pairs, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
         return GS_OK;
     }
-    if (!proj->rec || !proj->rect || !proj->tiles_touched) return GS_ERR_INVALID_ARG;
+    if (!proj->rec || !proj->rect || !proj->tiles_touched || !proj->tile_mask) return GS_ERR_INVALID_ARG;
 
     uint32_t *n_vis = w.small;
     uint32_t *counters = w.small + 1;  // one per pass
@@ -574,12 +471,11 @@ extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const 
     uint32_t *buf_v[2] = {w.pv, reinterpret_cast<uint32_t *>(bins->keys) + cap};
     const int e = (tile_passes & 1) ? 0 : 1;
     const unsigned np = (unsigned)((total + kPairChunk - 1) / kPairChunk);
-    pair_count_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, reinterpret_cast<const uint2 *>(proj->rect),
-                                                  reinterpret_cast<const float4 *>(proj->rec), (uint32_t)n, vt, n_vis,
-                                                  w.cnt, w.msk, w.block_sums);
+    pair_count_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, proj->tiles_touched, n_vis, w.block_sums);
     scan_sums_kernel<<<1, 1024, 0, s>>>(w.block_sums, np, cap, bins->n_pairs, bins->status);
-    pair_emit_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, reinterpret_cast<const uint2 *>(proj->rect), w.msk,
-                                                 w.cnt, n_vis, (uint32_t)n, vt, w.block_sums, cap,
+    pair_emit_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, reinterpret_cast<const uint2 *>(proj->rect),
+                                                  reinterpret_cast<const unsigned long long *>(proj->tile_mask),
+                                                 proj->tiles_touched, n_vis, (uint32_t)n, vt, w.block_sums, cap,
                                                  buf_k[e], buf_v[e], hist_tile, tile_passes);
     st = launch_status();
     if (st != GS_OK) return st;

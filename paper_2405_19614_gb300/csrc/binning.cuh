@@ -23,14 +23,13 @@ constexpr int kSmallWords = 1 + kDepthPasses + kMaxTilePasses + (kDepthPasses + 
 // records and a pair capacity cap, each region 256-byte aligned: scan block
 // sums; the small counters and histograms; two ping-pong buffers of the drawn
 // records' depth keys and ids; their depth-sorted (depth, id) pairs; two
-// look-back regions; the (tile id, depth rank) pair buffer; the kept tile
-// count and tile keep-mask of each depth-sorted record.
+// look-back regions; the (tile id, depth rank) pair buffer.
 struct BinOffsets {
     size_t block_sums = 0, small = 0, small_bytes = 0;
     size_t rz[2] = {0, 0}, rid[2] = {0, 0};
     size_t recs = 0, lb_bytes = 0;
     size_t lb[2] = {0, 0};
-    size_t pk = 0, pv = 0, cnt = 0, msk = 0, bytes = 0;
+    size_t pk = 0, pv = 0, bytes = 0;
 };
 
 constexpr BinOffsets bin_offsets(int64_t n_records, int64_t cap)
@@ -60,10 +59,6 @@ constexpr BinOffsets bin_offsets(int64_t n_records, int64_t cap)
     off += align256(sizeof(uint32_t) * (size_t)cap);
     o.pv = off;
     off += align256(sizeof(uint32_t) * (size_t)cap);
-    o.cnt = off;
-    off += align256(sizeof(uint32_t) * (size_t)n_records);
-    o.msk = off;
-    off += align256(sizeof(uint64_t) * (size_t)n_records);
     o.bytes = off;
     return o;
 }

@@ -16,7 +16,7 @@
 // and a pair capacity of at most kNoAllocMaxPairs (2,097,152 each); larger
 // calls are rejected with GS_ERR_CAPACITY before anything is enqueued.  The
 // array is exactly the workspace gs_bin_sort needs at both limits (about
-// 89 MiB), computed at compile time from the same layout, so every call
+// 65 MiB), computed at compile time from the same layout, so every call
 // within the limits fits.
 //
 // Sharing: every call uses the same array and it keeps the previous call's
@@ -41,7 +41,7 @@ constexpr int64_t kNoAllocMaxPairs = int64_t(1) << 21;    // 2,097,152 pairs
 // the workspace layout is monotone in both sizes, so its size at the limits
 // bounds every call within them
 constexpr size_t kNoAllocScratchBytes = bin_offsets(kNoAllocMaxRecords, kNoAllocMaxPairs).bytes;
-static_assert(kNoAllocScratchBytes <= (size_t(90) << 20), "the fixed scratch array stays about 89 MiB");
+static_assert(kNoAllocScratchBytes <= (size_t(66) << 20), "the fixed scratch array stays about 65 MiB");
 static_assert(kNoAllocScratchBytes % 256 == 0, "whole 256-byte regions");
 
 static __device__ __align__(256) unsigned char g_bin_scratch[kNoAllocScratchBytes];

@@ -238,6 +238,72 @@ __device__ __forceinline__ float pixel_remainder(float f, float xh, float xl, fl
 constexpr float kNegHalfLog2e = -0x1.715476p-1f;
 constexpr float kLog2eF = 0x1.715476p+0f;
 
+// Tiles of a rectangle of at most 64 tiles (w x h, row-major bits from tile
+// (x0, y0)) that a splat can reach with alpha >= 1/255.  With d = pixel -
+// mean (mean u + du, v + dv) and q(d) = P dx^2 + 2 B dx dy + Q dy^2,
+// (P, B, Q) = -(A', B'/2, C') of the record, log2 of the raw alpha is
+// log2 o - q(d), so the pixels that can blend lie in the ellipse q <= K,
+// K = log2 o - log2(1/255) + margin.  The margin, 1.5e-3 + 3.2e-5
+// (sqrt(PQ) + |B|)^2 / (PQ - B^2), is twice the bound on the FP32 evaluation
+// error of the per-pixel test inside that ellipse (whose terms are at most
+// K (sqrt(PQ) + |B|)^2 / (PQ - B^2) in magnitude).  For each tile row, a
+// horizontal band of pixel centres y in [a, b], the ellipse's points in the
+// band form an x-interval: an end is the ellipse's own extreme point x = +-X,
+// X = sqrt(K Q / (PQ - B^2)) at y = -+B X / Q, when that lies in the band, else
+// where the band's edge y = c crosses the ellipse, x = (-B c +- sqrt(PK -
+// (PQ - B^2) c^2)) / P.  A tile is kept when its pixel centres' x-range meets
+// the interval widened by 2e-3 + 2e-5 X (more than the rounding of the ends).
+// So a dropped tile is one where every pixel would skip the splat.  One fixed
+// sequence of correctly rounded operations, so the tile lists are
+// reproducible bit for bit.
+__device__ __forceinline__ unsigned long long tile_keep_mask(float u, float v, float du, float dv, float log2o,
+                                                             float A2, float B2, float C2, int x0, int y0, int w,
+                                                             int h, int tw, int th)
+{
+    constexpr float kCut = -0x1.ffa37cp+2f;  // log2(1/255) rounded to FP32
+    const float P = -A2, Q = -C2, B = MUL(-0.5f, B2);
+    const float D = SUB(MUL(P, Q), MUL(B, B));
+    if (!(D > 0.0f)) return ~0ull >> (64 - w * h);  // degenerate: keep every tile
+    const float r = ADD(__fsqrt_rn(MUL(P, Q)), fabsf(B));
+    const float K = ADD(SUB(log2o, kCut), ADD(1.5e-3f, DIV(MUL(3.2e-5f, MUL(r, r)), D)));
+    if (!(K > 0.0f)) return 0ull;  // no pixel reaches the cut
+    const float X = __fsqrt_rn(DIV(MUL(K, Q), D));
+    const float yR = DIV(MUL(-B, X), Q), yL = -yR;  // heights of the rightmost and leftmost points
+    const float delta = ADD(2e-3f, MUL(2e-5f, X));
+    const float PK = MUL(P, K);
+    unsigned long long mask = 0ull;
+    #pragma unroll 1
+    for (int j = 0; j < h; j++) {
+        const float cy0 = (float)((y0 + j) * th) + 0.5f, cy1 = ADD(cy0, (float)(th - 1));
+        const float a = SUB(SUB(cy0, v), dv), b = SUB(SUB(cy1, v), dv);
+        float xr, xl;
+        if (yR >= a && yR <= b) {
+            xr = X;
+        } else {
+            const float c = yR > b ? b : a;
+            const float disc = SUB(PK, MUL(MUL(D, c), c));
+            if (!(disc >= 0.0f)) continue;  // the band misses the ellipse
+            xr = DIV(ADD(MUL(-B, c), __fsqrt_rn(disc)), P);
+        }
+        if (yL >= a && yL <= b) {
+            xl = -X;
+        } else {
+            const float c = yL > b ? b : a;
+            const float disc = SUB(PK, MUL(MUL(D, c), c));
+            if (!(disc >= 0.0f)) continue;
+            xl = DIV(SUB(MUL(-B, c), __fsqrt_rn(disc)), P);
+        }
+        const float lo = SUB(xl, delta), hi = ADD(xr, delta);
+        #pragma unroll 1
+        for (int i = 0; i < w; i++) {
+            const float cx0 = (float)((x0 + i) * tw) + 0.5f, cx1 = ADD(cx0, (float)(tw - 1));
+            const float e0 = SUB(SUB(cx0, u), du), e1 = SUB(SUB(cx1, u), du);
+            if (lo <= e1 && e0 <= hi) mask |= 1ull << (j * w + i);
+        }
+    }
+    return mask;
+}
+
 #undef MUL
 #undef ADD
 #undef SUB
@@ -252,6 +318,7 @@ struct ProjectArgs {
     uint2 *rect;
     int32_t *radii;
     uint32_t *tiles_touched;
+    unsigned long long *tile_mask;
 };
 
 template <int DEG>
@@ -341,14 +408,25 @@ __global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable v
         const float dv = pixel_remainder(V.fy, yh, yl, zh, zl, V.cy, g.v);
         const uint32_t r0 = (uint32_t)g.x0 | ((uint32_t)g.y0 << 16);
         const uint32_t r1 = (uint32_t)g.x1 | ((uint32_t)g.y1 << 16);
+        const float A2 = __fdiv_rn(__fmul_rn(kNegHalfLog2e, g.cc), g.det);
+        const float B2 = __fdiv_rn(__fmul_rn(kLog2eF, g.cb), g.det);
+        const float C2 = __fdiv_rn(__fmul_rn(kNegHalfLog2e, g.ca), g.det);
         a.rec[3 * o + 0] = make_float4(g.u, g.v, g.z, log2o);
-        a.rec[3 * o + 1] = make_float4(__fdiv_rn(__fmul_rn(kNegHalfLog2e, g.cc), g.det),
-                                       __fdiv_rn(__fmul_rn(kLog2eF, g.cb), g.det),
-                                       __fdiv_rn(__fmul_rn(kNegHalfLog2e, g.ca), g.det), du);
+        a.rec[3 * o + 1] = make_float4(A2, B2, C2, du);
         a.rec[3 * o + 2] = make_float4(col[0], col[1], col[2], dv);
         a.rect[o] = make_uint2(r0, r1);
         a.radii[o] = g.radius;
-        a.tiles_touched[o] = (uint32_t)((g.x1 - g.x0 + 1) * (g.y1 - g.y0 + 1));
+        // the tiles the splat can reach: the kept bits of a rectangle of up to
+        // 64 tiles (written only for drawn records), else the whole rectangle
+        const int w = g.x1 - g.x0 + 1, h = g.y1 - g.y0 + 1;
+        uint32_t touched = (uint32_t)(w * h);
+        if (w * h <= 64) {
+            const unsigned long long mask =
+                tile_keep_mask(g.u, g.v, du, dv, log2o, A2, B2, C2, g.x0, g.y0, w, h, vt.v[v].tile_w, vt.v[v].tile_h);
+            a.tile_mask[o] = mask;
+            touched = (uint32_t)__popcll(mask);
+        }
+        a.tiles_touched[o] = touched;
     }
 }
 
@@ -366,9 +444,10 @@ extern "C" gs_status_t gs_project(const gs_params_t *params, const gs_view_t *vi
     if (st != GS_OK) return st;
     if (params->n == 0) return GS_OK;
     if (!params->means || !params->log_scales || !params->quats || !params->opacity_logit || !params->sh ||
-        !out->rec || !out->rect || !out->radii || !out->tiles_touched)
+        !out->rec || !out->rect || !out->radii || !out->tiles_touched || !out->tile_mask)
         return GS_ERR_INVALID_ARG;
-    if (reinterpret_cast<uintptr_t>(out->rect) & 7) return GS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(out->rect) & 7) || (reinterpret_cast<uintptr_t>(out->tile_mask) & 7))
+        return GS_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(out->rec) & 15) || (reinterpret_cast<uintptr_t>(params->quats) & 15))
         return GS_ERR_INVALID_ARG;
     if ((params->sh_degree == 1 || params->sh_degree == 3) && (reinterpret_cast<uintptr_t>(params->sh) & 15))
@@ -387,6 +466,7 @@ extern "C" gs_status_t gs_project(const gs_params_t *params, const gs_view_t *vi
     a.rect = reinterpret_cast<uint2 *>(out->rect);
     a.radii = out->radii;
     a.tiles_touched = out->tiles_touched;
+    a.tile_mask = reinterpret_cast<unsigned long long *>(out->tile_mask);
     const int threads = 128;
     const unsigned blocks = (unsigned)((params->n + threads - 1) / threads);
     cudaStream_t s = as_stream(stream);

@@ -62,11 +62,14 @@ def test_projection_and_binning_bit_exact(name, scene, cams):
     rec, radii, tt, rect = gpu_geom(rast)
     np.testing.assert_array_equal(radii, geom["radius"])
     vis = geom["radius"] > 0
-    np.testing.assert_array_equal(tt, geom["tiles_touched"])
+    np.testing.assert_array_equal(tt, geom["kept"])
     np.testing.assert_array_equal(rect[vis], geom["rect"][vis])
     np.testing.assert_array_equal(rec[vis][:, 0:3].view(np.uint32), geom["uvz"][vis].view(np.uint32))
-    # the exact tile test kept fewer pairs than the rectangles hold
-    assert rast.n_pairs() < int(tt.astype(np.int64).sum())
+    # the tiles each splat keeps (exact tile test), bit for bit
+    mask = rast.proj["tile_mask"].cpu().numpy().view(np.uint64)
+    small = vis & ((rect[:, 2] - rect[:, 0] + 1) * (rect[:, 3] - rect[:, 1] + 1) <= 64)
+    np.testing.assert_array_equal(mask[small], geom["tile_mask"][small])
+    assert int(geom["kept"].sum()) < int(geom["tiles_touched"].sum())
     bins = oracle.bin_tiles(cams, geom)
     keys, vals, ranges = gpu_bins(rast)
     assert rast.n_pairs() == bins["n_pairs"]

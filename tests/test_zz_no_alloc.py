@@ -76,7 +76,8 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
     big = MAX_RECORDS + 1  # one record past the limit; nothing is enqueued
     proj = dict(rec=torch.zeros(16, device="cuda"), rect=torch.zeros(4, 2, dtype=torch.int32, device="cuda"),
                 radii=torch.zeros(4, dtype=torch.int32, device="cuda"),
-                tiles_touched=torch.zeros(4, dtype=torch.int32, device="cuda"))
+                tiles_touched=torch.zeros(4, dtype=torch.int32, device="cuda"),
+                tile_mask=torch.zeros(4, dtype=torch.int64, device="cuda"))
     bins = dict(keys=torch.zeros(4, dtype=torch.int64, device="cuda"),
                 vals=torch.zeros(4, dtype=torch.int32, device="cuda"),
                 ranges=torch.zeros(12, 2, dtype=torch.int32, device="cuda"),
