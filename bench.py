@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=0, help="run N untimed steps and exit (for ncu)")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default kernel variants")
     ap.add_argument("--no-configs", action="store_true", help="skip the other workloads (configs key)")
+    ap.add_argument("--tile", default="", help="tile shape WxH instead of tuning it (with --variants)")
+    ap.add_argument("--variants", default="", help="compositing variants F,B instead of tuning them")
     ap.add_argument("--configs", default="1,2,3,5", help="other workloads measured after the headline")
     return ap.parse_args()
 
@@ -288,9 +290,10 @@ def traffic_sources_sha256(stage, root=None):
 def kernel_traffic(stage, workload, rast):
     """DRAM bytes per launch of a stage's kernel from the committed ncu
     counters (profiles/traffic.json: one record per stage with the workload,
-    kernel variant, bytes per launch and the SHA-256 of the kernel's sources
-    when they were taken), or None when there is none for this kernel,
-    variant and workload, or when the kernel's sources have changed since."""
+    tile shape, kernel variant, bytes per launch and the SHA-256 of the
+    kernel's sources when they were taken), or None when there is none for
+    this kernel, tile, variant and workload, or when the kernel's sources have
+    changed since."""
     import json
 
     import paper_2405_19614_gb300 as gs
@@ -302,6 +305,8 @@ def kernel_traffic(stage, workload, rast):
     except (OSError, ValueError):
         return None
     if not rec or rec.get("workload") != workload:
+        return None
+    if rast is not None and list(rec.get("tile", [])) != list(rast.tile):
         return None
     _, bwd_variant, _, _ = gs.gs_get_render_variants()
     if traffic_sources_sha256(stage) != rec.get("sources_sha256") or int(rec.get("variant", -1)) != bwd_variant:
@@ -820,7 +825,19 @@ def main_ours(args):
     step.run()
     torch.cuda.synchronize()
     tuned = None
-    if not args.no_tune and not args.profile_steps:
+    if args.tile or args.variants:
+        import paper_2405_19614_gb300 as gs_
+        if args.tile:
+            tw, th = (int(x) for x in args.tile.lower().split("x"))
+            r = step.rast
+            step.rast = gs_.Rasterizer(r.n, r.sh_degree, r.intr, r.size, r.pair_capacity, r.device, r.near_z, r.blur,
+                                       tile=(tw, th))
+        if args.variants:
+            fv, bv = (int(x) for x in args.variants.split(","))
+            gs_.gs_set_render_variants(fv, bv)
+        tuned = {"tile": list(step.rast.tile), "fwd": gs_.gs_get_render_variants()[0],
+                 "bwd": gs_.gs_get_render_variants()[1], "given": True}
+    elif not args.no_tune and not args.profile_steps:
         step.rast, tuned = tune_tiles(step.rast, step.params, step.viewmats, step.d_rgb, step.d_depth)
     for _ in range(max(1, args.warmup)):
         step.run()

@@ -27,11 +27,17 @@ def test_traffic_is_reported_for_the_profiled_sources_only(tmp_path, monkeypatch
                     root / "paper_2405_19614_gb300" / "csrc")
     (root / "profiles").mkdir()
     _, variant, _, _ = gs.gs_get_render_variants()
-    rec = dict(workload=WORKLOAD, variant=variant, bytes_per_launch=123456,
+    rec = dict(workload=WORKLOAD, tile=[32, 16], variant=variant, bytes_per_launch=123456,
                sources_sha256=bench.traffic_sources_sha256("render_bwd", str(root)))
     (root / "profiles" / "traffic.json").write_text(json.dumps({"render_bwd": rec}))
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.kernel_traffic("render_bwd", WORKLOAD, None) == 123456  # record matches the sources
+
+    class R:
+        tile = (32, 16)
+    assert bench.kernel_traffic("render_bwd", WORKLOAD, R()) == 123456
+    R.tile = (16, 16)
+    assert bench.kernel_traffic("render_bwd", WORKLOAD, R()) is None  # another tile shape
     assert bench.kernel_traffic("render_bwd", "another-workload", None) is None
     assert bench.kernel_traffic("ssim", WORKLOAD, None) is None  # no capture for that stage
     # the backward source differs by one byte: nothing is reported
