@@ -19,7 +19,7 @@ BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgs.so")
 
 SOURCES = ["project.cu", "binning.cu", "binning_noalloc.cu", "sort.cu", "render_fwd.cu", "render_bwd.cu", "project_bwd.cu",
-           "loss.cu", "ssim.cu", "reproj.cu", "adam.cu", "map_update.cu", "spatial.cu", "frames.cu"]
+           "loss.cu", "ssim.cu", "reproj.cu", "adam.cu", "map_update.cu", "spatial.cu", "frames.cu", "tma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -118,20 +118,27 @@ constexpr int kRenderThreads = 128;
 #ifndef GS_BWD_BLOCKS_PPT4
 #define GS_BWD_BLOCKS_PPT4 5
 #endif
-template <int PPT>
+// With TMA staging the next chunk waits in shared memory, not registers, and
+// four pixels a thread fit one more block per SM.
+#ifndef GS_BWD_BLOCKS_PPT4_TMA
+#define GS_BWD_BLOCKS_PPT4_TMA 6
+#endif
+template <int PPT, bool TMA = false>
 struct RenderOccupancy {
-    static constexpr int fwd = PPT <= 2 ? 8 : PPT == 4 ? 6 : 4;
-    static constexpr int bwd = PPT <= 2 ? 8 : PPT == 4 ? GS_BWD_BLOCKS_PPT4 : 4;
+    static constexpr int fwd = PPT <= 2 ? 8 : PPT == 4 ? (TMA ? 7 : 6) : 4;
+    static constexpr int bwd = PPT <= 2 ? 8 : PPT == 4 ? (TMA ? GS_BWD_BLOCKS_PPT4_TMA : GS_BWD_BLOCKS_PPT4) : 4;
 };
 
 // Kernel variants the autotuner picks from: a band shape as (pixels per
 // thread, band width) (1, 8) (2, 8) (2, 16) (4, 8) (4, 16) (8, 16), each with a
-// staged chunk of 32 (variants 0-5) or 64 list entries (6-11).  A warp's band
-// is BW x PPT * 32 / BW pixels; a thread's pixels share a column, 32 / BW rows
-// apart.
+// staged chunk of 32 (variants 0-5) or 64 list entries (6-11) loaded by the
+// lanes, or of 32 (12-17) or 64 (18-23) gathered by the tensor memory
+// accelerator.  A warp's band is BW x PPT * 32 / BW pixels; a thread's pixels
+// share a column, 32 / BW rows apart.
 constexpr int kBandVariants = 6;
-constexpr int kFwdVariants = 2 * kBandVariants;
-constexpr int kBwdVariants = 2 * kBandVariants;
+constexpr int kFwdVariants = 4 * kBandVariants;
+constexpr int kBwdVariants = 4 * kBandVariants;
+inline bool variant_gathers(int var) { return var >= 2 * kBandVariants; }
 constexpr int kVariantPPT[kBandVariants] = {1, 2, 2, 4, 4, 8};
 constexpr int kVariantBW[kBandVariants] = {8, 8, 16, 8, 16, 16};
 int render_variant_fwd();

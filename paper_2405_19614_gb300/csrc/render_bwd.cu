@@ -34,6 +34,7 @@
 // entry rarely reaches more than one band.  PPT is picked by the autotuner.
 #include "common.cuh"
 #include "render.cuh"
+#include "tma.cuh"
 
 namespace gs {
 
@@ -47,6 +48,7 @@ struct RenderBwdArgs {
     const float *d_rgb, *d_depth, *d_alpha;
     float *grad2d;
     uint32_t *work_counter;
+    uint32_t *status;  // device error word (a bounded wait that expired), may be null
     uint32_t n_items;  // (view, tile, band) work items, set by the launcher
 };
 
@@ -78,19 +80,36 @@ __device__ __forceinline__ void load_bwd_entry(const RenderBwdArgs &a, int64_t r
     }
 }
 
-template <int PPT, int BW, int CH>
-__global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
-    render_bwd_kernel(RenderBwdArgs a, ViewTable vt)
+// CH list entries (32 or 64: one or two a lane) are loaded, culled and staged
+// together, the next CH loaded while they are walked: by the lanes' own loads
+// (TMA = false), or gathered four records at a time by the tensor memory
+// accelerator into a second shared-memory buffer (tma.cuh).
+template <int PPT, int BW, int CH, bool TMA>
+__global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd)
+    render_bwd_kernel(RenderBwdArgs a, ViewTable vt, const __grid_constant__ CUtensorMap rec_map)
 {
     constexpr int WARPS = kRenderThreads / 32;
     constexpr int RS = 32 / BW;   // rows between a thread's pixels
     constexpr int BH = PPT * RS;  // band height (width BW)
     constexpr int NC = CH / 32;   // entries a lane stages per chunk
-    __shared__ float4 s_rec[WARPS][3][CH];
-    __shared__ uint32_t s_gid[WARPS][CH];
+    __shared__ float4 s_rec[TMA ? 1 : WARPS][3][TMA ? 1 : CH];
+    __shared__ uint32_t s_gid[WARPS][TMA ? 2 : 1][CH];  // Gaussian index of each staged entry (per buffer)
     __shared__ __align__(16) float s_red[WARPS][kRedRows][kRedPitch];
     __shared__ uint32_t s_bgid[WARPS][kBatch];
+    constexpr int kBufBytes = (CH / kGatherRows) * kGatherSlot;
+    __shared__ alignas(128) unsigned char s_tbuf[TMA ? WARPS : 1][2][TMA ? kBufBytes : 16];
+    __shared__ alignas(8) uint64_t s_bar[WARPS][2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t phase = 0;  // TMA: bit k = parity of barrier k's next phase
+    bool tma_failed = false;
+    if (TMA) {
+        if (lane == 0) {
+            mbar_init(&s_bar[warp][0], 1);
+            mbar_init(&s_bar[warp][1], 1);
+            fence_mbar_init();
+        }
+        __syncwarp();
+    }
     const int red_entry = lane / kAcc, red_value = lane % kAcc;  // the row this lane adds up
     for (;;) {
         uint32_t wi = 0;
@@ -175,152 +194,235 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::bwd)
         }
         const uint32_t warp_last = __reduce_max_sync(kFullMask, my_last);
 
+        // the gradients of one staged entry (p, c, col) of Gaussian gid at list
+        // position pos: every pixel pair of the thread, then the warp's sums
+        auto grad_entry = [&](const float4 &p, const float4 &c, const float4 &col, uint32_t gid, uint32_t pos) {
+            // per pixel pair: colour (3) and depth gradients, and the sums
+            // G, S1, S2 (of t = dL/dalpha o g), accumulated two pixels at a time
+            float2 gc[4] = {f2(0.f), f2(0.f), f2(0.f), f2(0.f)};
+            float2 G2 = f2(0.f), S12 = f2(0.f), S22 = f2(0.f);
+            bool contrib = false;
+            const SplatColumn kc = splat_column(p, c, sx);
+            if (pos < my_last) {
+                // the blend tests of all the thread's pixels first, then the
+                // pairs with a blended pixel (independent chains interleave)
+                float2 l2[NP], dy[NP];
+                bool hx[NP], hy[NP];
+                #pragma unroll
+                for (int i = 0; i < NP; i++) {
+                    l2[i] = splat_log2a2(kc, p, c, col,
+                                         f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f),
+                                         &dy[i]);
+                    hx[i] = pos < last[2 * i] && l2[i].x >= kLog2AlphaMin;
+                    hy[i] = pos < last[2 * i + 1] && l2[i].y >= kLog2AlphaMin;
+                }
+                #pragma unroll
+                for (int i = 0; i < NP; i++) {
+                    if (!(hx[i] || hy[i])) continue;
+                    contrib = true;
+                    // a pixel of the pair that does not blend this entry takes
+                    // raw alpha 0, so its w, t and sums are exactly zero
+                    const float2 araw = f2(hx[i] ? ex2_approx(l2[i].x) : 0.0f, hy[i] ? ex2_approx(l2[i].y) : 0.0f);
+                    const float2 al = f2(fminf(kAlphaMax, araw.x), fminf(kAlphaMax, araw.y));
+                    // where the clamp is in force (decided on l2) no gradient passes
+                    const bool cx = l2[i].x >= kLog2AlphaMax, cy = l2[i].y >= kLog2AlphaMax;
+                    const float2 om = __ffma2_rn(al, f2(-1.0f), f2(1.0f));
+                    // 1 - alpha >= 0.01: the fast reciprocal is within 2 ulp
+                    const float2 inv = f2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
+                    const float2 Tb = __fmul2_rn(T[i], inv);
+                    const float2 w = __fmul2_rn(al, Tb);
+                    gc[0] = __ffma2_rn(gC0[i], w, gc[0]);
+                    gc[1] = __ffma2_rn(gC1[i], w, gc[1]);
+                    gc[2] = __ffma2_rn(gC2[i], w, gc[2]);
+                    gc[3] = __ffma2_rn(gD[i], w, gc[3]);
+                    float2 wgt = __fmul2_rn(f2(col.x), gC0[i]);
+                    wgt = __ffma2_rn(f2(col.y), gC1[i], wgt);
+                    wgt = __ffma2_rn(f2(col.z), gC2[i], wgt);
+                    wgt = __ffma2_rn(f2(p.z), gD[i], wgt);
+                    const float2 dalpha = __ffma2_rn(Tb, wgt, __fmul2_rn(R[i], inv));
+                    R[i] = __ffma2_rn(f2(-wgt.x, -wgt.y), w, R[i]);
+                    // T of a pixel that does not blend stays exact
+                    T[i] = f2(hx[i] ? Tb.x : T[i].x, hy[i] ? Tb.y : T[i].y);
+                    const float2 tg = __fmul2_rn(dalpha, araw);
+                    const float2 t = f2(cx ? 0.0f : tg.x, cy ? 0.0f : tg.y);
+                    const float2 u = __fmul2_rn(t, dy[i]);
+                    G2 = __fadd2_rn(G2, t);
+                    S12 = __fadd2_rn(S12, u);
+                    S22 = __ffma2_rn(u, dy[i], S22);
+                }
+            }
+            if (__any_sync(kFullMask, contrib)) {
+                // staged conic (A', B', C') = -log2(e) (A/2, B, C/2)
+                const float G = G2.x + G2.y, S1 = S12.x + S12.y, S2 = S22.x + S22.y;
+                const float dx = kc.dx, dxG = dx * G;
+                float gr[kAcc];
+                gr[0] = (2.0f * kLn2) * c.x * dxG + kLn2 * c.y * S1;  // -(A dx G + B S1)
+                gr[1] = kLn2 * c.y * dxG + (2.0f * kLn2) * c.z * S1;  // -(B dx G + C S1)
+                gr[2] = -0.5f * dx * dxG;
+                gr[3] = -dx * S1;
+                gr[4] = -0.5f * S2;
+                gr[5] = G * ex2_approx(-p.w);  // dL/do = G / o
+                gr[6] = gc[0].x + gc[0].y;
+                gr[7] = gc[1].x + gc[1].y;
+                gr[8] = gc[2].x + gc[2].y;
+                gr[9] = gc[3].x + gc[3].y;
+                #pragma unroll
+                for (int k = 0; k < kAcc; k++) s_red[warp][nb * kAcc + k][lane] = gr[k];
+                if (lane == 0) s_bgid[warp][nb] = gid;
+                if (++nb == kBatch) flush();
+            }
+        };
+
         // chunks [lo, hi) of the list, from the warp's last blend down to 0,
         // CH entries a chunk; within a chunk the entries are taken from the
         // highest index down
         uint32_t hi = warp_last;
         uint32_t lo = hi > (uint32_t)CH ? hi - CH : 0u;
-        float4 n0[NC], n1[NC], n2[NC];
-        uint32_t ng[NC];
-        #pragma unroll
-        for (int c = 0; c < NC; c++)
-            load_bwd_entry(a, rbase, b + lo + 32 * c + lane, lo + 32 * c + lane < hi, n0[c], n1[c], n2[c], ng[c]);
-        while (hi > 0) {
-            const uint32_t nlo = lo > (uint32_t)CH ? lo - CH : 0u;
-            uint32_t todo[NC];
-            __syncwarp();  // the previous chunk's records have been read
-            #pragma unroll
-            for (int c = 0; c < NC; c++) {
-                const float4 r0 = n0[c], r1 = n1[c], r2 = n2[c];
-                const uint32_t g_self = ng[c];
-                const bool have = lo + 32 * c + lane < hi;
-                if (lo > 0)
-                    load_bwd_entry(a, rbase, b + nlo + 32 * c + lane, nlo + 32 * c + lane < lo, n0[c], n1[c], n2[c],
-                                   ng[c]);
-                todo[c] = __ballot_sync(kFullMask, have && !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
-                s_rec[warp][0][32 * c + lane] = r0;
-                s_rec[warp][1][32 * c + lane] = r1;
-                s_rec[warp][2][32 * c + lane] = r2;
-                s_gid[warp][32 * c + lane] = g_self;
-            }
-            __syncwarp();
-            #pragma unroll
-            for (int cc = NC - 1; cc >= 0; cc--)
-            while (todo[cc]) {
-                const int bit = 31 - __clz(todo[cc]);
-                todo[cc] &= ~(1u << bit);
-                const int slot = 32 * cc + bit;
-                const uint32_t pos = lo + (uint32_t)slot;
-                // per pixel pair: colour (3) and depth gradients, and the sums
-                // G, S1, S2 (of t = dL/dalpha o g), accumulated two pixels at a time
-                float2 gc[4] = {f2(0.f), f2(0.f), f2(0.f), f2(0.f)};
-                float2 G2 = f2(0.f), S12 = f2(0.f), S22 = f2(0.f);
-                bool contrib = false;
-                const float4 p = s_rec[warp][0][slot];
-                const float4 c = s_rec[warp][1][slot];
-                const float4 col = s_rec[warp][2][slot];
-                const SplatColumn kc = splat_column(p, c, sx);
-                if (pos < my_last) {
-                    // the blend tests of all the thread's pixels first, then the
-                    // pairs with a blended pixel (independent chains interleave)
-                    float2 l2[NP], dy[NP];
-                    bool hx[NP], hy[NP];
-                    #pragma unroll
-                    for (int i = 0; i < NP; i++) {
-                        l2[i] = splat_log2a2(kc, p, c, col,
-                                             f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f),
-                                             &dy[i]);
-                        hx[i] = pos < last[2 * i] && l2[i].x >= kLog2AlphaMin;
-                        hy[i] = pos < last[2 * i + 1] && l2[i].y >= kLog2AlphaMin;
-                    }
-                    #pragma unroll
-                    for (int i = 0; i < NP; i++) {
-                        if (!(hx[i] || hy[i])) continue;
-                        contrib = true;
-                        // a pixel of the pair that does not blend this entry takes
-                        // raw alpha 0, so its w, t and sums are exactly zero
-                        const float2 araw = f2(hx[i] ? ex2_approx(l2[i].x) : 0.0f, hy[i] ? ex2_approx(l2[i].y) : 0.0f);
-                        const float2 al = f2(fminf(kAlphaMax, araw.x), fminf(kAlphaMax, araw.y));
-                        // where the clamp is in force (decided on l2) no gradient passes
-                        const bool cx = l2[i].x >= kLog2AlphaMax, cy = l2[i].y >= kLog2AlphaMax;
-                        const float2 om = __ffma2_rn(al, f2(-1.0f), f2(1.0f));
-                        // 1 - alpha >= 0.01: the fast reciprocal is within 2 ulp
-                        const float2 inv = f2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
-                        const float2 Tb = __fmul2_rn(T[i], inv);
-                        const float2 w = __fmul2_rn(al, Tb);
-                        gc[0] = __ffma2_rn(gC0[i], w, gc[0]);
-                        gc[1] = __ffma2_rn(gC1[i], w, gc[1]);
-                        gc[2] = __ffma2_rn(gC2[i], w, gc[2]);
-                        gc[3] = __ffma2_rn(gD[i], w, gc[3]);
-                        float2 wgt = __fmul2_rn(f2(col.x), gC0[i]);
-                        wgt = __ffma2_rn(f2(col.y), gC1[i], wgt);
-                        wgt = __ffma2_rn(f2(col.z), gC2[i], wgt);
-                        wgt = __ffma2_rn(f2(p.z), gD[i], wgt);
-                        const float2 dalpha = __ffma2_rn(Tb, wgt, __fmul2_rn(R[i], inv));
-                        R[i] = __ffma2_rn(f2(-wgt.x, -wgt.y), w, R[i]);
-                        // T of a pixel that does not blend stays exact
-                        T[i] = f2(hx[i] ? Tb.x : T[i].x, hy[i] ? Tb.y : T[i].y);
-                        const float2 tg = __fmul2_rn(dalpha, araw);
-                        const float2 t = f2(cx ? 0.0f : tg.x, cy ? 0.0f : tg.y);
-                        const float2 u = __fmul2_rn(t, dy[i]);
-                        G2 = __fadd2_rn(G2, t);
-                        S12 = __fadd2_rn(S12, u);
-                        S22 = __ffma2_rn(u, dy[i], S22);
-                    }
+        if constexpr (TMA) {
+            // the chunk [l0, h0) into buffer kb: each lane fetches its entries'
+            // Gaussian indices, every fourth lane gathers four records
+            auto issue = [&](uint32_t l0, uint32_t h0, int kb) {
+                int row[NC];
+                #pragma unroll
+                for (int c = 0; c < NC; c++) {
+                    const uint32_t idx = l0 + 32 * c + lane;
+                    const uint32_t g = a.vals[b + (idx < h0 ? idx : l0)];  // past the end: a valid row, unused
+                    s_gid[warp][kb][32 * c + lane] = g;
+                    row[c] = (int)(rbase + g);
                 }
-                if (__any_sync(kFullMask, contrib)) {
-                    // staged conic (A', B', C') = -log2(e) (A/2, B, C/2)
-                    const float G = G2.x + G2.y, S1 = S12.x + S12.y, S2 = S22.x + S22.y;
-                    const float dx = kc.dx, dxG = dx * G;
-                    float gr[kAcc];
-                    gr[0] = (2.0f * kLn2) * c.x * dxG + kLn2 * c.y * S1;  // -(A dx G + B S1)
-                    gr[1] = kLn2 * c.y * dxG + (2.0f * kLn2) * c.z * S1;  // -(B dx G + C S1)
-                    gr[2] = -0.5f * dx * dxG;
-                    gr[3] = -dx * S1;
-                    gr[4] = -0.5f * S2;
-                    gr[5] = G * ex2_approx(-p.w);  // dL/do = G / o
-                    gr[6] = gc[0].x + gc[0].y;
-                    gr[7] = gc[1].x + gc[1].y;
-                    gr[8] = gc[2].x + gc[2].y;
-                    gr[9] = gc[3].x + gc[3].y;
-                    #pragma unroll
-                    for (int k = 0; k < kAcc; k++) s_red[warp][nb * kAcc + k][lane] = gr[k];
-                    if (lane == 0) s_bgid[warp][nb] = s_gid[warp][slot];
-                    if (++nb == kBatch) flush();
+                if (lane == 0) mbar_arrive_expect_tx(&s_bar[warp][kb], CH * kRecBytes);
+                __syncwarp();
+                #pragma unroll
+                for (int c = 0; c < NC; c++) {
+                    const int r1 = __shfl_down_sync(kFullMask, row[c], 1);
+                    const int r2 = __shfl_down_sync(kFullMask, row[c], 2);
+                    const int r3 = __shfl_down_sync(kFullMask, row[c], 3);
+                    if ((lane & 3) == 0)
+                        tma_gather4(&s_tbuf[warp][kb][rec_offset(32 * c + lane)], &rec_map, row[c], r1, r2, r3,
+                                    &s_bar[warp][kb]);
                 }
+            };
+            auto wait = [&](int kb) {
+                const bool ok = mbar_wait_parity(&s_bar[warp][kb], (phase >> kb) & 1u);
+                phase ^= 1u << kb;
+                return __all_sync(kFullMask, ok);
+            };
+            bool pend[2] = {false, false};
+            int kb = 0;
+            if (hi > 0) {
+                issue(lo, hi, 0);
+                pend[0] = true;
             }
-            hi = lo;
-            lo = nlo;
+            while (hi > 0) {
+                const uint32_t nlo = lo > (uint32_t)CH ? lo - CH : 0u;
+                if (lo > 0) {
+                    issue(nlo, lo, kb ^ 1);
+                    pend[kb ^ 1] = true;
+                }
+                pend[kb] = false;
+                if (!wait(kb)) {
+                    tma_failed = true;
+                    break;
+                }
+                const unsigned char *buf = s_tbuf[warp][kb];
+                uint32_t todo[NC];
+                #pragma unroll
+                for (int c = 0; c < NC; c++) {
+                    const int slot = 32 * c + lane;
+                    const float4 r0 = *reinterpret_cast<const float4 *>(buf + rec_offset(slot));
+                    const float4 r1 = *reinterpret_cast<const float4 *>(buf + rec_offset(slot) + 16);
+                    todo[c] = __ballot_sync(kFullMask, lo + slot < hi && !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
+                }
+                #pragma unroll
+                for (int cc = NC - 1; cc >= 0; cc--)
+                    while (todo[cc]) {
+                        const int bit = 31 - __clz(todo[cc]);
+                        todo[cc] &= ~(1u << bit);
+                        const int slot = 32 * cc + bit;
+                        const float4 *r = reinterpret_cast<const float4 *>(buf + rec_offset(slot));
+                        grad_entry(r[0], r[1], r[2], s_gid[warp][kb][slot], lo + (uint32_t)slot);
+                    }
+                __syncwarp();  // buffer kb is read before it is filled again
+                hi = lo;
+                lo = nlo;
+                kb ^= 1;
+            }
+            // a chunk gathered ahead of a walk that stopped
+            #pragma unroll
+            for (int k2 = 0; k2 < 2; k2++)
+                if (pend[k2] && !wait(k2)) tma_failed = true;
+        } else {
+            float4 n0[NC], n1[NC], n2[NC];
+            uint32_t ng[NC];
+            #pragma unroll
+            for (int c = 0; c < NC; c++)
+                load_bwd_entry(a, rbase, b + lo + 32 * c + lane, lo + 32 * c + lane < hi, n0[c], n1[c], n2[c], ng[c]);
+            while (hi > 0) {
+                const uint32_t nlo = lo > (uint32_t)CH ? lo - CH : 0u;
+                uint32_t todo[NC];
+                __syncwarp();  // the previous chunk's records have been read
+                #pragma unroll
+                for (int c = 0; c < NC; c++) {
+                    const float4 r0 = n0[c], r1 = n1[c], r2 = n2[c];
+                    const uint32_t g_self = ng[c];
+                    const bool have = lo + 32 * c + lane < hi;
+                    if (lo > 0)
+                        load_bwd_entry(a, rbase, b + nlo + 32 * c + lane, nlo + 32 * c + lane < lo, n0[c], n1[c],
+                                       n2[c], ng[c]);
+                    todo[c] = __ballot_sync(kFullMask, have && !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
+                    s_rec[warp][0][32 * c + lane] = r0;
+                    s_rec[warp][1][32 * c + lane] = r1;
+                    s_rec[warp][2][32 * c + lane] = r2;
+                    s_gid[warp][0][32 * c + lane] = g_self;
+                }
+                __syncwarp();
+                #pragma unroll
+                for (int cc = NC - 1; cc >= 0; cc--)
+                    while (todo[cc]) {
+                        const int bit = 31 - __clz(todo[cc]);
+                        todo[cc] &= ~(1u << bit);
+                        const int slot = 32 * cc + bit;
+                        grad_entry(s_rec[warp][0][slot], s_rec[warp][1][slot], s_rec[warp][2][slot],
+                                   s_gid[warp][0][slot], lo + (uint32_t)slot);
+                    }
+                hi = lo;
+                lo = nlo;
+            }
         }
         if (nb > 0) flush();
+        if (TMA && tma_failed) {  // a gather never completed: report it and stop taking work
+            if (lane == 0) raise_status(a.status, GS_ERR_TIMEOUT);
+            break;
+        }
     }
 }
 
-template <int PPT, int BW, int CH>
-static gs_status_t launch_bwd(RenderBwdArgs a, ViewTable vt, cudaStream_t s)
+template <int PPT, int BW, int CH, bool TMA>
+static gs_status_t launch_bwd(RenderBwdArgs a, ViewTable vt, const CUtensorMap &map, cudaStream_t s)
 {
     // work items: the bands of every tile of every view (tile shapes are per view)
     a.n_items = render_items(&vt, BW, PPT * (32 / BW));
-    auto kern = render_bwd_kernel<PPT, BW, CH>;
+    auto kern = render_bwd_kernel<PPT, BW, CH, TMA>;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, 0);
     const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
     const int64_t blocks_needed = ((int64_t)a.n_items + kRenderThreads / 32 - 1) / (kRenderThreads / 32);
     const int grid = (int)(slots < blocks_needed ? slots : blocks_needed);
-    kern<<<grid > 0 ? grid : 1, kRenderThreads, 0, s>>>(a, vt);
+    kern<<<grid > 0 ? grid : 1, kRenderThreads, 0, s>>>(a, vt, map);
     return launch_status();
 }
 
-template <int CH>
-static gs_status_t dispatch_bwd_ch(int base, const RenderBwdArgs &a, const ViewTable &vt, cudaStream_t s)
+template <int CH, bool TMA>
+static gs_status_t dispatch_bwd_band(int base, const RenderBwdArgs &a, const ViewTable &vt, const CUtensorMap &map,
+                                     cudaStream_t s)
 {
     switch (base) {
-    case 0: return launch_bwd<1, 8, CH>(a, vt, s);
-    case 1: return launch_bwd<2, 8, CH>(a, vt, s);
-    case 2: return launch_bwd<2, 16, CH>(a, vt, s);
-    case 3: return launch_bwd<4, 8, CH>(a, vt, s);
-    case 4: return launch_bwd<4, 16, CH>(a, vt, s);
-    default: return launch_bwd<8, 16, CH>(a, vt, s);
+    case 0: return launch_bwd<1, 8, CH, TMA>(a, vt, map, s);
+    case 1: return launch_bwd<2, 8, CH, TMA>(a, vt, map, s);
+    case 2: return launch_bwd<2, 16, CH, TMA>(a, vt, map, s);
+    case 3: return launch_bwd<4, 8, CH, TMA>(a, vt, map, s);
+    case 4: return launch_bwd<4, 16, CH, TMA>(a, vt, map, s);
+    default: return launch_bwd<8, 16, CH, TMA>(a, vt, map, s);
     }
 }
 
@@ -347,7 +449,6 @@ extern "C" gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t 
         return GS_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(grad2d) & 15) return GS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
-    if (cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
     RenderBwdArgs a = {};
     a.rec = reinterpret_cast<const float4 *>(proj->rec);
     a.n = n;
@@ -360,6 +461,19 @@ extern "C" gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t 
     a.d_alpha = d_alpha;
     a.grad2d = grad2d;
     a.work_counter = work_counter;
-    const int var = fitting_variant(vt, render_variant_bwd());
-    return var < kBandVariants ? dispatch_bwd_ch<32>(var, a, vt, s) : dispatch_bwd_ch<64>(var - kBandVariants, a, vt, s);
+    a.status = bins->status;
+    // the variant and, for the gathering variants, the record tensor map (a
+    // gathering variant whose map cannot be made runs with lane loads)
+    int var = fitting_variant(vt, render_variant_bwd());
+    CUtensorMap map = {};
+    if (variant_gathers(var) && make_record_map(reinterpret_cast<const float *>(a.rec), n * vt.n_views, &map) != GS_OK)
+        var -= 2 * kBandVariants;
+    if (cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
+    const int base = var % kBandVariants;
+    switch (var / kBandVariants) {
+    case 0: return dispatch_bwd_band<32, false>(base, a, vt, map, s);
+    case 1: return dispatch_bwd_band<64, false>(base, a, vt, map, s);
+    case 2: return dispatch_bwd_band<32, true>(base, a, vt, map, s);
+    default: return dispatch_bwd_band<64, true>(base, a, vt, map, s);
+    }
 }

@@ -15,6 +15,7 @@
 // workload by the autotuner, with the band width BW.
 #include "common.cuh"
 #include "render.cuh"
+#include "tma.cuh"
 
 namespace gs {
 
@@ -27,6 +28,7 @@ struct RenderFwdArgs {
     uint32_t *n_contrib;
     uint32_t *n_eval, *n_blend;  // STATS variant only
     uint32_t *work_counter;
+    uint32_t *status;  // device error word (a bounded wait that expired), may be null
     uint32_t n_items;  // (view, tile, band) work items, set by the launcher
     // LOSS variant only: the L1 terms of a6 evaluated as each pixel finishes
     const float *trgb, *tdepth;
@@ -54,10 +56,13 @@ __device__ __forceinline__ void load_entry(const RenderFwdArgs &a, int64_t rbase
 // STATS = true counts, per pixel, the list entries evaluated and blended (the
 // algorithmic work of the compositing, without culling) instead of writing the
 // image.  CH list entries (32 or 64: one or two a lane) are loaded, culled and
-// staged together; the next CH are loaded while they are walked.
-template <int PPT, int BW, int CH, bool STATS, bool LOSS>
-__global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) render_fwd_kernel(RenderFwdArgs a,
-                                                                                             ViewTable vt)
+// staged together; the next CH are loaded while they are walked: by the
+// lanes' own loads into registers (TMA = false), or, with TMA, gathered four
+// records at a time by the tensor memory accelerator straight into a second
+// shared-memory buffer (tma.cuh), which takes the prefetch out of registers.
+template <int PPT, int BW, int CH, bool TMA, bool STATS, bool LOSS>
+__global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd) render_fwd_kernel(
+    RenderFwdArgs a, ViewTable vt, const __grid_constant__ CUtensorMap rec_map)
 {
     __shared__ float s_loss[kRenderThreads / 32];
     float lacc = 0.0f;  // LOSS: this thread's share of the loss
@@ -65,8 +70,22 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
     constexpr int RS = 32 / BW;   // rows between a thread's pixels
     constexpr int BH = PPT * RS;  // band height (width BW)
     constexpr int NC = CH / 32;   // entries a lane stages per chunk
-    __shared__ float4 s_rec[WARPS][3][CH];  // (u, v, z, log2 o), (base-2 conic, du), (rgb, dv) of a chunk
+    // (u, v, z, log2 o), (base-2 conic, du), (rgb, dv) of a chunk
+    __shared__ float4 s_rec[TMA ? 1 : WARPS][3][TMA ? 1 : CH];
+    constexpr int kBufBytes = (CH / kGatherRows) * kGatherSlot;
+    __shared__ alignas(128) unsigned char s_tbuf[TMA ? WARPS : 1][2][TMA ? kBufBytes : 16];
+    __shared__ alignas(8) uint64_t s_bar[WARPS][2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t phase = 0;     // TMA: bit k = parity of barrier k's next phase
+    bool tma_failed = false;
+    if (TMA) {
+        if (lane == 0) {
+            mbar_init(&s_bar[warp][0], 1);
+            mbar_init(&s_bar[warp][1], 1);
+            fence_mbar_init();
+        }
+        __syncwarp();
+    }
     for (;;) {
         uint32_t wi = 0;
         if (lane == 0) wi = atomicAdd(a.work_counter, 1u);
@@ -110,6 +129,119 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
             live[k] = k < PPT && px < V.width && (py0 + RS * k) < V.height;
             alive += live[k];
         }
+        // the walk of one staged entry (p, c, col): the thread's pixel pairs
+        auto blend_entry = [&](const float4 &p, const float4 &cc, const float4 &col, uint32_t pos) {
+            const SplatColumn kc = splat_column(p, cc, sx);
+            // two pixels per packed evaluation and update; branch-free per
+            // pixel (a skipped pixel adds exactly zero), so the chains interleave
+            #pragma unroll
+            for (int i = 0; i < NP; i++) {
+                float2 dy;
+                const float2 l2 = splat_log2a2(
+                    kc, p, cc, col, f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f),
+                    &dy);
+                const float2 al = f2(alpha_of_l2(l2.x), alpha_of_l2(l2.y));
+                const float2 tT = __fmul2_rn(T[i], __fadd2_rn(f2(1.0f), f2(-al.x, -al.y)));  // T (1 - alpha)
+                const float2 aT = __fmul2_rn(al, T[i]);
+                bool blend[2];
+                #pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int k = 2 * i + h;
+                    const bool hit = live[k] && (h ? l2.y : l2.x) >= kLog2AlphaMin;
+                    const bool stop = hit && (h ? tT.y : tT.x) < kTMin;  // stops before this entry
+                    blend[h] = hit && !stop;
+                    if (STATS) {
+                        n_eval[k] += live[k];
+                        n_blend[k] += blend[h];
+                    }
+                    last[k] = blend[h] ? pos + 1u : last[k];
+                    live[k] = live[k] && !stop;
+                    alive -= stop;
+                }
+                const float2 w = f2(blend[0] ? aT.x : 0.0f, blend[1] ? aT.y : 0.0f);
+                C0[i] = __ffma2_rn(f2(col.x), w, C0[i]);
+                C1[i] = __ffma2_rn(f2(col.y), w, C1[i]);
+                C2[i] = __ffma2_rn(f2(col.z), w, C2[i]);
+                D[i] = __ffma2_rn(f2(p.z), w, D[i]);
+                T[i] = f2(blend[0] ? tT.x : T[i].x, blend[1] ? tT.y : T[i].y);
+            }
+        };
+        if constexpr (TMA) {
+            // chunks through two shared-memory buffers: the next chunk's
+            // records are gathered by the TMA while this one is walked
+            auto issue = [&](uint32_t m0, int kb) {
+                int row[NC];
+                #pragma unroll
+                for (int c = 0; c < NC; c++) {
+                    const uint32_t idx = m0 + 32 * c + lane;
+                    row[c] = (int)(rbase + a.vals[idx < e ? idx : m0]);  // past the end: a valid row, unused
+                }
+                if (lane == 0) mbar_arrive_expect_tx(&s_bar[warp][kb], CH * kRecBytes);
+                __syncwarp();
+                #pragma unroll
+                for (int c = 0; c < NC; c++) {
+                    const int r1 = __shfl_down_sync(kFullMask, row[c], 1);
+                    const int r2 = __shfl_down_sync(kFullMask, row[c], 2);
+                    const int r3 = __shfl_down_sync(kFullMask, row[c], 3);
+                    if ((lane & 3) == 0)
+                        tma_gather4(&s_tbuf[warp][kb][rec_offset(32 * c + lane)], &rec_map, row[c], r1, r2, r3,
+                                    &s_bar[warp][kb]);
+                }
+            };
+            auto wait = [&](int kb) {
+                const bool ok = mbar_wait_parity(&s_bar[warp][kb], (phase >> kb) & 1u);
+                phase ^= 1u << kb;
+                return __all_sync(kFullMask, ok);
+            };
+            bool pend[2] = {false, false};
+            int kb = 0;
+            if (b < e) {
+                issue(b, 0);
+                pend[0] = true;
+            }
+            for (uint32_t m = b; m < e; m += CH, kb ^= 1) {
+                if (!__any_sync(kFullMask, alive > 0)) break;
+                if (m + CH < e) {
+                    issue(m + CH, kb ^ 1);
+                    pend[kb ^ 1] = true;
+                }
+                pend[kb] = false;
+                if (!wait(kb)) {
+                    tma_failed = true;
+                    break;
+                }
+                const unsigned char *buf = s_tbuf[warp][kb];
+                uint32_t todo[NC];
+                #pragma unroll
+                for (int c = 0; c < NC; c++) {
+                    const int slot = 32 * c + lane;
+                    const float4 p = *reinterpret_cast<const float4 *>(buf + rec_offset(slot));
+                    const float4 cc = *reinterpret_cast<const float4 *>(buf + rec_offset(slot) + 16);
+                    const bool keep = m + slot < e && (STATS || !splat_misses_box(p, cc, bx0, bx1, by0, by1));
+                    todo[c] = alive == 0 ? 0u : __ballot_sync(kFullMask, keep);
+                }
+                #pragma unroll
+                for (int c = 0; c < NC; c++) {
+                    while (todo[c]) {
+                        const int j = __ffs(todo[c]) - 1;
+                        todo[c] &= todo[c] - 1;
+                        const int slot = 32 * c + j;
+                        const float4 *r = reinterpret_cast<const float4 *>(buf + rec_offset(slot));
+                        blend_entry(r[0], r[1], r[2], m - b + (uint32_t)slot);
+                        if (alive == 0) {
+                            #pragma unroll
+                            for (int c2 = 0; c2 < NC; c2++) todo[c2] = 0;
+                            break;
+                        }
+                    }
+                }
+                __syncwarp();  // buffer kb is read before it is filled again
+            }
+            // a chunk gathered ahead of a walk that stopped early
+            #pragma unroll
+            for (int k2 = 0; k2 < 2; k2++)
+                if (pend[k2] && !wait(k2)) tma_failed = true;
+        } else {
         float4 n0[NC], n1[NC], n2[NC];  // this lane's entries of the next chunk
         #pragma unroll
         for (int c = 0; c < NC; c++) load_entry(a, rbase, b + 32 * c + lane, e, n0[c], n1[c], n2[c]);
@@ -136,43 +268,8 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
                     const int j = __ffs(todo[c]) - 1;
                     todo[c] &= todo[c] - 1;
                     const int slot = 32 * c + j;
-                    const float4 p = s_rec[warp][0][slot];
-                    const float4 cc = s_rec[warp][1][slot];
-                    const float4 col = s_rec[warp][2][slot];
-                    const SplatColumn kc = splat_column(p, cc, sx);
-                    // two pixels per packed evaluation and update; branch-free per
-                    // pixel (a skipped pixel adds exactly zero), so the chains interleave
-                    #pragma unroll
-                    for (int i = 0; i < NP; i++) {
-                        float2 dy;
-                        const float2 l2 = splat_log2a2(
-                            kc, p, cc, col,
-                            f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f), &dy);
-                        const float2 al = f2(alpha_of_l2(l2.x), alpha_of_l2(l2.y));
-                        const float2 tT = __fmul2_rn(T[i], __fadd2_rn(f2(1.0f), f2(-al.x, -al.y)));  // T (1 - alpha)
-                        const float2 aT = __fmul2_rn(al, T[i]);
-                        bool blend[2];
-                        #pragma unroll
-                        for (int h = 0; h < 2; h++) {
-                            const int k = 2 * i + h;
-                            const bool hit = live[k] && (h ? l2.y : l2.x) >= kLog2AlphaMin;
-                            const bool stop = hit && (h ? tT.y : tT.x) < kTMin;  // stops before this entry
-                            blend[h] = hit && !stop;
-                            if (STATS) {
-                                n_eval[k] += live[k];
-                                n_blend[k] += blend[h];
-                            }
-                            last[k] = blend[h] ? m - b + (uint32_t)slot + 1u : last[k];
-                            live[k] = live[k] && !stop;
-                            alive -= stop;
-                        }
-                        const float2 w = f2(blend[0] ? aT.x : 0.0f, blend[1] ? aT.y : 0.0f);
-                        C0[i] = __ffma2_rn(f2(col.x), w, C0[i]);
-                        C1[i] = __ffma2_rn(f2(col.y), w, C1[i]);
-                        C2[i] = __ffma2_rn(f2(col.z), w, C2[i]);
-                        D[i] = __ffma2_rn(f2(p.z), w, D[i]);
-                        T[i] = f2(blend[0] ? tT.x : T[i].x, blend[1] ? tT.y : T[i].y);
-                    }
+                    blend_entry(s_rec[warp][0][slot], s_rec[warp][1][slot], s_rec[warp][2][slot],
+                                m - b + (uint32_t)slot);
                     if (alive == 0) {
                         #pragma unroll
                         for (int c2 = 0; c2 < NC; c2++) todo[c2] = 0;
@@ -180,6 +277,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
                     }
                 }
             }
+        }
         }
         #pragma unroll
         for (int k = 0; k < PPT; k++) {
@@ -221,6 +319,10 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
                 }
             }
         }
+        if (TMA && tma_failed) {  // a gather never completed: report it and stop taking work
+            if (lane == 0) raise_status(a.status, GS_ERR_TIMEOUT);
+            break;
+        }
     }
     if (LOSS) {  // one atomic per block (every warp has left the item loop)
         lacc = warp_sum(lacc);
@@ -235,40 +337,57 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT>::fwd) ren
     }
 }
 
-template <int PPT, int BW, int CH, bool STATS, bool LOSS = false>
-static gs_status_t launch_fwd(RenderFwdArgs a, ViewTable vt, cudaStream_t s)
+template <int PPT, int BW, int CH, bool TMA, bool STATS, bool LOSS = false>
+static gs_status_t launch_fwd(RenderFwdArgs a, ViewTable vt, const CUtensorMap &map, cudaStream_t s)
 {
     // work items: the bands of every tile of every view (tile shapes are per view)
     a.n_items = render_items(&vt, BW, PPT * (32 / BW));
-    auto kern = render_fwd_kernel<PPT, BW, CH, STATS, LOSS>;
+    auto kern = render_fwd_kernel<PPT, BW, CH, TMA, STATS, LOSS>;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, 0);
     const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
     const int64_t blocks_needed = ((int64_t)a.n_items + kRenderThreads / 32 - 1) / (kRenderThreads / 32);
     const int grid = (int)(slots < blocks_needed ? slots : blocks_needed);
-    kern<<<grid > 0 ? grid : 1, kRenderThreads, 0, s>>>(a, vt);
+    kern<<<grid > 0 ? grid : 1, kRenderThreads, 0, s>>>(a, vt, map);
     return launch_status();
 }
 
-template <int CH, bool STATS, bool LOSS>
-static gs_status_t dispatch_fwd_ch(int base, const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
+template <int CH, bool TMA, bool STATS, bool LOSS>
+static gs_status_t dispatch_fwd_band(int base, const RenderFwdArgs &a, const ViewTable &vt, const CUtensorMap &map,
+                                     cudaStream_t s)
 {
     switch (base) {
-    case 0: return launch_fwd<1, 8, CH, STATS, LOSS>(a, vt, s);
-    case 1: return launch_fwd<2, 8, CH, STATS, LOSS>(a, vt, s);
-    case 2: return launch_fwd<2, 16, CH, STATS, LOSS>(a, vt, s);
-    case 3: return launch_fwd<4, 8, CH, STATS, LOSS>(a, vt, s);
-    case 4: return launch_fwd<4, 16, CH, STATS, LOSS>(a, vt, s);
-    default: return launch_fwd<8, 16, CH, STATS, LOSS>(a, vt, s);
+    case 0: return launch_fwd<1, 8, CH, TMA, STATS, LOSS>(a, vt, map, s);
+    case 1: return launch_fwd<2, 8, CH, TMA, STATS, LOSS>(a, vt, map, s);
+    case 2: return launch_fwd<2, 16, CH, TMA, STATS, LOSS>(a, vt, map, s);
+    case 3: return launch_fwd<4, 8, CH, TMA, STATS, LOSS>(a, vt, map, s);
+    case 4: return launch_fwd<4, 16, CH, TMA, STATS, LOSS>(a, vt, map, s);
+    default: return launch_fwd<8, 16, CH, TMA, STATS, LOSS>(a, vt, map, s);
     }
 }
 
-template <bool STATS, bool LOSS = false>
-static gs_status_t dispatch_fwd(const RenderFwdArgs &a, const ViewTable &vt, cudaStream_t s)
+// The variant to launch and, for the gathering variants, the record tensor
+// map (host work only: nothing is enqueued).  A gathering variant whose map
+// cannot be made (no records) runs as the same variant with lane loads.
+static int prepare_fwd(const RenderFwdArgs &a, const ViewTable &vt, int var, CUtensorMap *map)
 {
-    const int var = fitting_variant(vt, render_variant_fwd());
-    return var < kBandVariants ? dispatch_fwd_ch<32, STATS, LOSS>(var, a, vt, s)
-                               : dispatch_fwd_ch<64, STATS, LOSS>(var - kBandVariants, a, vt, s);
+    var = fitting_variant(vt, var);
+    if (variant_gathers(var) && make_record_map(reinterpret_cast<const float *>(a.rec), a.n * vt.n_views, map) != GS_OK)
+        var -= 2 * kBandVariants;
+    return var;
+}
+
+template <bool STATS, bool LOSS = false>
+static gs_status_t dispatch_fwd(int var, const RenderFwdArgs &a, const ViewTable &vt, const CUtensorMap &map,
+                                cudaStream_t s)
+{
+    const int base = var % kBandVariants;
+    switch (var / kBandVariants) {
+    case 0: return dispatch_fwd_band<32, false, STATS, LOSS>(base, a, vt, map, s);
+    case 1: return dispatch_fwd_band<64, false, STATS, LOSS>(base, a, vt, map, s);
+    case 2: return dispatch_fwd_band<32, true, STATS, LOSS>(base, a, vt, map, s);
+    default: return dispatch_fwd_band<64, true, STATS, LOSS>(base, a, vt, map, s);
+    }
 }
 
 }  // namespace gs
@@ -287,7 +406,6 @@ extern "C" gs_status_t gs_render_fwd(const gs_projected_t *proj, int64_t n, cons
         !bins->vals || (n > 0 && !proj->rec))
         return GS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
-    if (cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
     RenderFwdArgs a = {};
     a.rec = reinterpret_cast<const float4 *>(proj->rec);
     a.n = n;
@@ -299,7 +417,11 @@ extern "C" gs_status_t gs_render_fwd(const gs_projected_t *proj, int64_t n, cons
     a.final_T = img->final_T;
     a.n_contrib = img->n_contrib;
     a.work_counter = work_counter;
-    return dispatch_fwd<false>(a, vt, s);
+    a.status = bins->status;
+    CUtensorMap map = {};
+    const int var = prepare_fwd(a, vt, render_variant_fwd(), &map);
+    if (cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
+    return dispatch_fwd<false>(var, a, vt, map, s);
 }
 
 extern "C" gs_status_t gs_render_fwd_l1(const gs_projected_t *proj, int64_t n, const gs_bins_t *bins,
@@ -316,7 +438,6 @@ extern "C" gs_status_t gs_render_fwd_l1(const gs_projected_t *proj, int64_t n, c
         !bins->vals || (n > 0 && !proj->rec) || !target_rgb || !target_depth || !loss || !d_rgb || !d_depth)
         return GS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
-    if (cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
     RenderFwdArgs a = {};
     a.rec = reinterpret_cast<const float4 *>(proj->rec);
     a.n = n;
@@ -328,6 +449,7 @@ extern "C" gs_status_t gs_render_fwd_l1(const gs_projected_t *proj, int64_t n, c
     a.final_T = img->final_T;
     a.n_contrib = img->n_contrib;
     a.work_counter = work_counter;
+    a.status = bins->status;
     // the weights of gs_loss_l1, over all pixels of the views
     a.kc = (float)((double)w_c / (3.0 * (double)vt.n_pix_total));
     a.kd = (float)((double)w_d / (double)vt.n_pix_total);
@@ -338,7 +460,10 @@ extern "C" gs_status_t gs_render_fwd_l1(const gs_projected_t *proj, int64_t n, c
     a.loss = loss;
     a.d_rgb = d_rgb;
     a.d_depth = d_depth;
-    return dispatch_fwd<false, true>(a, vt, s);
+    CUtensorMap map = {};
+    const int var = prepare_fwd(a, vt, render_variant_fwd(), &map);
+    if (cudaMemsetAsync(work_counter, 0, sizeof(uint32_t), s) != cudaSuccess) return GS_ERR_CUDA;
+    return dispatch_fwd<false, true>(var, a, vt, map, s);
 }
 
 extern "C" gs_status_t gs_render_stats(const gs_projected_t *proj, int64_t n, const gs_bins_t *bins,
@@ -360,7 +485,9 @@ extern "C" gs_status_t gs_render_stats(const gs_projected_t *proj, int64_t n, co
     a.n_eval = n_eval;
     a.n_blend = n_blend;
     a.work_counter = work_counter;
-    return launch_fwd<1, 16, 32, true>(a, vt, s);
+    a.status = bins->status;
+    const CUtensorMap none = {};
+    return launch_fwd<1, 16, 32, false, true>(a, vt, none, s);
 }
 
 // Compositing kernel variants in use (see kFwdVariants), set by the

@@ -1,0 +1,45 @@
+// Host side of the record tensor maps (tma.cuh): encoded with the driver's
+// cuTensorMapEncodeTiled, looked up once through the runtime's driver entry
+// point query (no link against the driver library).
+#include <mutex>
+
+#include "tma.cuh"
+
+namespace gs {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+gs_status_t make_record_map(const float *rec, int64_t rows, CUtensorMap *map)
+{
+    if (!rec || rows < 1 || rows >= (int64_t(1) << 31) || (reinterpret_cast<uintptr_t>(rec) & 15))
+        return GS_ERR_INVALID_ARG;
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return GS_ERR_UNSUPPORTED;
+    const cuuint64_t dims[2] = {(cuuint64_t)kRecFloats, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)kRecBytes};  // bytes between rows, a multiple of 16
+    const cuuint32_t box[2] = {(cuuint32_t)kRecFloats, 1u};  // one row of 48 bytes (gather4 boxes are one row high)
+    const cuuint32_t estrides[2] = {1u, 1u};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(rec), dims, strides, box,
+                          estrides, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? GS_OK : GS_ERR_INVALID_ARG;
+}
+
+}  // namespace gs
