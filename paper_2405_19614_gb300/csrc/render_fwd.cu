@@ -78,6 +78,9 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t phase = 0;     // TMA: bit k = parity of barrier k's next phase
     bool tma_failed = false;
+    // the tensor map's address in the parameter space (taken here, outside
+    // any lambda, so that it is the parameter itself and not a copy)
+    const CUtensorMap *map = &rec_map;
     if (TMA) {
         if (lane == 0) {
             mbar_init(&s_bar[warp][0], 1);
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
                     const int r2 = __shfl_down_sync(kFullMask, row[c], 2);
                     const int r3 = __shfl_down_sync(kFullMask, row[c], 3);
                     if ((lane & 3) == 0)
-                        tma_gather4(&s_tbuf[warp][kb][rec_offset(32 * c + lane)], &rec_map, row[c], r1, r2, r3,
+                        tma_gather4(&s_tbuf[warp][kb][rec_offset(32 * c + lane)], map, row[c], r1, r2, r3,
                                     &s_bar[warp][kb]);
                 }
             };
@@ -218,7 +221,8 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
                     const float4 p = *reinterpret_cast<const float4 *>(buf + rec_offset(slot));
                     const float4 cc = *reinterpret_cast<const float4 *>(buf + rec_offset(slot) + 16);
                     const bool keep = m + slot < e && (STATS || !splat_misses_box(p, cc, bx0, bx1, by0, by1));
-                    todo[c] = alive == 0 ? 0u : __ballot_sync(kFullMask, keep);
+                    todo[c] = __ballot_sync(kFullMask, keep);  // every lane takes part
+                    if (alive == 0) todo[c] = 0;
                 }
                 #pragma unroll
                 for (int c = 0; c < NC; c++) {

@@ -20,7 +20,7 @@ constexpr int kRecFloats = 12;
 constexpr int kRecBytes = 4 * kRecFloats;  // 48
 constexpr int kGatherRows = 4;             // rows per gather4
 constexpr int kGatherSlot = 256;           // bytes between gather4 destinations (128-byte aligned)
-constexpr uint32_t kTmaSpinLimit = 1u << 22;  // waits of about 32 ns before a wait gives up
+constexpr uint32_t kTmaSpinLimit = 1u << 16;  // tries (each may suspend briefly) before a wait gives up
 
 // A record (row r) lands at slot r % 4 of group r / 4 of a chunk buffer.
 __host__ __device__ constexpr int rec_offset(int slot)
@@ -42,6 +42,7 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 __device__ __forceinline__ void fence_mbar_init()
 {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
@@ -51,7 +52,9 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
 }
 
 // Waits until the barrier's phase with the given parity has completed; gives
-// up after kTmaSpinLimit tries (returns false).
+// up after kTmaSpinLimit tries (returns false).  A gather completes within
+// microseconds; the limit is far beyond that and still ends a broken wait in
+// well under a second.
 __device__ __forceinline__ bool mbar_wait_parity(uint64_t *bar, uint32_t parity)
 {
     const uint32_t a = smem_addr(bar);
