@@ -127,7 +127,8 @@ def tune_tiles(rast, params, viewmats, d_rgb, d_depth, candidates=TILE_CANDIDATE
         if r.status() != 0:  # this shape overflows the pair capacity
             continue
         total = binning + t["fwd_ms"][str(t["fwd"])] + t["bwd_ms"][str(t["bwd"])]
-        results[f"{tile[0]}x{tile[1]}"] = dict(total_ms=total, binning_ms=binning, fwd=t["fwd"], bwd=t["bwd"])
+        results[f"{tile[0]}x{tile[1]}"] = dict(total_ms=total, binning_ms=binning, fwd=t["fwd"], bwd=t["bwd"],
+                                               fwd_ms=t["fwd_ms"], bwd_ms=t["bwd_ms"])
         if best is None or total < best[0]:
             best = (total, r, t)
         elif r is not rast:
