@@ -8,6 +8,17 @@ namespace gs {
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+// A 16-byte shared-memory load the compiler may not move out of a loop (the
+// value stays in shared memory, not in registers, between uses).
+__device__ __forceinline__ float4 ld_shared_f4(const float4 *p)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)));
+    return v;
+}
+
 // 2^x by the approximate base-2 exponential instruction (a relative error of
 // a few units in the last place; results below 2^-126 flush to zero).
 __device__ __forceinline__ float ex2_approx(float x)
@@ -123,10 +134,16 @@ constexpr int kRenderThreads = 128;
 #ifndef GS_BWD_BLOCKS_PPT4_TMA
 #define GS_BWD_BLOCKS_PPT4_TMA 6
 #endif
+// Eight pixels a thread (upstream gradients in shared memory): about 120
+// registers; at 96 (five blocks) the compiler needs 20 % more instructions.
+#ifndef GS_BWD_BLOCKS_PPT8
+#define GS_BWD_BLOCKS_PPT8 4
+#endif
 template <int PPT, bool TMA = false>
 struct RenderOccupancy {
     static constexpr int fwd = PPT <= 2 ? 8 : PPT == 4 ? (TMA ? 7 : 6) : 4;
-    static constexpr int bwd = PPT <= 2 ? 8 : PPT == 4 ? (TMA ? GS_BWD_BLOCKS_PPT4_TMA : GS_BWD_BLOCKS_PPT4) : 4;
+    static constexpr int bwd = PPT <= 2 ? 8 : PPT == 4 ? (TMA ? GS_BWD_BLOCKS_PPT4_TMA : GS_BWD_BLOCKS_PPT4)
+                                                         : GS_BWD_BLOCKS_PPT8;
 };
 
 // Kernel variants the autotuner picks from: a band shape as (pixels per

@@ -31,7 +31,10 @@
 // entries); the 30 lanes holding a total add them to HBM in one predicated
 // atomic instruction.  Per
 // warp band rather than per tile costs few extra atomics: after culling an
-// entry rarely reaches more than one band.  PPT is picked by the autotuner.
+// entry rarely reaches more than one band.  With eight pixels a thread a band
+// is a 16 x 16 item whose two halves are culled apart: an entry kept in both
+// is reduced once, an entry kept in one is tested in that half only.  PPT is
+// picked by the autotuner.
 #include "common.cuh"
 #include "render.cuh"
 #include "tma.cuh"
@@ -92,6 +95,15 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
     constexpr int RS = 32 / BW;   // rows between a thread's pixels
     constexpr int BH = PPT * RS;  // band height (width BW)
     constexpr int NC = CH / 32;   // entries a lane stages per chunk
+    constexpr int NP = (PPT + 1) / 2;  // pixel pairs a thread
+    // eight pixels a thread (a 16 x 16 item): the item's upper and lower
+    // halves (rows [0, BH / 2) and [BH / 2, BH), two pixel pairs each) are
+    // culled apart, so an entry kept in one half costs the tests of that half
+    // only, and an entry kept in both is reduced once for the whole item; the
+    // upstream gradients wait in shared memory (each lane reads its own) to
+    // keep the registers of four more pixels free
+    constexpr bool SPLIT = PPT == 8;
+    __shared__ float4 s_up[SPLIT ? WARPS : 1][SPLIT ? NP : 1][2][32];
     __shared__ float4 s_rec[TMA ? 1 : WARPS][3][TMA ? 1 : CH];
     __shared__ uint32_t s_gid[WARPS][TMA ? 2 : 1][CH];  // Gaussian index of each staged entry (per buffer)
     __shared__ __align__(16) float s_red[WARPS][kRedRows][kRedPitch];
@@ -134,6 +146,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
         const float sx = (float)px + 0.5f;
         const float bx0 = (float)(tx0 + bxo) + 0.5f, bx1 = bx0 + (float)(BW - 1);
         const float by0 = (float)(ty0 + byo) + 0.5f, by1 = by0 + (float)(BH - 1);
+        const float bym = by0 + (float)(BH / 2 - 1);  // last row centre of the upper half
         const uint32_t b = a.ranges[2 * item];
         const int64_t rbase = (int64_t)v * a.n;
         // entries waiting in s_red, and their reduction
@@ -161,7 +174,6 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
         // R = gA T_final - (sum over later blended entries of (c.gC + z gD) alpha T)
         // pixel state in pairs (pixels 2i, 2i + 1 of the thread) for packed
         // FP32x2 updates; with one pixel a thread the second is never blended
-        constexpr int NP = (PPT + 1) / 2;
         float2 T[NP], gC0[NP], gC1[NP], gC2[NP], gD[NP], R[NP];
         uint32_t last[2 * NP];
         uint32_t my_last = 0;
@@ -194,12 +206,19 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
             gC2[i] = f2(c2[0], c2[1]);
             gD[i] = f2(d[0], d[1]);
             R[i] = f2(r[0], r[1]);
+            if constexpr (SPLIT) {
+                s_up[warp][i][0][lane] = make_float4(c0[0], c0[1], c1[0], c1[1]);
+                s_up[warp][i][1][lane] = make_float4(c2[0], c2[1], d[0], d[1]);
+            }
         }
         const uint32_t warp_last = __reduce_max_sync(kFullMask, my_last);
 
         // the gradients of one staged entry (p, c, col) of Gaussian gid at list
         // position pos: every pixel pair of the thread, then the warp's sums
-        auto grad_entry = [&](const float4 &p, const float4 &c, const float4 &col, uint32_t gid, uint32_t pos) {
+        // halves: bit 0 = the entry is kept in the upper half, bit 1 = in the
+        // lower half (both set without the split)
+        auto grad_entry = [&](const float4 &p, const float4 &c, const float4 &col, uint32_t gid, uint32_t pos,
+                              uint32_t halves) {
             // per pixel pair: colour (3) and depth gradients, and the sums
             // G, S1, S2 (of t = dL/dalpha o g), accumulated two pixels at a time
             float2 gc[4] = {f2(0.f), f2(0.f), f2(0.f), f2(0.f)};
@@ -207,51 +226,71 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
             bool contrib = false;
             const SplatColumn kc = splat_column(p, c, sx);
             if (pos < my_last) {
-                // the blend tests of all the thread's pixels first, then the
-                // pairs with a blended pixel (independent chains interleave)
-                float2 l2[NP], dy[NP];
-                bool hx[NP], hy[NP];
+                // per group of pixel pairs (a half of the item with the split,
+                // else all of them): the blend tests first, then the pairs
+                // with a blended pixel (independent chains interleave)
+                constexpr int GROUPS = SPLIT ? 2 : 1, GP = NP / GROUPS;
                 #pragma unroll
-                for (int i = 0; i < NP; i++) {
-                    l2[i] = splat_log2a2(kc, p, c, col,
-                                         f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f),
-                                         &dy[i]);
-                    hx[i] = pos < last[2 * i] && l2[i].x >= kLog2AlphaMin;
-                    hy[i] = pos < last[2 * i + 1] && l2[i].y >= kLog2AlphaMin;
-                }
-                #pragma unroll
-                for (int i = 0; i < NP; i++) {
-                    if (!(hx[i] || hy[i])) continue;
-                    contrib = true;
-                    // a pixel of the pair that does not blend this entry takes
-                    // raw alpha 0, so its w, t and sums are exactly zero
-                    const float2 araw = f2(hx[i] ? ex2_approx(l2[i].x) : 0.0f, hy[i] ? ex2_approx(l2[i].y) : 0.0f);
-                    const float2 al = f2(fminf(kAlphaMax, araw.x), fminf(kAlphaMax, araw.y));
-                    // where the clamp is in force (decided on l2) no gradient passes
-                    const bool cx = l2[i].x >= kLog2AlphaMax, cy = l2[i].y >= kLog2AlphaMax;
-                    const float2 om = __ffma2_rn(al, f2(-1.0f), f2(1.0f));
-                    // 1 - alpha >= 0.01: the fast reciprocal is within 2 ulp
-                    const float2 inv = f2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
-                    const float2 Tb = __fmul2_rn(T[i], inv);
-                    const float2 w = __fmul2_rn(al, Tb);
-                    gc[0] = __ffma2_rn(gC0[i], w, gc[0]);
-                    gc[1] = __ffma2_rn(gC1[i], w, gc[1]);
-                    gc[2] = __ffma2_rn(gC2[i], w, gc[2]);
-                    gc[3] = __ffma2_rn(gD[i], w, gc[3]);
-                    float2 wgt = __fmul2_rn(f2(col.x), gC0[i]);
-                    wgt = __ffma2_rn(f2(col.y), gC1[i], wgt);
-                    wgt = __ffma2_rn(f2(col.z), gC2[i], wgt);
-                    wgt = __ffma2_rn(f2(p.z), gD[i], wgt);
-                    const float2 dalpha = __ffma2_rn(Tb, wgt, __fmul2_rn(R[i], inv));
-                    R[i] = __ffma2_rn(f2(-wgt.x, -wgt.y), w, R[i]);
-                    // T of a pixel that does not blend stays exact
-                    T[i] = f2(hx[i] ? Tb.x : T[i].x, hy[i] ? Tb.y : T[i].y);
-                    const float2 tg = __fmul2_rn(dalpha, araw);
-                    const float2 t = f2(cx ? 0.0f : tg.x, cy ? 0.0f : tg.y);
-                    const float2 u = __fmul2_rn(t, dy[i]);
-                    G2 = __fadd2_rn(G2, t);
-                    S12 = __fadd2_rn(S12, u);
-                    S22 = __ffma2_rn(u, dy[i], S22);
+                for (int h = 0; h < GROUPS; h++) {
+                    // a half the entry cannot reach (the warp agrees) is not tested
+                    if (SPLIT && !((halves >> h) & 1u)) continue;
+                    float2 l2[GP], dy[GP];
+                    bool hx[GP], hy[GP];
+                    #pragma unroll
+                    for (int j = 0; j < GP; j++) {
+                        const int i = h * GP + j;
+                        l2[j] = splat_log2a2(
+                            kc, p, c, col,
+                            f2((float)(py0 + RS * 2 * i) + 0.5f, (float)(py0 + RS * (2 * i + 1)) + 0.5f), &dy[j]);
+                        hx[j] = pos < last[2 * i] && l2[j].x >= kLog2AlphaMin;
+                        hy[j] = pos < last[2 * i + 1] && l2[j].y >= kLog2AlphaMin;
+                    }
+                    #pragma unroll
+                    for (int j = 0; j < GP; j++) {
+                        const int i = h * GP + j;
+                        if (!(hx[j] || hy[j])) continue;
+                        contrib = true;
+                        // the pair's upstream gradients
+                        float2 uc0 = gC0[i], uc1 = gC1[i], uc2 = gC2[i], ud = gD[i];
+                        if constexpr (SPLIT) {
+                            const float4 q0 = ld_shared_f4(&s_up[warp][i][0][lane]);
+                            const float4 q1 = ld_shared_f4(&s_up[warp][i][1][lane]);
+                            uc0 = f2(q0.x, q0.y);
+                            uc1 = f2(q0.z, q0.w);
+                            uc2 = f2(q1.x, q1.y);
+                            ud = f2(q1.z, q1.w);
+                        }
+                        // a pixel of the pair that does not blend this entry takes
+                        // raw alpha 0, so its w, t and sums are exactly zero
+                        const float2 araw =
+                            f2(hx[j] ? ex2_approx(l2[j].x) : 0.0f, hy[j] ? ex2_approx(l2[j].y) : 0.0f);
+                        const float2 al = f2(fminf(kAlphaMax, araw.x), fminf(kAlphaMax, araw.y));
+                        // where the clamp is in force (decided on l2) no gradient passes
+                        const bool cx = l2[j].x >= kLog2AlphaMax, cy = l2[j].y >= kLog2AlphaMax;
+                        const float2 om = __ffma2_rn(al, f2(-1.0f), f2(1.0f));
+                        // 1 - alpha >= 0.01: the fast reciprocal is within 2 ulp
+                        const float2 inv = f2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
+                        const float2 Tb = __fmul2_rn(T[i], inv);
+                        const float2 w = __fmul2_rn(al, Tb);
+                        gc[0] = __ffma2_rn(uc0, w, gc[0]);
+                        gc[1] = __ffma2_rn(uc1, w, gc[1]);
+                        gc[2] = __ffma2_rn(uc2, w, gc[2]);
+                        gc[3] = __ffma2_rn(ud, w, gc[3]);
+                        float2 wgt = __fmul2_rn(f2(col.x), uc0);
+                        wgt = __ffma2_rn(f2(col.y), uc1, wgt);
+                        wgt = __ffma2_rn(f2(col.z), uc2, wgt);
+                        wgt = __ffma2_rn(f2(p.z), ud, wgt);
+                        const float2 dalpha = __ffma2_rn(Tb, wgt, __fmul2_rn(R[i], inv));
+                        R[i] = __ffma2_rn(f2(-wgt.x, -wgt.y), w, R[i]);
+                        // T of a pixel that does not blend stays exact
+                        T[i] = f2(hx[j] ? Tb.x : T[i].x, hy[j] ? Tb.y : T[i].y);
+                        const float2 tg = __fmul2_rn(dalpha, araw);
+                        const float2 t = f2(cx ? 0.0f : tg.x, cy ? 0.0f : tg.y);
+                        const float2 u = __fmul2_rn(t, dy[j]);
+                        G2 = __fadd2_rn(G2, t);
+                        S12 = __fadd2_rn(S12, u);
+                        S22 = __ffma2_rn(u, dy[j], S22);
+                    }
                 }
             }
             if (__any_sync(kFullMask, contrib)) {
@@ -274,6 +313,22 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
                 if (lane == 0) s_bgid[warp][nb] = gid;
                 if (++nb == kBatch) flush();
             }
+        };
+
+        // the warp's cull of a staged chunk, one entry a lane: upper = the
+        // entries that can reach alpha >= 1/255 in the item (in its upper half
+        // with the split), lower = in its lower half (none without the split)
+        auto cull = [&](const float4 &r0, const float4 &r1, bool have, uint32_t &upper, uint32_t &lower) {
+            if constexpr (SPLIT) {
+                upper = __ballot_sync(kFullMask, have && !splat_misses_box(r0, r1, bx0, bx1, by0, bym));
+                lower = __ballot_sync(kFullMask, have && !splat_misses_box(r0, r1, bx0, bx1, bym + 1.0f, by1));
+            } else {
+                upper = __ballot_sync(kFullMask, have && !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
+                lower = 0u;
+            }
+        };
+        auto halves_of = [&](uint32_t upper, uint32_t lower, int bit) -> uint32_t {
+            return SPLIT ? ((upper >> bit) & 1u) | (((lower >> bit) & 1u) << 1) : 3u;
         };
 
         // chunks [lo, hi) of the list, from the warp's last blend down to 0,
@@ -328,13 +383,14 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
                     break;
                 }
                 const unsigned char *buf = s_tbuf[warp][kb];
-                uint32_t todo[NC];
+                uint32_t todo[NC], upper[NC], lower[NC];
                 #pragma unroll
                 for (int c = 0; c < NC; c++) {
                     const int slot = 32 * c + lane;
                     const float4 r0 = *reinterpret_cast<const float4 *>(buf + rec_offset(slot));
                     const float4 r1 = *reinterpret_cast<const float4 *>(buf + rec_offset(slot) + 16);
-                    todo[c] = __ballot_sync(kFullMask, lo + slot < hi && !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
+                    cull(r0, r1, lo + slot < hi, upper[c], lower[c]);
+                    todo[c] = upper[c] | lower[c];
                 }
                 #pragma unroll
                 for (int cc = NC - 1; cc >= 0; cc--)
@@ -343,7 +399,8 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
                         todo[cc] &= ~(1u << bit);
                         const int slot = 32 * cc + bit;
                         const float4 *r = reinterpret_cast<const float4 *>(buf + rec_offset(slot));
-                        grad_entry(r[0], r[1], r[2], s_gid[warp][kb][slot], lo + (uint32_t)slot);
+                        grad_entry(r[0], r[1], r[2], s_gid[warp][kb][slot], lo + (uint32_t)slot,
+                                   halves_of(upper[cc], lower[cc], bit));
                     }
                 __syncwarp();  // buffer kb is read before it is filled again
                 hi = lo;
@@ -362,7 +419,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
                 load_bwd_entry(a, rbase, b + lo + 32 * c + lane, lo + 32 * c + lane < hi, n0[c], n1[c], n2[c], ng[c]);
             while (hi > 0) {
                 const uint32_t nlo = lo > (uint32_t)CH ? lo - CH : 0u;
-                uint32_t todo[NC];
+                uint32_t todo[NC], upper[NC], lower[NC];
                 __syncwarp();  // the previous chunk's records have been read
                 #pragma unroll
                 for (int c = 0; c < NC; c++) {
@@ -372,7 +429,8 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
                     if (lo > 0)
                         load_bwd_entry(a, rbase, b + nlo + 32 * c + lane, nlo + 32 * c + lane < lo, n0[c], n1[c],
                                        n2[c], ng[c]);
-                    todo[c] = __ballot_sync(kFullMask, have && !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
+                    cull(r0, r1, have, upper[c], lower[c]);
+                    todo[c] = upper[c] | lower[c];
                     s_rec[warp][0][32 * c + lane] = r0;
                     s_rec[warp][1][32 * c + lane] = r1;
                     s_rec[warp][2][32 * c + lane] = r2;
@@ -386,7 +444,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
                         todo[cc] &= ~(1u << bit);
                         const int slot = 32 * cc + bit;
                         grad_entry(s_rec[warp][0][slot], s_rec[warp][1][slot], s_rec[warp][2][slot],
-                                   s_gid[warp][0][slot], lo + (uint32_t)slot);
+                                   s_gid[warp][0][slot], lo + (uint32_t)slot, halves_of(upper[cc], lower[cc], bit));
                     }
                 hi = lo;
                 lo = nlo;
