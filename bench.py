@@ -233,7 +233,7 @@ def run_plain(c, step, rs):
                       step.d_rgb[base:base + P], step.d_depth[base:base + P])
         if step.zeta > 0:
             gs.gs_loss_ssim(r.img["rgb"], step.target_rgb[base:base + P], r.views, step.zeta * P / step.rast.n_pix,
-                            step.loss, step.d_rgb[base:base + P], step.ssim_ws)
+                            step.loss, step.d_rgb[base:base + P], step.ssim_ws, r.bins["status"])
         # the first view writes the parameter gradients, the others add to them
         r.backward(step.params, vm, step.d_rgb[base:base + P], step.d_depth[base:base + P], None, step.grads,
                    step.d_twist[v:v + 1], overwrite_grads=(v == 0))

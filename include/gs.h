@@ -318,10 +318,27 @@ size_t gs_ssim_workspace_size(int64_t n_pixels);
  * Adds weight * (1 - mean SSIM) over all pixels and channels of the views to
  * *loss and its gradient to d_rgb [P,3] (+=, so it sums with gs_loss_l1's).
  * rgb, target_rgb [P,3] device; views host; workspace device, >=
- * gs_ssim_workspace_size(P) bytes. */
+ * gs_ssim_workspace_size(P) bytes, 16-byte aligned for the staged gradient
+ * pass (else a slower pass runs).  status: device error word, may be NULL; an
+ * asynchronous copy that never completes sets bit GS_ERR_TIMEOUT there (the
+ * bounded wait gives up, the affected tiles' gradients are missing). */
 gs_status_t gs_loss_ssim(const float *rgb, const float *target_rgb, const gs_view_t *views, int32_t n_views,
                          float weight, float *loss, float *d_rgb, void *workspace, size_t workspace_bytes,
-                         void *stream);
+                         uint32_t *status, void *stream);
+
+/* Check of the asynchronous timeout path of the SSIM gradient pass (the
+ * paper has no counterpart; the staged copies and their bounded waits are this
+ * library's design).  Runs gs_loss_ssim with weight 1 on the same arguments,
+ * but the gradient pass's barrier expects 16 bytes more than its staged copy
+ * delivers, so every block's bounded wait gives up: each block sets bit
+ * GS_ERR_TIMEOUT in *status and returns without touching d_rgb (the loss is
+ * still added).  The copies themselves complete, so nothing is left in
+ * flight.  GS_ERR_UNSUPPORTED when the staged pass cannot run for these views
+ * (a width or first pixel not a multiple of 4, or a workspace not 16-byte
+ * aligned); GS_ERR_INVALID_ARG for a null status. */
+gs_status_t gs_check_ssim_timeout(const float *rgb, const float *target_rgb, const gs_view_t *views,
+                                  int32_t n_views, float *loss, float *d_rgb, void *workspace, size_t workspace_bytes,
+                                  uint32_t *status, void *stream);
 
 /* Bytes of the per-(view, Gaussian) 2D gradient buffer: n_views * n * 12 floats. */
 size_t gs_grad2d_size(int64_t n, int32_t n_views);

@@ -20,7 +20,7 @@ from ._lib import (GS_MAX_ADAM_GROUPS, GS_MAX_VIEWS, GS_TILE, GsAdamGroup, GsBin
                    GsParamGrads, GsParams, GsProjected, GsView, check)
 
 __all__ = ["gs_get_device_status", "gs_workspace_size", "gs_check_lookback_timeout", "gs_project", "gs_bin_sort", "gs_bin_sort_noalloc", "gs_render_fwd", "gs_render_fwd_l1", "gs_render_stats", "gs_set_render_variants",
-           "gs_get_render_variants", "gs_loss_l1", "gs_loss_ssim", "gs_render_bwd", "gs_render_bwd_splats",
+           "gs_get_render_variants", "gs_loss_l1", "gs_loss_ssim", "gs_check_ssim_timeout", "gs_render_bwd", "gs_render_bwd_splats",
            "gs_project_bwd", "gs_decode_keyframes", "gs_reproj_loss_grad", "gs_adam_step", "gs_pose_update", "gs_densify",
            "gs_prune_select", "gs_compact_rows", "gs_spatial_order_workspace_size", "gs_spatial_order",
            "gs_select_views", "Rasterizer", "rasterize", "make_views", "variant_fits",
@@ -203,10 +203,21 @@ def gs_ssim_workspace_size(n_pixels):
     return int(lib().gs_ssim_workspace_size(int(n_pixels)))
 
 
-def gs_loss_ssim(rgb, target_rgb, views, weight, loss, d_rgb, workspace, stream=None):
-    """Adds weight * (1 - mean SSIM) to loss and its gradient to d_rgb (+=)."""
+def gs_loss_ssim(rgb, target_rgb, views, weight, loss, d_rgb, workspace, status=None, stream=None):
+    """Adds weight * (1 - mean SSIM) to loss and its gradient to d_rgb (+=);
+    status: optional device error word (uint32) for a staged copy that timed out."""
     check(lib().gs_loss_ssim(_ptr(rgb), _ptr(target_rgb), views, len(views), float(weight), _ptr(loss), _ptr(d_rgb),
-                             _ptr(workspace), workspace.numel(), _stream(stream)), "gs_loss_ssim")
+                             _ptr(workspace), workspace.numel(), _ptr(status) if status is not None else None,
+                             _stream(stream)), "gs_loss_ssim")
+
+
+def gs_check_ssim_timeout(rgb, target_rgb, views, loss, d_rgb, workspace, status, stream=None):
+    """The SSIM pass with a staged copy whose barrier never completes (see
+    include/gs.h): every block's bounded wait gives up and sets GS_ERR_TIMEOUT
+    in status."""
+    check(lib().gs_check_ssim_timeout(_ptr(rgb), _ptr(target_rgb), views, len(views), _ptr(loss), _ptr(d_rgb),
+                                      _ptr(workspace), workspace.numel(), _ptr(status), _stream(stream)),
+          "gs_check_ssim_timeout")
 
 
 def gs_render_bwd_splats(proj, n, bins, views, img, d_rgb, d_depth, d_alpha, grad2d, work_counter, stream=None):

@@ -83,7 +83,8 @@ SIGNATURES = {
     "gs_decode_keyframes": ([c_p, c_p, c_i64, c_f, c_p, c_p, c_p], c_i32),
     "gs_loss_l1": ([c_p, c_p, c_p, c_p, c_p, c_i64, c_f, c_f, c_i32, c_f, c_p, c_p, c_p, c_p], c_i32),
     "gs_ssim_workspace_size": ([c_i64], c_sz),
-    "gs_loss_ssim": ([c_p, c_p, P(GsView), c_i32, c_f, c_p, c_p, c_p, c_sz, c_p], c_i32),
+    "gs_loss_ssim": ([c_p, c_p, P(GsView), c_i32, c_f, c_p, c_p, c_p, c_sz, c_p, c_p], c_i32),
+    "gs_check_ssim_timeout": ([c_p, c_p, P(GsView), c_i32, c_p, c_p, c_p, c_sz, c_p, c_p], c_i32),
     "gs_grad2d_size": ([c_i64, c_i32], c_sz),
     "gs_render_bwd_splats": ([P(GsProjected), c_i64, P(GsBins), P(GsView), c_i32, P(GsImage), c_p, c_p, c_p,
                               c_p, c_p, c_p], c_i32),

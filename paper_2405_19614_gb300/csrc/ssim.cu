@@ -19,8 +19,10 @@
 //   dL/dx = g (G*ds/dmx + 2 x G*ds/dE[x^2] + y G*ds/dE[xy]),  g = -weight/(3P)
 // to d_rgb.
 //
-// The gradient kernel double-buffers the staging, so one channel's maps are
-// copied while the previous channel is filtered.  Both filters are done with
+// The gradient kernel stages a channel's three maps while the previous
+// channel is filtered: with the tensor memory accelerator (one 4-D box per
+// channel, below) where every view's width is a multiple of 4, else by
+// double-buffered 4-byte asynchronous copies.  Both filters are done with
 // each value read once from shared memory: the
 // horizontal pass gives each thread one halo row and eight output columns
 // (lanes are consecutive rows, so row pitches are odd for conflict-free
@@ -30,6 +32,7 @@
 
 #include "common.cuh"
 #include "async_copy.cuh"
+#include "tma.cuh"
 
 namespace gs {
 
@@ -138,6 +141,49 @@ __device__ __forceinline__ void ssim_vpass(const SsimTiles &T, const float *h, i
             #pragma unroll
             for (int m = 0; m < NM; m++) out[p][m] = __ffma2_rn(w[t], make_float2(f[m], f[m]), out[p][m]);
         }
+    }
+}
+
+// Gradient kernels, end of a channel: the vertical pass of the three filtered
+// maps and dL/dx = G*ds/dmx + 2 x G*ds/dE[x^2] + y G*ds/dE[xy] into s_out.
+__device__ __forceinline__ void ssim_grad_channel_out(const SsimTiles &T, const float *s_h, float *s_out, int vc,
+                                                      int vr0, int ch, const float (&xs)[kSsimGrp],
+                                                      const float (&ys)[kSsimGrp])
+{
+    float2 fp[kSsimGrp / 2][3];
+    ssim_vpass<3>(T, s_h, vc, vr0, fp);
+    #pragma unroll
+    for (int o = 0; o < kSsimGrp; o++) {
+        float f[3];
+        #pragma unroll
+        for (int m = 0; m < 3; m++) f[m] = (o & 1) ? fp[o >> 1][m].y : fp[o >> 1][m].x;
+        s_out[(vr0 + o) * kSsimOutPitch + 3 * vc + ch] = f[0] + 2.f * xs[o] * f[1] + ys[o] * f[2];
+    }
+}
+
+// Gradient kernels, end of the tile: d_rgb += gsc * s_out.  The tile's rows of
+// d_rgb are contiguous runs of 3 * 32 floats; all reads are issued before the
+// writes.
+__device__ __forceinline__ void ssim_grad_write(const float *s_out, float *__restrict__ d_rgb, float gsc, int tid,
+                                                int x0, int y0, int W, int H, int64_t pb)
+{
+    constexpr int kPer = kSsimTH * 3 * kSsimTW / kSsimThreads;
+    static_assert(kPer * kSsimThreads == kSsimTH * 3 * kSsimTW, "whole rounds");
+    int64_t idx[kPer];
+    float cur[kPer];
+    #pragma unroll
+    for (int i = 0; i < kPer; i++) {
+        const int e = tid + i * kSsimThreads;
+        const int r = e / (3 * kSsimTW), q = e - r * (3 * kSsimTW);
+        const int gy = y0 + r, gx = x0 + q / 3;
+        idx[i] = (gx < W && gy < H) ? 3 * (pb + (int64_t)gy * W + x0) + q : -1;
+        cur[i] = idx[i] >= 0 ? d_rgb[idx[i]] : 0.0f;
+    }
+    #pragma unroll
+    for (int i = 0; i < kPer; i++) {
+        const int e = tid + i * kSsimThreads;
+        const int r = e / (3 * kSsimTW), q = e - r * (3 * kSsimTW);
+        if (idx[i] >= 0) d_rgb[idx[i]] = cur[i] + gsc * s_out[r * kSsimOutPitch + q];
     }
 }
 
@@ -331,6 +377,118 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_grad_kernel(const float *__
                 }
         }
         __syncthreads();
+        ssim_grad_channel_out(T, s_h, s_out, vc, vr0, ch, xs, ys);
+        __syncthreads();
+    }
+    ssim_grad_write(s_out, d_rgb, gsc, tid, x0, y0, W, H, pb);
+}
+
+// TMA staging of the gradient kernel: a view's nine partial maps are one 4-D
+// tensor (4 floats, W / 4 groups of 4, H rows, 9 maps), and a channel's three
+// maps over the tile and its halo are one box of 13 groups (image columns
+// x0 - 8 .. x0 + 43, of which x0 - 5 .. x0 + 36 are used) x 58 rows x 3 maps.
+// It lands in shared memory with a row pitch of 52 floats, 13 16-byte groups:
+// in the horizontal pass a lane reads its row 16 bytes at a time, and the
+// eight rows of each quarter-warp then fall on eight different bank groups.
+// Rows and columns outside the view read as zero: the window's zero padding.
+constexpr int kSsimTmaGroups = 13;
+constexpr int kSsimTmaPitch = 4 * kSsimTmaGroups;  // 52 floats
+constexpr int kSsimTmaLead = 8;                    // staged columns left of the tile (x0 - 8: 16-byte aligned)
+constexpr uint32_t kSsimTmaBytes = sizeof(float) * 3 * kSsimRows * kSsimTmaPitch;
+constexpr size_t kSsimGradTmaSmem = kSsimTmaBytes + sizeof(float) * 3 * kSsimRows * kSsimHPitch;
+static_assert(kSsimTmaPitch >= kSsimTmaLead + kSsimTW + kSsimR, "a staged row covers the window");
+static_assert(kSsimTW % 4 == 0 && kSsimTmaLead % 4 == 0 && kSsimSeg % 4 == 0, "16-byte aligned groups");
+
+struct SsimMaps {
+    CUtensorMap m[GS_MAX_VIEWS];
+};
+
+// Its outputs stay in registers (a thread's six pixels of one column, all
+// three channels) instead of a shared-memory tile: 59 KB of shared memory a
+// block, three blocks per SM.
+__global__ void __launch_bounds__(kSsimThreads, 3) ssim_grad_tma_kernel(const float *__restrict__ x,
+                                                                     const float *__restrict__ y, SsimTiles T,
+                                                                     const __grid_constant__ SsimMaps maps,
+                                                                     float *__restrict__ d_rgb, float gsc,
+                                                                     uint32_t *status, uint32_t extra_tx)
+{
+    extern __shared__ __align__(128) float smem[];
+    float *s_in = smem;                                 // [3][rows][52]: a channel's three maps (TMA box)
+    float *s_h = smem + 3 * kSsimRows * kSsimTmaPitch;  // [3][rows][33]
+    __shared__ alignas(8) uint64_t s_bar;
+    int v, x0, y0;
+    ssim_tile_of(T, blockIdx.x, &v, &x0, &y0);
+    const int W = T.width[v], H = T.height[v];
+    const int64_t pb = T.pix_base[v];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int hrow = (warp >> 2) * 32 + lane, hseg = warp & 3;
+    const int vc = lane, vr0 = warp * kSsimGrp;
+    const CUtensorMap *map = &maps.m[v];
+    if (tid == 0) {
+        mbar_init(&s_bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    // channel ch's box into s_in, by one thread, after every earlier read of
+    // s_in (extra_tx > 0 makes the barrier wait for bytes that never come)
+    auto issue = [&](int ch) {
+        if (tid == 0) {
+            fence_proxy_async_shared();
+            mbar_arrive_expect_tx(&s_bar, kSsimTmaBytes + extra_tx);  // extra_tx: 0 but in the timeout check
+            tma_load_4d(s_in, map, 0, (x0 - kSsimTmaLead) / 4, y0 - kSsimR, 3 * ch, &s_bar);
+        }
+    };
+    issue(0);
+    uint32_t parity = 0;
+    const int gx = x0 + vc;
+    float g_out[kSsimGrp][3];  // dL/dx of the thread's pixels, per channel
+    for (int ch = 0; ch < 3; ch++) {
+        // this channel's image values for the output pixels, loaded ahead of the filtering
+        float xs[kSsimGrp], ys[kSsimGrp];
+        #pragma unroll
+        for (int o = 0; o < kSsimGrp; o++) {
+            const int gy = y0 + vr0 + o;
+            xs[o] = ys[o] = 0.0f;
+            if (gx < W && gy < H) {
+                const int64_t p = pb + (int64_t)gy * W + gx;
+                xs[o] = x[3 * p + ch];
+                ys[o] = y[3 * p + ch];
+            }
+        }
+        const bool ok = mbar_wait_parity(&s_bar, parity);
+        parity ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            // the box never arrived: report it, give the copy one more bounded
+            // wait (it must not land in a later block's shared memory), stop
+            if (tid == 0) raise_status(status, GS_ERR_TIMEOUT);
+            mbar_wait_parity(&s_bar, parity ^ 1u);
+            return;
+        }
+        if (hrow < kSsimRows) {
+            // staged column j holds image column x0 - 8 + j; halo column i of
+            // this segment (image column x0 - 5 + 8 hseg + i) is j = 3 + i
+            const float *r0 = s_in + hrow * kSsimTmaPitch + hseg * kSsimSeg;
+            float2 acc[kSsimSeg / 2][3];
+            ssim_hpass<3>(T, [&](int i, float (&f)[3]) {
+                const int j = kSsimTmaLead - kSsimR + i;
+                #pragma unroll
+                for (int m = 0; m < 3; m++) {
+                    const float4 q =
+                        *reinterpret_cast<const float4 *>(r0 + m * kSsimRows * kSsimTmaPitch + (j & ~3));
+                    f[m] = (j & 3) == 0 ? q.x : (j & 3) == 1 ? q.y : (j & 3) == 2 ? q.z : q.w;
+                }
+            }, acc);
+            #pragma unroll
+            for (int p = 0; p < kSsimSeg / 2; p++)
+                #pragma unroll
+                for (int m = 0; m < 3; m++) {
+                    float *dst = s_h + (m * kSsimRows + hrow) * kSsimHPitch + hseg * kSsimSeg + 2 * p;
+                    dst[0] = acc[p][m].x;
+                    dst[1] = acc[p][m].y;
+                }
+        }
+        __syncthreads();
+        if (ch < 2) issue(ch + 1);  // in flight while this channel is finished
         float2 fp[kSsimGrp / 2][3];
         ssim_vpass<3>(T, s_h, vc, vr0, fp);
         #pragma unroll
@@ -338,29 +496,34 @@ __global__ void __launch_bounds__(kSsimThreads) ssim_grad_kernel(const float *__
             float f[3];
             #pragma unroll
             for (int m = 0; m < 3; m++) f[m] = (o & 1) ? fp[o >> 1][m].y : fp[o >> 1][m].x;
-            s_out[(vr0 + o) * kSsimOutPitch + 3 * vc + ch] = f[0] + 2.f * xs[o] * f[1] + ys[o] * f[2];
+            #pragma unroll
+            for (int c = 0; c < 3; c++)
+                if (c == ch) g_out[o][c] = f[0] + 2.f * xs[o] * f[1] + ys[o] * f[2];
         }
-        __syncthreads();
+        __syncthreads();  // s_h is read before the next channel's horizontal pass writes it
     }
-    // the tile's rows of d_rgb are contiguous runs of 3 * 32 floats; all
-    // reads are issued before the writes
-    constexpr int kPer = kSsimTH * 3 * kSsimTW / kSsimThreads;
-    static_assert(kPer * kSsimThreads == kSsimTH * 3 * kSsimTW, "whole rounds");
-    int64_t idx[kPer];
-    float cur[kPer];
+    // d_rgb += gsc * dL/dx: a warp's pixels of one row are 32 consecutive RGB
+    // triples; all reads are issued before the writes
+    float cur[kSsimGrp][3];
     #pragma unroll
-    for (int i = 0; i < kPer; i++) {
-        const int e = tid + i * kSsimThreads;
-        const int r = e / (3 * kSsimTW), q = e - r * (3 * kSsimTW);
-        const int gy = y0 + r, gx = x0 + q / 3;
-        idx[i] = (gx < W && gy < H) ? 3 * (pb + (int64_t)gy * W + x0) + q : -1;
-        cur[i] = idx[i] >= 0 ? d_rgb[idx[i]] : 0.0f;
+    for (int o = 0; o < kSsimGrp; o++) {
+        const int gy = y0 + vr0 + o;
+        #pragma unroll
+        for (int c = 0; c < 3; c++) cur[o][c] = 0.0f;
+        if (gx < W && gy < H) {
+            const int64_t p = pb + (int64_t)gy * W + gx;
+            #pragma unroll
+            for (int c = 0; c < 3; c++) cur[o][c] = d_rgb[3 * p + c];
+        }
     }
     #pragma unroll
-    for (int i = 0; i < kPer; i++) {
-        const int e = tid + i * kSsimThreads;
-        const int r = e / (3 * kSsimTW), q = e - r * (3 * kSsimTW);
-        if (idx[i] >= 0) d_rgb[idx[i]] = cur[i] + gsc * s_out[r * kSsimOutPitch + q];
+    for (int o = 0; o < kSsimGrp; o++) {
+        const int gy = y0 + vr0 + o;
+        if (gx < W && gy < H) {
+            const int64_t p = pb + (int64_t)gy * W + gx;
+            #pragma unroll
+            for (int c = 0; c < 3; c++) d_rgb[3 * p + c] = cur[o][c] + gsc * g_out[o][c];
+        }
     }
 }
 
@@ -408,10 +571,28 @@ static gs_status_t ssim_set_smem_limits()
     if (cudaFuncSetAttribute(ssim_stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSsimStatsSmem) !=
             cudaSuccess ||
         cudaFuncSetAttribute(ssim_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSsimGradSmem) !=
-            cudaSuccess)
+            cudaSuccess ||
+        cudaFuncSetAttribute(ssim_grad_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSsimGradTmaSmem) != cudaSuccess)
         return GS_ERR_CUDA;
     done[dev] = true;
     return GS_OK;
+}
+
+// The per-view tensor maps of the partial maps at `partial` ([9][n_pix]
+// floats), or false when a view's rows are not 16-byte aligned (its width or
+// first pixel not a multiple of 4) or a map cannot be made.
+static bool make_ssim_maps(const SsimTiles &T, const float *partial, SsimMaps *maps)
+{
+    if (T.n_pix % 4 || (reinterpret_cast<uintptr_t>(partial) & 15)) return false;
+    for (int v = 0; v < T.n_views; v++) {
+        if (T.width[v] % 4 || T.pix_base[v] % 4) return false;
+        const uint64_t dims[4] = {4, (uint64_t)T.width[v] / 4, (uint64_t)T.height[v], 9};
+        const uint64_t strides[3] = {16, 4 * (uint64_t)T.width[v], 4 * (uint64_t)T.n_pix};
+        const uint32_t box[4] = {4, kSsimTmaGroups, kSsimRows, 3};
+        if (make_tensor_map_4d(partial + T.pix_base[v], dims, strides, box, &maps->m[v]) != GS_OK) return false;
+    }
+    return true;
 }
 
 }  // namespace gs
@@ -423,9 +604,10 @@ extern "C" size_t gs_ssim_workspace_size(int64_t n_pixels)
     return n_pixels < 0 ? 0 : sizeof(float) * 9 * (size_t)n_pixels;
 }
 
-extern "C" gs_status_t gs_loss_ssim(const float *rgb, const float *target_rgb, const gs_view_t *views,
-                                    int32_t n_views, float weight, float *loss, float *d_rgb, void *workspace,
-                                    size_t workspace_bytes, void *stream)
+// Both passes; extra_tx > 0 (the timeout check) requires the staged pass.
+static gs_status_t ssim_launch(const float *rgb, const float *target_rgb, const gs_view_t *views, int32_t n_views,
+                               float weight, float *loss, float *d_rgb, void *workspace, size_t workspace_bytes,
+                               uint32_t *status, uint32_t extra_tx, void *stream)
 {
     if (!rgb || !target_rgb || !loss || !d_rgb || !workspace) return GS_ERR_INVALID_ARG;
     SsimTiles T;
@@ -440,6 +622,32 @@ extern "C" gs_status_t gs_loss_ssim(const float *rgb, const float *target_rgb, c
     const float scale = (float)(-(double)weight / (3.0 * (double)P));
     // weight * (1 - mean s): block 0 adds the constant weight, every block -weight/(3P) times its sum of s
     ssim_stats_kernel<<<blocks, kSsimThreads, kSsimStatsSmem, s>>>(rgb, target_rgb, T, partial, loss, scale, weight);
-    ssim_grad_kernel<<<blocks, kSsimThreads, kSsimGradSmem, s>>>(rgb, target_rgb, T, partial, d_rgb, scale);
+    static SsimMaps maps;  // 8 KB: static, not on the stack; copied into the launch's parameters
+    static std::mutex maps_mu;
+    std::lock_guard<std::mutex> lock(maps_mu);
+    if (make_ssim_maps(T, partial, &maps))
+        ssim_grad_tma_kernel<<<blocks, kSsimThreads, kSsimGradTmaSmem, s>>>(rgb, target_rgb, T, maps, d_rgb, scale,
+                                                                            status, extra_tx);
+    else if (extra_tx == 0)
+        ssim_grad_kernel<<<blocks, kSsimThreads, kSsimGradSmem, s>>>(rgb, target_rgb, T, partial, d_rgb, scale);
+    else
+        return GS_ERR_UNSUPPORTED;
     return launch_status();
+}
+
+extern "C" gs_status_t gs_loss_ssim(const float *rgb, const float *target_rgb, const gs_view_t *views,
+                                    int32_t n_views, float weight, float *loss, float *d_rgb, void *workspace,
+                                    size_t workspace_bytes, uint32_t *status, void *stream)
+{
+    return ssim_launch(rgb, target_rgb, views, n_views, weight, loss, d_rgb, workspace, workspace_bytes, status, 0,
+                       stream);
+}
+
+extern "C" gs_status_t gs_check_ssim_timeout(const float *rgb, const float *target_rgb, const gs_view_t *views,
+                                             int32_t n_views, float *loss, float *d_rgb, void *workspace,
+                                             size_t workspace_bytes, uint32_t *status, void *stream)
+{
+    if (!status) return GS_ERR_INVALID_ARG;
+    return ssim_launch(rgb, target_rgb, views, n_views, 1.0f, loss, d_rgb, workspace, workspace_bytes, status, 16,
+                       stream);
 }

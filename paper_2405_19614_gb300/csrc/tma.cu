@@ -42,4 +42,28 @@ gs_status_t make_record_map(const float *rec, int64_t rows, CUtensorMap *map)
     return r == CUDA_SUCCESS ? GS_OK : GS_ERR_INVALID_ARG;
 }
 
+gs_status_t make_tensor_map_4d(const float *base, const uint64_t dims[4], const uint64_t strides[3],
+                               const uint32_t box[4], CUtensorMap *map)
+{
+    if (!base || (reinterpret_cast<uintptr_t>(base) & 15)) return GS_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; k++)
+        if (strides[k] % 16 || strides[k] == 0) return GS_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; k++)
+        if (dims[k] == 0 || box[k] == 0 || box[k] > 256) return GS_ERR_INVALID_ARG;
+    if ((box[0] * sizeof(float)) % 16) return GS_ERR_INVALID_ARG;
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return GS_ERR_UNSUPPORTED;
+    cuuint64_t d[4], st[3];
+    cuuint32_t b[4], es[4] = {1u, 1u, 1u, 1u};
+    for (int k = 0; k < 4; k++) {
+        d[k] = dims[k];
+        b[k] = box[k];
+    }
+    for (int k = 0; k < 3; k++) st[k] = strides[k];
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), d, st, b, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? GS_OK : GS_ERR_INVALID_ARG;
+}
+
 }  // namespace gs

@@ -83,7 +83,32 @@ __device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// A 4-D box of the tensor into shared memory at dst (128-byte aligned),
+// completing on bar; c0 is the innermost coordinate.
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cta.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Orders this thread's earlier shared-memory accesses (generic proxy) before
+// its later asynchronous copies into shared memory.
+__device__ __forceinline__ void fence_proxy_async_shared()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Host: the tensor map of rows x 12 FP32 records at rec (16-byte aligned).
 gs_status_t make_record_map(const float *rec, int64_t rows, CUtensorMap *map);
+
+// Host: a 4-D FP32 tensor map, dims[0] innermost (contiguous), strides[k] the
+// bytes between consecutive indices of dimension k + 1 (multiples of 16),
+// base 16-byte aligned; out-of-range elements of a box read as zero.
+gs_status_t make_tensor_map_4d(const float *base, const uint64_t dims[4], const uint64_t strides[3],
+                               const uint32_t box[4], CUtensorMap *map);
 
 }  // namespace gs

@@ -154,7 +154,7 @@ class MappingStep:
         if self.zeta > 0:
             tok = mark("ssim")
             gs_loss_ssim(r.img["rgb"], self.target_rgb, r.views, self.zeta, self.loss, self.d_rgb, self.ssim_ws,
-                         stream)
+                         r.bins["status"], stream)
             close(tok)
         if side:
             main.wait_stream(self.side)  # the re-projection has overlapped the render

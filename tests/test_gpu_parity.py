@@ -429,12 +429,24 @@ def test_every_compositing_variant_matches():
         gs.gs_set_render_variants(fwd0, bwd0)
 
 
-def test_ssim_term_parity():
-    """The SSIM term of L_m against the FP64 oracle on uneven views, added on
-    top of an existing gradient."""
+SSIM_SIZES = {
+    # odd widths: the gradient pass stages with 4-byte copies
+    "odd": [[45, 37], [64, 48], [19, 23], [131, 101]],
+    # widths a multiple of 4: the gradient pass stages with the tensor memory accelerator
+    "aligned": [[44, 37], [64, 48], [20, 23], [132, 101], [200, 120]],
+    # full-size views (the mapping workloads' 1200x680 and 1280x720; one odd width)
+    "fullsize": [[1200, 680], [1280, 720]],
+    "fullsize-odd": [[962, 541]],
+}
+
+
+@pytest.mark.parametrize("sizes", list(SSIM_SIZES))
+def test_ssim_term_parity(sizes):
+    """The SSIM term of L_m against the FP64 oracle on uneven views (several
+    tiles and ragged edges), added on top of an existing gradient."""
     from oracle import ssim as S
     rng = np.random.default_rng(7)
-    size = np.array([[45, 37], [64, 48], [19, 23], [131, 101]])  # several tiles and ragged edges
+    size = np.array(SSIM_SIZES[sizes])
     P = int((size[:, 0] * size[:, 1]).sum())
     x = rng.uniform(0, 1, (P, 3)).astype(np.float32)
     y = np.clip(x + rng.normal(0, 0.15, x.shape), 0, 1).astype(np.float32)
@@ -444,11 +456,15 @@ def test_ssim_term_parity():
     base = rng.normal(0, 1e-5, (P, 3)).astype(np.float32)
     d_rgb = t(base)
     ws = torch.empty(gs.gs_ssim_workspace_size(P), dtype=torch.uint8, device="cuda")
-    gs.gs_loss_ssim(t(x), t(y), views, 0.3, loss, d_rgb, ws)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gs.gs_loss_ssim(t(x), t(y), views, 0.3, loss, d_rgb, ws, status)
     torch.cuda.synchronize()
-    assert abs(float(loss) - 0.25 - L) <= 2e-6 * max(1.0, L)
+    assert gs.gs_get_device_status(status) == 0
     e = rel_l2(d_rgb.cpu().numpy() - base, g)
+    le = abs(float(loss) - 0.25 - L)
     print(f"SSIM gradient rel-L2 err = {e:.3e}, loss {float(loss) - 0.25:.6f} vs {L:.6f}")
+    parity_log(dict(kind="ssim", name=f"ssim-{sizes}", pixels=P, views=len(size), loss_abs_err=le, grad_rel_l2=e))
+    assert le <= 2e-6 * max(1.0, L)
     assert e <= GRAD_TOL
 
 
