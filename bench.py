@@ -339,6 +339,34 @@ def stage_work(w):
     }
 
 
+def survey_bytes(w):
+    """HBM bytes of one step by the per-stage byte model stated for the path
+    (per view: a1 12 N + 272 per drawn record, a2 4 per drawn record + 12 per
+    pair, a3 8 per pair + 24 per pair per 8-bit pass of the (tile, depth) key,
+    a4 8 per pair, a5 44 per pair + 28 per pixel, a6 16 per pixel, a7 44 per
+    pair + 48 per pixel + 40 per drawn record, a8 276 per drawn record + the
+    parameter gradients once, a10 28 per parameter), plus the SSIM term's 144
+    per pixel: the step's HBM roofline against that model rather than the
+    per-stage floors."""
+    N, V, P, K, Vv, T, S = (w[k] for k in ("N", "V", "P", "K", "V_vis", "T", "sh_floats"))
+    param_b = 4 * (11 + S)
+    key_bits = max(1, (T - 1).bit_length()) + 32
+    passes = (key_bits + 7) // 8
+    parts = {
+        "a1": 12 * N * V + 272 * Vv,
+        "a2": 4 * Vv + 12 * K,
+        "a3": 8 * K + passes * 24 * K,
+        "a4": 8 * K,
+        "a5": 44 * K + 28 * P,
+        "a6": 16 * P,
+        "a7": 44 * K + 48 * P + 40 * Vv,
+        "a8": 276 * Vv + param_b * N,
+        "a10": 7 * param_b * N,
+        "ssim": 144 * P,
+    }
+    return parts
+
+
 # --------------------------------------------------------------------------
 # CPU oracle baselines (bounded strips of the same workload)
 # --------------------------------------------------------------------------
@@ -1112,6 +1140,11 @@ def main_ours(args):
         "roofline": roofline,
         "roofline_step": {"floor_ms": step_floor, "ms": ms, "frac": step_floor / ms,
                           "stages": {k: floor_ms(k) for k in stage_ms if k in works}},
+        # the same step against the per-stage byte model of the path (all HBM)
+        "roofline_step_bytes": (lambda sb: {"bytes": sum(sb.values()), "ms": ms,
+                                            "achieved_gbs": sum(sb.values()) / ms / 1e6, "peak_gbs": hbm_peak,
+                                            "frac": sum(sb.values()) / ms / 1e6 / hbm_peak, "parts": sb})(
+            survey_bytes(w)),
         "clocks": clk,
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,

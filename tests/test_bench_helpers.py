@@ -68,3 +68,16 @@ def test_oracle_pool_plan_fits_the_budget():
     assert rows == 680 and per_core == 2  # a whole view is 7.6 s; two of them near 12 s
     rows, per_core = p.plan(3.0)
     assert rows % 16 == 0 and per_core == 1 and abs(p.fixed + rows * p.per_row - 3.0) < 0.2
+
+
+def test_survey_bytes_follow_the_stated_model():
+    import bench
+    w = dict(N=10, V=2, P=100, T=300, K=40, V_vis=15, sh_floats=48)
+    sb = bench.survey_bytes(w)
+    # 300 tiles: 9 bits + 32 depth bits = 41 bits, 6 passes of 8 bits
+    assert sb["a3"] == 8 * 40 + 6 * 24 * 40
+    assert sb["a1"] == 12 * 10 * 2 + 272 * 15
+    assert sb["a8"] == 276 * 15 + 4 * 59 * 10
+    assert sb["a10"] == 7 * 4 * 59 * 10
+    assert sum(sb.values()) == (240 + 4080) + (60 + 480) + (320 + 5760) + 320 + (1760 + 2800) + 1600 + \
+        (1760 + 4800 + 600) + (4140 + 2360) + 16520 + 14400
