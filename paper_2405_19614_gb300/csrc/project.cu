@@ -84,15 +84,11 @@ struct Geom {
     int32_t x0, y0, x1, y1;
 };
 
-// The FP32 geometry contract.  Returns false when the Gaussian touches no tile.
-__device__ __forceinline__ bool geometry(const float m[3], const float ls[3], const float q[4], const float *E,
-                                         const ViewInfo &V, float near_z, float blur, Geom &g)
+// The FP32 geometry contract, in two parts: the world covariance S (symmetric,
+// view-independent, so computed once per Gaussian; false for a degenerate
+// quaternion, which no view draws), then per view the projection.
+__device__ __forceinline__ bool world_covariance(const float ls[3], const float q[4], float S[3][3])
 {
-    float x = ADD(ADD(ADD(MUL(E[0], m[0]), MUL(E[1], m[1])), MUL(E[2], m[2])), E[3]);
-    float y = ADD(ADD(ADD(MUL(E[4], m[0]), MUL(E[5], m[1])), MUL(E[6], m[2])), E[7]);
-    float z = ADD(ADD(ADD(MUL(E[8], m[0]), MUL(E[9], m[1])), MUL(E[10], m[2])), E[11]);
-    if (!(z > near_z)) return false;
-
     float nq = ADD(ADD(ADD(MUL(q[0], q[0]), MUL(q[1], q[1])), MUL(q[2], q[2])), MUL(q[3], q[3]));
     if (!(nq > 0.0f)) return false;
     float sq = __fsqrt_rn(nq);
@@ -114,7 +110,6 @@ __device__ __forceinline__ bool geometry(const float m[3], const float ls[3], co
     for (int i = 0; i < 3; i++)
         #pragma unroll
         for (int j = 0; j < 3; j++) M[i][j] = MUL(R[i][j], s[j]);
-    float S[3][3];
     #pragma unroll
     for (int i = 0; i < 3; i++)
         #pragma unroll
@@ -122,9 +117,20 @@ __device__ __forceinline__ bool geometry(const float m[3], const float ls[3], co
             S[i][j] = ADD(ADD(MUL(M[i][0], M[j][0]), MUL(M[i][1], M[j][1])), MUL(M[i][2], M[j][2]));
             S[j][i] = S[i][j];
         }
+    return true;
+}
 
-    float limx = MUL(1.3f, DIV(MUL(0.5f, (float)V.width), V.fx));
-    float limy = MUL(1.3f, DIV(MUL(0.5f, (float)V.height), V.fy));
+// The per-view part.  Returns false when the Gaussian touches no tile.  lim:
+// the view's (limx, limy) = 1.3 (0.5 width / fx, 0.5 height / fy).
+__device__ __forceinline__ bool geometry(const float m[3], const float S[3][3], const float *E, const ViewInfo &V,
+                                         const float *lim, float near_z, float blur, Geom &g)
+{
+    float x = ADD(ADD(ADD(MUL(E[0], m[0]), MUL(E[1], m[1])), MUL(E[2], m[2])), E[3]);
+    float y = ADD(ADD(ADD(MUL(E[4], m[0]), MUL(E[5], m[1])), MUL(E[6], m[2])), E[7]);
+    float z = ADD(ADD(ADD(MUL(E[8], m[0]), MUL(E[9], m[1])), MUL(E[10], m[2])), E[11]);
+    if (!(z > near_z)) return false;
+
+    const float limx = lim[0], limy = lim[1];
     float xz = DIV(x, z), yz = DIV(y, z);
     xz = fminf(limx, fmaxf(-limx, xz));
     yz = fminf(limy, fmaxf(-limy, yz));
@@ -327,6 +333,7 @@ __global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable v
     constexpr int K = ShCount<DEG>::value;
     __shared__ float s_E[GS_MAX_VIEWS][12];
     __shared__ float s_c[GS_MAX_VIEWS][3];
+    __shared__ float s_lim[GS_MAX_VIEWS][2];
     for (int k = threadIdx.x; k < vt.n_views * 12; k += blockDim.x) s_E[k / 12][k % 12] = a.viewmats[k];
     __syncthreads();
     for (int v = threadIdx.x; v < vt.n_views; v += blockDim.x) {
@@ -334,6 +341,10 @@ __global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable v
         const float *E = s_E[v];
         #pragma unroll
         for (int i = 0; i < 3; i++) s_c[v][i] = -(E[i] * E[3] + E[4 + i] * E[7] + E[8 + i] * E[11]);
+        // the view's clamp of x/z and y/z (in the geometry contract's operations)
+        const ViewInfo &V = vt.v[v];
+        s_lim[v][0] = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)V.width), V.fx));
+        s_lim[v][1] = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, (float)V.height), V.fy));
     }
     __syncthreads();
 
@@ -351,6 +362,8 @@ __global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable v
     q[2] = q4.z;
     q[3] = q4.w;
     const float log2o = geom_log2_opacity(__ldg(a.opacity_logit + i));
+    float S[3][3];
+    const bool cov_ok = world_covariance(ls, q, S);
     // the SH coefficients are read only for the views the Gaussian is drawn
     // in (they come from L1 after the first): 48 registers fewer a thread than
     // holding them across the view loop, and no read for a Gaussian no view draws
@@ -376,7 +389,7 @@ __global__ void __launch_bounds__(128) project_kernel(ProjectArgs a, ViewTable v
     for (int v = 0; v < vt.n_views; v++) {
         const int64_t o = (int64_t)v * a.n + i;
         Geom g;
-        if (!geometry(m, ls, q, s_E[v], vt.v[v], a.near_z, a.blur, g)) {
+        if (!cov_ok || !geometry(m, S, s_E[v], vt.v[v], s_lim[v], a.near_z, a.blur, g)) {
             a.radii[o] = 0;
             a.tiles_touched[o] = 0;
             continue;
