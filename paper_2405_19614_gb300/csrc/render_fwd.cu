@@ -120,7 +120,6 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
         float2 T[NP], C0[NP], C1[NP], C2[NP], D[NP];
         uint32_t last[2 * NP], n_eval[2 * NP], n_blend[2 * NP];
         bool live[2 * NP];
-        int alive = 0;
         #pragma unroll
         for (int i = 0; i < NP; i++) {
             T[i] = f2(1.0f);
@@ -130,8 +129,14 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
         for (int k = 0; k < 2 * NP; k++) {
             last[k] = n_eval[k] = n_blend[k] = 0;
             live[k] = k < PPT && px < V.width && (py0 + RS * k) < V.height;
-            alive += live[k];
         }
+        // whether any pixel of the warp has transmittance left
+        auto warp_alive = [&]() {
+            bool any = false;
+            #pragma unroll
+            for (int k = 0; k < 2 * NP; k++) any = any || live[k];
+            return __any_sync(kFullMask, any);
+        };
         // the walk of one staged entry (p, c, col): the thread's pixel pairs
         auto blend_entry = [&](const float4 &p, const float4 &cc, const float4 &col, uint32_t pos) {
             const SplatColumn kc = splat_column(p, cc, sx);
@@ -159,7 +164,6 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
                     }
                     last[k] = blend[h] ? pos + 1u : last[k];
                     live[k] = live[k] && !stop;
-                    alive -= stop;
                 }
                 const float2 w = f2(blend[0] ? aT.x : 0.0f, blend[1] ? aT.y : 0.0f);
                 C0[i] = __ffma2_rn(f2(col.x), w, C0[i]);
@@ -203,7 +207,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
                 pend[0] = true;
             }
             for (uint32_t m = b; m < e; m += CH, kb ^= 1) {
-                if (!__any_sync(kFullMask, alive > 0)) break;
+                if (!warp_alive()) break;
                 if (m + CH < e) {
                     issue(m + CH, kb ^ 1);
                     pend[kb ^ 1] = true;
@@ -222,7 +226,6 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
                     const float4 cc = *reinterpret_cast<const float4 *>(buf + rec_offset(slot) + 16);
                     const bool keep = m + slot < e && (STATS || !splat_misses_box(p, cc, bx0, bx1, by0, by1));
                     todo[c] = __ballot_sync(kFullMask, keep);  // every lane takes part
-                    if (alive == 0) todo[c] = 0;
                 }
                 #pragma unroll
                 for (int c = 0; c < NC; c++) {
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
                         const int slot = 32 * c + j;
                         const float4 *r = reinterpret_cast<const float4 *>(buf + rec_offset(slot));
                         blend_entry(r[0], r[1], r[2], m - b + (uint32_t)slot);
-                        if (alive == 0) {
+                        if (!warp_alive()) {  // the warp's pixels are done (a warp-uniform exit)
                             #pragma unroll
                             for (int c2 = 0; c2 < NC; c2++) todo[c2] = 0;
                             break;
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
         #pragma unroll
         for (int c = 0; c < NC; c++) load_entry(a, rbase, b + 32 * c + lane, e, n0[c], n1[c], n2[c]);
         for (uint32_t m = b; m < e; m += CH) {
-            if (!__any_sync(kFullMask, alive > 0)) break;
+            if (!warp_alive()) break;
             uint32_t todo[NC];
             __syncwarp();  // the previous chunk's records have been read
             #pragma unroll
@@ -260,7 +263,6 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
                 if (m + CH < e) load_entry(a, rbase, m + CH + 32 * c + lane, e, n0[c], n1[c], n2[c]);
                 const bool keep = have && (STATS || !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
                 todo[c] = __ballot_sync(kFullMask, keep);
-                if (alive == 0) todo[c] = 0;
                 s_rec[warp][0][32 * c + lane] = r0;
                 s_rec[warp][1][32 * c + lane] = r1;
                 s_rec[warp][2][32 * c + lane] = r2;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
                     const int slot = 32 * c + j;
                     blend_entry(s_rec[warp][0][slot], s_rec[warp][1][slot], s_rec[warp][2][slot],
                                 m - b + (uint32_t)slot);
-                    if (alive == 0) {
+                    if (!warp_alive()) {  // the warp's pixels are done (a warp-uniform exit)
                         #pragma unroll
                         for (int c2 = 0; c2 < NC; c2++) todo[c2] = 0;
                         break;
