@@ -225,10 +225,14 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
             float2 G2 = f2(0.f), S12 = f2(0.f), S22 = f2(0.f);
             bool contrib = false;
             const SplatColumn kc = splat_column(p, c, sx);
-            if (pos < my_last) {
+            {
                 // per group of pixel pairs (a half of the item with the split,
                 // else all of them): the blend tests first, then the pairs
-                // with a blended pixel (independent chains interleave)
+                // with a blended pixel (independent chains interleave).  No
+                // test of pos against the thread's own last blend: the warp
+                // walks below its largest last blend, so some thread always
+                // tests, and a thread past its pixels' last blends finds no
+                // blended pixel (pos >= last) without a branch of its own
                 constexpr int GROUPS = SPLIT ? 2 : 1, GP = NP / GROUPS;
                 #pragma unroll
                 for (int h = 0; h < GROUPS; h++) {
