@@ -252,7 +252,11 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
                     #pragma unroll
                     for (int j = 0; j < GP; j++) {
                         const int i = h * GP + j;
-                        if (!(hx[j] || hy[j])) continue;
+                        // a warp-uniform skip: a pair that no lane blends is
+                        // skipped by all; a lane whose pair does not blend
+                        // runs the body with raw alpha 0, which changes none
+                        // of its state and adds exactly zero
+                        if (!__any_sync(kFullMask, hx[j] || hy[j])) continue;
                         contrib = true;
                         // the pair's upstream gradients
                         float2 uc0 = gC0[i], uc1 = gC1[i], uc2 = gC2[i], ud = gD[i];
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
                     }
                 }
             }
-            if (__any_sync(kFullMask, contrib)) {
+            if (contrib) {  // warp-uniform: set under the warp-uniform pair skip
                 // staged conic (A', B', C') = -log2(e) (A/2, B, C/2)
                 const float G = G2.x + G2.y, S1 = S12.x + S12.y, S2 = S22.x + S22.y;
                 const float dx = kc.dx, dxG = dx * G;
