@@ -368,8 +368,10 @@ __global__ void __launch_bounds__(kColorThreads, 3) project_bwd_color_kernel(Pro
     if (want_twist) flush_twist(a.d_twist, vt.n_views, s_tw);
 }
 
-// Geometry path: one thread per Gaussian.
-__global__ void __launch_bounds__(128) project_bwd_geom_kernel(ProjectBwdArgs a, ViewTable vt)
+// Geometry path: one thread per Gaussian.  Five blocks per SM (96 registers,
+// a few bytes of spill): the kernel waits on loads, and the fifth block's
+// warps hide more of them than the spill costs.
+__global__ void __launch_bounds__(128, 5) project_bwd_geom_kernel(ProjectBwdArgs a, ViewTable vt)
 {
     __shared__ float s_E[GS_MAX_VIEWS][12];
     __shared__ float s_tw[GS_MAX_VIEWS][6];
