@@ -129,8 +129,8 @@ constexpr int kRenderThreads = 128;
 #ifndef GS_BWD_BLOCKS_PPT4
 #define GS_BWD_BLOCKS_PPT4 5
 #endif
-// With TMA staging the next chunk waits in shared memory, not registers, and
-// four pixels a thread fit one more block per SM.
+// With TMA staging or asynchronous copies the next chunk waits in shared
+// memory, not registers, and four pixels a thread fit one more block per SM.
 #ifndef GS_BWD_BLOCKS_PPT4_TMA
 #define GS_BWD_BLOCKS_PPT4_TMA 6
 #endif
@@ -148,8 +148,10 @@ struct RenderOccupancy {
 
 // Kernel variants the autotuner picks from: a band shape as (pixels per
 // thread, band width) (1, 8) (2, 8) (2, 16) (4, 8) (4, 16) (8, 16), each with a
-// staged chunk of 32 (variants 0-5) or 64 list entries (6-11) loaded by the
-// lanes, or of 32 (12-17) or 64 (18-23) gathered by the tensor memory
+// staged chunk of 32 list entries loaded by the lanes into registers (variants
+// 0-5); of 64 so loaded (6-11) in the forward, of 32 copied by the lanes'
+// asynchronous copies into a second shared-memory buffer (6-11) in the
+// backward; or of 32 (12-17) or 64 (18-23) gathered by the tensor memory
 // accelerator.  A warp's band is BW x PPT * 32 / BW pixels; a thread's pixels
 // share a column, 32 / BW rows apart.
 constexpr int kBandVariants = 6;

@@ -35,6 +35,7 @@
 // is a 16 x 16 item whose two halves are culled apart: an entry kept in both
 // is reduced once, an entry kept in one is tested in that half only.  PPT is
 // picked by the autotuner.
+#include "async_copy.cuh"
 #include "common.cuh"
 #include "render.cuh"
 #include "tma.cuh"
@@ -87,10 +88,15 @@ __device__ __forceinline__ void load_bwd_entry(const RenderBwdArgs &a, int64_t r
 // together, the next CH loaded while they are walked: by the lanes' own loads
 // (TMA = false), or gathered four records at a time by the tensor memory
 // accelerator into a second shared-memory buffer (tma.cuh).
-template <int PPT, int BW, int CH, bool TMA>
-__global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd)
+// ASYNC (32-entry chunks): the lanes copy the next chunk's records into a
+// second shared-memory buffer with their own asynchronous copies (through L1,
+// like the lane loads, but holding no registers), and load the Gaussian
+// indices one chunk further ahead.
+template <int PPT, int BW, int CH, bool TMA, bool ASYNC = false>
+__global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA || ASYNC>::bwd)
     render_bwd_kernel(RenderBwdArgs a, ViewTable vt, const __grid_constant__ CUtensorMap rec_map)
 {
+    static_assert(!(TMA && ASYNC) && (!ASYNC || CH == 32), "one staging mode; asynchronous copies of 32 entries");
     constexpr int WARPS = kRenderThreads / 32;
     constexpr int RS = 32 / BW;   // rows between a thread's pixels
     constexpr int BH = PPT * RS;  // band height (width BW)
@@ -104,8 +110,8 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
     // keep the registers of four more pixels free
     constexpr bool SPLIT = PPT == 8;
     __shared__ float4 s_up[SPLIT ? WARPS : 1][SPLIT ? NP : 1][2][32];
-    __shared__ float4 s_rec[TMA ? 1 : WARPS][3][TMA ? 1 : CH];
-    __shared__ uint32_t s_gid[WARPS][TMA ? 2 : 1][CH];  // Gaussian index of each staged entry (per buffer)
+    __shared__ float4 s_rec[TMA ? 1 : WARPS][ASYNC ? 2 : 1][3][TMA ? 1 : CH];  // (per buffer, ASYNC)
+    __shared__ uint32_t s_gid[WARPS][TMA || ASYNC ? 2 : 1][CH];  // Gaussian index of each staged entry (per buffer)
     __shared__ __align__(16) float s_red[WARPS][kRedRows][kRedPitch];
     __shared__ uint32_t s_bgid[WARPS][kBatch];
     constexpr int kBufBytes = (CH / kGatherRows) * kGatherSlot;
@@ -419,6 +425,49 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
             #pragma unroll
             for (int k2 = 0; k2 < 2; k2++)
                 if (pend[k2] && !wait(k2)) tma_failed = true;
+        } else if constexpr (ASYNC) {
+            auto gid_at = [&](uint32_t l0, uint32_t h0) -> uint32_t {
+                const uint32_t idx = l0 + lane;
+                return idx < h0 ? a.vals[b + idx] : 0u;
+            };
+            // chunk [l0, h0) into buffer kb, the indices g already loaded
+            auto copy = [&](uint32_t l0, uint32_t h0, uint32_t g, int kb) {
+                s_gid[warp][kb][lane] = g;
+                if (l0 + lane < h0) {
+                    const float4 *src = a.rec + 3 * (rbase + g);
+                    cp_async16_ca(&s_rec[warp][kb][0][lane], src);
+                    cp_async16_ca(&s_rec[warp][kb][1][lane], src + 1);
+                    cp_async16_ca(&s_rec[warp][kb][2][lane], src + 2);
+                }
+                cp_async_commit();
+            };
+            int kb = 0;
+            if (hi > 0) copy(lo, hi, gid_at(lo, hi), 0);
+            uint32_t nlo = lo > (uint32_t)CH ? lo - CH : 0u;
+            uint32_t g_next = lo > 0 ? gid_at(nlo, lo) : 0u;  // indices of the next chunk
+            while (hi > 0) {
+                cp_async_wait<0>();
+                __syncwarp();  // every lane's copies of this chunk have landed
+                if (lo > 0) {
+                    copy(nlo, lo, g_next, kb ^ 1);
+                    const uint32_t nnlo = nlo > (uint32_t)CH ? nlo - CH : 0u;
+                    g_next = nlo > 0 ? gid_at(nnlo, nlo) : 0u;
+                }
+                uint32_t upper, lower;
+                cull(s_rec[warp][kb][0][lane], s_rec[warp][kb][1][lane], lo + lane < hi, upper, lower);
+                uint32_t todo = upper | lower;
+                while (todo) {
+                    const int bit = 31 - __clz(todo);
+                    todo &= ~(1u << bit);
+                    grad_entry(s_rec[warp][kb][0][bit], s_rec[warp][kb][1][bit], s_rec[warp][kb][2][bit],
+                               s_gid[warp][kb][bit], lo + (uint32_t)bit, halves_of(upper, lower, bit));
+                }
+                __syncwarp();  // buffer kb is read before it is filled again
+                hi = lo;
+                lo = nlo;
+                nlo = lo > (uint32_t)CH ? lo - CH : 0u;
+                kb ^= 1;
+            }
         } else {
             float4 n0[NC], n1[NC], n2[NC];
             uint32_t ng[NC];
@@ -439,9 +488,9 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
                                        n2[c], ng[c]);
                     cull(r0, r1, have, upper[c], lower[c]);
                     todo[c] = upper[c] | lower[c];
-                    s_rec[warp][0][32 * c + lane] = r0;
-                    s_rec[warp][1][32 * c + lane] = r1;
-                    s_rec[warp][2][32 * c + lane] = r2;
+                    s_rec[warp][0][0][32 * c + lane] = r0;
+                    s_rec[warp][0][1][32 * c + lane] = r1;
+                    s_rec[warp][0][2][32 * c + lane] = r2;
                     s_gid[warp][0][32 * c + lane] = g_self;
                 }
                 __syncwarp();
@@ -451,7 +500,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
                         const int bit = 31 - __clz(todo[cc]);
                         todo[cc] &= ~(1u << bit);
                         const int slot = 32 * cc + bit;
-                        grad_entry(s_rec[warp][0][slot], s_rec[warp][1][slot], s_rec[warp][2][slot],
+                        grad_entry(s_rec[warp][0][0][slot], s_rec[warp][0][1][slot], s_rec[warp][0][2][slot],
                                    s_gid[warp][0][slot], lo + (uint32_t)slot, halves_of(upper[cc], lower[cc], bit));
                     }
                 hi = lo;
@@ -466,12 +515,12 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::bwd
     }
 }
 
-template <int PPT, int BW, int CH, bool TMA>
+template <int PPT, int BW, int CH, bool TMA, bool ASYNC = false>
 static gs_status_t launch_bwd(RenderBwdArgs a, ViewTable vt, const CUtensorMap &map, cudaStream_t s)
 {
     // work items: the bands of every tile of every view (tile shapes are per view)
     a.n_items = render_items(&vt, BW, PPT * (32 / BW));
-    auto kern = render_bwd_kernel<PPT, BW, CH, TMA>;
+    auto kern = render_bwd_kernel<PPT, BW, CH, TMA, ASYNC>;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, 0);
     const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
@@ -481,17 +530,17 @@ static gs_status_t launch_bwd(RenderBwdArgs a, ViewTable vt, const CUtensorMap &
     return launch_status();
 }
 
-template <int CH, bool TMA>
+template <int CH, bool TMA, bool ASYNC = false>
 static gs_status_t dispatch_bwd_band(int base, const RenderBwdArgs &a, const ViewTable &vt, const CUtensorMap &map,
                                      cudaStream_t s)
 {
     switch (base) {
-    case 0: return launch_bwd<1, 8, CH, TMA>(a, vt, map, s);
-    case 1: return launch_bwd<2, 8, CH, TMA>(a, vt, map, s);
-    case 2: return launch_bwd<2, 16, CH, TMA>(a, vt, map, s);
-    case 3: return launch_bwd<4, 8, CH, TMA>(a, vt, map, s);
-    case 4: return launch_bwd<4, 16, CH, TMA>(a, vt, map, s);
-    default: return launch_bwd<8, 16, CH, TMA>(a, vt, map, s);
+    case 0: return launch_bwd<1, 8, CH, TMA, ASYNC>(a, vt, map, s);
+    case 1: return launch_bwd<2, 8, CH, TMA, ASYNC>(a, vt, map, s);
+    case 2: return launch_bwd<2, 16, CH, TMA, ASYNC>(a, vt, map, s);
+    case 3: return launch_bwd<4, 8, CH, TMA, ASYNC>(a, vt, map, s);
+    case 4: return launch_bwd<4, 16, CH, TMA, ASYNC>(a, vt, map, s);
+    default: return launch_bwd<8, 16, CH, TMA, ASYNC>(a, vt, map, s);
     }
 }
 
@@ -541,7 +590,7 @@ extern "C" gs_status_t gs_render_bwd_splats(const gs_projected_t *proj, int64_t 
     const int base = var % kBandVariants;
     switch (var / kBandVariants) {
     case 0: return dispatch_bwd_band<32, false>(base, a, vt, map, s);
-    case 1: return dispatch_bwd_band<64, false>(base, a, vt, map, s);
+    case 1: return dispatch_bwd_band<32, false, true>(base, a, vt, map, s);
     case 2: return dispatch_bwd_band<32, true>(base, a, vt, map, s);
     default: return dispatch_bwd_band<64, true>(base, a, vt, map, s);
     }
