@@ -8,8 +8,8 @@ Two levels, both timed with CUDA events on the caller's own workload:
   compositing variants whose bands divide the tile: pixels per thread and
   band width ((1, 8) (2, 8) (2, 16) (4, 8) (4, 16) (8, 16)), each with its
   ways of staging a chunk of list entries in shared memory (lane loads of 32
-  or, forward, 64 entries; backward, asynchronous copies of 32; gathers by
-  the tensor memory accelerator of 32 or 64).  Every variant computes the
+  entries, asynchronous copies of 32, gathers by the tensor memory
+  accelerator of 32 or 64).  Every variant computes the
   same result (the forward bit for bit, the backward up to the order of
   floating-point additions).
 * ``tune_tiles``: the tile shape.  For each candidate the rasterizer is

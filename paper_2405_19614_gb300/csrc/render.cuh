@@ -139,9 +139,14 @@ constexpr int kRenderThreads = 128;
 #ifndef GS_BWD_BLOCKS_PPT8
 #define GS_BWD_BLOCKS_PPT8 4
 #endif
+#ifndef GS_FWD_BLOCKS_PPT2_ASYNC
+#define GS_FWD_BLOCKS_PPT2_ASYNC 10
+#endif
 template <int PPT, bool TMA = false>
 struct RenderOccupancy {
     static constexpr int fwd = PPT <= 2 ? 8 : PPT == 4 ? (TMA ? 7 : 6) : 4;
+    // forward with asynchronous copies (no prefetch registers)
+    static constexpr int fwd_async = PPT <= 2 ? GS_FWD_BLOCKS_PPT2_ASYNC : PPT == 4 ? 7 : 4;
     static constexpr int bwd = PPT <= 2 ? 8 : PPT == 4 ? (TMA ? GS_BWD_BLOCKS_PPT4_TMA : GS_BWD_BLOCKS_PPT4)
                                                          : GS_BWD_BLOCKS_PPT8;
 };
@@ -149,10 +154,9 @@ struct RenderOccupancy {
 // Kernel variants the autotuner picks from: a band shape as (pixels per
 // thread, band width) (1, 8) (2, 8) (2, 16) (4, 8) (4, 16) (8, 16), each with a
 // staged chunk of 32 list entries loaded by the lanes into registers (variants
-// 0-5); of 64 so loaded (6-11) in the forward, of 32 copied by the lanes'
-// asynchronous copies into a second shared-memory buffer (6-11) in the
-// backward; or of 32 (12-17) or 64 (18-23) gathered by the tensor memory
-// accelerator.  A warp's band is BW x PPT * 32 / BW pixels; a thread's pixels
+// 0-5), of 32 copied by the lanes' asynchronous copies into a second
+// shared-memory buffer (6-11), or of 32 (12-17) or 64 (18-23) gathered by the
+// tensor memory accelerator.  A warp's band is BW x PPT * 32 / BW pixels; a thread's pixels
 // share a column, 32 / BW rows apart.
 constexpr int kBandVariants = 6;
 constexpr int kFwdVariants = 4 * kBandVariants;

@@ -13,6 +13,7 @@
 // shared-memory slot (records are in the base-2 form of render.cuh) and walks them; it stops once all its pixels have run out
 // of transmittance.  Warps never wait for one another.  PPT is chosen per
 // workload by the autotuner, with the band width BW.
+#include "async_copy.cuh"
 #include "common.cuh"
 #include "render.cuh"
 #include "tma.cuh"
@@ -60,10 +61,15 @@ __device__ __forceinline__ void load_entry(const RenderFwdArgs &a, int64_t rbase
 // lanes' own loads into registers (TMA = false), or, with TMA, gathered four
 // records at a time by the tensor memory accelerator straight into a second
 // shared-memory buffer (tma.cuh), which takes the prefetch out of registers.
-template <int PPT, int BW, int CH, bool TMA, bool STATS, bool LOSS>
-__global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd) render_fwd_kernel(
+// ASYNC (32-entry chunks): the lanes copy the next chunk's records into a
+// second shared-memory buffer with their own asynchronous copies (through L1,
+// holding no registers) and load the Gaussian indices one chunk further ahead.
+template <int PPT, int BW, int CH, bool TMA, bool STATS, bool LOSS, bool ASYNC = false>
+__global__ void __launch_bounds__(kRenderThreads, ASYNC ? RenderOccupancy<PPT, true>::fwd_async
+                                                        : RenderOccupancy<PPT, TMA>::fwd) render_fwd_kernel(
     RenderFwdArgs a, ViewTable vt, const __grid_constant__ CUtensorMap rec_map)
 {
+    static_assert(!(TMA && ASYNC) && (!ASYNC || CH == 32), "one staging mode; asynchronous copies of 32 entries");
     __shared__ float s_loss[kRenderThreads / 32];
     float lacc = 0.0f;  // LOSS: this thread's share of the loss
     constexpr int WARPS = kRenderThreads / 32;
@@ -71,7 +77,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
     constexpr int BH = PPT * RS;  // band height (width BW)
     constexpr int NC = CH / 32;   // entries a lane stages per chunk
     // (u, v, z, log2 o), (base-2 conic, du), (rgb, dv) of a chunk
-    __shared__ float4 s_rec[TMA ? 1 : WARPS][3][TMA ? 1 : CH];
+    __shared__ float4 s_rec[TMA ? 1 : WARPS][ASYNC ? 2 : 1][3][TMA ? 1 : CH];
     constexpr int kBufBytes = (CH / kGatherRows) * kGatherSlot;
     __shared__ alignas(128) unsigned char s_tbuf[TMA ? WARPS : 1][2][TMA ? kBufBytes : 16];
     __shared__ alignas(8) uint64_t s_bar[WARPS][2];
@@ -248,6 +254,46 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
             #pragma unroll
             for (int k2 = 0; k2 < 2; k2++)
                 if (pend[k2] && !wait(k2)) tma_failed = true;
+        } else if constexpr (ASYNC) {
+            auto gid_at = [&](uint32_t m0) -> uint32_t {
+                const uint32_t idx = m0 + lane;
+                return idx < e ? a.vals[idx] : 0u;
+            };
+            // chunk [m0, m0 + 32) into buffer kb, its Gaussian indices g already loaded
+            auto copy = [&](uint32_t m0, uint32_t g, int kb) {
+                if (m0 + lane < e) {
+                    const float4 *src = a.rec + 3 * (rbase + g);
+                    cp_async16_ca(&s_rec[warp][kb][0][lane], src);
+                    cp_async16_ca(&s_rec[warp][kb][1][lane], src + 1);
+                    cp_async16_ca(&s_rec[warp][kb][2][lane], src + 2);
+                }
+                cp_async_commit();
+            };
+            int kb = 0;
+            if (b < e) copy(b, gid_at(b), 0);
+            uint32_t g_next = b + CH < e ? gid_at(b + CH) : 0u;  // indices of the next chunk
+            for (uint32_t m = b; m < e; m += CH, kb ^= 1) {
+                if (!warp_alive()) break;
+                cp_async_wait<0>();
+                __syncwarp();  // every lane's copies of this chunk have landed
+                if (m + CH < e) {
+                    copy(m + CH, g_next, kb ^ 1);
+                    g_next = m + 2 * CH < e ? gid_at(m + 2 * CH) : 0u;
+                }
+                const bool keep = m + lane < e && (STATS || !splat_misses_box(s_rec[warp][kb][0][lane],
+                                                                              s_rec[warp][kb][1][lane], bx0, bx1,
+                                                                              by0, by1));
+                uint32_t todo = __ballot_sync(kFullMask, keep);
+                while (todo) {
+                    const int j = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    blend_entry(s_rec[warp][kb][0][j], s_rec[warp][kb][1][j], s_rec[warp][kb][2][j],
+                                m - b + (uint32_t)j);
+                    if (!warp_alive()) break;  // the warp's pixels are done (a warp-uniform exit)
+                }
+                __syncwarp();  // buffer kb is read before it is filled again
+            }
+            cp_async_wait<0>();  // a chunk copied ahead of a walk that stopped early
         } else {
         float4 n0[NC], n1[NC], n2[NC];  // this lane's entries of the next chunk
         #pragma unroll
@@ -263,9 +309,9 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
                 if (m + CH < e) load_entry(a, rbase, m + CH + 32 * c + lane, e, n0[c], n1[c], n2[c]);
                 const bool keep = have && (STATS || !splat_misses_box(r0, r1, bx0, bx1, by0, by1));
                 todo[c] = __ballot_sync(kFullMask, keep);
-                s_rec[warp][0][32 * c + lane] = r0;
-                s_rec[warp][1][32 * c + lane] = r1;
-                s_rec[warp][2][32 * c + lane] = r2;
+                s_rec[warp][0][0][32 * c + lane] = r0;
+                s_rec[warp][0][1][32 * c + lane] = r1;
+                s_rec[warp][0][2][32 * c + lane] = r2;
             }
             __syncwarp();
             #pragma unroll
@@ -274,7 +320,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
                     const int j = __ffs(todo[c]) - 1;
                     todo[c] &= todo[c] - 1;
                     const int slot = 32 * c + j;
-                    blend_entry(s_rec[warp][0][slot], s_rec[warp][1][slot], s_rec[warp][2][slot],
+                    blend_entry(s_rec[warp][0][0][slot], s_rec[warp][0][1][slot], s_rec[warp][0][2][slot],
                                 m - b + (uint32_t)slot);
                     if (!warp_alive()) {  // the warp's pixels are done (a warp-uniform exit)
                         #pragma unroll
@@ -343,12 +389,12 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA>::fwd
     }
 }
 
-template <int PPT, int BW, int CH, bool TMA, bool STATS, bool LOSS = false>
+template <int PPT, int BW, int CH, bool TMA, bool STATS, bool LOSS = false, bool ASYNC = false>
 static gs_status_t launch_fwd(RenderFwdArgs a, ViewTable vt, const CUtensorMap &map, cudaStream_t s)
 {
     // work items: the bands of every tile of every view (tile shapes are per view)
     a.n_items = render_items(&vt, BW, PPT * (32 / BW));
-    auto kern = render_fwd_kernel<PPT, BW, CH, TMA, STATS, LOSS>;
+    auto kern = render_fwd_kernel<PPT, BW, CH, TMA, STATS, LOSS, ASYNC>;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRenderThreads, 0);
     const int64_t slots = (int64_t)num_sms() * (per_sm > 0 ? per_sm : 1);
@@ -358,17 +404,17 @@ static gs_status_t launch_fwd(RenderFwdArgs a, ViewTable vt, const CUtensorMap &
     return launch_status();
 }
 
-template <int CH, bool TMA, bool STATS, bool LOSS>
+template <int CH, bool TMA, bool STATS, bool LOSS, bool ASYNC = false>
 static gs_status_t dispatch_fwd_band(int base, const RenderFwdArgs &a, const ViewTable &vt, const CUtensorMap &map,
                                      cudaStream_t s)
 {
     switch (base) {
-    case 0: return launch_fwd<1, 8, CH, TMA, STATS, LOSS>(a, vt, map, s);
-    case 1: return launch_fwd<2, 8, CH, TMA, STATS, LOSS>(a, vt, map, s);
-    case 2: return launch_fwd<2, 16, CH, TMA, STATS, LOSS>(a, vt, map, s);
-    case 3: return launch_fwd<4, 8, CH, TMA, STATS, LOSS>(a, vt, map, s);
-    case 4: return launch_fwd<4, 16, CH, TMA, STATS, LOSS>(a, vt, map, s);
-    default: return launch_fwd<8, 16, CH, TMA, STATS, LOSS>(a, vt, map, s);
+    case 0: return launch_fwd<1, 8, CH, TMA, STATS, LOSS, ASYNC>(a, vt, map, s);
+    case 1: return launch_fwd<2, 8, CH, TMA, STATS, LOSS, ASYNC>(a, vt, map, s);
+    case 2: return launch_fwd<2, 16, CH, TMA, STATS, LOSS, ASYNC>(a, vt, map, s);
+    case 3: return launch_fwd<4, 8, CH, TMA, STATS, LOSS, ASYNC>(a, vt, map, s);
+    case 4: return launch_fwd<4, 16, CH, TMA, STATS, LOSS, ASYNC>(a, vt, map, s);
+    default: return launch_fwd<8, 16, CH, TMA, STATS, LOSS, ASYNC>(a, vt, map, s);
     }
 }
 
@@ -390,7 +436,7 @@ static gs_status_t dispatch_fwd(int var, const RenderFwdArgs &a, const ViewTable
     const int base = var % kBandVariants;
     switch (var / kBandVariants) {
     case 0: return dispatch_fwd_band<32, false, STATS, LOSS>(base, a, vt, map, s);
-    case 1: return dispatch_fwd_band<64, false, STATS, LOSS>(base, a, vt, map, s);
+    case 1: return dispatch_fwd_band<32, false, STATS, LOSS, true>(base, a, vt, map, s);
     case 2: return dispatch_fwd_band<32, true, STATS, LOSS>(base, a, vt, map, s);
     default: return dispatch_fwd_band<64, true, STATS, LOSS>(base, a, vt, map, s);
     }
