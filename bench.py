@@ -271,7 +271,7 @@ def work_counts(step):
                 C=int(r.img["n_contrib"].sum(dtype=torch.int64)), sh_floats=3 * (r.sh_degree + 1) ** 2)
 
 
-TRAFFIC_SOURCES = {"render_bwd": ("render_bwd.cu", "render.cuh", "common.cuh", "tma.cuh")}
+TRAFFIC_SOURCES = {"render_bwd": ("render_bwd.cu", "render.cuh", "common.cuh", "tma.cuh", "async_copy.cuh")}
 
 
 def traffic_sources_sha256(stage, root=None):
