@@ -682,7 +682,8 @@ def measure_tracking_config(args, device):
     """The TUM-shaped tracking workload: 100 pose-only iterations of the joint
     loss (rendering L1 with the gate plus the keypoint re-projection term) from a
     perturbed pose, set up with the library's own calls, the loop replayed as
-    100 graph launches of one iteration."""
+    100 graph launches of one iteration, on the tile shape whose iteration is
+    fastest."""
     import torch
 
     import paper_2405_19614_gb300 as gs
@@ -720,14 +721,41 @@ def measure_tracking_config(args, device):
     kp = dict(points=torch.as_tensor(pts[ok].astype(np.float32), device=device),
               obs=torch.as_tensor(obs.astype(np.float32), device=device))
     E0 = moved(c["init_offset"], E_true)
-    step = TrackingStep(p, cams["intr"], cams["size"], E0.cpu().numpy(), t_rgb, t_depth, keypoints=kp,
-                        w_rpj=c["w_rpj"], w_c=c["w_c"], w_d=c["w_d"], gamma=c["gamma"], device=device)
     del r
 
-    def reset():
-        step.viewmats.copy_(E0)
-        for b in (step.twist, step.m, step.v, step.step_count):
-            b.zero_()
+    def make(tile):
+        return TrackingStep(p, cams["intr"], cams["size"], E0.cpu().numpy(), t_rgb, t_depth, keypoints=kp,
+                            w_rpj=c["w_rpj"], w_c=c["w_c"], w_d=c["w_d"], gamma=c["gamma"], device=device,
+                            tile=tile)
+
+    def reset_of(st):
+        def reset():
+            st.viewmats.copy_(E0)
+            for b in (st.twist, st.m, st.v, st.step_count):
+                b.zero_()
+        return reset
+
+    # the tile shape: the one whose iteration (launched eagerly, 20 times from
+    # the start pose) is fastest
+    tile_ms = {}
+    for tile in ((8, 8), (16, 8), (16, 16), (32, 16), (32, 32), (64, 32)):
+        st = make(tile)
+        for _ in range(3):
+            st.run()
+        reset_of(st)()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(20):
+            st.run()
+        t1.record()
+        torch.cuda.synchronize()
+        if st.rast.status() == 0:
+            tile_ms[f"{tile[0]}x{tile[1]}"] = t0.elapsed_time(t1) / 20
+        del st
+    best = min(tile_ms, key=tile_ms.get)
+    step = make(tuple(int(x) for x in best.split("x")))
+    reset = reset_of(step)
 
     iters = c["iters"]
     for _ in range(3):
@@ -776,6 +804,7 @@ def measure_tracking_config(args, device):
            "timing": ("CUDA graph of one iteration replayed" if graph_ms is not None else "eager launches"),
            "eager": {"ms_per_loop": eager_ms, "iters_per_s": 1e3 * iters / eager_ms},
            "pose_centre_error_cm": {"start": err0_cm, "after": err_cm},
+           "tile": list(step.rast.tile), "tile_ms_per_iter": {k: round(v, 4) for k, v in tile_ms.items()},
            "status": step.rast.status()}
     if not args.no_cpu:
         cpu = oracle_view_sample(c, 0)
