@@ -82,9 +82,16 @@ __global__ void __launch_bounds__(kEmitThreads) vis_count_kernel(const uint32_t 
 // *count, flagged when it exceeds cap.
 constexpr int kScanPer = 16;
 
+// When n_items_dev is set, only the first ceil(*n_items_dev / chunk) sums are
+// scanned (the others belong to chunks past the drawn records and are neither
+// written nor read).
 __global__ void __launch_bounds__(1024) scan_sums_kernel(uint64_t *sums, int64_t nb, int64_t cap, uint32_t *count,
-                                                         uint32_t *status)
+                                                         uint32_t *status, const uint32_t *n_items_dev, int chunk)
 {
+    if (n_items_dev) {
+        const int64_t used = ((int64_t)*n_items_dev + chunk - 1) / chunk;
+        nb = used < nb ? used : nb;
+    }
     __shared__ uint64_t tmp[32];
     __shared__ uint64_t carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -170,9 +177,10 @@ __global__ void __launch_bounds__(kEmitThreads) vis_compact_kernel(const float *
 // block's chunk (thread t holds j = first + 2 t, first + 2 t + 1); recs holds
 // (depth bits, record id) pairs.
 __device__ __forceinline__ void chunk_counts(const uint2 *__restrict__ recs, const uint32_t *__restrict__ tt,
-                                             uint32_t n_vis, uint32_t (&r)[kPairItems], uint32_t (&c)[kPairItems])
+                                             uint32_t n_vis, uint32_t chunk, uint32_t (&r)[kPairItems],
+                                             uint32_t (&c)[kPairItems])
 {
-    const int64_t first = (int64_t)blockIdx.x * kPairChunk + (int64_t)threadIdx.x * kPairItems;
+    const int64_t first = (int64_t)chunk * kPairChunk + (int64_t)threadIdx.x * kPairItems;
     #pragma unroll
     for (int k = 0; k < kPairItems; k++) {
         const int64_t j = first + k;
@@ -182,26 +190,26 @@ __device__ __forceinline__ void chunk_counts(const uint2 *__restrict__ recs, con
 }
 
 // 2a. Pairs of each block of kPairChunk depth-sorted records.
+// Persistent over the chunks of the drawn records (their number is known
+// only here): a grid sized to the GPU, not to every record slot, most of which
+// are undrawn on a multi-view batch.
 __global__ void __launch_bounds__(kEmitThreads) pair_count_kernel(const uint2 *__restrict__ recs,
                                                                   const uint32_t *__restrict__ tt,
                                                                   const uint32_t *n_vis_p, uint64_t *block_sums)
 {
     __shared__ uint64_t tmp[kEmitThreads / 32];
-    // the grid covers every record slot; chunks past the drawn records
-    // (about four in five on a multi-view batch) only report an empty sum
     const uint32_t n_vis = *n_vis_p;
-    if ((int64_t)blockIdx.x * kPairChunk >= (int64_t)n_vis) {
-        if (threadIdx.x == 0) block_sums[blockIdx.x] = 0;
-        return;
+    const uint32_t n_chunks = (n_vis + kPairChunk - 1) / kPairChunk;
+    for (uint32_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
+        uint32_t r[kPairItems], c[kPairItems];
+        chunk_counts(recs, tt, n_vis, chunk, r, c);
+        uint64_t s = 0;
+        #pragma unroll
+        for (int k = 0; k < kPairItems; k++) s += c[k];
+        uint64_t all;
+        block_exclusive_scan_u64(s, tmp, &all);
+        if (threadIdx.x == 0) block_sums[chunk] = all;
     }
-    uint32_t r[kPairItems], c[kPairItems];
-    chunk_counts(recs, tt, n_vis, r, c);
-    uint64_t s = 0;
-    #pragma unroll
-    for (int k = 0; k < kPairItems; k++) s += c[k];
-    uint64_t all;
-    block_exclusive_scan_u64(s, tmp, &all);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = all;
 }
 
 // Index of the (k + 1)-th set bit of m (m has more than k set bits).
@@ -232,10 +240,15 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
     constexpr int kRun = 8;  // consecutive pairs a thread emits per round
     __shared__ uint32_t s_tk[kEmitThreads * kRun], s_tv[kEmitThreads * kRun];
     const uint32_t n_vis = *n_vis_p;
-    if ((int64_t)blockIdx.x * kPairChunk >= (int64_t)n_vis) return;  // no drawn record: nothing to emit
+    const uint32_t n_chunks = (n_vis + kPairChunk - 1) / kPairChunk;
+    if (blockIdx.x >= n_chunks) return;  // no drawn record: nothing to emit
     clear_hist(h, tile_passes);
+    // persistent over the drawn records' chunks (see pair_count_kernel); the
+    // digit histograms gather over all of a block's chunks
+    for (uint32_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
+    __syncthreads();  // the previous chunk's shared arrays have been read
     uint32_t r[kPairItems], c[kPairItems];
-    chunk_counts(recs, tt, n_vis, r, c);
+    chunk_counts(recs, tt, n_vis, chunk, r, c);
     uint64_t sum = 0;
     #pragma unroll
     for (int k = 0; k < kPairItems; k++) sum += c[k];
@@ -256,8 +269,8 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
     }
     if (threadIdx.x == 0) s_excl[kPairChunk] = (uint32_t)block_total;
     __syncthreads();
-    const uint64_t base = block_off[blockIdx.x];
-    const uint32_t j0 = blockIdx.x * kPairChunk;
+    const uint64_t base = block_off[chunk];
+    const uint32_t j0 = chunk * kPairChunk;
     const uint32_t nq = (uint32_t)block_total;
     // each thread makes kRun consecutive pairs: one search for the first, then
     // a walk along the rectangle's rows (and on to the next records); the
@@ -344,6 +357,7 @@ __global__ void __launch_bounds__(kEmitThreads) pair_emit_kernel(const uint2 *__
         }
         __syncthreads();
     }
+    }  // chunks
     __syncthreads();
     flush_hist(h, tile_passes, hist);
 }
@@ -452,7 +466,7 @@ extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const 
     // 1. drawn records sorted by depth
     const unsigned nb = (unsigned)((total + kEmitChunk - 1) / kEmitChunk);
     vis_count_kernel<<<nb, kEmitThreads, 0, s>>>(proj->tiles_touched, total, w.block_sums);
-    scan_sums_kernel<<<1, 1024, 0, s>>>(w.block_sums, nb, total, n_vis, bins->status);
+    scan_sums_kernel<<<1, 1024, 0, s>>>(w.block_sums, nb, total, n_vis, bins->status, nullptr, 1);
     vis_compact_kernel<<<nb, kEmitThreads, 0, s>>>(proj->rec, proj->tiles_touched, total, w.block_sums, w.rz[0],
                                                    w.rid[0], hist_depth);
     for (int p = 0; p < kDepthPasses; p++) {
@@ -470,10 +484,13 @@ extern "C" gs_status_t gs_bin_sort(const gs_projected_t *proj, int64_t n, const 
     uint32_t *buf_k[2] = {w.pk, reinterpret_cast<uint32_t *>(bins->keys)};
     uint32_t *buf_v[2] = {w.pv, reinterpret_cast<uint32_t *>(bins->keys) + cap};
     const int e = (tile_passes & 1) ? 0 : 1;
+    // chunks of the drawn records: at most np, known on the device only; both
+    // kernels are persistent over them with grids sized to the GPU
     const unsigned np = (unsigned)((total + kPairChunk - 1) / kPairChunk);
-    pair_count_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, proj->tiles_touched, n_vis, w.block_sums);
-    scan_sums_kernel<<<1, 1024, 0, s>>>(w.block_sums, np, cap, bins->n_pairs, bins->status);
-    pair_emit_kernel<<<np, kEmitThreads, 0, s>>>(w.recs, reinterpret_cast<const uint2 *>(proj->rect),
+    const unsigned pgrid = (unsigned)(np < (unsigned)num_sms() * 8u ? np : (unsigned)num_sms() * 8u);
+    pair_count_kernel<<<pgrid, kEmitThreads, 0, s>>>(w.recs, proj->tiles_touched, n_vis, w.block_sums);
+    scan_sums_kernel<<<1, 1024, 0, s>>>(w.block_sums, np, cap, bins->n_pairs, bins->status, n_vis, kPairChunk);
+    pair_emit_kernel<<<pgrid, kEmitThreads, 0, s>>>(w.recs, reinterpret_cast<const uint2 *>(proj->rect),
                                                   reinterpret_cast<const unsigned long long *>(proj->tile_mask),
                                                  proj->tiles_touched, n_vis, (uint32_t)n, vt, w.block_sums, cap,
                                                  buf_k[e], buf_v[e], hist_tile, tile_passes);
