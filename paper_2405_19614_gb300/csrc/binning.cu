@@ -150,11 +150,25 @@ __global__ void __launch_bounds__(kEmitThreads) vis_compact_kernel(const float *
     const int64_t first = (int64_t)blockIdx.x * kEmitChunk + (int64_t)threadIdx.x * kEmitItems;
     bool vis[kEmitItems];
     uint64_t s = 0;
-    #pragma unroll
-    for (int k = 0; k < kEmitItems; k++) {
-        const int64_t o = first + k;
-        vis[k] = o < total && tt[o] > 0;
-        s += vis[k];
+    static_assert(kEmitItems == 8, "two 16-byte loads a thread");
+    if (first + kEmitItems <= total && (reinterpret_cast<uintptr_t>(tt) & 15) == 0) {
+        // the thread's eight counts as two 16-byte loads (the warp's loads are
+        // one contiguous kilobyte)
+        const uint4 a = reinterpret_cast<const uint4 *>(tt + first)[0];
+        const uint4 b = reinterpret_cast<const uint4 *>(tt + first)[1];
+        const uint32_t t8[kEmitItems] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        #pragma unroll
+        for (int k = 0; k < kEmitItems; k++) {
+            vis[k] = t8[k] > 0;
+            s += vis[k];
+        }
+    } else {
+        #pragma unroll
+        for (int k = 0; k < kEmitItems; k++) {
+            const int64_t o = first + k;
+            vis[k] = o < total && tt[o] > 0;
+            s += vis[k];
+        }
     }
     uint32_t z[kEmitItems];
     #pragma unroll
