@@ -276,14 +276,18 @@ gs_status_t gs_render_stats(const gs_projected_t *proj, int64_t n, const gs_bins
                             const gs_view_t *views, int32_t n_views, uint32_t *n_eval, uint32_t *n_blend,
                             uint32_t *work_counter, void *stream);
 
-/* Kernel variants of the compositing (a5, a7): (pixels per thread, band
- * width BW), a warp's band of a 16x16 tile being BW x (pixels per thread *
- * 32 / BW) pixels, as indices 0..5 into (1,8) (2,8) (2,16) (4,8) (4,16)
- * (8,16) for both the forward and the backward (defaults: forward 1,
- * backward 3).  All variants compute the same result; the autotuner times
- * them on the workload and sets the fastest.  The setting is process-wide and
- * read when a kernel is launched.  GS_ERR_INVALID_ARG for an index out of
- * range. */
+/* Kernel variants of the compositing (a5, a7), 0..23 for both the forward and
+ * the backward: index % 6 is the band shape (pixels per thread, band width
+ * BW), a warp's band of a tile being BW x (pixels per thread * 32 / BW)
+ * pixels, in (1,8) (2,8) (2,16) (4,8) (4,16) (8,16); index / 6 the staging of
+ * the list entries in shared memory: 32 loaded by the lanes into registers,
+ * 32 copied by the lanes' asynchronous copies into a second buffer, or 32 or
+ * 64 gathered by the tensor memory accelerator (a band that does not divide
+ * a view's tile falls back to the (2, 8) band of the same staging; defaults:
+ * forward 7, backward 9, the asynchronous-copy (2, 8) and (4, 8)).  All
+ * variants compute the same result; the autotuner times them on the workload
+ * and sets the fastest.  The setting is process-wide and read when a kernel
+ * is launched.  GS_ERR_INVALID_ARG for an index out of range. */
 gs_status_t gs_set_render_variants(int32_t fwd, int32_t bwd);
 
 /* Current variants and the number of each (any pointer may be NULL). */

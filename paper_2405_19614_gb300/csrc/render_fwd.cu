@@ -545,8 +545,8 @@ extern "C" gs_status_t gs_render_stats(const gs_projected_t *proj, int64_t n, co
 // Compositing kernel variants in use (see kFwdVariants), set by the
 // autotuner; defaults suit 1200x680 views of room-scale scenes.
 namespace gs {
-static int g_variant_fwd = 1;
-static int g_variant_bwd = 3;
+static int g_variant_fwd = 7;  // (2, 8) bands, asynchronous-copy staging
+static int g_variant_bwd = 9;  // (4, 8) bands, asynchronous-copy staging
 int render_variant_fwd() { return g_variant_fwd; }
 int render_variant_bwd() { return g_variant_bwd; }
 }  // namespace gs
