@@ -26,15 +26,17 @@
 // conservative test as the forward); warps never wait for one another.  All
 // threads of a warp are at the same entry at the same time: a thread sums its
 // PPT pixels' terms in registers, and the warp reduces the ten gradients of
-// three entries at a time through a transposed table in shared memory (ten
-// column stores a lane per entry, then one 32-value row sum a lane per three
-// entries); the 30 lanes holding a total add them to HBM in one predicated
-// atomic instruction.  Per
+// three or four entries at a time through a transposed table in shared memory
+// (five paired column stores a lane per entry, then one 32-pair row sum a
+// lane per batch); the lanes holding a total pair add them to HBM in one
+// predicated paired atomic instruction.  Per
 // warp band rather than per tile costs few extra atomics: after culling an
 // entry rarely reaches more than one band.  With eight pixels a thread a band
 // is a 16 x 16 item whose two halves are culled apart: an entry kept in both
 // is reduced once, an entry kept in one is tested in that half only.  PPT is
 // picked by the autotuner.
+#include <type_traits>
+
 #include "async_copy.cuh"
 #include "common.cuh"
 #include "render.cuh"
@@ -57,16 +59,23 @@ struct RenderBwdArgs {
 };
 
 constexpr int kAcc = 10;
-// The ten sums of kBatch consecutive entries are reduced over the warp
-// together: every lane stores its values as one column of a kBatch * 10 x 32
-// table in shared memory (rows padded to kRedPitch floats: column stores and
-// the 16-byte row loads below are free of bank conflicts), then lane j adds up
-// row j and the 30 lanes holding a total add them to HBM in one predicated
-// atomic instruction.
-constexpr int kBatch = 3;
-constexpr int kRedRows = kBatch * kAcc;
-constexpr int kRedPitch = 36;
-static_assert(kRedRows <= 32, "one row per lane");
+// The ten sums of a batch of consecutive entries are reduced over the warp
+// together: every lane stores its values as five pairs, one column of a
+// (batch * 5) x 32 table of pairs in shared memory (rows padded to kRedPitch
+// pairs: the 8-byte column stores and the 16-byte row loads below are free of
+// bank conflicts), then lane j adds up row j and the lanes holding a total
+// pair add it to HBM in one predicated paired atomic instruction (the pairs
+// are 8-byte aligned: grad2d rows are 48 bytes, their base 16-byte aligned).
+constexpr int kPairs = kAcc / 2;
+constexpr int kRedPitch = 34;
+// Entries a batch: four where the larger table still leaves room in shared
+// memory for the blocks per SM the launch bounds ask for (four or eight pixels
+// a thread, staged by lane loads or asynchronous copies), else three.
+template <int PPT, bool TMA>
+struct RedBatch {
+    static constexpr int value = PPT >= 4 && !TMA ? 4 : 3;
+    static_assert(value * kPairs <= 32, "one row per lane");
+};
 
 // Record and index of list entry idx (zeros past the end of the walk).
 __device__ __forceinline__ void load_bwd_entry(const RenderBwdArgs &a, int64_t rbase, uint32_t idx, bool valid,
@@ -112,7 +121,8 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA || AS
     __shared__ float4 s_up[SPLIT ? WARPS : 1][SPLIT ? NP : 1][2][32];
     __shared__ float4 s_rec[TMA ? 1 : WARPS][ASYNC ? 2 : 1][3][TMA ? 1 : CH];  // (per buffer, ASYNC)
     __shared__ uint32_t s_gid[WARPS][TMA || ASYNC ? 2 : 1][CH];  // Gaussian index of each staged entry (per buffer)
-    __shared__ __align__(16) float s_red[WARPS][kRedRows][kRedPitch];
+    constexpr int kBatch = RedBatch<PPT, TMA>::value;
+    __shared__ __align__(16) float2 s_red[WARPS][kBatch * kPairs][kRedPitch];
     __shared__ uint32_t s_bgid[WARPS][kBatch];
     constexpr int kBufBytes = (CH / kGatherRows) * kGatherSlot;
     __shared__ alignas(128) unsigned char s_tbuf[TMA ? WARPS : 1][2][TMA ? kBufBytes : 16];
@@ -131,7 +141,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA || AS
         }
         __syncwarp();
     }
-    const int red_entry = lane / kAcc, red_value = lane % kAcc;  // the row this lane adds up
+    const int red_entry = lane / kPairs, red_pair = lane % kPairs;  // the row this lane adds up
     for (;;) {
         uint32_t wi = 0;
         if (lane == 0) wi = atomicAdd(a.work_counter, 1u);
@@ -160,17 +170,20 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA || AS
         auto flush = [&]() {
             __syncwarp();  // every lane's columns (and lane 0's ids) are written
             if (red_entry < nb) {
+                // the row's 32 pairs, two a load, in two running sums
                 const float4 *row = reinterpret_cast<const float4 *>(&s_red[warp][lane][0]);
                 float4 q = row[0];
-                float2 lo = make_float2(q.x, q.y), hi = make_float2(q.z, q.w);
+                float2 even = make_float2(q.x, q.y), odd = make_float2(q.z, q.w);
                 #pragma unroll
-                for (int c = 1; c < 8; c++) {
+                for (int c = 1; c < 16; c++) {
                     q = row[c];
-                    lo = __fadd2_rn(lo, make_float2(q.x, q.y));
-                    hi = __fadd2_rn(hi, make_float2(q.z, q.w));
+                    even = __fadd2_rn(even, make_float2(q.x, q.y));
+                    odd = __fadd2_rn(odd, make_float2(q.z, q.w));
                 }
-                const float r = (lo.x + lo.y) + (hi.x + hi.y);
-                if (r != 0.0f) atomicAdd(a.grad2d + 12 * (rbase + s_bgid[warp][red_entry]) + red_value, r);
+                const float2 r = __fadd2_rn(even, odd);
+                if (r.x != 0.0f || r.y != 0.0f)
+                    atomicAdd(reinterpret_cast<float2 *>(a.grad2d + 12 * (rbase + s_bgid[warp][red_entry])) + red_pair,
+                              r);
             }
             __syncwarp();  // the table may be written again
             nb = 0;
@@ -255,15 +268,13 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA || AS
                         hx[j] = pos < last[2 * i] && l2[j].x >= kLog2AlphaMin;
                         hy[j] = pos < last[2 * i + 1] && l2[j].y >= kLog2AlphaMin;
                     }
-                    #pragma unroll
-                    for (int j = 0; j < GP; j++) {
+                    // the body of pair j of this group, run by every lane of
+                    // the warp: a lane whose pair does not blend runs it with
+                    // raw alpha 0, which changes none of its state and adds
+                    // exactly zero
+                    auto pair_body = [&](auto J) {
+                        constexpr int j = decltype(J)::value;
                         const int i = h * GP + j;
-                        // a warp-uniform skip: a pair that no lane blends is
-                        // skipped by all; a lane whose pair does not blend
-                        // runs the body with raw alpha 0, which changes none
-                        // of its state and adds exactly zero
-                        if (!__any_sync(kFullMask, hx[j] || hy[j])) continue;
-                        contrib = true;
                         // the pair's upstream gradients
                         float2 uc0 = gC0[i], uc1 = gC1[i], uc2 = gC2[i], ud = gD[i];
                         if constexpr (SPLIT) {
@@ -304,6 +315,29 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA || AS
                         G2 = __fadd2_rn(G2, t);
                         S12 = __fadd2_rn(S12, u);
                         S22 = __ffma2_rn(u, dy[j], S22);
+                    };
+                    // warp-uniform skips: a pair that no lane blends is skipped by all
+                    bool act[GP];
+                    #pragma unroll
+                    for (int j = 0; j < GP; j++) {
+                        act[j] = __any_sync(kFullMask, hx[j] || hy[j]);
+                        contrib = contrib || act[j];
+                    }
+                    if constexpr (GP == 2) {
+                        // both pairs blended (about half the kept entries): one
+                        // block of straight-line code, in which the two pairs'
+                        // independent chains interleave
+                        if (act[0] && act[1]) {
+                            pair_body(std::integral_constant<int, 0>{});
+                            pair_body(std::integral_constant<int, 1>{});
+                        } else if (act[0]) {
+                            pair_body(std::integral_constant<int, 0>{});
+                        } else if (act[1]) {
+                            pair_body(std::integral_constant<int, 1>{});
+                        }
+                    } else {
+                        static_assert(GP == 1, "one or two pixel pairs a group");
+                        if (act[0]) pair_body(std::integral_constant<int, 0>{});
                     }
                 }
             }
@@ -323,7 +357,7 @@ __global__ void __launch_bounds__(kRenderThreads, RenderOccupancy<PPT, TMA || AS
                 gr[8] = gc[2].x + gc[2].y;
                 gr[9] = gc[3].x + gc[3].y;
                 #pragma unroll
-                for (int k = 0; k < kAcc; k++) s_red[warp][nb * kAcc + k][lane] = gr[k];
+                for (int k = 0; k < kPairs; k++) s_red[warp][nb * kPairs + k][lane] = f2(gr[2 * k], gr[2 * k + 1]);
                 if (lane == 0) s_bgid[warp][nb] = gid;
                 if (++nb == kBatch) flush();
             }

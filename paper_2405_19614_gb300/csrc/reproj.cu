@@ -16,34 +16,62 @@ __global__ void __launch_bounds__(256) reproj_kernel(const float *__restrict__ p
     __shared__ float s_acc[GS_MAX_VIEWS][7];
     for (int k = threadIdx.x; k < vt.n_views * 7; k += blockDim.x) s_acc[k / 7][k % 7] = 0.0f;
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int v = view_ids ? view_ids[i] : 0;
-        if (v < 0 || v >= vt.n_views) continue;
-        const float *E = viewmats + 12 * v;
-        const float X = pts[3 * i], Y = pts[3 * i + 1], Z = pts[3 * i + 2];
-        const float x = E[0] * X + E[1] * Y + E[2] * Z + E[3];
-        const float y = E[4] * X + E[5] * Y + E[6] * Z + E[7];
-        const float z = E[8] * X + E[9] * Y + E[10] * Z + E[11];
-        if (!(z > near_z)) continue;
-        const ViewInfo &V = vt.v[v];
-        const float rz = 1.0f / z;
-        const float rx = obs[2 * i] - (V.fx * x * rz + V.cx);
-        const float ry = obs[2 * i + 1] - (V.fy * y * rz + V.cy);
-        const float nr = sqrtf(rx * rx + ry * ry);
-        float c[7] = {scale * nr, 0, 0, 0, 0, 0, 0};
-        if (nr > 0.0f) {
-            const float gu = -scale * rx / nr, gw = -scale * ry / nr;
-            const float gx = gu * V.fx * rz, gy = gw * V.fy * rz;
-            const float gz = -(gu * V.fx * x + gw * V.fy * y) * rz * rz;
-            c[1] = gx;
-            c[2] = gy;
-            c[3] = gz;
-            c[4] = y * gz - z * gy;
-            c[5] = z * gx - x * gz;
-            c[6] = x * gy - y * gx;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps step through the keypoints together (the sums below are
+    // warp-wide), a lane past the end or behind the camera adding nothing
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+        const int64_t i = i0 + lane;
+        float c[7] = {0, 0, 0, 0, 0, 0, 0};
+        int v = i < n ? (view_ids ? view_ids[i] : 0) : -1;
+        if (v >= vt.n_views) v = -1;
+        if (v >= 0) {
+            const float *E = viewmats + 12 * v;
+            const float X = pts[3 * i], Y = pts[3 * i + 1], Z = pts[3 * i + 2];
+            const float x = E[0] * X + E[1] * Y + E[2] * Z + E[3];
+            const float y = E[4] * X + E[5] * Y + E[6] * Z + E[7];
+            const float z = E[8] * X + E[9] * Y + E[10] * Z + E[11];
+            if (z > near_z) {
+                const ViewInfo &V = vt.v[v];
+                const float rz = 1.0f / z;
+                const float rx = obs[2 * i] - (V.fx * x * rz + V.cx);
+                const float ry = obs[2 * i + 1] - (V.fy * y * rz + V.cy);
+                const float nr = sqrtf(rx * rx + ry * ry);
+                c[0] = scale * nr;
+                if (nr > 0.0f) {
+                    const float gu = -scale * rx / nr, gw = -scale * ry / nr;
+                    const float gx = gu * V.fx * rz, gy = gw * V.fy * rz;
+                    const float gz = -(gu * V.fx * x + gw * V.fy * y) * rz * rz;
+                    c[1] = gx;
+                    c[2] = gy;
+                    c[3] = gz;
+                    c[4] = y * gz - z * gy;
+                    c[5] = z * gx - x * gz;
+                    c[6] = x * gy - y * gx;
+                }
+            } else {
+                v = -1;
+            }
         }
-        #pragma unroll
-        for (int k = 0; k < 7; k++) atomicAdd(&s_acc[v][k], c[k]);
+        // keypoints come grouped by view: when every contributing lane has the
+        // same view the warp adds up its terms and one lane adds them to the
+        // block's sums, else each lane adds its own
+        const int vmax = __reduce_max_sync(kFullMask, v);
+        if (vmax < 0) continue;
+        if (__all_sync(kFullMask, v == vmax || v < 0)) {
+            #pragma unroll
+            for (int k = 0; k < 7; k++) {
+                #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(kFullMask, c[k], o);
+            }
+            if (lane == 0) {
+                #pragma unroll
+                for (int k = 0; k < 7; k++) atomicAdd(&s_acc[vmax][k], c[k]);
+            }
+        } else if (v >= 0) {
+            #pragma unroll
+            for (int k = 0; k < 7; k++) atomicAdd(&s_acc[v][k], c[k]);
+        }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < vt.n_views * 7; k += blockDim.x) {
