@@ -130,17 +130,23 @@ constexpr int kRenderThreads = 128;
 #define GS_BWD_BLOCKS_PPT4 5
 #endif
 // With TMA staging or asynchronous copies the next chunk waits in shared
-// memory, not registers, and four pixels a thread fit one more block per SM.
+// memory, not registers, and four pixels a thread would fit six blocks per SM
+// at 80 registers; but the interleaved bodies of a thread's two pixel pairs
+// want more: five blocks (95 registers) measured 3 % faster than six, four
+// (110 registers) 3.5 % slower than five.
 #ifndef GS_BWD_BLOCKS_PPT4_TMA
-#define GS_BWD_BLOCKS_PPT4_TMA 6
+#define GS_BWD_BLOCKS_PPT4_TMA 5
 #endif
 // Eight pixels a thread (upstream gradients in shared memory): about 120
 // registers; at 96 (five blocks) the compiler needs 20 % more instructions.
 #ifndef GS_BWD_BLOCKS_PPT8
 #define GS_BWD_BLOCKS_PPT8 4
 #endif
+// Forward, up to two pixels a thread, asynchronous-copy staging: nine blocks
+// (56 registers) measured 0.8 % faster than eight (64 registers) and 2.3 %
+// faster than ten (47 registers).
 #ifndef GS_FWD_BLOCKS_PPT2_ASYNC
-#define GS_FWD_BLOCKS_PPT2_ASYNC 10
+#define GS_FWD_BLOCKS_PPT2_ASYNC 9
 #endif
 template <int PPT, bool TMA = false>
 struct RenderOccupancy {
