@@ -284,11 +284,37 @@ __global__ void __launch_bounds__(kRenderThreads, ASYNC ? RenderOccupancy<PPT, t
                                                                               s_rec[warp][kb][1][lane], bx0, bx1,
                                                                               by0, by1));
                 uint32_t todo = __ballot_sync(kFullMask, keep);
-                while (todo) {
-                    const int j = __ffs(todo) - 1;
-                    todo &= todo - 1;
+                // kept entries four (or two) at a time, in one block of
+                // straight-line code: a later entry's evaluation (which needs
+                // no pixel state) overlaps an earlier entry's blend.  The
+                // warp's liveness is tested after each group: an entry walked
+                // after the warp's pixels have stopped changes nothing (no
+                // pixel is live).  (The same grouping as a lambda shared with
+                // the other stagings spilled here and measured 2.4 % slower.)
+                auto blend_bit = [&](int j) {
                     blend_entry(s_rec[warp][kb][0][j], s_rec[warp][kb][1][j], s_rec[warp][kb][2][j],
                                 m - b + (uint32_t)j);
+                };
+                auto pop = [&]() {
+                    const int j = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    return j;
+                };
+                while (todo) {
+                    const int n_left = __popc(todo);
+                    if (n_left >= 4) {
+                        const int j0 = pop(), j1 = pop(), j2 = pop(), j3 = pop();
+                        blend_bit(j0);
+                        blend_bit(j1);
+                        blend_bit(j2);
+                        blend_bit(j3);
+                    } else if (n_left >= 2) {
+                        const int j0 = pop(), j1 = pop();
+                        blend_bit(j0);
+                        blend_bit(j1);
+                    } else {
+                        blend_bit(pop());
+                    }
                     if (!warp_alive()) break;  // the warp's pixels are done (a warp-uniform exit)
                 }
                 __syncwarp();  // buffer kb is read before it is filled again
