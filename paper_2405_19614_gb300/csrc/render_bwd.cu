@@ -26,7 +26,7 @@
 // conservative test as the forward); warps never wait for one another.  All
 // threads of a warp are at the same entry at the same time: a thread sums its
 // PPT pixels' terms in registers, and the warp reduces the ten gradients of
-// three or four entries at a time through a transposed table in shared memory
+// three to five entries at a time through a transposed table in shared memory
 // (five paired column stores a lane per entry, then one 32-pair row sum a
 // lane per batch); the lanes holding a total pair add them to HBM in one
 // predicated paired atomic instruction.  Per
@@ -68,12 +68,15 @@ constexpr int kAcc = 10;
 // are 8-byte aligned: grad2d rows are 48 bytes, their base 16-byte aligned).
 constexpr int kPairs = kAcc / 2;
 constexpr int kRedPitch = 34;
-// Entries a batch: four where the larger table still leaves room in shared
-// memory for the blocks per SM the launch bounds ask for (four or eight pixels
-// a thread, staged by lane loads or asynchronous copies), else three.
+// Entries a batch: as many as the table can hold while the block still leaves
+// room in shared memory for the blocks per SM the launch bounds ask for: five
+// with four pixels a thread (five blocks per SM; five entries a batch measured
+// 2 % faster than four), four with eight pixels a thread (four blocks, the
+// upstream gradients in shared memory as well), three with TMA staging (its
+// gather buffers) or one or two pixels a thread (eight blocks).
 template <int PPT, bool TMA>
 struct RedBatch {
-    static constexpr int value = PPT >= 4 && !TMA ? 4 : 3;
+    static constexpr int value = TMA ? 3 : PPT == 4 ? 5 : PPT == 8 ? 4 : 3;
     static_assert(value * kPairs <= 32, "one row per lane");
 };
 
