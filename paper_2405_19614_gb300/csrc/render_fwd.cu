@@ -293,7 +293,9 @@ __global__ void __launch_bounds__(kRenderThreads, ASYNC ? RenderOccupancy<PPT, t
                 // the other stagings spilled here and measured 2.4 % slower.)
                 // Eight pixels a thread walk one entry at a time: their four
                 // pixel pairs already interleave, and grouped entries measured
-                // 18 % slower at that register budget.
+                // 18 % slower at that register budget.  Groups of eight (two
+                // pixels a thread) spill: 0.727 ms at nine blocks per SM, 0.716
+                // at eight, against 0.718 for groups of four at nine.
                 constexpr int kGroup = PPT >= 8 ? 1 : 4;
                 auto blend_bit = [&](int j) {
                     blend_entry(s_rec[warp][kb][0][j], s_rec[warp][kb][1][j], s_rec[warp][kb][2][j],
