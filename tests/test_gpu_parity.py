@@ -315,7 +315,11 @@ def test_loss_l1_and_gate_parity():
         np.testing.assert_allclose(d_depth.cpu().numpy(), dD, rtol=1e-6, atol=1e-12)
 
 
-def test_reprojection_parity():
+@pytest.mark.parametrize("order", ["mixed", "grouped"])
+def test_reprojection_parity(order):
+    """Keypoints of mixed views (every warp adds lane by lane) and grouped by
+    view, as a frame's keypoints come (whole warps of one view add up their
+    terms first), with a ragged last warp."""
     rng = np.random.default_rng(4)
     vms = np.stack([scenes.look_at((0.2 * k, -0.1, 0.0), (0.1, 0.2, 3.0)) for k in range(2)])
     cams = scenes.cams_from([[525, 525, 320, 240]] * 2, [[640, 480]] * 2, vms)
@@ -324,6 +328,8 @@ def test_reprojection_parity():
     pts[:5, 2] = -2.0  # behind the cameras: left out
     pts = pts.astype(np.float32)
     vid = rng.integers(0, 2, n).astype(np.int32)
+    if order == "grouped":
+        vid = np.sort(vid)
     obs = rng.uniform(0, 640, (n, 2)).astype(np.float32)
     L, g = oracle.reproj(pts.astype(np.float64), obs.astype(np.float64), cams, weight=1.5, view_ids=vid)
     loss = torch.zeros(1, device="cuda")
