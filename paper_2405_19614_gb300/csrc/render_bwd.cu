@@ -25,7 +25,10 @@
 // keeping only the entries that can reach alpha = 1/255 in its band (the same
 // conservative test as the forward); warps never wait for one another.  All
 // threads of a warp are at the same entry at the same time: a thread sums its
-// PPT pixels' terms in registers, and the warp reduces the ten gradients of
+// PPT pixels' terms in registers, two pixels at a time (a pixel pair that no
+// lane blends is skipped by the warp; two pairs that both blend run as one
+// straight-line block, so that their chains interleave and their copies of
+// the entry's values are shared), and the warp reduces the ten gradients of
 // three to five entries at a time through a transposed table in shared memory
 // (five paired column stores a lane per entry, then one 32-pair row sum a
 // lane per batch); the lanes holding a total pair add them to HBM in one
