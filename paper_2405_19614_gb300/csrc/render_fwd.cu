@@ -4,15 +4,18 @@
 //
 // One persistent launch covers every (view, tile, band) work item of every
 // view: warps pull items from an atomic counter, so views of different sizes
-// share one launch and long tiles do not hold up a static schedule.  A band is
-// BW x PPT * 32 / BW pixels of a 16x16 tile and each thread owns PPT pixels of
-// it (one column, rows r, r + 32 / BW, ...).  A warp walks its tile's list in chunks of 32
-// entries, one per lane, loading the next chunk's records while it works on
-// the current one, drops (in parallel) the entries that provably cannot reach
-// alpha = 1/255 in its band (splat_misses_box), stages the rest in its own
-// shared-memory slot (records are in the base-2 form of render.cuh) and walks them; it stops once all its pixels have run out
-// of transmittance.  Warps never wait for one another.  PPT is chosen per
-// workload by the autotuner, with the band width BW.
+// (and tile shapes) share one launch and long tiles do not hold up a static
+// schedule.  A band is BW x PPT * 32 / BW pixels of a tile and each thread
+// owns PPT pixels of it (one column, rows r, r + 32 / BW, ...).  A warp walks
+// its tile's list in chunks of 32 (or 64) entries, one per lane, fetching the
+// next chunk while it works on the current one (into registers, by
+// asynchronous copies or by the tensor memory accelerator into shared
+// memory), drops (in parallel) the entries that provably cannot reach
+// alpha = 1/255 in its band (splat_misses_box), and walks the rest (records
+// in the base-2 form of render.cuh), with asynchronous-copy staging four
+// entries at a time; it stops once all its pixels have run out of
+// transmittance.  Warps never wait for one another.  The band shape and the
+// staging are chosen per workload by the autotuner.
 #include "async_copy.cuh"
 #include "common.cuh"
 #include "render.cuh"
